@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the exact MPDP join-order DP on one GB300 (or N replicas).
+
+A step optimizes one batch of synthetic queries: 64 snowflake join trees of 25
+relations (depth <= 4, fanout 1..5; cardinalities 10^U(2,8), selectivities
+10^U(-6,-1)), every query through the whole hot path (ingest, unrank+filter,
+per-level evaluate/prune/scatter, plan fetch).  Inputs are resident in device
+memory when the timed region starts; the L2 cache is flushed (256 MiB write)
+before every timed step, outside the step's events.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle (DPCCP on one
+host core) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms/query & queries/s at 25 relations; CCP pairs/s; learned-IDP plan-cost ratio"
+UNIT = "queries/s"
+N_RELS = 25
+QUERIES_PER_STEP = 64
+FLUSH_BYTES = 256 << 20
+# Issue-slot peak of the integer filter: 152 SMs x 4 schedulers x 32 lanes x clock.
+SMS, SCHEDULERS, LANES = 152, 4, 32
+# Algorithmic integer operations of the filter (unrank+connectivity), per
+# unranked subset (next-bit-permutation step + loop) and per vertex expanded by
+# the connectivity test (find lowest, clear lowest, load adjacency, and-not,
+# two ors, compare).
+OPS_PER_SUBSET = 9
+OPS_PER_STEP = 8
+# Algorithmic memo bytes: two lookups of (4-byte key + 8-byte cost) per CCP pair
+# and one 16-byte entry written per connected set.
+BYTES_PER_CCP = 24
+BYTES_PER_SET = 16
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--queries", type=int, default=QUERIES_PER_STEP)
+    p.add_argument("--cpu-sample-s", type=float, default=15.0)
+    p.add_argument("--no-star", action="store_true", help="skip the 25-relation star line")
+    p.add_argument("--no-verify", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def workload(rank: int, q: int):
+    from paper_2202_13511_gb300 import workloads as W
+    return [W.snowflake(N_RELS, seed=rank * q + i) for i in range(q)]
+
+
+def workload_desc(q):
+    return (f"snowflake join trees, {N_RELS} relations, depth<=4, fanout 1-5, "
+            f"{q} queries per step (seeds 0..{q - 1}, offset {q}*rank)")
+
+
+def read_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), hw=parts[5],
+                                 hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def cpu_baseline(queries, budget_s: float):
+    """The oracle (DPCCP, one core) on a bounded prefix of the workload."""
+    import oracle
+    oracle.build()
+    done = 0
+    t0 = time.perf_counter()
+    for q in queries:
+        oracle.dpccp(q)
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {done} of the step's {len(queries)} queries, DPCCP on 1 host core, "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    queries = workload(0, args.queries)
+    per_step = 2  # bounded sample per step: two queries of the workload
+    for i in range(args.warmup):
+        for q in queries[(i * per_step) % len(queries):][:per_step]:
+            oracle.dpccp(q)
+    t0 = time.perf_counter()
+    done = 0
+    for s in range(args.steps):
+        base = (s * per_step) % len(queries)
+        for q in queries[base:base + per_step]:
+            oracle.dpccp(q)
+            done += 1
+    el = time.perf_counter() - t0
+    value = done / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(args.queries), "relations": N_RELS,
+                   "queries_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} queries per step, DPCCP on 1 host core"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2202_13511_gb300 import mpdp
+    from paper_2202_13511_gb300 import workloads as W
+
+    Q = args.queries
+    queries = workload(rank, Q)
+    stream = torch.cuda.current_stream()
+    opt = mpdp.Optimizer(local_rank, stream=stream.cuda_stream)
+
+    # device-resident inputs and outputs
+    d_card = [torch.tensor(q.card, dtype=torch.float64, device="cuda") for q in queries]
+    d_edges = [torch.from_numpy(mpdp.pack_edges(q.edges).view(np.uint8).copy()).cuda()
+               for q in queries]
+    d_nodes = torch.zeros((Q, (2 * N_RELS - 1) * 40), dtype=torch.uint8, device="cuda")
+    d_cost = torch.zeros(Q, dtype=torch.float64, device="cuda")
+    d_status = torch.full((Q,), -100, dtype=torch.int32, device="cuda")
+
+    def step():
+        for i, q in enumerate(queries):
+            opt.optimize_device(q.n, len(q.edges), d_card[i], d_edges[i], d_nodes[i],
+                                d_cost[i:i + 1], d_status[i:i + 1])
+
+    # host-path pass: per-query counters (CCP pairs, filter work, transfer bytes)
+    stats = [opt.optimize(q).stats for q in queries]
+    launches_per_query = None
+    for _ in range(max(args.warmup, 3)):
+        step()
+        launches_per_query = opt.launch_count()
+    torch.cuda.synchronize()
+    assert int((d_status != 0).sum().item()) == 0, "device reported an error"
+    if not args.no_verify and rank == 0:
+        import oracle
+        for i in (0, Q - 1):
+            ref = oracle.dpccp(queries[i])
+            assert float(d_cost[i].item()) == ref.opt_cost, "cost differs from the oracle"
+            nodes = mpdp.nodes_from_bytes(d_nodes[i, :(2 * N_RELS - 1) * 40].cpu().numpy())
+            sig = mpdp.Plan(cost=0.0, nodes=nodes).signature()
+            assert sig == oracle.plan_signature(oracle.plan_from_memo(queries[i], ref))
+
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local_rank)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for s in range(args.steps):
+        flush.zero_()
+        starts[s].record(stream)
+        step()
+        ends[s].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = Q * world * args.steps / (total_ms / 1000.0)
+    ccp_per_step = sum(int(s["ccp_pairs"]) for s in stats)
+
+    # end to end through the host-buffer C ABI: pinned staging, H2D, DP, D2H
+    for _ in range(2):
+        opt.optimize_batch(queries)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        opt.optimize_batch(queries)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": Q * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": sum(int(s["h2d_bytes"]) for s in stats),
+           "d2h_bytes_per_step": sum(int(s["d2h_bytes"]) for s in stats)}
+
+    # kernel timing pass: CUDA events around every launch, on the launch stream
+    prof_steps = min(args.steps, 5)
+    opt.profile(True)
+    for _ in range(prof_steps):
+        flush.zero_()
+        step()
+    kt = opt.profile_read()
+    opt.profile(False)
+    peaks = read_peaks()
+    dom = max(kt, key=lambda k: kt[k]["ms"])
+    roof = roofline(dom, kt[dom], stats, prof_steps, peaks, clocks)
+    kernel_share = {k: round(v["ms"] / max(sum(x["ms"] for x in kt.values()), 1e-12), 4)
+                    for k, v in kt.items() if v["launches"]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(Q), "relations": N_RELS, "queries_per_step": Q,
+                   "memo": "dense", "inputs": "device-resident",
+                   "l2": "flushed before every timed step (256 MiB write, outside the events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "ms_per_query": total_ms / args.steps / Q,
+        "ccp_pairs_per_s": ccp_per_step * world * args.steps / (total_ms / 1000.0),
+        "e2e": e2e,
+        "gpu_launches": int(launches_per_query) * Q * args.steps,
+        "clocks": clocks,
+        "roofline": roof,
+        "kernel_share": kernel_share,
+    }
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline(queries, args.cpu_sample_s)
+    if rank == 0 and not args.no_star:
+        line["star25"] = star_line(opt, torch, mpdp, W, peaks)
+    opt.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline(kind, timing, stats, prof_steps, peaks, clocks):
+    launches = max(timing["launches"], 1)
+    avg_s = timing["ms"] / launches / 1000.0
+    if kind == "filter":
+        ops = sum(OPS_PER_SUBSET * int(s["sets_unranked"]) + OPS_PER_STEP * int(s["filter_steps"])
+                  for s in stats) / len(stats)
+        mhz = 2070.0
+        peak = SMS * SCHEDULERS * LANES * mhz * 1e6 / 1e12
+        ach = ops / avg_s / 1e12
+        return {"kernel": "k_filter", "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "Tops/s", "frac": ach / peak, "traffic": None,
+                "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz (issue slots)",
+                "ops_per_launch": ops, "avg_launch_ms": avg_s * 1000.0}
+    # memo-traffic kernels: algorithmic bytes per launch
+    nbytes = sum(BYTES_PER_CCP * int(s["ccp_pairs"]) + BYTES_PER_SET * int(s["sets_connected"])
+                 for s in stats) * prof_steps / launches / max(prof_steps, 1)
+    peak = (peaks or {}).get("hbm_gbs", 6800.0)
+    ach = nbytes / avg_s / 1e9
+    return {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
+            "bytes_per_launch": nbytes, "avg_launch_ms": avg_s * 1000.0}
+
+
+def star_line(opt, torch, mpdp, W, peaks):
+    """25-relation star (16.8M connected sets, 201M CCP pairs per query)."""
+    import numpy as np
+    q = W.star(N_RELS, seed=0)
+    st = opt.optimize(q).stats
+    d_card = torch.tensor(q.card, dtype=torch.float64, device="cuda")
+    d_edges = torch.from_numpy(mpdp.pack_edges(q.edges).view(np.uint8).copy()).cuda()
+    d_nodes = torch.zeros((2 * N_RELS - 1) * 40, dtype=torch.uint8, device="cuda")
+    d_cost = torch.zeros(1, dtype=torch.float64, device="cuda")
+    d_status = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def run():
+        opt.optimize_device(q.n, len(q.edges), d_card, d_edges, d_nodes, d_cost, d_status)
+
+    for _ in range(3):
+        run()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    reps = 10
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        run()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / reps
+    assert int(d_status.item()) == 0
+    opt.profile(True)
+    for _ in range(3):
+        flush.zero_()
+        run()
+    kt = opt.profile_read()
+    opt.profile(False)
+    dom = max(kt, key=lambda k: kt[k]["ms"])
+    return {"workload": "star join, 25 relations (fact 0 + 24 dimensions), seed 0",
+            "ms_per_query": ms, "queries_per_s": 1000.0 / ms,
+            "ccp_pairs_per_s": int(st["ccp_pairs"]) / (ms / 1000.0),
+            "ccp_pairs": int(st["ccp_pairs"]), "sets_connected": int(st["sets_connected"]),
+            "roofline": roofline(dom, kt[dom], [st], 3, peaks, None),
+            "kernel_share": {k: round(v["ms"] / max(sum(x["ms"] for x in kt.values()), 1e-12), 4)
+                             for k, v in kt.items() if v["launches"]}}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,236 @@
+/*
+ * mpdp.h - C ABI of the GB300 (sm_103a) MPDP join-order optimizer.
+ *
+ * The library finds the cheapest bushy join tree without cross products for a
+ * query join graph, with the MPDP dynamic program of "Efficient Massively
+ * Parallel Join Optimization for Large Queries" (arXiv 2202.13511):
+ *   - the DP runs level by level over relation-set sizes k = 2..n (Sec. 2.1.1,
+ *     the level dependency rule; Sec. 5, Algorithm "MPDP on GPU");
+ *   - each level unranks every k-subset, keeps the connected ones (Sec. 5,
+ *     "Unrank", "Filter"), enumerates their CCP pairs either by removing each
+ *     edge (tree join graphs, Algorithm 2, Sec. 3.1) or block by block
+ *     (Algorithm 4, Sec. 3.2), costs every pair, keeps the best per set
+ *     ("Prune", fused) and stores it in the memo ("Scatter");
+ *   - the plan is fetched recursively from the memo (Sec. 5, last paragraph).
+ *
+ * Cost model (the paper's own is unspecified, Sec. 6.1): C_out.
+ *   cost({R_i}) = 0;  cost(L join R) = (cost(L) + cost(R)) + card(L u R),
+ *   card(S) = product, in this fixed order, over the relations r of S in
+ *   ascending index of: card[r], then sel(j, r) for every j in S with j < r
+ *   and an edge (j, r), in ascending j.  All arithmetic is IEEE-754 binary64,
+ *   round to nearest, no fused multiply-add.
+ * Ties: the chosen split of S is the lexicographic minimum of (cost, left)
+ * where left is the numerically smaller of the two relation bitmaps.
+ * Results are therefore bit-identical to any exact DP with the same rules.
+ *
+ * Relation sets are bitmaps: bit i is relation i.
+ * All functions return 0 (MPDP_OK) or a negative MPDP_ERR_* code; none of them
+ * aborts.  A context is used by one host thread at a time.
+ */
+#ifndef MPDP_H
+#define MPDP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPDP_ABI_VERSION 1
+/* Exact mode uses 32-bit relation bitmaps; memory grows as 2^n (see
+ * mpdp_workspace_bytes), so n is further capped by the memo budget. */
+#define MPDP_MAX_EXACT_RELS 30
+#define MPDP_MAX_LEVELS 33
+
+enum {
+    MPDP_OK = 0,
+    MPDP_ERR_INVALID_ARG = -1,      /* bad index, duplicate edge, non-finite or <= 0 value */
+    MPDP_ERR_DISCONNECTED = -2,     /* no plan without cross products exists */
+    MPDP_ERR_TOO_LARGE = -3,        /* n above the mode's limit */
+    MPDP_ERR_OOM = -4,              /* device allocation failed or memo arena full */
+    MPDP_ERR_ADMISSION = -5,        /* request exceeds the memo budget */
+    MPDP_ERR_BUFFER_TOO_SMALL = -6, /* caller's node buffer has fewer than 2n-1 entries */
+    MPDP_ERR_TIMEOUT = -7,          /* a bounded device wait gave up */
+    MPDP_ERR_PROBE_LIMIT = -8,      /* memo probe found no entry within the table */
+    MPDP_ERR_CUDA = -9,             /* a CUDA runtime call failed */
+    MPDP_ERR_BAD_HANDLE = -10,      /* unknown or released handle */
+    MPDP_ERR_NOT_IMPLEMENTED = -11,
+    MPDP_ERR_STALE = -12,           /* the handle's memo was overwritten by a later query */
+    MPDP_ERR_INTERNAL = -13         /* an internal consistency check failed */
+};
+
+enum { MPDP_COST_COUT = 0 };
+
+enum {
+    MPDP_MODE_EXACT = 0,
+    MPDP_MODE_IDP2 = 1,
+    MPDP_MODE_UNIONDP = 2,
+    MPDP_MODE_IDP2_LEARNED = 3,
+    MPDP_MODE_UNIONDP_LEARNED = 4
+};
+
+/* CCP enumeration: AUTO picks TREE when the join graph is a tree
+ * (connected with n-1 edges), BLOCKS otherwise.  BLOCKS is correct on trees
+ * too (every block is one edge). */
+enum { MPDP_ENUM_AUTO = 0, MPDP_ENUM_TREE = 1, MPDP_ENUM_BLOCKS = 2 };
+
+/* Memo layout.  DENSE: arrays indexed directly by the relation bitmap
+ * (12 bytes x 2^n).  HASH: one open-addressing table per level, Murmur3 fmix32
+ * hash, linear probing, 16-byte slots {key, left, cost}, capacity the power of
+ * two >= 2x the level's connected-set count (Sec. 5, memo of "MPDP on GPU"). */
+enum { MPDP_MEMO_DENSE = 0, MPDP_MEMO_HASH = 1 };
+
+typedef struct mpdp_ctx mpdp_ctx; /* opaque, owned by the library */
+
+/* One join predicate between relations u and v (0 <= u, v < n, u != v) with
+ * selectivity 0 < sel <= 1.  No duplicate pairs. 16 bytes. */
+typedef struct {
+    int32_t u, v;
+    double sel;
+} mpdp_edge;
+
+/* A query as host arrays.  The library copies everything it needs before
+ * mpdp_optimize returns; the caller keeps ownership. */
+typedef struct {
+    int32_t n_rels;          /* number of relations, >= 1 */
+    int32_t n_edges;         /* number of join predicates */
+    const double *card;      /* [n_rels] base cardinalities, finite and > 0 */
+    const mpdp_edge *edges;  /* [n_edges] */
+    int32_t cost_model;      /* MPDP_COST_COUT */
+    int32_t mode;            /* MPDP_MODE_* */
+    int32_t k;               /* heuristic sub-problem size (IDP2 / UnionDP), <= 25 */
+    int32_t reserved;        /* must be 0 */
+} mpdp_query;
+
+/* One node of the result plan.  Node 0 is the root; children have larger
+ * indices than their parent (breadth-first order).  40 bytes. */
+typedef struct {
+    int32_t left, right;  /* child node indices; -1 for a leaf */
+    int32_t rel;          /* leaf: relation index; join: -1 */
+    int32_t n_leaves;     /* relations under this node */
+    uint64_t set;         /* relation bitmap of the node (0 if n > 64) */
+    double card;          /* card(set) */
+    double cost;          /* C_out cost of the subtree (0 for a leaf) */
+} mpdp_plan_node;
+
+/* Counters of one optimization (Sec. 2.2: EvaluatedCounter and CCP-Counter).
+ * pairs_evaluated counts the join pairs the enumeration examined: one per
+ * edge of G[S] in tree mode (Algorithm 2), one per unordered bipartition
+ * {lb, rb} of each block in block mode (Algorithm 4's loop over every
+ * non-empty proper lb visits each of these twice).  ccp_pairs counts each
+ * unordered CCP pair once. */
+typedef struct {
+    uint64_t sets_unranked;    /* k-subsets unranked, k = 2..n */
+    uint64_t sets_connected;   /* connected sets, k = 2..n */
+    uint64_t pairs_evaluated;
+    uint64_t ccp_pairs;
+    uint64_t memo_bytes;       /* device bytes of the memo used by this query */
+    uint64_t heavy_sets;       /* sets evaluated by the warp-per-set path */
+    double device_ms;          /* device time of the DP (CUDA events) */
+    int32_t enumeration;       /* MPDP_ENUM_TREE or MPDP_ENUM_BLOCKS as run */
+    int32_t memo_kind;         /* MPDP_MEMO_* as run */
+    uint64_t h2d_bytes;        /* host -> device bytes copied for this query */
+    uint64_t d2h_bytes;        /* device -> host bytes copied for this query */
+    uint64_t filter_steps;     /* vertices expanded by the filter's connectivity tests */
+    uint64_t connected_per_level[MPDP_MAX_LEVELS];
+    uint64_t evaluated_per_level[MPDP_MAX_LEVELS];
+    uint64_t ccp_per_level[MPDP_MAX_LEVELS];
+} mpdp_stats;
+
+/* Tuning knobs; mpdp_get_config returns the defaults of a new context. */
+typedef struct {
+    int32_t memo_kind;        /* MPDP_MEMO_DENSE (default) or MPDP_MEMO_HASH */
+    int32_t enumeration;      /* MPDP_ENUM_AUTO (default), _TREE, _BLOCKS */
+    int32_t heavy_threshold;  /* block mode: sets with more pairs than this go to
+                                 the warp-per-set kernel (default 64) */
+    int32_t use_ccc;          /* 1 (default): collaborative context collection
+                                 in the warp-per-set kernel (Sec. 5) */
+    int32_t use_graphs;       /* 1 (default): replay a captured CUDA graph per shape */
+    int32_t run_length;       /* k-subsets unranked per lane (1..32, default 32) */
+} mpdp_config;
+
+/* Create a context on CUDA device `device`.  memo_budget_bytes caps the device
+ * workspace (0 = 64 GiB).  cuda_stream is a cudaStream_t borrowed for all work
+ * of the context; NULL means the CUDA default stream.  The caller keeps the
+ * stream alive for the life of the context. */
+int mpdp_create(mpdp_ctx **out, int device, size_t memo_budget_bytes, void *cuda_stream);
+void mpdp_destroy(mpdp_ctx *ctx);
+int mpdp_set_config(mpdp_ctx *ctx, const mpdp_config *cfg);
+int mpdp_get_config(const mpdp_ctx *ctx, mpdp_config *cfg);
+
+/* Device workspace the exact mode needs for n relations under cfg. */
+size_t mpdp_workspace_bytes(int32_t n_rels, const mpdp_config *cfg);
+
+/* Validate the query on the host, enqueue its optimization on the context's
+ * stream and return a handle at once (asynchronous).  Exact mode: n <= 30. */
+int mpdp_optimize(mpdp_ctx *ctx, const mpdp_query *q, int64_t *handle);
+
+/* Enqueue nq queries; handles[i] receives each one's handle.  Returns the
+ * first error; queries before it stay enqueued. */
+int mpdp_optimize_batch(mpdp_ctx *ctx, const mpdp_query *qs, int32_t nq, int64_t *handles);
+
+/* Block until the handle's optimization is done and copy out its plan.
+ * nodes: caller buffer of cap >= 2n-1 entries (may be NULL when cap == 0 to
+ * read only cost / stats).  n_nodes, cost, st may be NULL. */
+int mpdp_get_plan(mpdp_ctx *ctx, int64_t handle, mpdp_plan_node *nodes, int32_t cap,
+                  int32_t *n_nodes, double *cost, mpdp_stats *st);
+
+/* Forget a handle (its host result buffer is reused). */
+int mpdp_release(mpdp_ctx *ctx, int64_t handle);
+
+/* Device-resident form: inputs and outputs are device pointers, everything is
+ * enqueued on the context's stream and nothing waits for the device.
+ *   d_card [n_rels] doubles, d_edges [n_edges] mpdp_edge (validated on device);
+ *   d_nodes [>= 2n-1] plan nodes, d_cost one double, d_status one int32
+ *   receiving 0 or an MPDP_ERR_* code once the work has run.
+ * Returns MPDP_OK when the work was enqueued. */
+int mpdp_optimize_device(mpdp_ctx *ctx, int32_t n_rels, int32_t n_edges, const double *d_card,
+                         const mpdp_edge *d_edges, int32_t cost_model, mpdp_plan_node *d_nodes,
+                         double *d_cost, int32_t *d_status);
+
+/* Wait for all work of the context; returns the first device-reported error
+ * of work enqueued since the previous call, or MPDP_OK. */
+int mpdp_sync(mpdp_ctx *ctx);
+
+/* Read memo entries of the most recent exact optimization of the context
+ * (the handle must be that one, else MPDP_ERR_STALE).  sets: host array of
+ * connected relation bitmaps; costs / lefts: host outputs.  A singleton reads
+ * (0, 0).  Used to check every connected set against a reference. */
+int mpdp_memo_lookup(mpdp_ctx *ctx, int64_t handle, const uint64_t *sets, int32_t count,
+                     double *costs, uint64_t *lefts);
+
+/* Number of kernel launches the last mpdp_optimize / _device call enqueued. */
+int32_t mpdp_last_launch_count(const mpdp_ctx *ctx);
+
+/* Kernel classes timed by the profiling mode. */
+enum {
+    MPDP_KC_STAGE = 0,   /* device-path input gather */
+    MPDP_KC_INGEST = 1,  /* graph build and validation */
+    MPDP_KC_FILTER = 2,  /* unrank + connectivity filter, all levels */
+    MPDP_KC_MEMO_INIT = 3, /* hash memo layout and clear */
+    MPDP_KC_EVAL = 4,    /* per-level evaluate + prune + scatter (thread per set) */
+    MPDP_KC_HEAVY = 5,   /* per-level block-per-set evaluation (block mode) */
+    MPDP_KC_EXTRACT = 6, /* plan fetch */
+    MPDP_KC_PUBLISH = 7, /* device-path output copy */
+    MPDP_KC_COUNT = 8
+};
+
+/* Profiling mode (off by default).  While on, work is launched kernel by
+ * kernel (no graph replay) with a pair of CUDA events on the context's stream
+ * around every launch.  mpdp_profile_read waits for the stream, adds the
+ * elapsed times per kernel class since the previous read into ms[MPDP_KC_COUNT]
+ * and the launch counts into launches[MPDP_KC_COUNT], and resets them. */
+int mpdp_profile(mpdp_ctx *ctx, int enable);
+int mpdp_profile_read(mpdp_ctx *ctx, double *ms, uint64_t *launches);
+
+/* Static text for an error code. */
+const char *mpdp_strerror(int code);
+/* Text of the last CUDA error seen by this context (or ""). */
+const char *mpdp_last_error(const mpdp_ctx *ctx);
+int32_t mpdp_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPDP_H */

@@ -1,0 +1,367 @@
+"""Python binding of the C ABI in ``include/mpdp.h`` (argument marshalling only).
+
+Every step of the join-order DP runs in the CUDA library ``libmpdp.so``; this
+module only converts queries into the ABI's structs, calls the entry points
+with the same names, and converts plans back.  There is no CPU fallback: if
+the library cannot be loaded, every call raises.
+
+PyTorch is used only for device memory and streams (``optimize_device`` takes
+tensors resident on the GPU; ``Optimizer(stream=...)`` borrows a CUDA stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+MPDP_OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "DISCONNECTED", -3: "TOO_LARGE", -4: "OOM", -5: "ADMISSION",
+    -6: "BUFFER_TOO_SMALL", -7: "TIMEOUT", -8: "PROBE_LIMIT", -9: "CUDA", -10: "BAD_HANDLE",
+    -11: "NOT_IMPLEMENTED", -12: "STALE", -13: "INTERNAL",
+}
+ERR = {v: k for k, v in ERRORS.items()}
+
+MODE_EXACT, MODE_IDP2, MODE_UNIONDP, MODE_IDP2_LEARNED, MODE_UNIONDP_LEARNED = range(5)
+ENUM_AUTO, ENUM_TREE, ENUM_BLOCKS = range(3)
+MEMO_DENSE, MEMO_HASH = range(2)
+MAX_LEVELS = 33
+
+
+class MPDPError(RuntimeError):
+    def __init__(self, code: int, what: str = "", detail: str = ""):
+        name = ERRORS.get(code, str(code))
+        msg = f"{what}: MPDP_ERR_{name} ({code})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+        self.code = code
+        self.name = name
+
+
+class Edge(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_int32), ("v", ctypes.c_int32), ("sel", ctypes.c_double)]
+
+
+class QueryC(ctypes.Structure):
+    _fields_ = [("n_rels", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("card", ctypes.POINTER(ctypes.c_double)), ("edges", ctypes.POINTER(Edge)),
+                ("cost_model", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class PlanNode(ctypes.Structure):
+    _fields_ = [("left", ctypes.c_int32), ("right", ctypes.c_int32), ("rel", ctypes.c_int32),
+                ("n_leaves", ctypes.c_int32), ("set", ctypes.c_uint64),
+                ("card", ctypes.c_double), ("cost", ctypes.c_double)]
+
+
+class StatsC(ctypes.Structure):
+    _fields_ = [("sets_unranked", ctypes.c_uint64), ("sets_connected", ctypes.c_uint64),
+                ("pairs_evaluated", ctypes.c_uint64), ("ccp_pairs", ctypes.c_uint64),
+                ("memo_bytes", ctypes.c_uint64), ("heavy_sets", ctypes.c_uint64),
+                ("device_ms", ctypes.c_double), ("enumeration", ctypes.c_int32),
+                ("memo_kind", ctypes.c_int32), ("h2d_bytes", ctypes.c_uint64),
+                ("d2h_bytes", ctypes.c_uint64), ("filter_steps", ctypes.c_uint64),
+                ("connected_per_level", ctypes.c_uint64 * MAX_LEVELS),
+                ("evaluated_per_level", ctypes.c_uint64 * MAX_LEVELS),
+                ("ccp_per_level", ctypes.c_uint64 * MAX_LEVELS)]
+
+
+class ConfigC(ctypes.Structure):
+    _fields_ = [("memo_kind", ctypes.c_int32), ("enumeration", ctypes.c_int32),
+                ("heavy_threshold", ctypes.c_int32), ("use_ccc", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32), ("run_length", ctypes.c_int32)]
+
+
+EDGE_DTYPE = np.dtype([("u", "<i4"), ("v", "<i4"), ("sel", "<f8")])
+NODE_DTYPE = np.dtype([("left", "<i4"), ("right", "<i4"), ("rel", "<i4"), ("n_leaves", "<i4"),
+                       ("set", "<u8"), ("card", "<f8"), ("cost", "<f8")])
+assert EDGE_DTYPE.itemsize == ctypes.sizeof(Edge) == 16
+assert NODE_DTYPE.itemsize == ctypes.sizeof(PlanNode) == 40
+
+# Every exported entry point declared in include/mpdp.h.
+EXPORTS = [
+    "mpdp_create", "mpdp_destroy", "mpdp_set_config", "mpdp_get_config",
+    "mpdp_workspace_bytes", "mpdp_optimize", "mpdp_optimize_batch", "mpdp_get_plan",
+    "mpdp_release", "mpdp_optimize_device", "mpdp_sync", "mpdp_memo_lookup",
+    "mpdp_last_launch_count", "mpdp_strerror", "mpdp_last_error", "mpdp_abi_version",
+    "mpdp_profile", "mpdp_profile_read",
+]
+
+KERNEL_CLASSES = ["stage", "ingest", "filter", "memo_init", "eval", "heavy", "extract", "publish"]
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load libmpdp.so (building it first when it is missing or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB_PATH
+    if build_if_missing and not _build.up_to_date():
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    c_ctx = ctypes.c_void_p
+    L.mpdp_create.argtypes = [P(c_ctx), ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]
+    L.mpdp_destroy.argtypes = [c_ctx]
+    L.mpdp_destroy.restype = None
+    L.mpdp_set_config.argtypes = [c_ctx, P(ConfigC)]
+    L.mpdp_get_config.argtypes = [c_ctx, P(ConfigC)]
+    L.mpdp_workspace_bytes.argtypes = [ctypes.c_int32, P(ConfigC)]
+    L.mpdp_workspace_bytes.restype = ctypes.c_size_t
+    L.mpdp_optimize.argtypes = [c_ctx, P(QueryC), P(ctypes.c_int64)]
+    L.mpdp_optimize_batch.argtypes = [c_ctx, P(QueryC), ctypes.c_int32, P(ctypes.c_int64)]
+    L.mpdp_get_plan.argtypes = [c_ctx, ctypes.c_int64, P(PlanNode), ctypes.c_int32,
+                                P(ctypes.c_int32), P(ctypes.c_double), P(StatsC)]
+    L.mpdp_release.argtypes = [c_ctx, ctypes.c_int64]
+    L.mpdp_optimize_device.argtypes = [c_ctx, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]
+    L.mpdp_sync.argtypes = [c_ctx]
+    L.mpdp_memo_lookup.argtypes = [c_ctx, ctypes.c_int64, P(ctypes.c_uint64), ctypes.c_int32,
+                                   P(ctypes.c_double), P(ctypes.c_uint64)]
+    L.mpdp_last_launch_count.argtypes = [c_ctx]
+    L.mpdp_last_launch_count.restype = ctypes.c_int32
+    L.mpdp_strerror.argtypes = [ctypes.c_int]
+    L.mpdp_strerror.restype = ctypes.c_char_p
+    L.mpdp_last_error.argtypes = [c_ctx]
+    L.mpdp_last_error.restype = ctypes.c_char_p
+    L.mpdp_abi_version.restype = ctypes.c_int32
+    L.mpdp_profile.argtypes = [c_ctx, ctypes.c_int]
+    L.mpdp_profile_read.argtypes = [c_ctx, P(ctypes.c_double), P(ctypes.c_uint64)]
+    for f in ("mpdp_profile", "mpdp_profile_read", "mpdp_create", "mpdp_set_config", "mpdp_get_config", "mpdp_optimize",
+              "mpdp_optimize_batch", "mpdp_get_plan", "mpdp_release", "mpdp_optimize_device",
+              "mpdp_sync", "mpdp_memo_lookup"):
+        getattr(L, f).restype = ctypes.c_int
+    _LIB = L
+    return L
+
+
+@dataclass
+class Plan:
+    cost: float
+    nodes: np.ndarray                 # NODE_DTYPE records, node 0 = root
+    stats: Dict = field(default_factory=dict)
+    handle: int = -1
+
+    def signature(self, i: int = 0):
+        """Nested (set, left-subtree, right-subtree) form; leaves are their set."""
+        nd = self.nodes[i]
+        if nd["left"] < 0:
+            return int(nd["set"])
+        return (int(nd["set"]), self.signature(int(nd["left"])), self.signature(int(nd["right"])))
+
+
+def pack_edges(edges) -> np.ndarray:
+    arr = np.zeros(len(edges), dtype=EDGE_DTYPE)
+    for i, (u, v, s) in enumerate(edges):
+        arr[i] = (u, v, s)
+    return arr
+
+
+class _Packed:
+    """ABI view of one query (keeps its arrays alive)."""
+
+    def __init__(self, q, mode: int = MODE_EXACT, k: int = 0):
+        self.card = np.ascontiguousarray(np.asarray(q.card, dtype=np.float64))
+        self.edges = pack_edges(q.edges)
+        self.c = QueryC()
+        self.c.n_rels = int(q.n)
+        self.c.n_edges = len(q.edges)
+        self.c.card = self.card.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self.c.edges = self.edges.ctypes.data_as(ctypes.POINTER(Edge)) if len(q.edges) else \
+            ctypes.cast(None, ctypes.POINTER(Edge))
+        self.c.cost_model = 0
+        self.c.mode = mode
+        self.c.k = k
+        self.c.reserved = 0
+
+
+def _stats_dict(st: StatsC, n: int) -> Dict:
+    L = n + 1
+    return dict(
+        sets_unranked=st.sets_unranked, sets_connected=st.sets_connected,
+        pairs_evaluated=st.pairs_evaluated, ccp_pairs=st.ccp_pairs, memo_bytes=st.memo_bytes,
+        heavy_sets=st.heavy_sets, device_ms=st.device_ms, enumeration=st.enumeration,
+        memo_kind=st.memo_kind, h2d_bytes=st.h2d_bytes, d2h_bytes=st.d2h_bytes,
+        filter_steps=st.filter_steps,
+        connected_per_level=np.array(st.connected_per_level[:L], dtype=np.uint64),
+        evaluated_per_level=np.array(st.evaluated_per_level[:L], dtype=np.uint64),
+        ccp_per_level=np.array(st.ccp_per_level[:L], dtype=np.uint64),
+    )
+
+
+class Optimizer:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0, memo_budget_bytes: int = 0, stream: Optional[int] = None,
+                 **config):
+        self._lib = load()
+        self._ctx = ctypes.c_void_p()
+        rc = self._lib.mpdp_create(ctypes.byref(self._ctx), int(device), int(memo_budget_bytes),
+                                   ctypes.c_void_p(stream or 0))
+        self._check(rc, "mpdp_create")
+        self._n = {}
+        if config:
+            self.set_config(**config)
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, rc: int, what: str):
+        if rc != MPDP_OK:
+            detail = ""
+            if getattr(self, "_ctx", None) and self._ctx.value:
+                detail = (self._lib.mpdp_last_error(self._ctx) or b"").decode()
+            raise MPDPError(rc, what, detail)
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            self._lib.mpdp_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- configuration ----------------------------------------------------
+    def get_config(self) -> Dict:
+        c = ConfigC()
+        self._check(self._lib.mpdp_get_config(self._ctx, ctypes.byref(c)), "mpdp_get_config")
+        return {f: getattr(c, f) for f, _ in ConfigC._fields_}
+
+    def set_config(self, **kw):
+        cur = self.get_config()
+        for k, v in kw.items():
+            if k not in cur:
+                raise KeyError(k)
+            cur[k] = int(v)
+        c = ConfigC(**cur)
+        self._check(self._lib.mpdp_set_config(self._ctx, ctypes.byref(c)), "mpdp_set_config")
+
+    def launch_count(self) -> int:
+        return int(self._lib.mpdp_last_launch_count(self._ctx))
+
+    # -- host path --------------------------------------------------------
+    def submit(self, q, mode: int = MODE_EXACT, k: int = 0) -> int:
+        p = _Packed(q, mode, k)
+        h = ctypes.c_int64(-1)
+        self._check(self._lib.mpdp_optimize(self._ctx, ctypes.byref(p.c), ctypes.byref(h)),
+                    "mpdp_optimize")
+        self._n[h.value] = int(q.n)
+        return h.value
+
+    def get_plan(self, handle: int, release: bool = True) -> Plan:
+        n = self._n.get(handle, 32)
+        cap = max(2 * n - 1, 1)
+        nodes = np.zeros(cap, dtype=NODE_DTYPE)
+        nn = ctypes.c_int32(0)
+        cost = ctypes.c_double(0.0)
+        st = StatsC()
+        rc = self._lib.mpdp_get_plan(self._ctx, handle,
+                                     nodes.ctypes.data_as(ctypes.POINTER(PlanNode)), cap,
+                                     ctypes.byref(nn), ctypes.byref(cost), ctypes.byref(st))
+        if rc != MPDP_OK:
+            if release:
+                self.release(handle)
+            self._check(rc, "mpdp_get_plan")
+        plan = Plan(cost=cost.value, nodes=nodes[:nn.value].copy(), stats=_stats_dict(st, n),
+                    handle=handle)
+        if release:
+            self.release(handle)
+        return plan
+
+    def release(self, handle: int):
+        self._check(self._lib.mpdp_release(self._ctx, handle), "mpdp_release")
+        self._n.pop(handle, None)
+
+    def optimize(self, q, mode: int = MODE_EXACT, k: int = 0, keep: bool = False) -> Plan:
+        """Optimize one query through mpdp_optimize + mpdp_get_plan."""
+        h = self.submit(q, mode, k)
+        return self.get_plan(h, release=not keep)
+
+    def optimize_batch(self, queries: Sequence, mode: int = MODE_EXACT, k: int = 0) -> List[Plan]:
+        packed = [_Packed(q, mode, k) for q in queries]
+        arr = (QueryC * len(packed))(*[p.c for p in packed])
+        hs = (ctypes.c_int64 * len(packed))()
+        rc = self._lib.mpdp_optimize_batch(self._ctx, arr, len(packed), hs)
+        for q, h in zip(queries, hs):
+            if h >= 0:
+                self._n[h] = int(q.n)
+        if rc != MPDP_OK:
+            for h in hs:
+                if h >= 0:
+                    self.release(h)
+            self._check(rc, "mpdp_optimize_batch")
+        return [self.get_plan(h) for h in hs]
+
+    def memo_lookup(self, handle: int, sets) -> (np.ndarray, np.ndarray):
+        s = np.ascontiguousarray(np.asarray(sets, dtype=np.uint64))
+        costs = np.zeros(len(s), dtype=np.float64)
+        lefts = np.zeros(len(s), dtype=np.uint64)
+        rc = self._lib.mpdp_memo_lookup(self._ctx, handle,
+                                        s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), len(s),
+                                        costs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        lefts.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        self._check(rc, "mpdp_memo_lookup")
+        return costs, lefts
+
+    # -- device path --------------------------------------------------------
+    def optimize_device(self, n: int, n_edges: int, d_card, d_edges, d_nodes, d_cost, d_status):
+        """Enqueue one optimization whose inputs and outputs are device
+        tensors (or raw device pointers); returns without waiting."""
+        def ptr(x):
+            return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+        rc = self._lib.mpdp_optimize_device(self._ctx, int(n), int(n_edges), ptr(d_card),
+                                            ptr(d_edges), 0, ptr(d_nodes), ptr(d_cost),
+                                            ptr(d_status))
+        self._check(rc, "mpdp_optimize_device")
+
+    def sync(self) -> int:
+        return int(self._lib.mpdp_sync(self._ctx))
+
+    # -- profiling ----------------------------------------------------------
+    def profile(self, enable: bool):
+        self._check(self._lib.mpdp_profile(self._ctx, int(bool(enable))), "mpdp_profile")
+
+    def profile_read(self) -> Dict[str, Dict]:
+        """Per kernel class: summed device ms and launches since the last read."""
+        ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+        ln = (ctypes.c_uint64 * len(KERNEL_CLASSES))()
+        self._check(self._lib.mpdp_profile_read(self._ctx, ms, ln), "mpdp_profile_read")
+        return {k: dict(ms=ms[i], launches=int(ln[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def workspace_bytes(n: int, memo_kind: int = MEMO_DENSE) -> int:
+    L = load()
+    c = ConfigC(memo_kind, 0, 64, 1, 1, 32)
+    return int(L.mpdp_workspace_bytes(n, ctypes.byref(c)))
+
+
+def strerror(code: int) -> str:
+    return load().mpdp_strerror(code).decode()
+
+
+def nodes_from_bytes(buf: np.ndarray) -> np.ndarray:
+    """View a raw byte buffer (e.g. copied from a device tensor) as plan nodes."""
+    return np.frombuffer(np.ascontiguousarray(buf).tobytes(), dtype=NODE_DTYPE)

@@ -1,0 +1,67 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/mpdp.h, and its host-only helpers behave."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2202_13511_gb300 import mpdp
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "mpdp.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(mpdp_[a-z_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_binding_exports():
+    assert declared_functions() == sorted(mpdp.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = mpdp.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_struct_sizes_match_header():
+    assert ctypes.sizeof(mpdp.Edge) == 16
+    assert ctypes.sizeof(mpdp.PlanNode) == 40
+    assert ctypes.sizeof(mpdp.QueryC) == 40
+    assert ctypes.sizeof(mpdp.ConfigC) == 24
+    assert ctypes.sizeof(mpdp.StatsC) == 6 * 8 + 8 + 8 + 3 * 8 + 3 * 33 * 8
+
+
+def test_abi_version_and_strerror():
+    lib = mpdp.load()
+    assert lib.mpdp_abi_version() == 1
+    assert mpdp.strerror(0) == "ok"
+    for code in mpdp.ERRORS:
+        assert mpdp.strerror(code) != "unknown error"
+    assert mpdp.strerror(-999) == "unknown error"
+
+
+def test_workspace_bytes_host_only():
+    # dense memo: 12 bytes per bitmap plus the per-level lists
+    b20 = mpdp.workspace_bytes(20, mpdp.MEMO_DENSE)
+    assert b20 >= 12 * 2 ** 20 + 8 * (2 ** 20 - 21)
+    assert mpdp.workspace_bytes(21) > b20
+    assert mpdp.workspace_bytes(0) == 0
+    assert mpdp.workspace_bytes(31) == 0
+    h = mpdp.workspace_bytes(20, mpdp.MEMO_HASH)
+    assert h > 0
+
+
+def test_create_without_gpu_fails_cleanly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(mpdp.MPDPError) as ei:
+        mpdp.Optimizer(0)
+    assert ei.value.code == mpdp.ERR["CUDA"]

@@ -1,0 +1,288 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+The bar is bit-exact: optimal cost bits, chosen plan, every compared memo
+entry (cost and left mask) and the integer counters (connected sets, CCP
+pairs and evaluated pairs per level).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_13511_gb300 import mpdp
+from paper_2202_13511_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KINDS = ["star", "chain", "cycle", "clique", "snowflake", "cyclic"]
+CONFIGS = {
+    "dense_auto": dict(memo_kind=mpdp.MEMO_DENSE, enumeration=mpdp.ENUM_AUTO),
+    "hash_auto": dict(memo_kind=mpdp.MEMO_HASH, enumeration=mpdp.ENUM_AUTO),
+    "dense_blocks": dict(memo_kind=mpdp.MEMO_DENSE, enumeration=mpdp.ENUM_BLOCKS),
+    "hash_blocks": dict(memo_kind=mpdp.MEMO_HASH, enumeration=mpdp.ENUM_BLOCKS),
+}
+
+
+@pytest.fixture(scope="module")
+def opt():
+    o = mpdp.Optimizer(0)
+    yield o
+    o.close()
+
+
+def set_cfg(opt, **kw):
+    base = dict(memo_kind=mpdp.MEMO_DENSE, enumeration=mpdp.ENUM_AUTO, heavy_threshold=64,
+                use_ccc=1, use_graphs=1, run_length=32)
+    base.update(kw)
+    opt.set_config(**base)
+
+
+def is_tree(q):
+    return len(q.edges) == q.n - 1
+
+
+def check(opt, q, ref=None, memo="all", sample=20000, block_counts=None):
+    """Optimize q on the GPU and compare with the oracle result ref."""
+    if ref is None:
+        ref = oracle.dpccp(q)
+    plan = opt.optimize(q, keep=True)
+    try:
+        assert np.float64(plan.cost).tobytes() == np.float64(ref.opt_cost).tobytes()
+        assert plan.signature() == oracle.plan_signature(oracle.plan_from_memo(q, ref))
+        st = plan.stats
+        n = q.n
+        assert np.array_equal(st["connected_per_level"][2:], ref.connected[2:n + 1])
+        assert np.array_equal(st["ccp_per_level"][2:], ref.ccp[2:n + 1])
+        assert st["sets_unranked"] == 2 ** n - n - 1
+        tree_mode = st["enumeration"] == mpdp.ENUM_TREE
+        if tree_mode:
+            assert np.array_equal(st["evaluated_per_level"], st["ccp_per_level"])
+        elif block_counts is not None:
+            assert np.array_equal(st["evaluated_per_level"][2:], block_counts[2:n + 1])
+        if memo and n >= 2:
+            sets = ref.connected_sets()
+            if memo == "sample" and len(sets) > sample:
+                rng = np.random.default_rng(q.seed + 17 * n)
+                sets = np.sort(rng.choice(sets, size=sample, replace=False))
+            costs, lefts = opt.memo_lookup(plan.handle, sets)
+            assert np.array_equal(costs.view(np.uint64), ref.cost[sets].view(np.uint64))
+            assert np.array_equal(lefts, ref.left[sets].astype(np.uint64))
+        return plan
+    finally:
+        opt.release(plan.handle)
+
+
+@pytest.mark.parametrize("cfg", list(CONFIGS))
+@pytest.mark.parametrize("kind", KINDS)
+def test_small_exhaustive(opt, cfg, kind):
+    """Every n from 1 to 12, two seeds: whole memo, plan, counters."""
+    set_cfg(opt, **CONFIGS[cfg])
+    for n in range(1, 13):
+        for seed in range(2):
+            q = W.make(kind, n, seed=seed)
+            ref = oracle.dpccp(q)
+            bc = None
+            if n <= 12 and ("blocks" in cfg or not is_tree(q)):
+                bc, _ = oracle.block_enum_counts(q)
+            check(opt, q, ref, block_counts=bc)
+
+
+@pytest.mark.parametrize("kind", ["star", "snowflake", "cyclic", "cycle", "chain"])
+@pytest.mark.parametrize("n", [14, 16, 18])
+def test_medium_whole_memo(opt, kind, n):
+    for cfg in ("dense_auto", "hash_auto"):
+        set_cfg(opt, **CONFIGS[cfg])
+        q = W.make(kind, n, seed=n)
+        check(opt, q)
+
+
+@pytest.mark.parametrize("cfg", ["dense_auto", "hash_auto"])
+def test_clique_14(opt, cfg):
+    """Config: 14-relation cliques (one block per set; the heavy path)."""
+    set_cfg(opt, **CONFIGS[cfg])
+    for seed in range(2):
+        q = W.clique(14, seed=seed)
+        plan = check(opt, q, memo="all")
+        assert plan.stats["ccp_pairs"] == (3 ** 14 - 2 ** 15 + 1) // 2
+        assert plan.stats["pairs_evaluated"] == plan.stats["ccp_pairs"]
+
+
+@pytest.mark.parametrize("n", [20, 25])
+def test_snowflake_full_size(opt, n):
+    """Config: acyclic snowflake queries of 20 and 25 relations (tree mode)."""
+    set_cfg(opt)
+    for seed in range(3):
+        q = W.snowflake(n, seed=seed)
+        check(opt, q, memo="sample")
+
+
+def test_snowflake_25_blocks_and_hash(opt):
+    """Block-based enumeration and the hash memo agree on trees too."""
+    q = W.snowflake(25, seed=5)
+    ref = oracle.dpccp(q)
+    for cfg in ("hash_auto", "dense_blocks", "hash_blocks"):
+        set_cfg(opt, **CONFIGS[cfg])
+        check(opt, q, ref, memo="sample")
+
+
+def test_star_25(opt):
+    """The headline shape: 25-relation star, 16.8M connected sets, 201M CCPs."""
+    set_cfg(opt)
+    q = W.star(25, seed=0)
+    ref = oracle.dpccp(q)
+    plan = check(opt, q, ref, memo="sample")
+    assert plan.stats["ccp_pairs"] == 24 * 2 ** 23
+    assert plan.stats["sets_connected"] == 2 ** 24
+
+
+@pytest.mark.parametrize("n", [15, 17, 20])
+def test_cyclic(opt, n):
+    """Config: random spanning tree + 10-30% extra edges (block enumeration)."""
+    for cfg in ("dense_auto", "hash_auto"):
+        set_cfg(opt, **CONFIGS[cfg])
+        for seed in range(2):
+            q = W.cyclic(n, seed=seed)
+            check(opt, q, memo="sample")
+
+
+@pytest.mark.parametrize("threshold", [0, 3, 1 << 30])
+@pytest.mark.parametrize("ccc", [0, 1])
+def test_heavy_path_and_ccc(opt, threshold, ccc):
+    """All sets through the block-per-set kernel, some, or none; with and
+    without collaborative context collection: same results."""
+    set_cfg(opt, heavy_threshold=threshold, use_ccc=ccc)
+    for q in (W.cyclic(12, seed=3), W.clique(9, seed=1), W.cycle(11, seed=2)):
+        bc, _ = oracle.block_enum_counts(q)
+        check(opt, q, block_counts=bc)
+
+
+@pytest.mark.parametrize("run", [1, 5, 32])
+def test_run_lengths(opt, run):
+    """Ragged unrank runs (run lengths that do not divide C(n,k))."""
+    set_cfg(opt, run_length=run)
+    for q in (W.snowflake(13, seed=1), W.cyclic(11, seed=4), W.star(9, seed=2)):
+        check(opt, q)
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_graphs_on_off(opt, graphs):
+    set_cfg(opt, use_graphs=graphs)
+    for q in (W.snowflake(16, seed=2), W.cyclic(13, seed=1)):
+        p1 = check(opt, q)
+        assert opt.launch_count() > 0
+        del p1
+
+
+@pytest.mark.parametrize("kind", ["star", "clique", "cycle", "chain"])
+@pytest.mark.parametrize("n", [6, 9, 12])
+def test_ties(opt, kind, n):
+    """All-equal cardinalities and selectivities: many exact ties."""
+    set_cfg(opt)
+    base = W.make(kind, n, 0)
+    q = W.uniform_values(n, [(u, v) for (u, v, _s) in base.edges])
+    check(opt, q)
+    set_cfg(opt, memo_kind=mpdp.MEMO_HASH, enumeration=mpdp.ENUM_BLOCKS)
+    check(opt, q)
+
+
+def test_max_size_chain(opt):
+    """Largest exact size the oracle reaches (28) on a chain: 268M subsets
+    unranked, 406 connected sets."""
+    set_cfg(opt)
+    q = W.chain(28, seed=0)
+    plan = check(opt, q, memo="all")
+    assert plan.stats["ccp_pairs"] == (28 ** 3 - 28) // 6
+
+
+def test_max_size_30_counts(opt):
+    """n = 30, the exact-mode maximum: closed-form counts on a chain."""
+    set_cfg(opt)
+    q = W.chain(30, seed=0)
+    plan = opt.optimize(q)
+    assert plan.stats["sets_connected"] == 30 * 31 // 2 - 30
+    assert plan.stats["ccp_pairs"] == (30 ** 3 - 30) // 6
+    assert plan.stats["sets_unranked"] == 2 ** 30 - 31
+    assert len(plan.nodes) == 59
+
+
+def test_single_relation(opt):
+    set_cfg(opt)
+    q = W.Query(n=1, card=[123.0], edges=[])
+    plan = opt.optimize(q)
+    assert plan.cost == 0.0 and len(plan.nodes) == 1 and plan.nodes[0]["rel"] == 0
+
+
+def test_errors(opt):
+    set_cfg(opt)
+    q = W.chain(5, 0)
+    bad = [W.Query(n=5, card=q.card, edges=q.edges + [(0, 1, 0.5)]),
+           W.Query(n=5, card=q.card, edges=q.edges[:-1] + [(3, 4, 0.0)]),
+           W.Query(n=5, card=[1.0, float("nan"), 1.0, 1.0, 1.0], edges=q.edges)]
+    for b in bad:
+        with pytest.raises(mpdp.MPDPError) as ei:
+            opt.optimize(b)
+        assert ei.value.code == mpdp.ERR["INVALID_ARG"]
+    with pytest.raises(mpdp.MPDPError) as ei:
+        opt.optimize(W.Query(n=5, card=q.card, edges=q.edges[:2]))
+    assert ei.value.code == mpdp.ERR["DISCONNECTED"]
+    with pytest.raises(mpdp.MPDPError) as ei:
+        opt.optimize(W.chain(31, 0))
+    assert ei.value.code == mpdp.ERR["TOO_LARGE"]
+    # the context stays usable
+    check(opt, W.cyclic(10, seed=9))
+
+
+def test_determinism(opt):
+    set_cfg(opt)
+    q = W.cyclic(16, seed=7)
+    ref = oracle.dpccp(q)
+    a = check(opt, q, ref)
+    b = check(opt, q, ref)
+    assert a.signature() == b.signature() and a.cost == b.cost
+
+
+def test_batch_matches_single(opt):
+    set_cfg(opt)
+    qs = W.mixed_stream(12, seed=3, n_lo=6, n_hi=14)
+    plans = opt.optimize_batch(qs)
+    for q, p in zip(qs, plans):
+        ref = oracle.dpccp(q)
+        assert p.cost == ref.opt_cost
+        assert p.signature() == oracle.plan_signature(oracle.plan_from_memo(q, ref))
+
+
+def test_device_path(opt):
+    """Inputs and outputs resident in device memory (torch tensors)."""
+    torch = pytest.importorskip("torch")
+    set_cfg(opt)
+    for q in (W.snowflake(18, seed=4), W.cyclic(14, seed=2), W.star(12, seed=1)):
+        ref = oracle.dpccp(q)
+        d_card = torch.tensor(q.card, dtype=torch.float64, device="cuda")
+        e = mpdp.pack_edges(q.edges)
+        d_edges = torch.from_numpy(e.view(np.uint8).copy()).cuda()
+        d_nodes = torch.zeros((2 * q.n - 1) * 40, dtype=torch.uint8, device="cuda")
+        d_cost = torch.zeros(1, dtype=torch.float64, device="cuda")
+        d_status = torch.full((1,), 99, dtype=torch.int32, device="cuda")
+        opt.optimize_device(q.n, len(q.edges), d_card, d_edges, d_nodes, d_cost, d_status)
+        assert opt.sync() == 0
+        assert int(d_status.item()) == 0
+        assert float(d_cost.item()) == ref.opt_cost
+        nodes = mpdp.nodes_from_bytes(d_nodes.cpu().numpy())
+        plan = mpdp.Plan(cost=float(d_cost.item()), nodes=nodes)
+        assert plan.signature() == oracle.plan_signature(oracle.plan_from_memo(q, ref))
+
+
+def test_device_path_invalid_input_reports_status(opt):
+    """The device path validates on the device and reports, without faulting."""
+    torch = pytest.importorskip("torch")
+    set_cfg(opt)
+    q = W.chain(6, 0)
+    edges = q.edges + [(0, 1, 0.5)]  # duplicate pair
+    d_card = torch.tensor(q.card, dtype=torch.float64, device="cuda")
+    d_edges = torch.from_numpy(mpdp.pack_edges(edges).view(np.uint8).copy()).cuda()
+    d_nodes = torch.zeros(11 * 40, dtype=torch.uint8, device="cuda")
+    d_cost = torch.zeros(1, dtype=torch.float64, device="cuda")
+    d_status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    opt.optimize_device(6, len(edges), d_card, d_edges, d_nodes, d_cost, d_status)
+    opt.sync()
+    assert int(d_status.item()) == mpdp.ERR["INVALID_ARG"]
+    check(opt, W.cyclic(9, seed=1))
