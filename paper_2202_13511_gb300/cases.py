@@ -1,0 +1,53 @@
+"""Run one workload shape through the device path (for profiler captures).
+
+    python -m paper_2202_13511_gb300.cases --kind star --n 25 --reps 3
+
+Builds nothing and checks nothing beyond the device status word; it exists so
+that a profiler can capture the kernels of one shape in isolation.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+
+import numpy as np
+
+
+def main(argv=None) -> int:
+    p = argparse.ArgumentParser()
+    p.add_argument("--kind", default="snowflake")
+    p.add_argument("--n", type=int, default=25)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--queries", type=int, default=1)
+    p.add_argument("--reps", type=int, default=2)
+    p.add_argument("--memo", choices=["dense", "hash"], default="dense")
+    p.add_argument("--enumeration", choices=["auto", "tree", "blocks"], default="auto")
+    a = p.parse_args(argv)
+    import torch
+    from . import mpdp
+    from . import workloads as W
+    torch.cuda.set_device(0)
+    opt = mpdp.Optimizer(0, stream=torch.cuda.current_stream().cuda_stream,
+                         memo_kind={"dense": mpdp.MEMO_DENSE, "hash": mpdp.MEMO_HASH}[a.memo],
+                         enumeration={"auto": mpdp.ENUM_AUTO, "tree": mpdp.ENUM_TREE,
+                                      "blocks": mpdp.ENUM_BLOCKS}[a.enumeration])
+    qs = [W.make(a.kind, a.n, seed=a.seed + i) for i in range(a.queries)]
+    bufs = []
+    for q in qs:
+        bufs.append((torch.tensor(q.card, dtype=torch.float64, device="cuda"),
+                     torch.from_numpy(mpdp.pack_edges(q.edges).view(np.uint8).copy()).cuda(),
+                     torch.zeros((2 * q.n - 1) * 40, dtype=torch.uint8, device="cuda"),
+                     torch.zeros(1, dtype=torch.float64, device="cuda"),
+                     torch.full((1,), -100, dtype=torch.int32, device="cuda")))
+    for _ in range(a.reps):
+        for q, (c, e, nd, co, st) in zip(qs, bufs):
+            opt.optimize_device(q.n, len(q.edges), c, e, nd, co, st)
+    torch.cuda.synchronize()
+    bad = [int(b[4].item()) for b in bufs if int(b[4].item()) != 0]
+    opt.close()
+    print(f"{a.kind}-{a.n} x{a.queries} reps={a.reps} status={'ok' if not bad else bad}")
+    return 0 if not bad else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -197,9 +197,10 @@ static int ensure_workspace(mpdp_ctx* ctx, int n, int memo_kind)
     if (ctx->ws_block && ctx->ws.n_cap >= n && (!need_dense || ctx->ws_dense) &&
         (!need_hash || ctx->ws_hash))
         return MPDP_OK;
+    // keep the capacity reached so far, but only the memo kind asked for now
     const int new_n = n > ctx->ws.n_cap ? n : ctx->ws.n_cap;
-    const bool dense = ctx->ws_dense || need_dense;
-    const bool hash = ctx->ws_hash || need_hash;
+    const bool dense = need_dense;
+    const bool hash = need_hash;
     const size_t bytes = workspace_bytes(new_n, dense, hash);
     if (bytes > ctx->budget) return MPDP_ERR_ADMISSION;
     CK(ctx, cudaStreamSynchronize(ctx->stream));
