@@ -166,8 +166,10 @@ size_t mpdp_workspace_bytes(int32_t n_rels, const mpdp_config *cfg);
  * stream and return a handle at once (asynchronous).  Exact mode: n <= 30. */
 int mpdp_optimize(mpdp_ctx *ctx, const mpdp_query *q, int64_t *handle);
 
-/* Enqueue nq queries; handles[i] receives each one's handle.  Returns the
- * first error; queries before it stay enqueued. */
+/* Enqueue nq queries as device batches (all queries of a batch share every
+ * kernel launch; a batch is split only when it would exceed the memo budget
+ * or 1024 queries); handles[i] receives each one's handle.  The whole call is
+ * validated first: on an error nothing is enqueued. */
 int mpdp_optimize_batch(mpdp_ctx *ctx, const mpdp_query *qs, int32_t nq, int64_t *handles);
 
 /* Block until the handle's optimization is done and copy out its plan.
@@ -179,18 +181,34 @@ int mpdp_get_plan(mpdp_ctx *ctx, int64_t handle, mpdp_plan_node *nodes, int32_t 
 /* Forget a handle (its host result buffer is reused). */
 int mpdp_release(mpdp_ctx *ctx, int64_t handle);
 
-/* Device-resident form: inputs and outputs are device pointers, everything is
- * enqueued on the context's stream and nothing waits for the device.
- *   d_card [n_rels] doubles, d_edges [n_edges] mpdp_edge (validated on device);
- *   d_nodes [>= 2n-1] plan nodes, d_cost one double, d_status one int32
- *   receiving 0 or an MPDP_ERR_* code once the work has run.
- * Returns MPDP_OK when the work was enqueued. */
+/* Plan nodes reserved per query in the device-path output arrays. */
+#define MPDP_PLAN_STRIDE 63
+
+/* Device-resident batch: the nq queries' inputs and outputs are device
+ * pointers; everything is enqueued on the context's stream as one device
+ * batch (shared launches) and nothing waits for the device.
+ *   n_rels[nq], n_edges[nq]: HOST arrays of the queries' sizes (they size the
+ *     launches; exact mode needs n <= 30);
+ *   d_card: device, the queries' cardinalities back to back (sum of n_rels);
+ *   d_edges: device, the queries' edges back to back (sum of n_edges);
+ *     contents are validated on the device;
+ *   d_nodes: device, nq * MPDP_PLAN_STRIDE plan nodes (query i at
+ *     i * MPDP_PLAN_STRIDE); d_cost: nq doubles; d_status: nq int32 receiving
+ *     0 or an MPDP_ERR_* code once the work has run.
+ * Returns MPDP_OK when the work was enqueued, MPDP_ERR_ADMISSION when the
+ * batch does not fit the memo budget, MPDP_ERR_TOO_LARGE for nq > 1024. */
+int mpdp_optimize_batch_device(mpdp_ctx *ctx, int32_t nq, const int32_t *n_rels,
+                               const int32_t *n_edges, const double *d_card,
+                               const mpdp_edge *d_edges, int32_t cost_model,
+                               mpdp_plan_node *d_nodes, double *d_cost, int32_t *d_status);
+
+/* Device-resident form of one query (a batch of one). */
 int mpdp_optimize_device(mpdp_ctx *ctx, int32_t n_rels, int32_t n_edges, const double *d_card,
                          const mpdp_edge *d_edges, int32_t cost_model, mpdp_plan_node *d_nodes,
                          double *d_cost, int32_t *d_status);
 
-/* Wait for all work of the context; returns the first device-reported error
- * of work enqueued since the previous call, or MPDP_OK. */
+/* Wait for all work enqueued on the context's stream.  Device-reported
+ * errors are delivered per query (mpdp_get_plan, or the d_status outputs). */
 int mpdp_sync(mpdp_ctx *ctx);
 
 /* Read memo entries of the most recent exact optimization of the context

@@ -1,19 +1,21 @@
-// C ABI of the MPDP optimizer: contexts, handles, workspace, CUDA graphs.
+// C ABI of the MPDP optimizer: contexts, batches, handles, workspace, graphs.
 //
-// One exact optimization (Algorithm "MPDP on GPU", Sec. 5) is enqueued as:
-//   host -> device copy of the staged query (host path) or a gather kernel
-//   (device path); the DP pipeline (replayed from a CUDA graph captured once
-//   per shape); a device -> host copy of plan + counters (host path) or a
-//   publish kernel (device path).  Nothing in between waits for the host:
-//   the paper's per-level host round trip (Sec. 6.2, small queries) is gone.
+// Queries are optimized in device batches.  One batch is enqueued as:
+//   host -> device copy of the batch descriptors (and, on the host path, of
+//   the staged queries) or a gather kernel (device path); the DP pipeline,
+//   replayed from a CUDA graph captured once per batch shape; a device ->
+//   host copy of every query's plan + counters (host path) or a publish
+//   kernel (device path).  Nothing in between waits for the host: the
+//   paper's per-level host round trip (Sec. 6.2, small queries) is gone, and
+//   all queries of a batch share every launch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <string>
-#include <tuple>
 #include <vector>
 
 #include "../../include/mpdp.h"
@@ -23,15 +25,41 @@ using namespace mpdp;
 
 namespace {
 
-struct HandleSlot {
-    bool used = false;
-    int64_t handle = -1;
-    HostResult* host = nullptr;  // pinned
+const mpdp_config kDefaultConfig = {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 1, 32};
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int edges_max(int n) { return n * (n - 1) / 2; }
+
+// One submitted device batch and its pinned results.
+struct Record {
+    bool in_use = false;
+    int nq = 0;
+    int cap = 0;
+    int refs = 0;
+    unsigned long long seq = 0;
+    DevOut* host = nullptr;  // pinned, cap entries (same layout as DevOut)
     cudaEvent_t done = nullptr, t0 = nullptr, t1 = nullptr;
-    int n = 0;
-    int enumeration = 0;
     int memo_kind = 0;
-    uint64_t h2d_bytes = 0;
+    std::vector<int> n, enumeration;
+    std::vector<unsigned long long> h2d;
+};
+
+struct HandleRef {
+    int rec;
+    int idx;
+};
+
+// Pinned staging for one batch upload.
+struct StageSlot {
+    char* host = nullptr;
+    size_t cap = 0;
+    cudaEvent_t free_ev = nullptr;  // the copies out of this slot have run
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
 };
 
 // Profiling mode: a pair of events around every launch, summed per class.
@@ -69,23 +97,13 @@ struct EventHook : LaunchHook {
     }
 };
 
-struct DevOut {  // device twin of HostResult: one copy reads both back
-    DevResult result;
-    DevCounters counters;
+// Query as the host planner sees it.
+struct PlanQuery {
+    int n, m, enumeration;
+    const double* card;        // host path
+    const mpdp_edge* edges;    // host path
+    unsigned long long card_off, edge_off;  // device path
 };
-
-using GraphKey = std::tuple<int, int, int, int, int, int>;
-
-struct GraphEntry {
-    cudaGraphExec_t exec = nullptr;
-    int launches = 0;
-};
-
-const mpdp_config kDefaultConfig = {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 1, 32};
-
-size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
-
-int edges_max(int n) { return n * (n - 1) / 2; }
 
 }  // namespace
 
@@ -96,35 +114,46 @@ struct mpdp_ctx {
     size_t budget = 0;
     mpdp_config cfg = kDefaultConfig;
     int num_sms = 152;
-    Workspace ws;
-    DevOut* out = nullptr;
-    void* ws_block = nullptr;  // one allocation for all workspace buffers
-    size_t ws_bytes = 0;
-    bool ws_dense = false, ws_hash = false;
-    // ring of pinned staging buffers: the host can stage queries ahead of
-    // the device; each buffer's event marks its host->device copy as done
-    static constexpr int kStageRing = 32;
-    StagedQuery* h_staged = nullptr;  // pinned, kStageRing entries
-    cudaEvent_t staged_free[kStageRing] = {};
-    int stage_next = 0;
-    std::map<GraphKey, GraphEntry> graphs;
-    std::vector<HandleSlot> slots;
+    // fixed device part (kMaxBatch queries)
+    void* fixed = nullptr;
+    QDesc* d_desc = nullptr;
+    uint32_t* d_prefix = nullptr;
+    StagedQuery* d_staged = nullptr;
+    DevQuery* d_query = nullptr;
+    DevOut* d_out = nullptr;
+    HashLayout* d_layout = nullptr;
+    // variable device part
+    void* var = nullptr;
+    size_t var_bytes = 0;
+    size_t list_words = 0, memo_entries = 0, arena_slots = 0;
+    uint32_t* d_lists = nullptr;
+    uint32_t* d_heavy = nullptr;
+    double2* d_memo = nullptr;
+    uint32_t* d_left = nullptr;
+    HashSlot* d_arena = nullptr;
+    // host side
+    static constexpr int kRing = 4;
+    StageSlot ring[kRing];
+    int ring_next = 0;
+    std::vector<Record> recs;
+    std::map<int64_t, HandleRef> handles;
     int64_t next_handle = 1;
-    int64_t last_exact_handle = -1;
-    int last_memo_kind = MPDP_MEMO_DENSE;
+    unsigned long long seq = 0;
+    unsigned long long last_seq = 0;  // seq of the batch whose memo is in the workspace
+    std::map<std::vector<int>, GraphEntry> graphs;
     int last_launches = 0;
     bool profiling = false;
     EventHook hook;
     std::string last_error;
 };
 
-#define CK(ctx, call)                                                       \
-    do {                                                                    \
-        cudaError_t e__ = (call);                                           \
-        if (e__ != cudaSuccess) {                                           \
+#define CK(ctx, call)                                                                \
+    do {                                                                             \
+        cudaError_t e__ = (call);                                                    \
+        if (e__ != cudaSuccess) {                                                    \
             (ctx)->last_error = std::string(#call) + ": " + cudaGetErrorString(e__); \
-            return MPDP_ERR_CUDA;                                           \
-        }                                                                   \
+            return MPDP_ERR_CUDA;                                                    \
+        }                                                                            \
     } while (0)
 
 static bool finite_pos(double x) { return x > 0.0 && x <= 1.7976931348623157e308; }
@@ -141,8 +170,8 @@ static int validate_query(const mpdp_query* q, int max_n)
     if (!q->card || (m > 0 && !q->edges)) return MPDP_ERR_INVALID_ARG;
     for (int i = 0; i < n; i++)
         if (!finite_pos(q->card[i])) return MPDP_ERR_INVALID_ARG;
-    std::vector<uint64_t> adj((size_t)n * ((n + 63) / 64), 0);
     const int words = (n + 63) / 64;
+    std::vector<uint64_t> adj((size_t)n * words, 0);
     std::vector<int> parent(n);
     for (int i = 0; i < n; i++) parent[i] = i;
     auto find = [&](int x) {
@@ -169,17 +198,38 @@ static int validate_query(const mpdp_query* q, int max_n)
     return MPDP_OK;
 }
 
-static size_t workspace_bytes(int n, bool dense, bool hash)
+static int resolve_enumeration(const mpdp_config& cfg, int n, int m)
 {
-    size_t b = align_up(sizeof(StagedQuery)) + align_up(sizeof(DevQuery)) + align_up(sizeof(DevOut));
-    const size_t le = list_entries(n);
-    b += 2 * align_up(le * sizeof(uint32_t));
-    if (dense) {
-        const size_t full = (size_t)1 << n;
-        b += align_up(full * sizeof(double)) + align_up(full * sizeof(uint32_t));
-    }
-    if (hash) b += align_up(hash_arena_slots(n) * sizeof(HashSlot)) + align_up(sizeof(HashLayout));
-    return b;
+    if (cfg.enumeration == MPDP_ENUM_TREE || cfg.enumeration == MPDP_ENUM_BLOCKS) return cfg.enumeration;
+    return (m == n - 1) ? MPDP_ENUM_TREE : MPDP_ENUM_BLOCKS;
+}
+
+// Variable workspace of one query: list words, heavy words, dense entries, hash slots.
+struct QuerySize {
+    size_t lists = 0, heavy = 0, memo = 0, hash = 0;
+};
+
+static QuerySize query_size(int n, int enumeration, int memo_kind)
+{
+    QuerySize z;
+    z.lists = list_entries(n);
+    z.heavy = enumeration == MPDP_ENUM_BLOCKS ? z.lists : 0;
+    if (memo_kind == MPDP_MEMO_DENSE) z.memo = (size_t)1 << n;
+    else z.hash = hash_arena_slots(n);
+    return z;
+}
+
+static size_t var_bytes_of(size_t lists, size_t heavy, size_t memo, size_t hash)
+{
+    return align_up(lists * 4) + align_up(heavy * 4) + align_up(memo * sizeof(double2)) +
+           align_up(memo * sizeof(uint32_t)) + align_up(hash * sizeof(HashSlot));
+}
+
+static size_t fixed_bytes()
+{
+    return align_up(sizeof(QDesc) * kMaxBatch) + align_up(sizeof(uint32_t) * (kMaxBatch + 1)) +
+           align_up(sizeof(StagedQuery) * kMaxBatch) + align_up(sizeof(DevQuery) * kMaxBatch) +
+           align_up(sizeof(DevOut) * kMaxBatch) + align_up(sizeof(HashLayout) * kMaxBatch);
 }
 
 static void destroy_graphs(mpdp_ctx* ctx)
@@ -189,104 +239,211 @@ static void destroy_graphs(mpdp_ctx* ctx)
     ctx->graphs.clear();
 }
 
-// Make sure the workspace holds n relations with the memo kind requested.
-static int ensure_workspace(mpdp_ctx* ctx, int n, int memo_kind)
+static int ensure_fixed(mpdp_ctx* ctx)
 {
-    const bool need_dense = memo_kind == MPDP_MEMO_DENSE;
-    const bool need_hash = memo_kind == MPDP_MEMO_HASH;
-    if (ctx->ws_block && ctx->ws.n_cap >= n && (!need_dense || ctx->ws_dense) &&
-        (!need_hash || ctx->ws_hash))
-        return MPDP_OK;
-    // keep the capacity reached so far, but only the memo kind asked for now
-    const int new_n = n > ctx->ws.n_cap ? n : ctx->ws.n_cap;
-    const bool dense = need_dense;
-    const bool hash = need_hash;
-    const size_t bytes = workspace_bytes(new_n, dense, hash);
-    if (bytes > ctx->budget) return MPDP_ERR_ADMISSION;
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
-    destroy_graphs(ctx);
-    if (ctx->ws_block) cudaFree(ctx->ws_block);
-    ctx->ws_block = nullptr;
-    ctx->ws = Workspace();
+    if (ctx->fixed) return MPDP_OK;
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) {
+    if (cudaMalloc(&p, fixed_bytes()) != cudaSuccess) {
         cudaGetLastError();
-        ctx->last_error = std::string("cudaMalloc workspace: ") + cudaGetErrorString(e);
-        ctx->ws_dense = ctx->ws_hash = false;
         return MPDP_ERR_OOM;
     }
-    ctx->ws_block = p;
-    ctx->ws_bytes = bytes;
+    ctx->fixed = p;
     char* c = static_cast<char*>(p);
     auto take = [&](size_t sz) {
         char* r = c;
         c += align_up(sz);
         return r;
     };
-    Workspace& ws = ctx->ws;
-    ws.n_cap = new_n;
-    ws.staged = reinterpret_cast<StagedQuery*>(take(sizeof(StagedQuery)));
-    ws.query = reinterpret_cast<DevQuery*>(take(sizeof(DevQuery)));
-    ctx->out = reinterpret_cast<DevOut*>(take(sizeof(DevOut)));
-    ws.result = &ctx->out->result;
-    ws.counters = &ctx->out->counters;
-    const size_t le = list_entries(new_n);
-    ws.lists = reinterpret_cast<uint32_t*>(take(le * sizeof(uint32_t)));
-    ws.heavy = reinterpret_cast<uint32_t*>(take(le * sizeof(uint32_t)));
-    if (dense) {
-        const size_t full = (size_t)1 << new_n;
-        ws.dcost = reinterpret_cast<double*>(take(full * sizeof(double)));
-        ws.dleft = reinterpret_cast<uint32_t*>(take(full * sizeof(uint32_t)));
-    }
-    if (hash) {
-        ws.arena_slots = hash_arena_slots(new_n);
-        ws.arena = reinterpret_cast<HashSlot*>(take(ws.arena_slots * sizeof(HashSlot)));
-        ws.layout = reinterpret_cast<HashLayout*>(take(sizeof(HashLayout)));
-    }
-    ctx->ws_dense = dense;
-    ctx->ws_hash = hash;
-    ctx->last_exact_handle = -1;
-    // start from zeroed counters and result
-    CK(ctx, cudaMemsetAsync(ctx->out, 0, sizeof(DevOut), ctx->stream));
+    ctx->d_desc = reinterpret_cast<QDesc*>(take(sizeof(QDesc) * kMaxBatch));
+    ctx->d_prefix = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (kMaxBatch + 1)));
+    ctx->d_staged = reinterpret_cast<StagedQuery*>(take(sizeof(StagedQuery) * kMaxBatch));
+    ctx->d_query = reinterpret_cast<DevQuery*>(take(sizeof(DevQuery) * kMaxBatch));
+    ctx->d_out = reinterpret_cast<DevOut*>(take(sizeof(DevOut) * kMaxBatch));
+    ctx->d_layout = reinterpret_cast<HashLayout*>(take(sizeof(HashLayout) * kMaxBatch));
+    CK(ctx, cudaMemsetAsync(ctx->d_out, 0, sizeof(DevOut) * kMaxBatch, ctx->stream));
     return MPDP_OK;
 }
 
-static PipelineCfg pipeline_cfg(const mpdp_ctx* ctx, int n, int enumeration)
+// Grow the variable workspace to hold at least the given sizes.
+static int ensure_var(mpdp_ctx* ctx, size_t lists, size_t heavy, size_t memo, size_t hash)
 {
-    PipelineCfg pc;
-    pc.n = n;
-    pc.enumeration = enumeration;
-    pc.memo_kind = ctx->cfg.memo_kind;
-    pc.heavy_threshold = ctx->cfg.heavy_threshold;
-    pc.use_ccc = ctx->cfg.use_ccc;
-    pc.run_length = ctx->cfg.run_length;
-    pc.num_sms = ctx->num_sms;
-    pc.blocks_per_sm = 4;
-    return pc;
+    const size_t lw = std::max(lists, heavy);
+    if (ctx->var && lw <= ctx->list_words && memo <= ctx->memo_entries && hash <= ctx->arena_slots)
+        return MPDP_OK;
+    // grow every part to at least what it had, so alternating shapes do not thrash
+    size_t L = std::max(lw, ctx->list_words), M = std::max(memo, ctx->memo_entries),
+           H = std::max(hash, ctx->arena_slots);
+    if (var_bytes_of(L, L, M, H) + fixed_bytes() > ctx->budget) {
+        L = lw;  // only what this batch needs
+        M = memo;
+        H = hash;
+        if (var_bytes_of(L, L, M, H) + fixed_bytes() > ctx->budget) return MPDP_ERR_ADMISSION;
+    }
+    const size_t bytes = var_bytes_of(L, L, M, H);
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    destroy_graphs(ctx);
+    if (ctx->var) cudaFree(ctx->var);
+    ctx->var = nullptr;
+    ctx->list_words = ctx->memo_entries = ctx->arena_slots = 0;
+    ctx->last_seq = 0;
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->last_error = "cudaMalloc of the batch workspace failed";
+        return MPDP_ERR_OOM;
+    }
+    ctx->var = p;
+    ctx->var_bytes = bytes;
+    char* c = static_cast<char*>(p);
+    auto take = [&](size_t sz) {
+        char* r = c;
+        c += align_up(sz);
+        return r;
+    };
+    ctx->d_lists = reinterpret_cast<uint32_t*>(take(L * 4));
+    ctx->d_heavy = reinterpret_cast<uint32_t*>(take(L * 4));
+    ctx->d_memo = reinterpret_cast<double2*>(take(M * sizeof(double2)));
+    ctx->d_left = reinterpret_cast<uint32_t*>(take(M * sizeof(uint32_t)));
+    ctx->d_arena = reinterpret_cast<HashSlot*>(take(H * sizeof(HashSlot)));
+    ctx->list_words = L;
+    ctx->memo_entries = M;
+    ctx->arena_slots = H;
+    return MPDP_OK;
 }
 
-// Enqueue the DP pipeline on the work stream: graph replay or direct launches.
-static int run_pipeline(mpdp_ctx* ctx, int n, int enumeration, int* launches)
+static BatchArgs batch_args(const mpdp_ctx* ctx, int nq, int max_n)
 {
-    const PipelineCfg pc = pipeline_cfg(ctx, n, enumeration);
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nq = nq;
+    a.max_n = max_n;
+    a.desc = ctx->d_desc;
+    a.filter_block_prefix = ctx->d_prefix;
+    a.staged = ctx->d_staged;
+    a.query = ctx->d_query;
+    a.out = ctx->d_out;
+    a.lists = ctx->d_lists;
+    a.heavy = ctx->d_heavy;
+    a.memo = ctx->d_memo;
+    a.left = ctx->d_left;
+    a.arena = ctx->d_arena;
+    a.layout = ctx->d_layout;
+    a.arena_slots = ctx->arena_slots;
+    a.run = ctx->cfg.run_length;
+    a.heavy_threshold = ctx->cfg.heavy_threshold;
+    a.use_ccc = ctx->cfg.use_ccc;
+    return a;
+}
+
+// Split [0, count) into consecutive sub-batches that fit the budget.
+static int split_batches(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, std::vector<std::pair<int, int>>& out)
+{
+    const int kind = ctx->cfg.memo_kind;
+    size_t L = 0, H = 0, M = 0, A = 0;
+    int start = 0;
+    for (int i = 0; i < (int)qs.size(); i++) {
+        const QuerySize z = query_size(qs[i].n, qs[i].enumeration, kind);
+        if (var_bytes_of(z.lists, z.heavy, z.memo, z.hash) + fixed_bytes() > ctx->budget)
+            return MPDP_ERR_ADMISSION;
+        const bool full = (i - start) >= kMaxBatch;
+        const size_t lw = std::max(L + z.lists, H + z.heavy);
+        const size_t need = var_bytes_of(lw, lw, M + z.memo, A + z.hash) + fixed_bytes();
+        if (i > start && (full || need > ctx->budget)) {
+            out.emplace_back(start, i);
+            start = i;
+            L = H = M = A = 0;
+        }
+        L += z.lists;
+        H += z.heavy;
+        M += z.memo;
+        A += z.hash;
+    }
+    if (start < (int)qs.size()) out.emplace_back(start, (int)qs.size());
+    return MPDP_OK;
+}
+
+static int acquire_record(mpdp_ctx* ctx, int nq)
+{
+    int best = -1;
+    for (int i = 0; i < (int)ctx->recs.size(); i++)
+        if (!ctx->recs[i].in_use && ctx->recs[i].cap >= nq) {
+            best = i;
+            break;
+        }
+    if (best < 0) {
+        for (int i = 0; i < (int)ctx->recs.size(); i++)
+            if (!ctx->recs[i].in_use) {
+                best = i;
+                break;
+            }
+        if (best < 0) {
+            ctx->recs.emplace_back();
+            best = (int)ctx->recs.size() - 1;
+        }
+    }
+    Record& r = ctx->recs[best];
+    if (r.cap < nq) {
+        if (r.host) cudaFreeHost(r.host);
+        r.host = nullptr;
+        r.cap = 0;
+        if (cudaMallocHost(reinterpret_cast<void**>(&r.host), sizeof(DevOut) * nq) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        r.cap = nq;
+    }
+    if (!r.done) {
+        if (cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreate(&r.t0) != cudaSuccess || cudaEventCreate(&r.t1) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+    }
+    r.in_use = true;
+    r.nq = nq;
+    r.refs = 0;
+    return best;
+}
+
+// Next staging slot with room for `bytes`, once its previous copies have run.
+static int acquire_stage(mpdp_ctx* ctx, size_t bytes, char** host, int* slot)
+{
+    const int i = ctx->ring_next;
+    ctx->ring_next = (i + 1) % mpdp_ctx::kRing;
+    StageSlot& s = ctx->ring[i];
+    CK(ctx, cudaEventSynchronize(s.free_ev));
+    if (s.cap < bytes) {
+        if (s.host) cudaFreeHost(s.host);
+        s.host = nullptr;
+        s.cap = 0;
+        CK(ctx, cudaMallocHost(reinterpret_cast<void**>(&s.host), bytes));
+        s.cap = bytes;
+    }
+    *host = s.host;
+    *slot = i;
+    return MPDP_OK;
+}
+
+// Enqueue the DP pipeline of a planned batch: graph replay or direct launches.
+static int run_pipeline(mpdp_ctx* ctx, const BatchArgs& a, const BatchPlan& bp, const std::vector<int>& key,
+                        int* launches)
+{
     if (ctx->profiling || !ctx->cfg.use_graphs) {
-        CK(ctx, enqueue_pipeline(ctx->ws, pc, ctx->stream, launches,
+        CK(ctx, enqueue_pipeline(a, bp, ctx->cfg.memo_kind, ctx->stream, launches,
                                  ctx->profiling ? &ctx->hook : nullptr));
         return MPDP_OK;
     }
-    const GraphKey key(n, enumeration, pc.memo_kind, pc.heavy_threshold, pc.use_ccc, pc.run_length);
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
+        if (ctx->graphs.size() >= 256) destroy_graphs(ctx);
         GraphEntry g;
         cudaGraph_t graph = nullptr;
         CK(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = enqueue_pipeline(ctx->ws, pc, ctx->capture_stream, &g.launches);
+        cudaError_t e = enqueue_pipeline(a, bp, ctx->cfg.memo_kind, ctx->capture_stream, &g.launches);
         cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
-            ctx->last_error = std::string("graph capture: ") +
-                              cudaGetErrorString(e != cudaSuccess ? e : e2);
+            ctx->last_error = std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
             return MPDP_ERR_CUDA;
         }
         e = cudaGraphInstantiate(&g.exec, graph, 0);
@@ -302,35 +459,139 @@ static int run_pipeline(mpdp_ctx* ctx, int n, int enumeration, int* launches)
     return MPDP_OK;
 }
 
-static int resolve_enumeration(const mpdp_ctx* ctx, int n, int m)
+// Plan, upload and enqueue one device batch.  host_path: queries come from
+// host arrays (staged + copied); otherwise from caller device arrays.
+static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool host_path, const double* d_card,
+                        const mpdp_edge* d_edges, int* record_out, mpdp_plan_node* d_nodes, double* d_cost,
+                        int32_t* d_status)
 {
-    if (ctx->cfg.enumeration == MPDP_ENUM_TREE || ctx->cfg.enumeration == MPDP_ENUM_BLOCKS)
-        return ctx->cfg.enumeration;
-    return (m == n - 1) ? MPDP_ENUM_TREE : MPDP_ENUM_BLOCKS;
-}
-
-static int acquire_slot(mpdp_ctx* ctx, HandleSlot** out)
-{
-    for (auto& s : ctx->slots)
-        if (!s.used) {
-            *out = &s;
-            return MPDP_OK;
+    const int nq = (int)qs.size();
+    const int kind = ctx->cfg.memo_kind;
+    int rc = ensure_fixed(ctx);
+    if (rc != MPDP_OK) return rc;
+    size_t L = 0, H = 0, M = 0, A = 0;
+    for (const auto& q : qs) {
+        const QuerySize z = query_size(q.n, q.enumeration, kind);
+        L += z.lists;
+        H += z.heavy;
+        M += z.memo;
+        A += z.hash;
+    }
+    rc = ensure_var(ctx, L, H, M, A);
+    if (rc != MPDP_OK) return rc;
+    const size_t desc_bytes = sizeof(QDesc) * nq, pref_bytes = sizeof(uint32_t) * (nq + 1);
+    const size_t staged_off = align_up(desc_bytes) + align_up(pref_bytes);
+    const size_t stage_bytes = staged_off + (host_path ? sizeof(StagedQuery) * nq : 0);
+    char* h = nullptr;
+    int slot = 0;
+    rc = acquire_stage(ctx, stage_bytes, &h, &slot);
+    if (rc != MPDP_OK) return rc;
+    QDesc* hd = reinterpret_cast<QDesc*>(h);
+    uint32_t* hp = reinterpret_cast<uint32_t*>(h + align_up(desc_bytes));
+    StagedQuery* hs = reinterpret_cast<StagedQuery*>(h + staged_off);
+    BatchPlan bp;
+    bp.num_sms = ctx->num_sms;
+    std::vector<int> key = {nq, kind, ctx->cfg.heavy_threshold, ctx->cfg.use_ccc, ctx->cfg.run_length};
+    unsigned long long lbase = 0, mbase = 0;
+    uint32_t fblocks = 0;
+    int max_n = 0;
+    std::vector<unsigned long long> h2d(nq, 0);
+    for (int i = 0; i < nq; i++) {
+        const PlanQuery& q = qs[i];
+        QDesc& d = hd[i];
+        memset(&d, 0, sizeof(d));
+        d.n = q.n;
+        d.n_edges = q.m;
+        d.enumeration = q.enumeration;
+        d.cost_model = MPDP_COST_COUT;
+        d.memo_base = mbase;
+        d.list_base = lbase;
+        d.card_off = q.card_off;
+        d.edge_off = q.edge_off;
+        uint32_t qb = 0;
+        fill_levels(d, ctx->cfg.run_length, qb);
+        d.filter_block_base = fblocks;
+        hp[i] = fblocks;
+        fblocks += qb;
+        const QuerySize z = query_size(q.n, q.enumeration, kind);
+        lbase += z.lists;
+        mbase += z.memo;
+        if (q.n > max_n) max_n = q.n;
+        for (int k = 2; k <= q.n; k++) {
+            const unsigned long long c = binom_host(q.n, k);
+            if (q.enumeration == MPDP_ENUM_TREE) {
+                bp.tree_tiles[k] += (c + kEvalThreads - 1) / kEvalThreads;
+            } else {
+                bp.block_tiles[k] += (c + kEvalThreads - 1) / kEvalThreads;
+                bp.block_sets[k] += c;
+            }
         }
-    HandleSlot s;
-    CK(ctx, cudaMallocHost(reinterpret_cast<void**>(&s.host), sizeof(HostResult)));
-    CK(ctx, cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
-    CK(ctx, cudaEventCreate(&s.t0));
-    CK(ctx, cudaEventCreate(&s.t1));
-    ctx->slots.push_back(s);
-    *out = &ctx->slots.back();
+        key.push_back(q.n);
+        key.push_back(q.enumeration);
+        if (host_path) {
+            StagedQuery& sq = hs[i];
+            sq.n = q.n;
+            sq.n_edges = q.m;
+            sq.cost_model = MPDP_COST_COUT;
+            sq.pad = 0;
+            for (int r = 0; r < kMaxRels; r++) sq.card[r] = r < q.n ? q.card[r] : 1.0;
+            for (int e = 0; e < q.m; e++) sq.edges[e] = q.edges[e];
+        }
+    }
+    hp[nq] = fblocks;
+    bp.filter_blocks = fblocks;
+    CK(ctx, cudaMemcpyAsync(ctx->d_desc, hd, desc_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->d_prefix, hp, pref_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    if (host_path) {
+        for (int i = 0; i < nq; i++) {
+            const size_t bytes = offsetof(StagedQuery, edges) + (size_t)qs[i].m * sizeof(mpdp_edge);
+            h2d[i] = bytes;
+            CK(ctx, cudaMemcpyAsync(ctx->d_staged + i, hs + i, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        }
+    }
+    CK(ctx, cudaEventRecord(ctx->ring[slot].free_ev, ctx->stream));
+    const BatchArgs a = batch_args(ctx, nq, max_n);
+    LaunchHook* hook = ctx->profiling ? &ctx->hook : nullptr;
+    int launches = 0;
+    if (!host_path) {
+        CK(ctx, enqueue_stage_device(a, d_card, d_edges, ctx->stream, hook));
+        launches++;
+    }
+    int ri = -1;
+    if (host_path) {
+        ri = acquire_record(ctx, nq);
+        if (ri < 0) return MPDP_ERR_CUDA;
+        CK(ctx, cudaEventRecord(ctx->recs[ri].t0, ctx->stream));
+    }
+    int pl = 0;
+    rc = run_pipeline(ctx, a, bp, key, &pl);
+    if (rc != MPDP_OK) {
+        if (ri >= 0) ctx->recs[ri].in_use = false;
+        return rc;
+    }
+    launches += pl;
+    ctx->last_seq = ++ctx->seq;
+    if (host_path) {
+        Record& r = ctx->recs[ri];
+        CK(ctx, cudaEventRecord(r.t1, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(r.host, ctx->d_out, sizeof(DevOut) * nq, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaEventRecord(r.done, ctx->stream));
+        r.seq = ctx->seq;
+        r.memo_kind = kind;
+        r.n.resize(nq);
+        r.enumeration.resize(nq);
+        r.h2d = h2d;
+        for (int i = 0; i < nq; i++) {
+            r.n[i] = qs[i].n;
+            r.enumeration[i] = qs[i].enumeration;
+        }
+    } else {
+        CK(ctx, enqueue_publish(a, d_nodes, d_cost, d_status, ctx->stream, hook));
+        launches++;
+    }
+    ctx->last_launches = launches;
+    if (record_out) *record_out = ri;
     return MPDP_OK;
-}
-
-static HandleSlot* find_slot(mpdp_ctx* ctx, int64_t handle)
-{
-    for (auto& s : ctx->slots)
-        if (s.used && s.handle == handle) return &s;
-    return nullptr;
 }
 
 extern "C" {
@@ -366,7 +627,9 @@ size_t mpdp_workspace_bytes(int32_t n_rels, const mpdp_config* cfg)
 {
     if (n_rels < 1 || n_rels > MPDP_MAX_EXACT_RELS) return 0;
     const int kind = cfg ? cfg->memo_kind : MPDP_MEMO_DENSE;
-    return workspace_bytes(n_rels, kind == MPDP_MEMO_DENSE, kind == MPDP_MEMO_HASH);
+    const int en = cfg && cfg->enumeration == MPDP_ENUM_BLOCKS ? MPDP_ENUM_BLOCKS : MPDP_ENUM_TREE;
+    const QuerySize z = query_size(n_rels, en, kind);
+    return var_bytes_of(z.lists, z.heavy, z.memo, z.hash) + fixed_bytes();
 }
 
 int mpdp_create(mpdp_ctx** out, int device, size_t memo_budget_bytes, void* cuda_stream)
@@ -382,21 +645,15 @@ int mpdp_create(mpdp_ctx** out, int device, size_t memo_budget_bytes, void* cuda
     ctx->device = device;
     ctx->budget = memo_budget_bytes ? memo_budget_bytes : ((size_t)64 << 30);
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
-    if (cudaSetDevice(device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMallocHost(reinterpret_cast<void**>(&ctx->h_staged),
-                       sizeof(StagedQuery) * mpdp_ctx::kStageRing) != cudaSuccess) {
+    bool ok = cudaSetDevice(device) == cudaSuccess &&
+              cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < mpdp_ctx::kRing; i++)
+        ok = cudaEventCreateWithFlags(&ctx->ring[i].free_ev, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
         cudaGetLastError();
         mpdp_destroy(ctx);
         return MPDP_ERR_CUDA;
-    }
-    for (int i = 0; i < mpdp_ctx::kStageRing; i++) {
-        if (cudaEventCreateWithFlags(&ctx->staged_free[i], cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            mpdp_destroy(ctx);
-            return MPDP_ERR_CUDA;
-        }
     }
     *out = ctx;
     return MPDP_OK;
@@ -408,16 +665,18 @@ void mpdp_destroy(mpdp_ctx* ctx)
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     destroy_graphs(ctx);
-    for (auto& s : ctx->slots) {
-        if (s.host) cudaFreeHost(s.host);
-        if (s.done) cudaEventDestroy(s.done);
-        if (s.t0) cudaEventDestroy(s.t0);
-        if (s.t1) cudaEventDestroy(s.t1);
+    for (auto& r : ctx->recs) {
+        if (r.host) cudaFreeHost(r.host);
+        if (r.done) cudaEventDestroy(r.done);
+        if (r.t0) cudaEventDestroy(r.t0);
+        if (r.t1) cudaEventDestroy(r.t1);
     }
-    if (ctx->ws_block) cudaFree(ctx->ws_block);
-    if (ctx->h_staged) cudaFreeHost(ctx->h_staged);
-    for (int i = 0; i < mpdp_ctx::kStageRing; i++)
-        if (ctx->staged_free[i]) cudaEventDestroy(ctx->staged_free[i]);
+    for (int i = 0; i < mpdp_ctx::kRing; i++) {
+        if (ctx->ring[i].host) cudaFreeHost(ctx->ring[i].host);
+        if (ctx->ring[i].free_ev) cudaEventDestroy(ctx->ring[i].free_ev);
+    }
+    if (ctx->var) cudaFree(ctx->var);
+    if (ctx->fixed) cudaFree(ctx->fixed);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     cudaGetLastError();
     delete ctx;
@@ -440,76 +699,54 @@ int mpdp_get_config(const mpdp_ctx* ctx, mpdp_config* cfg)
     return MPDP_OK;
 }
 
-int mpdp_optimize(mpdp_ctx* ctx, const mpdp_query* q, int64_t* handle)
+int mpdp_optimize_batch(mpdp_ctx* ctx, const mpdp_query* qs, int32_t nq, int64_t* handles)
 {
-    if (!ctx || !q || !handle) return MPDP_ERR_INVALID_ARG;
-    *handle = -1;
-    if (q->mode != MPDP_MODE_EXACT) return MPDP_ERR_NOT_IMPLEMENTED;
-    int rc = validate_query(q, MPDP_MAX_EXACT_RELS);
-    if (rc != MPDP_OK) return rc;
+    if (!ctx || nq < 0 || (nq > 0 && (!qs || !handles))) return MPDP_ERR_INVALID_ARG;
+    for (int i = 0; i < nq; i++) handles[i] = -1;
+    std::vector<PlanQuery> pq(nq);
+    for (int i = 0; i < nq; i++) {
+        if (qs[i].mode != MPDP_MODE_EXACT) return MPDP_ERR_NOT_IMPLEMENTED;
+        const int rc = validate_query(&qs[i], MPDP_MAX_EXACT_RELS);
+        if (rc != MPDP_OK) return rc;
+        pq[i] = PlanQuery{qs[i].n_rels, qs[i].n_edges, resolve_enumeration(ctx->cfg, qs[i].n_rels, qs[i].n_edges),
+                          qs[i].card, qs[i].edges, 0, 0};
+    }
+    if (nq == 0) return MPDP_OK;
     CK(ctx, cudaSetDevice(ctx->device));
-    const int n = q->n_rels, m = q->n_edges;
-    rc = ensure_workspace(ctx, n, ctx->cfg.memo_kind);
+    std::vector<std::pair<int, int>> parts;
+    int rc = split_batches(ctx, pq, parts);
     if (rc != MPDP_OK) return rc;
-    const int enumeration = resolve_enumeration(ctx, n, m);
-    HandleSlot* slot = nullptr;
-    rc = acquire_slot(ctx, &slot);
-    if (rc != MPDP_OK) return rc;
-
-    // stage the query in the next ring buffer, once its previous copy has run
-    const int ring = ctx->stage_next;
-    ctx->stage_next = (ring + 1) % mpdp_ctx::kStageRing;
-    CK(ctx, cudaEventSynchronize(ctx->staged_free[ring]));
-    StagedQuery* h = ctx->h_staged + ring;
-    h->n = n;
-    h->n_edges = m;
-    h->cost_model = q->cost_model;
-    h->pad = 0;
-    for (int i = 0; i < kMaxRels; i++) h->card[i] = i < n ? q->card[i] : 1.0;
-    for (int e = 0; e < m; e++) h->edges[e] = q->edges[e];
-    const size_t bytes = offsetof(StagedQuery, edges) + (size_t)m * sizeof(mpdp_edge);
-    CK(ctx, cudaMemcpyAsync(ctx->ws.staged, h, bytes, cudaMemcpyHostToDevice, ctx->stream));
-    CK(ctx, cudaEventRecord(ctx->staged_free[ring], ctx->stream));
-
-    CK(ctx, cudaEventRecord(slot->t0, ctx->stream));
-    int launches = 0;
-    rc = run_pipeline(ctx, n, enumeration, &launches);
-    if (rc != MPDP_OK) return rc;
-    CK(ctx, cudaEventRecord(slot->t1, ctx->stream));
-    CK(ctx, cudaMemcpyAsync(slot->host, ctx->out, sizeof(HostResult), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaEventRecord(slot->done, ctx->stream));
-    slot->used = true;
-    slot->handle = ctx->next_handle++;
-    slot->n = n;
-    slot->enumeration = enumeration;
-    slot->memo_kind = ctx->cfg.memo_kind;
-    slot->h2d_bytes = bytes;
-    ctx->last_exact_handle = slot->handle;
-    ctx->last_memo_kind = ctx->cfg.memo_kind;
-    ctx->last_launches = launches;
-    *handle = slot->handle;
+    for (const auto& pr : parts) {
+        std::vector<PlanQuery> sub(pq.begin() + pr.first, pq.begin() + pr.second);
+        int ri = -1;
+        rc = submit_batch(ctx, sub, true, nullptr, nullptr, &ri, nullptr, nullptr, nullptr);
+        if (rc != MPDP_OK) return rc;
+        for (int i = pr.first; i < pr.second; i++) {
+            const int64_t h = ctx->next_handle++;
+            ctx->handles[h] = HandleRef{ri, i - pr.first};
+            ctx->recs[ri].refs++;
+            handles[i] = h;
+        }
+    }
     return MPDP_OK;
 }
 
-int mpdp_optimize_batch(mpdp_ctx* ctx, const mpdp_query* qs, int32_t nq, int64_t* handles)
+int mpdp_optimize(mpdp_ctx* ctx, const mpdp_query* q, int64_t* handle)
 {
-    if (!ctx || (nq > 0 && (!qs || !handles)) || nq < 0) return MPDP_ERR_INVALID_ARG;
-    for (int i = 0; i < nq; i++) handles[i] = -1;
-    for (int i = 0; i < nq; i++) {
-        int rc = mpdp_optimize(ctx, &qs[i], &handles[i]);
-        if (rc != MPDP_OK) return rc;
-    }
-    return MPDP_OK;
+    if (!ctx || !q || !handle) return MPDP_ERR_INVALID_ARG;
+    return mpdp_optimize_batch(ctx, q, 1, handle);
 }
 
 int mpdp_get_plan(mpdp_ctx* ctx, int64_t handle, mpdp_plan_node* nodes, int32_t cap, int32_t* n_nodes,
                   double* cost, mpdp_stats* st)
 {
     if (!ctx) return MPDP_ERR_INVALID_ARG;
-    HandleSlot* slot = find_slot(ctx, handle);
-    if (!slot) return MPDP_ERR_BAD_HANDLE;
-    CK(ctx, cudaEventSynchronize(slot->done));
-    const HostResult& r = *slot->host;
+    auto it = ctx->handles.find(handle);
+    if (it == ctx->handles.end()) return MPDP_ERR_BAD_HANDLE;
+    Record& rec = ctx->recs[it->second.rec];
+    const int idx = it->second.idx;
+    CK(ctx, cudaEventSynchronize(rec.done));
+    const DevOut& r = rec.host[idx];
     const int status = r.counters.status;
     if (status != MPDP_OK) return status;
     if (r.result.status != MPDP_OK) return r.result.status;
@@ -521,8 +758,9 @@ int mpdp_get_plan(mpdp_ctx* ctx, int64_t handle, mpdp_plan_node* nodes, int32_t 
     if (st) {
         memset(st, 0, sizeof(*st));
         const DevCounters& c = r.counters;
+        const int n = rec.n[idx];
         st->sets_unranked = c.unranked;
-        for (int k = 2; k <= slot->n && k < kLevels; k++) {
+        for (int k = 2; k <= n && k < kLevels; k++) {
             st->connected_per_level[k] = c.list_count[k];
             st->evaluated_per_level[k] = c.evaluated[k];
             st->ccp_per_level[k] = c.ccp[k];
@@ -530,18 +768,17 @@ int mpdp_get_plan(mpdp_ctx* ctx, int64_t handle, mpdp_plan_node* nodes, int32_t 
             st->pairs_evaluated += c.evaluated[k];
             st->ccp_pairs += c.ccp[k];
         }
-        st->connected_per_level[1] = (uint64_t)slot->n;
+        st->connected_per_level[1] = (uint64_t)n;
         st->heavy_sets = c.heavy;
-        st->memo_bytes = slot->memo_kind == MPDP_MEMO_DENSE
-                             ? ((uint64_t)12 << slot->n)
-                             : (uint64_t)c.memo_slots * sizeof(HashSlot);
+        st->memo_bytes = rec.memo_kind == MPDP_MEMO_DENSE ? ((uint64_t)20 << n)
+                                                          : (uint64_t)c.memo_slots * sizeof(HashSlot);
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, slot->t0, slot->t1) == cudaSuccess) st->device_ms = ms;
+        if (cudaEventElapsedTime(&ms, rec.t0, rec.t1) == cudaSuccess) st->device_ms = ms;
         else cudaGetLastError();
-        st->enumeration = slot->enumeration;
-        st->memo_kind = slot->memo_kind;
-        st->h2d_bytes = slot->h2d_bytes;
-        st->d2h_bytes = sizeof(HostResult);
+        st->enumeration = rec.enumeration[idx];
+        st->memo_kind = rec.memo_kind;
+        st->h2d_bytes = rec.h2d[idx];
+        st->d2h_bytes = sizeof(DevOut);
         st->filter_steps = c.filter_steps;
     }
     return MPDP_OK;
@@ -550,37 +787,50 @@ int mpdp_get_plan(mpdp_ctx* ctx, int64_t handle, mpdp_plan_node* nodes, int32_t 
 int mpdp_release(mpdp_ctx* ctx, int64_t handle)
 {
     if (!ctx) return MPDP_ERR_INVALID_ARG;
-    HandleSlot* slot = find_slot(ctx, handle);
-    if (!slot) return MPDP_ERR_BAD_HANDLE;
-    CK(ctx, cudaEventSynchronize(slot->done));
-    slot->used = false;
-    slot->handle = -1;
+    auto it = ctx->handles.find(handle);
+    if (it == ctx->handles.end()) return MPDP_ERR_BAD_HANDLE;
+    Record& rec = ctx->recs[it->second.rec];
+    CK(ctx, cudaEventSynchronize(rec.done));
+    ctx->handles.erase(it);
+    if (--rec.refs <= 0) rec.in_use = false;
     return MPDP_OK;
 }
 
-int mpdp_optimize_device(mpdp_ctx* ctx, int32_t n_rels, int32_t n_edges, const double* d_card,
-                         const mpdp_edge* d_edges, int32_t cost_model, mpdp_plan_node* d_nodes,
-                         double* d_cost, int32_t* d_status)
+int mpdp_optimize_batch_device(mpdp_ctx* ctx, int32_t nq, const int32_t* n_rels, const int32_t* n_edges,
+                               const double* d_card, const mpdp_edge* d_edges, int32_t cost_model,
+                               mpdp_plan_node* d_nodes, double* d_cost, int32_t* d_status)
 {
-    if (!ctx || !d_card || (n_edges > 0 && !d_edges) || !d_nodes || !d_cost || !d_status)
+    if (!ctx || nq < 0 || (nq > 0 && (!n_rels || !n_edges || !d_card || !d_nodes || !d_cost || !d_status)))
         return MPDP_ERR_INVALID_ARG;
-    if (n_rels < 1 || n_edges < 0 || n_edges > edges_max(n_rels)) return MPDP_ERR_INVALID_ARG;
-    if (n_rels > MPDP_MAX_EXACT_RELS) return MPDP_ERR_TOO_LARGE;
     if (cost_model != MPDP_COST_COUT) return MPDP_ERR_INVALID_ARG;
+    if (nq > kMaxBatch) return MPDP_ERR_TOO_LARGE;
+    std::vector<PlanQuery> pq(nq);
+    unsigned long long co = 0, eo = 0;
+    for (int i = 0; i < nq; i++) {
+        const int n = n_rels[i], m = n_edges[i];
+        if (n < 1 || m < 0 || m > edges_max(n)) return MPDP_ERR_INVALID_ARG;
+        if (n > MPDP_MAX_EXACT_RELS) return MPDP_ERR_TOO_LARGE;
+        pq[i] = PlanQuery{n, m, resolve_enumeration(ctx->cfg, n, m), nullptr, nullptr, co, eo};
+        co += n;
+        eo += m;
+    }
+    if (eo > 0 && !d_edges) return MPDP_ERR_INVALID_ARG;
+    if (nq == 0) return MPDP_OK;
     CK(ctx, cudaSetDevice(ctx->device));
-    int rc = ensure_workspace(ctx, n_rels, ctx->cfg.memo_kind);
+    std::vector<std::pair<int, int>> parts;
+    int rc = split_batches(ctx, pq, parts);
     if (rc != MPDP_OK) return rc;
-    const int enumeration = resolve_enumeration(ctx, n_rels, n_edges);
-    LaunchHook* hook = ctx->profiling ? &ctx->hook : nullptr;
-    CK(ctx, enqueue_stage_device(d_card, d_edges, n_rels, n_edges, cost_model, ctx->ws.staged,
-                                 ctx->stream, hook));
-    int launches = 0;
-    rc = run_pipeline(ctx, n_rels, enumeration, &launches);
-    if (rc != MPDP_OK) return rc;
-    CK(ctx, enqueue_publish(ctx->ws, d_nodes, d_cost, d_status, ctx->stream, hook));
-    ctx->last_launches = launches + 2;
-    ctx->last_exact_handle = -1;
-    return MPDP_OK;
+    if (parts.size() != 1) return MPDP_ERR_ADMISSION;
+    return submit_batch(ctx, pq, false, d_card, d_edges, nullptr, d_nodes, d_cost, d_status);
+}
+
+int mpdp_optimize_device(mpdp_ctx* ctx, int32_t n_rels, int32_t n_edges, const double* d_card,
+                         const mpdp_edge* d_edges, int32_t cost_model, mpdp_plan_node* d_nodes, double* d_cost,
+                         int32_t* d_status)
+{
+    if (!ctx) return MPDP_ERR_INVALID_ARG;
+    return mpdp_optimize_batch_device(ctx, 1, &n_rels, &n_edges, d_card, d_edges, cost_model, d_nodes, d_cost,
+                                      d_status);
 }
 
 int mpdp_profile(mpdp_ctx* ctx, int enable)
@@ -626,29 +876,28 @@ int mpdp_sync(mpdp_ctx* ctx)
 {
     if (!ctx) return MPDP_ERR_INVALID_ARG;
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    if (!ctx->out) return MPDP_OK;
-    int status = 0;
-    CK(ctx, cudaMemcpy(&status, &ctx->out->counters.status, sizeof(int), cudaMemcpyDeviceToHost));
-    return status;
+    return MPDP_OK;
 }
 
 int mpdp_memo_lookup(mpdp_ctx* ctx, int64_t handle, const uint64_t* sets, int32_t count, double* costs,
                      uint64_t* lefts)
 {
     if (!ctx || count < 0 || (count > 0 && (!sets || !costs || !lefts))) return MPDP_ERR_INVALID_ARG;
-    HandleSlot* slot = find_slot(ctx, handle);
-    if (!slot) return MPDP_ERR_BAD_HANDLE;
-    if (handle != ctx->last_exact_handle) return MPDP_ERR_STALE;
+    auto it = ctx->handles.find(handle);
+    if (it == ctx->handles.end()) return MPDP_ERR_BAD_HANDLE;
+    Record& rec = ctx->recs[it->second.rec];
+    const int idx = it->second.idx;
+    if (rec.seq != ctx->last_seq) return MPDP_ERR_STALE;
     if (count == 0) return MPDP_OK;
-    const uint64_t full = ((uint64_t)1 << slot->n) - 1;
+    const uint64_t full = ((uint64_t)1 << rec.n[idx]) - 1;
     std::vector<uint32_t> hs(count);
     for (int i = 0; i < count; i++) {
         if (sets[i] == 0 || (sets[i] & ~full)) return MPDP_ERR_INVALID_ARG;
         hs[i] = (uint32_t)sets[i];
     }
     CK(ctx, cudaSetDevice(ctx->device));
-    CK(ctx, cudaEventSynchronize(slot->done));
-    if (slot->host->counters.status != MPDP_OK) return slot->host->counters.status;
+    CK(ctx, cudaEventSynchronize(rec.done));
+    if (rec.host[idx].counters.status != MPDP_OK) return rec.host[idx].counters.status;
     uint32_t* d_sets = nullptr;
     double* d_costs = nullptr;
     uint32_t* d_lefts = nullptr;
@@ -661,10 +910,11 @@ int mpdp_memo_lookup(mpdp_ctx* ctx, int64_t handle, const uint64_t* sets, int32_
     }
     std::vector<uint32_t> hl(count);
     if (rc == MPDP_OK) {
-        cudaError_t e = cudaMemcpyAsync(d_sets, hs.data(), count * sizeof(uint32_t), cudaMemcpyHostToDevice,
-                                        ctx->stream);
+        const BatchArgs a = batch_args(ctx, rec.nq, 0);
+        cudaError_t e =
+            cudaMemcpyAsync(d_sets, hs.data(), count * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess)
-            e = enqueue_memo_lookup(ctx->ws, slot->memo_kind, d_sets, count, d_costs, d_lefts, ctx->stream);
+            e = enqueue_memo_lookup(a, rec.memo_kind, idx, d_sets, count, d_costs, d_lefts, ctx->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(costs, d_costs, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess)

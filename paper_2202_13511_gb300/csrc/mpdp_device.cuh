@@ -2,6 +2,7 @@
 //
 // Relation sets are 32-bit bitmaps (bit i = relation i), the fixed-width
 // bitmap sets of the paper (Sec. 2.2, "Implementation Details"; Sec. 5).
+// Every kernel works on a batch of queries; one query is a batch of one.
 #pragma once
 
 #include <cstddef>
@@ -15,6 +16,10 @@ constexpr int kMaxRels = 32;        // bitmap width
 constexpr int kLevels = MPDP_MAX_LEVELS;
 constexpr int kMaxEdges = kMaxRels * (kMaxRels - 1) / 2;
 constexpr int kEvalThreads = 256;
+constexpr int kFilterThreads = 256;
+constexpr int kMaxBatch = 1024;     // queries per device batch
+constexpr int kPlanNodes = 2 * kMaxRels - 1;
+constexpr unsigned kFull = 0xffffffffu;
 
 // Query as staged from the host (or gathered from caller device buffers).
 struct StagedQuery {
@@ -23,13 +28,16 @@ struct StagedQuery {
     mpdp_edge edges[kMaxEdges];
 };
 
-// Query as the kernels read it: adjacency bitmaps and a dense selectivity
-// matrix (1.0 where there is no edge).  Built on the device by k_ingest.
+// Query as the kernels read it.  Built on the device by k_ingest.
 struct DevQuery {
     int32_t n, n_edges, pad[2];
-    uint32_t adj[kMaxRels];
+    uint32_t adj[kMaxRels];          // adjacency bitmaps
+    uint32_t nbase[kMaxRels];        // first entry of relation r's neighbour list in nsel
     double card[kMaxRels];
-    double sel[kMaxRels * kMaxRels];  // sel[j * 32 + r]
+    double nsel[2 * kMaxEdges];      // nsel[nbase[r] + i]: sel of r's i-th neighbour (ascending)
+    // nbt[b][x]: union of the adjacency bitmaps of relations 8b + i for every
+    // bit i of the byte x, so N(S) = OR_b nbt[b][byte b of S] (4 lookups)
+    uint32_t nbt[4][256];
 };
 
 // Per-query device counters and status word.
@@ -37,12 +45,12 @@ struct DevCounters {
     unsigned long long unranked;
     unsigned long long heavy;
     unsigned long long memo_slots;
-    unsigned long long filter_steps;    // vertices expanded by the filter's tests
+    unsigned long long filter_steps;    // BFS rounds run by the filter's connectivity tests
     unsigned long long connected[kLevels];
     unsigned long long evaluated[kLevels];
     unsigned long long ccp[kLevels];
     unsigned int list_count[kLevels];   // connected sets of level k in the list
-    unsigned int heavy_count[kLevels];  // sets of level k sent to the warp kernel
+    unsigned int heavy_count[kLevels];  // sets of level k sent to the block-per-set kernel
     int status;                         // first MPDP_ERR_* raised on the device
     int pad;
 };
@@ -51,20 +59,22 @@ struct DevResult {
     double cost;
     int32_t n_nodes;
     int32_t status;
-    mpdp_plan_node nodes[2 * kMaxRels - 1];
+    mpdp_plan_node nodes[kPlanNodes];
 };
 
-// Host copy of one finished query: result and counters, read back together.
-struct HostResult {
+// Device twin of one query's result + counters: one copy reads both back.
+struct DevOut {
     DevResult result;
     DevCounters counters;
 };
 
-// Open-addressing memo: one table per level inside one arena.
-struct alignas(16) HashSlot {
+// Open-addressing memo slot: one 32-byte sector per probe.
+struct alignas(32) HashSlot {
     uint32_t key;    // relation bitmap; 0 = empty (the empty set is never stored)
     uint32_t left;   // left child bitmap of the best split
     double cost;     // C_out cost of the best plan
+    double card;     // card(S)
+    double pad;
 };
 
 struct HashLayout {
@@ -73,11 +83,42 @@ struct HashLayout {
     unsigned long long total_slots;
 };
 
+// Where one query of a batch lives in the batch workspace.
+struct QDesc {
+    int32_t n, n_edges, enumeration, cost_model;
+    unsigned long long memo_base;      // dense memo: entry of bitmap 0
+    unsigned long long list_base;      // first list word of the query
+    unsigned long long card_off;       // device path: offset of the query in the caller arrays
+    unsigned long long edge_off;
+    uint32_t list_off[kLevels];        // level k's region, relative to list_base
+    uint32_t warp_begin[kLevels + 1];  // first filter warp of level k, relative to the query
+    uint32_t filter_block_base;        // first filter block of the query
+    uint32_t pad;
+};
+
+// Everything a batch launch needs (passed by value).
+struct BatchArgs {
+    int nq;
+    int max_n;
+    const QDesc* desc;
+    const uint32_t* filter_block_prefix;  // [nq + 1]
+    StagedQuery* staged;
+    DevQuery* query;
+    DevOut* out;
+    uint32_t* lists;
+    uint32_t* heavy;
+    double2* memo;       // dense memo {cost, card}
+    uint32_t* left;      // dense memo left masks
+    HashSlot* arena;     // hash memo slots
+    HashLayout* layout;  // [nq]
+    unsigned long long arena_slots;
+    int run;             // ranks per lane in the filter (<= 32)
+    int heavy_threshold;
+    int use_ccc;
+};
+
 // Record the first device error; later errors keep the first code.
-__device__ __forceinline__ void raise_status(DevCounters* c, int code)
-{
-    atomicCAS(&c->status, 0, code);
-}
+__device__ __forceinline__ void raise_status(DevCounters* c, int code) { atomicCAS(&c->status, 0, code); }
 
 __device__ __forceinline__ int lowest(uint32_t s) { return __ffs(s) - 1; }
 
@@ -98,7 +139,6 @@ __device__ __forceinline__ uint32_t grow(uint32_t source, uint32_t restriction,
 }
 
 // connected(S): grow from the lowest member of S inside S reaches all of S.
-// Stops as soon as every member has been reached.
 __device__ __forceinline__ bool connected(uint32_t s, const uint32_t* __restrict__ adj)
 {
     uint32_t seen = s & (0u - s), frontier = seen;
@@ -113,24 +153,59 @@ __device__ __forceinline__ bool connected(uint32_t s, const uint32_t* __restrict
     return seen == s;
 }
 
+// Neighbourhood N(S) (every relation adjacent to a member of S) by byte tables.
+__device__ __forceinline__ uint32_t nbhd(uint32_t s, const uint32_t (*__restrict__ t)[256])
+{
+    return t[0][s & 255u] | t[1][(s >> 8) & 255u] | t[2][(s >> 16) & 255u] | t[3][s >> 24];
+}
+
+// connected(S) for |S| >= 2 by whole-frontier rounds: first reject S when a
+// member has no neighbour inside S (an isolated vertex of G[S]); otherwise
+// grow from min(S) one BFS layer per round until S is reached or growth stops.
+__device__ __forceinline__ bool connected_rounds(uint32_t s, const uint32_t (*__restrict__ t)[256],
+                                                 uint32_t& rounds)
+{
+    if (s & ~nbhd(s, t)) return false;
+    uint32_t seen = s & (0u - s);
+    while (true) {
+        rounds++;
+        const uint32_t nxt = (seen | nbhd(seen, t)) & s;
+        if (nxt == s) return true;
+        if (nxt == seen) return false;
+        seen = nxt;
+    }
+}
+
+// Shared-memory copy of one query for the evaluate kernels.
+struct SharedQuery {
+    uint32_t adj[kMaxRels];
+    uint32_t nbase[kMaxRels];
+    double card[kMaxRels];
+    double nsel[2 * kMaxEdges];
+};
+
+// sel(j, r) for an edge (j, r): entry of j in r's ascending neighbour list.
+__device__ __forceinline__ double sel_of(const SharedQuery& sq, int j, int r)
+{
+    return sq.nsel[sq.nbase[r] + __popc(sq.adj[r] & ((1u << j) - 1u))];
+}
+
 // card(S): product in the fixed order (relations ascending; after each
 // relation r, the selectivities of its edges to smaller members j ascending).
 // __dmul_rn keeps every step a separately rounded IEEE multiply.
-__device__ __forceinline__ double card_of(uint32_t s, const uint32_t* __restrict__ adj,
-                                          const double* __restrict__ card,
-                                          const double* __restrict__ sel)
+__device__ __forceinline__ double card_of(uint32_t s, const SharedQuery& sq)
 {
     double p = 1.0;
     uint32_t t = s;
     while (t) {
         int r = lowest(t);
         t &= t - 1;
-        p = __dmul_rn(p, card[r]);
-        uint32_t nb = adj[r] & s & ((1u << r) - 1u);
+        p = __dmul_rn(p, sq.card[r]);
+        uint32_t nb = sq.adj[r] & s & ((1u << r) - 1u);
         while (nb) {
             int j = lowest(nb);
             nb &= nb - 1;
-            p = __dmul_rn(p, sel[j * kMaxRels + r]);
+            p = __dmul_rn(p, sel_of(sq, j, r));
         }
     }
     return p;
@@ -153,24 +228,33 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h)
     return h;
 }
 
-// Memo indexed directly by the relation bitmap.
+// Memo indexed directly by the relation bitmap: entry {cost, card} and left.
 struct DenseMemo {
-    double* cost;
+    double2* cc0;      // batch arena
+    uint32_t* left0;
+    double2* cc;       // bound to one query
     uint32_t* left;
 
+    static constexpr size_t kSharedBytes = 16;
+
     __device__ __forceinline__ void setup(char*) {}
-    __device__ __forceinline__ double get_cost(uint32_t s, DevCounters*) const
+    // per thread; no shared memory involved
+    __device__ __forceinline__ void bind(const BatchArgs& a, int q)
     {
-        return __ldg(cost + s);
+        cc = cc0 + a.desc[q].memo_base;
+        left = left0 + a.desc[q].memo_base;
     }
-    __device__ __forceinline__ void get(uint32_t s, double& c, uint32_t& l, DevCounters*) const
+    __device__ __forceinline__ double get_cost(uint32_t s, DevCounters*) const { return __ldg(&cc[s].x); }
+    __device__ __forceinline__ void get(uint32_t s, double& c, double& card, uint32_t& l, DevCounters*) const
     {
-        c = cost[s];
+        const double2 v = cc[s];
+        c = v.x;
+        card = v.y;
         l = left[s];
     }
-    __device__ __forceinline__ void put(uint32_t s, int, double c, uint32_t l, DevCounters*)
+    __device__ __forceinline__ void put(uint32_t s, int, double c, double card, uint32_t l, DevCounters*)
     {
-        cost[s] = c;
+        cc[s] = make_double2(c, card);
         left[s] = l;
     }
 };
@@ -178,8 +262,7 @@ struct DenseMemo {
 // Memo as one open-addressing table per level (linear probing).
 struct HashMemo {
     HashSlot* arena;
-    const HashLayout* layout;
-    // per-block copy of the level table bases and masks (shared memory)
+    // the bound query's table bases and masks (shared memory)
     unsigned long long* s_base;
     unsigned int* s_mask;
 
@@ -189,54 +272,58 @@ struct HashMemo {
     {
         s_base = reinterpret_cast<unsigned long long*>(smem);
         s_mask = reinterpret_cast<unsigned int*>(smem + kLevels * sizeof(unsigned long long));
+    }
+    // cooperative: every thread of the block calls it; a barrier must follow
+    __device__ __forceinline__ void bind(const BatchArgs& a, int q)
+    {
         for (int i = threadIdx.x; i < kLevels; i += blockDim.x) {
-            s_base[i] = layout->base[i];
-            s_mask[i] = layout->mask[i];
+            s_base[i] = a.layout[q].base[i];
+            s_mask[i] = a.layout[q].mask[i];
         }
     }
-
-    __device__ __forceinline__ bool find(uint32_t s, double& c, uint32_t& l, DevCounters* cnt) const
+    __device__ __forceinline__ const HashSlot* find(uint32_t s, DevCounters* cnt) const
     {
-        int lvl = __popc(s);
+        const int lvl = __popc(s);
         const HashSlot* t = arena + s_base[lvl];
-        uint32_t m = s_mask[lvl];
+        const uint32_t m = s_mask[lvl];
         uint32_t h = fmix32(s) & m;
         for (uint32_t i = 0; i <= m; i++) {
-            uint4 v = __ldg(reinterpret_cast<const uint4*>(t + h));  // one 16-byte probe
-            if (v.x == s) {
-                l = v.y;
-                c = __hiloint2double(static_cast<int>(v.w), static_cast<int>(v.z));
-                return true;
-            }
-            if (v.x == 0u) break;
+            const uint32_t key = __ldg(&t[h].key);
+            if (key == s) return t + h;
+            if (key == 0u) break;
             h = (h + 1u) & m;
         }
         raise_status(cnt, MPDP_ERR_PROBE_LIMIT);
-        c = __longlong_as_double(0x7ff8000000000000ll);
-        l = 0xffffffffu;
-        return false;
+        return nullptr;
     }
     __device__ __forceinline__ double get_cost(uint32_t s, DevCounters* cnt) const
     {
-        double c;
-        uint32_t l;
-        find(s, c, l, cnt);
-        return c;
+        const HashSlot* e = find(s, cnt);
+        return e ? __ldg(&e->cost) : __longlong_as_double(0x7ff8000000000000ll);
     }
-    __device__ __forceinline__ void get(uint32_t s, double& c, uint32_t& l, DevCounters* cnt) const
+    __device__ __forceinline__ void get(uint32_t s, double& c, double& card, uint32_t& l, DevCounters* cnt) const
     {
-        find(s, c, l, cnt);
+        const HashSlot* e = find(s, cnt);
+        if (e) {
+            c = e->cost;
+            card = e->card;
+            l = e->left;
+        } else {
+            c = card = __longlong_as_double(0x7ff8000000000000ll);
+            l = 0xffffffffu;
+        }
     }
-    __device__ __forceinline__ void put(uint32_t s, int lvl, double c, uint32_t l, DevCounters* cnt)
+    __device__ __forceinline__ void put(uint32_t s, int lvl, double c, double card, uint32_t l,
+                                        DevCounters* cnt)
     {
         HashSlot* t = arena + s_base[lvl];
-        uint32_t m = s_mask[lvl];
+        const uint32_t m = s_mask[lvl];
         uint32_t h = fmix32(s) & m;
         for (uint32_t i = 0; i <= m; i++) {
-            uint32_t old = atomicCAS(&t[h].key, 0u, s);
-            if (old == 0u) {
+            if (atomicCAS(&t[h].key, 0u, s) == 0u) {
                 t[h].left = l;
                 t[h].cost = c;
+                t[h].card = card;
                 return;
             }
             h = (h + 1u) & m;

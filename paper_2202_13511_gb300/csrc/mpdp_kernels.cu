@@ -1,108 +1,192 @@
-// MPDP kernels for sm_103a.
+// MPDP kernels for sm_103a.  Every launch covers a batch of queries.
 //
-// One query runs as: ingest -> unrank+filter (all levels, one launch) ->
-// [hash layout + clear] -> evaluate level 2 .. n (one launch per level, plus
-// the block-per-set launch in block mode) -> plan fetch.  Level k's launch
-// only reads memo entries of levels < k, so launches are the level barrier
-// of the DP (Sec. 2.1.1; Sec. 5, Algorithm "MPDP on GPU").
+// A batch runs as: ingest (block per query) -> unrank+filter (all levels of
+// all queries, one launch) -> [hash layout + clear] -> evaluate level
+// 2 .. max n (one launch per level for the whole batch, plus the
+// block-per-set launch in block mode) -> plan fetch (block per query).
+// Level k's launch only reads memo entries of levels < k, so launches are the
+// level barrier of the DP (Sec. 2.1.1; Sec. 5, Algorithm "MPDP on GPU").
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <cstring>
 
 #include "mpdp_device.cuh"
 #include "mpdp_launch.h"
 
 namespace mpdp {
 
-constexpr unsigned kFull = 0xffffffffu;
+// ---------------------------------------------------------------------------
+// Block-wide helpers.
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Exclusive prefix over the batch's queries of f(q) into s_pref[0..nq];
+// returns the total.  Every thread of the block must call it.
+template <class F>
+__device__ uint32_t block_prefix(int nq, uint32_t* s_pref, F f)
+{
+    __shared__ uint32_t s_warp[32];
+    const int per = (nq + blockDim.x - 1) / blockDim.x;
+    const int lo = min(nq, (int)threadIdx.x * per), hi = min(nq, lo + per);
+    uint32_t sum = 0;
+    for (int q = lo; q < hi; q++) sum += f(q);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int w = 0; w < warp; w++) wbase += s_warp[w];
+    uint32_t run = wbase + incl - sum;
+    for (int q = lo; q < hi; q++) {
+        s_pref[q] = run;
+        run += f(q);
+    }
+    if (threadIdx.x == blockDim.x - 1) s_pref[nq] = run;
+    __syncthreads();
+    const uint32_t total = s_pref[nq];
+    __syncthreads();
+    return total;
+}
+
+// Query owning item t: the largest q with s_pref[q] <= t (items of queries
+// with no work are skipped since their range is empty).
+__device__ __forceinline__ int find_q(const uint32_t* s_pref, int nq, uint32_t t)
+{
+    int lo = 0, hi = nq - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_pref[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void load_query(SharedQuery& sq, const DevQuery* __restrict__ q)
+{
+    const int nsel = 2 * q->n_edges;
+    for (int i = threadIdx.x; i < nsel; i += blockDim.x) sq.nsel[i] = q->nsel[i];
+    if (threadIdx.x < kMaxRels) {
+        sq.adj[threadIdx.x] = q->adj[threadIdx.x];
+        sq.nbase[threadIdx.x] = q->nbase[threadIdx.x];
+        sq.card[threadIdx.x] = q->card[threadIdx.x];
+    }
+}
 
 // ---------------------------------------------------------------------------
-// a0: ingest.  Builds adjacency bitmaps and the selectivity matrix from the
-// staged edge list, validates every value, checks that the whole join graph
-// is connected, zeroes the counters and writes the implicit base entries
-// cost({R_i}) = 0 of the dense memo (Algorithm "MPDP on GPU", memo fill).
-__global__ void __launch_bounds__(256) k_ingest(const StagedQuery* __restrict__ st,
-                                                DevQuery* __restrict__ q,
-                                                DevCounters* __restrict__ cnt,
-                                                double* __restrict__ dcost,
-                                                uint32_t* __restrict__ dleft, int dense)
+// Device-path staging: gather each query from the caller's device buffers.
+__global__ void k_stage(BatchArgs a, const double* __restrict__ card, const mpdp_edge* __restrict__ edges)
 {
-    const int tid = threadIdx.x;
-    int* cw = reinterpret_cast<int*>(cnt);
-    for (int i = tid; i < (int)(sizeof(DevCounters) / sizeof(int)); i += blockDim.x) cw[i] = 0;
-    const int n = st->n;
-    const int m = st->n_edges;
-    for (int i = tid; i < kMaxRels * kMaxRels; i += blockDim.x) q->sel[i] = 1.0;
-    if (tid < kMaxRels) {
-        q->adj[tid] = 0u;
-        q->card[tid] = (tid < n) ? st->card[tid] : 1.0;
-    }
-    __syncthreads();
-    if (tid != 0) return;
-    int status = 0;
-    if (n < 1 || n > MPDP_MAX_EXACT_RELS) status = MPDP_ERR_TOO_LARGE;
-    else if (m < 0 || m > kMaxEdges || st->cost_model != MPDP_COST_COUT) status = MPDP_ERR_INVALID_ARG;
-    if (status == 0) {
-        for (int i = 0; i < n; i++) {
-            double c = st->card[i];
-            if (!(c > 0.0) || !(c <= 1.7976931348623157e308)) status = MPDP_ERR_INVALID_ARG;
-        }
-    }
-    uint32_t adj[kMaxRels];
-    for (int i = 0; i < kMaxRels; i++) adj[i] = 0u;
-    for (int e = 0; e < m && status == 0; e++) {
-        int u = st->edges[e].u, v = st->edges[e].v;
-        double s = st->edges[e].sel;
-        if (u < 0 || v < 0 || u >= n || v >= n || u == v || !(s > 0.0) || !(s <= 1.0) ||
-            (adj[u] >> v & 1u)) {
-            status = MPDP_ERR_INVALID_ARG;
-            break;
-        }
-        adj[u] |= 1u << v;
-        adj[v] |= 1u << u;
-        q->sel[u * kMaxRels + v] = s;
-        q->sel[v * kMaxRels + u] = s;
-    }
-    if (status == 0) {
-        uint32_t full = (n == 32) ? kFull : ((1u << n) - 1u);
-        if (grow(1u, full, adj) != full) status = MPDP_ERR_DISCONNECTED;
-    }
-    for (int i = 0; i < kMaxRels; i++) q->adj[i] = adj[i];
-    q->n = n;
-    q->n_edges = m;
-    cnt->status = status;
-    if (dense && status == 0) {
-        for (int i = 0; i < n; i++) {
-            dcost[1u << i] = 0.0;
-            dleft[1u << i] = 0u;
-        }
-    }
-}
-
-// Device-path staging: gather caller device buffers into the staged query.
-__global__ void k_stage(const double* __restrict__ card, const mpdp_edge* __restrict__ edges,
-                        int n, int m, int cost_model, StagedQuery* __restrict__ st)
-{
-    int tid = threadIdx.x;
-    if (tid == 0) {
+    const int q = blockIdx.x;
+    const QDesc& d = a.desc[q];
+    StagedQuery* st = a.staged + q;
+    const int n = d.n, m = d.n_edges;
+    if (threadIdx.x == 0) {
         st->n = n;
         st->n_edges = m;
-        st->cost_model = cost_model;
+        st->cost_model = d.cost_model;
     }
-    for (int i = tid; i < n && i < kMaxRels; i += blockDim.x) st->card[i] = card[i];
-    for (int e = tid; e < m && e < kMaxEdges; e += blockDim.x) st->edges[e] = edges[e];
+    for (int i = threadIdx.x; i < n && i < kMaxRels; i += blockDim.x) st->card[i] = card[d.card_off + i];
+    for (int e = threadIdx.x; e < m && e < kMaxEdges; e += blockDim.x) st->edges[e] = edges[d.edge_off + e];
 }
 
-// Device-path outputs: copy plan, cost and status to caller device buffers.
-__global__ void k_publish(const DevResult* __restrict__ res, const DevCounters* __restrict__ cnt,
-                          mpdp_plan_node* __restrict__ nodes, double* __restrict__ cost,
+// Device-path outputs: plan, cost and status of each query to caller buffers.
+__global__ void k_publish(BatchArgs a, mpdp_plan_node* __restrict__ nodes, double* __restrict__ cost,
                           int32_t* __restrict__ status)
 {
-    int n_nodes = res->n_nodes;
-    for (int i = threadIdx.x; i < n_nodes; i += blockDim.x) nodes[i] = res->nodes[i];
+    const int q = blockIdx.x;
+    const DevResult& r = a.out[q].result;
+    const int n_nodes = r.n_nodes;
+    for (int i = threadIdx.x; i < n_nodes; i += blockDim.x) nodes[(size_t)q * kPlanNodes + i] = r.nodes[i];
     if (threadIdx.x == 0) {
-        *cost = res->cost;
-        *status = cnt->status;
+        cost[q] = r.cost;
+        status[q] = a.out[q].counters.status;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a0: ingest (block per query).  Validates the staged query, builds the
+// adjacency bitmaps, per-relation ascending neighbour selectivity lists and
+// the byte neighbourhood tables, checks that the join graph is connected and
+// zeroes the counters.  The dense memo's base entries cost({R_i}) = 0 are
+// written here (Algorithm "MPDP on GPU", memo fill).
+__global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
+{
+    const int qi = blockIdx.x, tid = threadIdx.x;
+    const StagedQuery* __restrict__ st = a.staged + qi;
+    DevQuery* __restrict__ q = a.query + qi;
+    DevCounters* __restrict__ cnt = &a.out[qi].counters;
+    int* cw = reinterpret_cast<int*>(cnt);
+    for (int i = tid; i < (int)(sizeof(DevCounters) / sizeof(int)); i += blockDim.x) cw[i] = 0;
+    __shared__ int s_status;
+    if (tid == 0) {
+        const int n = st->n, m = st->n_edges;
+        int status = 0;
+        if (n < 1 || n > MPDP_MAX_EXACT_RELS) status = MPDP_ERR_TOO_LARGE;
+        else if (m < 0 || m > kMaxEdges || st->cost_model != MPDP_COST_COUT) status = MPDP_ERR_INVALID_ARG;
+        if (status == 0)
+            for (int i = 0; i < n; i++) {
+                const double c = st->card[i];
+                if (!(c > 0.0) || !(c <= 1.7976931348623157e308)) status = MPDP_ERR_INVALID_ARG;
+            }
+        uint32_t adj[kMaxRels];
+        for (int i = 0; i < kMaxRels; i++) adj[i] = 0u;
+        for (int e = 0; e < m && status == 0; e++) {
+            const int u = st->edges[e].u, v = st->edges[e].v;
+            const double s = st->edges[e].sel;
+            if (u < 0 || v < 0 || u >= n || v >= n || u == v || !(s > 0.0) || !(s <= 1.0) ||
+                (adj[u] >> v & 1u)) {
+                status = MPDP_ERR_INVALID_ARG;
+                break;
+            }
+            adj[u] |= 1u << v;
+            adj[v] |= 1u << u;
+        }
+        if (status == 0) {
+            const uint32_t full = (n == 32) ? kFull : ((1u << n) - 1u);
+            if (grow(1u, full, adj) != full) status = MPDP_ERR_DISCONNECTED;
+        }
+        uint32_t base = 0;
+        for (int r = 0; r < kMaxRels; r++) {
+            q->adj[r] = status == 0 ? adj[r] : 0u;
+            q->nbase[r] = base;
+            q->card[r] = (status == 0 && r < n) ? st->card[r] : 1.0;
+            if (status == 0) base += __popc(adj[r]);
+        }
+        if (status == 0)
+            for (int e = 0; e < m; e++) {
+                const int u = st->edges[e].u, v = st->edges[e].v;
+                q->nsel[q->nbase[u] + __popc(adj[u] & ((1u << v) - 1u))] = st->edges[e].sel;
+                q->nsel[q->nbase[v] + __popc(adj[v] & ((1u << u) - 1u))] = st->edges[e].sel;
+            }
+        q->n = n;
+        q->n_edges = status == 0 ? m : 0;
+        s_status = status;
+    }
+    __syncthreads();
+    const int status = s_status;
+    if (tid == 0) cnt->status = status;
+    if (status == 0 && dense) {
+        DenseMemo memo{a.memo, a.left, nullptr, nullptr};
+        memo.bind(a, qi);
+        if (tid < st->n) memo.put(1u << tid, 1, 0.0, q->card[tid], 0u, cnt);
+    }
+    for (int e = tid; e < 4 * 256; e += blockDim.x) {
+        const int b = e >> 8, x = e & 255;
+        uint32_t u = 0u;
+        for (int i = 0; i < 8; i++)
+            if (x >> i & 1) u |= q->adj[8 * b + i];
+        q->nbt[b][x] = u;
     }
 }
 
@@ -137,72 +221,73 @@ __device__ __forceinline__ uint32_t unrank_colex(uint32_t r, int k, int n,
 // set bits (the bit-permutation step the paper's unrank enhancement uses).
 __device__ __forceinline__ uint32_t next_colex(uint32_t s)
 {
-    uint32_t t = s | (s - 1u);
+    const uint32_t t = s | (s - 1u);
     return (t + 1u) | (((~t & (0u - ~t)) - 1u) >> __ffs(s));
 }
 
 // ---------------------------------------------------------------------------
-// a2 + a3: unrank every k-subset of every level and keep the connected ones.
-// Warps are assigned to one level each; lane l of a warp takes the run of
-// `run` consecutive ranks starting at warp_base + l * run, unranks its first
-// set and steps with next_colex.  Pass 1 tests connectivity and keeps one
-// flag bit per rank; a warp scan places every lane's connected sets, one
-// atomic per warp reserves room in the level's list, and pass 2 replays the
-// run writing the kept sets: each warp's output is a colex-ordered slice.
-__global__ void __launch_bounds__(256) k_filter(FilterParams p, const DevQuery* __restrict__ q,
-                                                DevCounters* __restrict__ cnt,
-                                                uint32_t* __restrict__ lists)
+// a2 + a3: unrank every k-subset of every level of every query and keep the
+// connected ones.  Each block belongs to one query; each warp to one level;
+// lane l of a warp takes the run of `run` consecutive ranks starting at
+// warp_base + l * run, unranks its first set and steps with next_colex.
+// Pass 1 tests connectivity (isolated-vertex rejection, then BFS rounds by
+// byte tables) and keeps one flag bit per rank; a warp scan places every
+// lane's connected sets, one atomic per warp reserves room in the level's
+// list, and pass 2 replays the run writing the kept sets: each warp's output
+// is a colex-ordered slice.
+__global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
 {
     __shared__ uint32_t s_binom[33 * 33];
-    __shared__ uint32_t s_adj[kMaxRels];
+    __shared__ uint32_t s_nbt[4][256];
+    // query of this block: the largest q with prefix[q] <= blockIdx.x
+    int lo = 0, hi = a.nq - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.filter_block_prefix[mid] <= blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const int qi = lo;
+    const QDesc& d = a.desc[qi];
+    const DevQuery* __restrict__ q = a.query + qi;
+    DevCounters* __restrict__ cnt = &a.out[qi].counters;
     for (int t = threadIdx.x; t < 33 * 33; t += blockDim.x) s_binom[t] = binom_dev(t / 33, t % 33);
-    if (threadIdx.x < kMaxRels) s_adj[threadIdx.x] = q->adj[threadIdx.x];
+    for (int t = threadIdx.x; t < 4 * 256; t += blockDim.x) s_nbt[t >> 8][t & 255] = q->nbt[t >> 8][t & 255];
     __syncthreads();
     if (cnt->status != 0) return;
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t warp = (blockIdx.x - a.filter_block_prefix[qi]) * (kFilterThreads / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
+    const int n = d.n;
     int k = -1;
-    for (int j = 2; j <= p.n; j++)
-        if (warp >= p.warp_begin[j] && warp < p.warp_begin[j + 1]) k = j;
-    if (k < 0) return;  // whole warp: past the last level
-    const uint32_t nr = p.nranks[k];
-    const unsigned long long r0 =
-        (unsigned long long)(warp - p.warp_begin[k]) * 32ull * (unsigned long long)p.run +
-        (unsigned long long)lane * (unsigned long long)p.run;
+    for (int j = 2; j <= n; j++)
+        if (warp >= d.warp_begin[j] && warp < d.warp_begin[j + 1]) k = j;
+    if (k < 0) return;  // whole warp: padding past the query's last level
+    const uint32_t nr = binom_dev(n, k);
+    const unsigned long long r0 = (unsigned long long)(warp - d.warp_begin[k]) * 32ull * (unsigned long long)a.run +
+                                  (unsigned long long)lane * (unsigned long long)a.run;
     uint32_t len = 0;
-    if (r0 < nr) len = (uint32_t)min((unsigned long long)p.run, (unsigned long long)nr - r0);
-    const uint32_t s0 = len ? unrank_colex((uint32_t)r0, k, p.n, s_binom) : 0u;
-    uint32_t s = s0, flags = 0u, steps = 0u;
+    if (r0 < nr) len = (uint32_t)min((unsigned long long)a.run, (unsigned long long)nr - r0);
+    const uint32_t s0 = len ? unrank_colex((uint32_t)r0, k, n, s_binom) : 0u;
+    uint32_t s = s0, flags = 0u, rounds = 0u;
     for (uint32_t i = 0; i < len; i++) {
-        // connected(S), counting the vertices expanded
-        uint32_t seen = s & (0u - s), frontier = seen;
-        while (frontier) {
-            const int x = lowest(frontier);
-            frontier &= frontier - 1u;
-            steps++;
-            const uint32_t nb = s_adj[x] & s & ~seen;
-            seen |= nb;
-            frontier |= nb;
-            if (seen == s) break;
-        }
-        if (seen == s) flags |= 1u << i;
+        if (connected_rounds(s, s_nbt, rounds)) flags |= 1u << i;
         s = next_colex(s);
     }
     const uint32_t c = __popc(flags);
     uint32_t incl = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t v = __shfl_up_sync(kFull, incl, o);
+        const uint32_t v = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += v;
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     uint32_t base = 0;
     if (lane == 0 && total) base = atomicAdd(&cnt->list_count[k], total);
     base = __shfl_sync(kFull, base, 0);
-    uint32_t* out = lists + p.list_off[k] + base + (incl - c);
+    uint32_t* out = a.lists + d.list_base + d.list_off[k] + base + (incl - c);
     s = s0;
     uint32_t w = 0;
-    for (uint32_t i = 0; i < len; i++) {
+    const uint32_t last = flags ? 32u - __clz(flags) : 0u;  // replay only up to the last kept rank
+    for (uint32_t i = 0; i < last; i++) {
         if (flags >> i & 1u) out[w++] = s;
         s = next_colex(s);
     }
@@ -210,143 +295,151 @@ __global__ void __launch_bounds__(256) k_filter(FilterParams p, const DevQuery* 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         done += __shfl_xor_sync(kFull, done, o);
-        steps += __shfl_xor_sync(kFull, steps, o);
+        rounds += __shfl_xor_sync(kFull, rounds, o);
     }
     if (lane == 0 && done) {
         atomicAdd(&cnt->unranked, (unsigned long long)done);
-        atomicAdd(&cnt->filter_steps, (unsigned long long)steps);
+        atomicAdd(&cnt->filter_steps, (unsigned long long)rounds);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Hash memo layout: per level k, capacity = the power of two >= 2x the level's
-// connected count (at least 16), carved from one arena.
-__global__ void k_hash_layout(int n, DevCounters* __restrict__ cnt, HashLayout* __restrict__ lay,
-                              unsigned long long arena_slots)
+// Hash memo layout: per query and level k, capacity = the power of two >= 2x
+// the level's connected count (at least 16), carved from one arena.
+__global__ void k_hash_layout(BatchArgs a)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     unsigned long long base = 0;
-    for (int k = 0; k < kLevels; k++) {
-        lay->base[k] = 0;
-        lay->mask[k] = 0;
+    for (int qi = 0; qi < a.nq; qi++) {
+        DevCounters* cnt = &a.out[qi].counters;
+        HashLayout* lay = a.layout + qi;
+        for (int k = 0; k < kLevels; k++) {
+            lay->base[k] = 0;
+            lay->mask[k] = 0;
+        }
+        const unsigned long long start = base;
+        const int n = a.desc[qi].n;
+        if (cnt->status == 0)
+            for (int k = 2; k <= n; k++) {
+                const unsigned long long want = 2ull * cnt->list_count[k];
+                unsigned long long cap = 16;
+                while (cap < want) cap <<= 1;
+                lay->base[k] = base;
+                lay->mask[k] = (unsigned int)(cap - 1);
+                base += cap;
+            }
+        lay->total_slots = base;  // end of this query's tables
+        cnt->memo_slots = base - start;
+        if (base > a.arena_slots) raise_status(cnt, MPDP_ERR_OOM);
     }
-    for (int k = 2; k <= n; k++) {
-        unsigned long long want = 2ull * cnt->list_count[k];
-        unsigned long long cap = 16;
-        while (cap < want) cap <<= 1;
-        lay->base[k] = base;
-        lay->mask[k] = (unsigned int)(cap - 1);
-        base += cap;
-    }
-    lay->total_slots = base;
-    cnt->memo_slots = base;
-    if (base > arena_slots) raise_status(cnt, MPDP_ERR_OOM);
 }
 
-__global__ void __launch_bounds__(256) k_hash_clear(const HashLayout* __restrict__ lay,
-                                                    const DevCounters* __restrict__ cnt,
-                                                    HashSlot* __restrict__ arena)
+__global__ void __launch_bounds__(256) k_hash_clear(BatchArgs a)
 {
-    if (cnt->status != 0) return;
-    const unsigned long long total = lay->total_slots;
-    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < total;
+    const unsigned long long total = a.layout[a.nq - 1].total_slots;
+    const unsigned long long lim = total < a.arena_slots ? total : a.arena_slots;
+    const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < lim;
          i += (unsigned long long)gridDim.x * blockDim.x)
-        reinterpret_cast<uint4*>(arena)[i] = z;
+        reinterpret_cast<double4_32a*>(a.arena)[i] = z;
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory copy of the query for the evaluate kernels.
-struct SharedQuery {
-    uint32_t adj[kMaxRels];
-    double card[kMaxRels];
-    double sel[kMaxRels * kMaxRels];
-};
-
-__device__ __forceinline__ void load_query(SharedQuery& sq, const DevQuery* __restrict__ q)
-{
-    for (int i = threadIdx.x; i < kMaxRels * kMaxRels; i += blockDim.x) sq.sel[i] = q->sel[i];
-    if (threadIdx.x < kMaxRels) {
-        sq.adj[threadIdx.x] = q->adj[threadIdx.x];
-        sq.card[threadIdx.x] = q->card[threadIdx.x];
-    }
-}
-
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
 // Cost one CCP pair (S_l, S_r) of S and fold it into the running best.
 // Singleton sides cost 0 (C_out base case) and need no memo read.
 template <class Memo>
 __device__ __forceinline__ void cost_pair(uint32_t sl, uint32_t sr, double card_s, const Memo& memo,
                                           DevCounters* cnt, double& bc, uint32_t& bl)
 {
-    double cl = (sl & (sl - 1u)) ? memo.get_cost(sl, cnt) : 0.0;
-    double cr = (sr & (sr - 1u)) ? memo.get_cost(sr, cnt) : 0.0;
-    double c = __dadd_rn(__dadd_rn(cl, cr), card_s);
-    uint32_t l = sl < sr ? sl : sr;
+    const double cl = (sl & (sl - 1u)) ? memo.get_cost(sl, cnt) : 0.0;
+    const double cr = (sr & (sr - 1u)) ? memo.get_cost(sr, cnt) : 0.0;
+    const double c = __dadd_rn(__dadd_rn(cl, cr), card_s);
+    const uint32_t l = sl < sr ? sl : sr;
     if (better(c, l, bc, bl)) {
         bc = c;
         bl = l;
     }
 }
 
+// Tiles of kEvalThreads sets of one query at level k for queries in mode `mode`.
+__device__ __forceinline__ uint32_t level_tiles(const BatchArgs& a, int q, int k, int mode)
+{
+    const QDesc& d = a.desc[q];
+    if (d.n < k || d.enumeration != mode) return 0u;
+    const DevCounters& c = a.out[q].counters;
+    if (c.status != 0) return 0u;
+    return (c.list_count[k] + kEvalThreads - 1) / kEvalThreads;
+}
+
 // ---------------------------------------------------------------------------
 // a4-a8, tree join graphs (Algorithm 2, MPDP:Tree).  One thread per connected
-// set S of level k.  Every connected S induces a tree; its CCP pairs are the
-// k-1 splits made by removing one edge of G[S].  A search from min(S) finds
-// each tree edge (x, v) once, with v on the far side from the root; the split
-// is S_l = grow({v}, S \ {x}) (the subtree under v), S_r = S \ S_l.  The best
-// (cost, left) over the k-1 splits is written to the memo: evaluate, prune and
-// scatter fused in one pass, one memo write per set.
+// set S of level k (tiles of 256 sets of one query per block iteration).
+// Every connected S induces a tree; its CCP pairs are the k-1 splits made by
+// removing one edge of G[S].  A search from min(S) finds each tree edge
+// (x, v) once, with v on the far side from the root; the split is
+// S_l = grow({v}, S \ {x}) (the subtree under v), S_r = S \ S_l.  The best
+// (cost, left) over the k-1 splits is written to the memo: evaluate, prune
+// and scatter fused in one pass, one memo write per set.
 template <class Memo>
-__global__ void __launch_bounds__(kEvalThreads) k_eval_tree(int k, uint32_t list_off,
-                                                            const DevQuery* __restrict__ q,
-                                                            DevCounters* __restrict__ cnt,
-                                                            const uint32_t* __restrict__ lists,
-                                                            Memo memo)
+__global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, Memo memo)
 {
     __shared__ SharedQuery sq;
-    __shared__ __align__(16) char s_memo[HashMemo::kSharedBytes];
-    load_query(sq, q);
+    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     memo.setup(s_memo);
-    __syncthreads();
-    if (cnt->status != 0) return;
-    const uint32_t count = cnt->list_count[k];
-    const uint32_t* list = lists + list_off;
+    const uint32_t tiles = block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, MPDP_ENUM_TREE); });
+    int cur = -1;
     unsigned long long sets = 0;
-    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count;
-         idx += gridDim.x * blockDim.x) {
-        const uint32_t s = list[idx];
-        const double card_s = card_of(s, sq.adj, sq.card, sq.sel);
-        double bc = __longlong_as_double(0x7ff0000000000000ll);  // +inf
-        uint32_t bl = kFull;
-        uint32_t vis = s & (0u - s), queue = vis;
-        while (queue) {
-            const int x = lowest(queue);
-            queue &= queue - 1u;
-            uint32_t ch = sq.adj[x] & s & ~vis;
-            vis |= ch;
-            queue |= ch;
-            const uint32_t rest = s & ~(1u << x);
-            while (ch) {
-                const int v = lowest(ch);
-                ch &= ch - 1u;
-                const uint32_t sl = grow(1u << v, rest, sq.adj);
-                cost_pair(sl, s ^ sl, card_s, memo, cnt, bc, bl);
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int qi = find_q(s_pref, a.nq, t);
+        if (qi != cur) {
+            if (cur >= 0) {
+                sets = warp_sum(sets);
+                if ((threadIdx.x & 31) == 0 && sets) {
+                    atomicAdd(&a.out[cur].counters.evaluated[k], sets * (unsigned long long)(k - 1));
+                    atomicAdd(&a.out[cur].counters.ccp[k], sets * (unsigned long long)(k - 1));
+                }
+                sets = 0;
             }
+            __syncthreads();
+            load_query(sq, a.query + qi);
+            memo.bind(a, qi);
+            __syncthreads();
+            cur = qi;
         }
-        memo.put(s, k, bc, bl, cnt);
-        sets++;
+        DevCounters* cnt = &a.out[qi].counters;
+        const uint32_t idx = (t - s_pref[qi]) * kEvalThreads + threadIdx.x;
+        if (idx < cnt->list_count[k]) {
+            const QDesc& d = a.desc[qi];
+            const uint32_t s = a.lists[d.list_base + d.list_off[k] + idx];
+            const double card_s = card_of(s, sq);
+            double bc = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+            uint32_t bl = kFull;
+            uint32_t vis = s & (0u - s), queue = vis;
+            while (queue) {
+                const int x = lowest(queue);
+                queue &= queue - 1u;
+                uint32_t ch = sq.adj[x] & s & ~vis;
+                vis |= ch;
+                queue |= ch;
+                const uint32_t rest = s & ~(1u << x);
+                while (ch) {
+                    const int v = lowest(ch);
+                    ch &= ch - 1u;
+                    const uint32_t sl = grow(1u << v, rest, sq.adj);
+                    cost_pair(sl, s ^ sl, card_s, memo, cnt, bc, bl);
+                }
+            }
+            memo.put(s, k, bc, card_s, bl, cnt);
+            sets++;
+        }
     }
-    sets = warp_sum(sets);
-    if ((threadIdx.x & 31) == 0 && sets) {
-        atomicAdd(&cnt->evaluated[k], sets * (unsigned long long)(k - 1));
-        atomicAdd(&cnt->ccp[k], sets * (unsigned long long)(k - 1));
+    if (cur >= 0) {
+        sets = warp_sum(sets);
+        if ((threadIdx.x & 31) == 0 && sets) {
+            atomicAdd(&a.out[cur].counters.evaluated[k], sets * (unsigned long long)(k - 1));
+            atomicAdd(&a.out[cur].counters.ccp[k], sets * (unsigned long long)(k - 1));
+        }
     }
 }
 
@@ -449,40 +542,52 @@ __device__ __forceinline__ uint32_t deposit(uint32_t t, uint32_t mask)
 // For each block B of G[S] and each lb (min(B) in lb, lb != B): rb = B \ lb;
 // the CCP block keeps the pair when lb and rb both induce connected subgraphs
 // (they are adjacent since B is connected); then S_l = grow(lb, S \ rb),
-// S_r = S \ S_l.  Sets whose pair count exceeds heavy_threshold go to the
+// S_r = S \ S_l.  Sets whose pair count exceeds the heavy threshold go to the
 // block-per-set kernel instead.
 template <class Memo>
-__global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(int k, uint32_t list_off,
-                                                              uint32_t heavy_threshold,
-                                                              const DevQuery* __restrict__ q,
-                                                              DevCounters* __restrict__ cnt,
-                                                              const uint32_t* __restrict__ lists,
-                                                              uint32_t* __restrict__ heavy, Memo memo)
+__global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k, Memo memo)
 {
     __shared__ SharedQuery sq;
-    __shared__ __align__(16) char s_memo[HashMemo::kSharedBytes];
-    load_query(sq, q);
+    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     memo.setup(s_memo);
-    __syncthreads();
-    if (cnt->status != 0) return;
-    const uint32_t count = cnt->list_count[k];
-    const uint32_t* list = lists + list_off;
+    const uint32_t tiles = block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, MPDP_ENUM_BLOCKS); });
+    int cur = -1;
     unsigned long long evaluated = 0, ccp = 0;
-    const uint32_t iters = (count + gridDim.x * blockDim.x - 1) / (gridDim.x * blockDim.x);
-    for (uint32_t it = 0; it < iters; it++) {
-        const uint32_t idx = it * gridDim.x * blockDim.x + blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int qi = find_q(s_pref, a.nq, t);
+        if (qi != cur) {
+            if (cur >= 0) {
+                evaluated = warp_sum(evaluated);
+                ccp = warp_sum(ccp);
+                if (lane == 0) {
+                    if (evaluated) atomicAdd(&a.out[cur].counters.evaluated[k], evaluated);
+                    if (ccp) atomicAdd(&a.out[cur].counters.ccp[k], ccp);
+                }
+                evaluated = ccp = 0;
+            }
+            __syncthreads();
+            load_query(sq, a.query + qi);
+            memo.bind(a, qi);
+            __syncthreads();
+            cur = qi;
+        }
+        DevCounters* cnt = &a.out[qi].counters;
+        const QDesc& d = a.desc[qi];
+        const uint32_t idx = (t - s_pref[qi]) * kEvalThreads + threadIdx.x;
         bool to_heavy = false;
         uint32_t s = 0u;
-        if (idx < count) {
-            s = list[idx];
+        if (idx < cnt->list_count[k]) {
+            s = a.lists[d.list_base + d.list_off[k] + idx];
             uint32_t blk[kMaxRels];
             const int nb = find_blocks(s, sq.adj, blk);
             uint32_t pairs = 0u;
             for (int j = 0; j < nb; j++) pairs += block_pairs(blk[j]);
-            if (pairs > heavy_threshold) {
+            if (pairs > (uint32_t)a.heavy_threshold) {
                 to_heavy = true;
             } else {
-                const double card_s = card_of(s, sq.adj, sq.card, sq.sel);
+                const double card_s = card_of(s, sq);
                 double bc = __longlong_as_double(0x7ff0000000000000ll);
                 uint32_t bl = kFull;
                 evaluated += pairs;
@@ -497,24 +602,25 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(int k, uint32_t li
                         cost_pair(sl, s ^ sl, card_s, memo, cnt, bc, bl);
                     }
                 }
-                memo.put(s, k, bc, bl, cnt);
+                memo.put(s, k, bc, card_s, bl, cnt);
             }
         }
         // warp-aggregated append of heavy sets
         const unsigned bal = __ballot_sync(kFull, to_heavy);
         if (bal) {
-            const int lane = threadIdx.x & 31;
             uint32_t base = 0;
             if (lane == 0) base = atomicAdd(&cnt->heavy_count[k], (uint32_t)__popc(bal));
             base = __shfl_sync(kFull, base, 0);
-            if (to_heavy) heavy[list_off + base + __popc(bal & ((1u << lane) - 1u))] = s;
+            if (to_heavy) a.heavy[d.list_base + d.list_off[k] + base + __popc(bal & ((1u << lane) - 1u))] = s;
         }
     }
-    evaluated = warp_sum(evaluated);
-    ccp = warp_sum(ccp);
-    if ((threadIdx.x & 31) == 0) {
-        if (evaluated) atomicAdd(&cnt->evaluated[k], evaluated);
-        if (ccp) atomicAdd(&cnt->ccp[k], ccp);
+    if (cur >= 0) {
+        evaluated = warp_sum(evaluated);
+        ccp = warp_sum(ccp);
+        if (lane == 0) {
+            if (evaluated) atomicAdd(&a.out[cur].counters.evaluated[k], evaluated);
+            if (ccp) atomicAdd(&a.out[cur].counters.ccp[k], ccp);
+        }
     }
 }
 
@@ -525,49 +631,67 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(int k, uint32_t li
 // memory and grows/costs them only when 32 are ready, so no lane idles on an
 // invalid pair during the expensive part.
 template <class Memo>
-__global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(int k, uint32_t list_off, int use_ccc,
-                                                             const DevQuery* __restrict__ q,
-                                                             DevCounters* __restrict__ cnt,
-                                                             const uint32_t* __restrict__ heavy,
-                                                             Memo memo)
+__global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k, Memo memo)
 {
     constexpr int kWarps = kEvalThreads / 32;
     __shared__ SharedQuery sq;
-    __shared__ __align__(16) char s_memo[HashMemo::kSharedBytes];
+    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     __shared__ uint32_t s_blk[kMaxRels];
-    __shared__ uint32_t s_pref[kMaxRels + 1];
+    __shared__ uint32_t s_bpref[kMaxRels + 1];
     __shared__ int s_nb;
     __shared__ double s_card;
     __shared__ uint32_t s_stash_l[kWarps][64];
     __shared__ uint32_t s_stash_r[kWarps][64];
     __shared__ double s_bc[kWarps];
     __shared__ uint32_t s_bl[kWarps];
-    load_query(sq, q);
     memo.setup(s_memo);
-    __syncthreads();
-    if (cnt->status != 0) return;
-    const uint32_t count = cnt->heavy_count[k];
+    const uint32_t total_sets = block_prefix(a.nq, s_pref, [&](int q) -> uint32_t {
+        const QDesc& d = a.desc[q];
+        if (d.n < k || d.enumeration != MPDP_ENUM_BLOCKS || a.out[q].counters.status != 0) return 0u;
+        return a.out[q].counters.heavy_count[k];
+    });
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long ccp = 0, evaluated = 0;
-    for (uint32_t h = blockIdx.x; h < count; h += gridDim.x) {
-        const uint32_t s = heavy[list_off + h];
+    int cur = -1;
+    unsigned long long ccp = 0, evaluated = 0, heavy = 0;
+    for (uint32_t h = blockIdx.x; h < total_sets; h += gridDim.x) {
+        const int qi = find_q(s_pref, a.nq, h);
+        if (qi != cur) {
+            if (cur >= 0) {
+                if (lane == 0 && ccp) atomicAdd(&a.out[cur].counters.ccp[k], ccp);
+                if (threadIdx.x == 0) {
+                    if (evaluated) atomicAdd(&a.out[cur].counters.evaluated[k], evaluated);
+                    if (heavy) atomicAdd(&a.out[cur].counters.heavy, heavy);
+                }
+                ccp = evaluated = heavy = 0;
+            }
+            __syncthreads();
+            load_query(sq, a.query + qi);
+            memo.bind(a, qi);
+            __syncthreads();
+            cur = qi;
+        }
+        DevCounters* cnt = &a.out[qi].counters;
+        const QDesc& d = a.desc[qi];
+        const uint32_t s = a.heavy[d.list_base + d.list_off[k] + (h - s_pref[qi])];
         if (threadIdx.x == 0) {
             uint32_t blk[kMaxRels];
             const int nb = find_blocks(s, sq.adj, blk);
             uint32_t acc = 0u;
             for (int j = 0; j < nb; j++) {
                 s_blk[j] = blk[j];
-                s_pref[j] = acc;
+                s_bpref[j] = acc;
                 acc += block_pairs(blk[j]);
             }
-            s_pref[nb] = acc;
+            s_bpref[nb] = acc;
             s_nb = nb;
-            s_card = card_of(s, sq.adj, sq.card, sq.sel);
+            s_card = card_of(s, sq);
             evaluated += acc;
+            heavy++;
         }
         __syncthreads();
         const int nb = s_nb;
-        const uint32_t total = s_pref[nb];
+        const uint32_t total = s_bpref[nb];
         const double card_s = s_card;
         double bc = __longlong_as_double(0x7ff0000000000000ll);
         uint32_t bl = kFull;
@@ -579,16 +703,16 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(int k, uint32_t lis
             uint32_t lb = 0u, rb = 0u;
             if (p < total) {
                 int j = 0;
-                while (j + 1 < nb && s_pref[j + 1] <= p) j++;
+                while (j + 1 < nb && s_bpref[j + 1] <= p) j++;
                 const uint32_t b = s_blk[j];
                 const uint32_t mn = b & (0u - b);
-                lb = mn | deposit(p - s_pref[j], b ^ mn);
+                lb = mn | deposit(p - s_bpref[j], b ^ mn);
                 rb = b ^ lb;
                 valid = connected(lb, sq.adj) && connected(rb, sq.adj);
             }
             const unsigned bal = __ballot_sync(kFull, valid);
             ccp += (lane == 0) ? (unsigned long long)__popc(bal) : 0ull;
-            if (!use_ccc) {
+            if (!a.use_ccc) {
                 if (valid) {
                     const uint32_t sl = grow(lb, s & ~rb, sq.adj);
                     cost_pair(sl, s ^ sl, card_s, memo, cnt, bc, bl);
@@ -611,7 +735,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(int k, uint32_t lis
             }
             __syncwarp();
         }
-        if (use_ccc && lane < (int)stash) {
+        if (a.use_ccc && lane < (int)stash) {
             const uint32_t l2 = s_stash_l[warp][lane], r2 = s_stash_r[warp][lane];
             const uint32_t sl = grow(l2, s & ~r2, sq.adj);
             cost_pair(sl, s ^ sl, card_s, memo, cnt, bc, bl);
@@ -637,78 +761,116 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(int k, uint32_t lis
                     bc = s_bc[w];
                     bl = s_bl[w];
                 }
-            memo.put(s, k, bc, bl, cnt);
+            memo.put(s, k, bc, card_s, bl, cnt);
         }
         __syncthreads();
     }
-    if (lane == 0 && ccp) atomicAdd(&cnt->ccp[k], ccp);
-    if (threadIdx.x == 0) {
-        if (evaluated) atomicAdd(&cnt->evaluated[k], evaluated);
-        if (count && blockIdx.x == 0) atomicAdd(&cnt->heavy, (unsigned long long)count);
+    if (cur >= 0) {
+        if (lane == 0 && ccp) atomicAdd(&a.out[cur].counters.ccp[k], ccp);
+        if (threadIdx.x == 0) {
+            if (evaluated) atomicAdd(&a.out[cur].counters.evaluated[k], evaluated);
+            if (heavy) atomicAdd(&a.out[cur].counters.heavy, heavy);
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
-// a9: plan fetch.  From the full set, read (cost, left) from the memo and
-// expand left and S \ left, breadth first; leaves are single relations.
+// a9: plan fetch (one warp per query).  From the full set, read (cost, card,
+// left) from the memo and expand left and S \ left, one tree depth at a time
+// with one lane per node of that depth; nodes end up in breadth-first order.
 template <class Memo>
-__global__ void k_extract(const DevQuery* __restrict__ q, DevCounters* __restrict__ cnt,
-                          DevResult* __restrict__ res, Memo memo)
+__global__ void __launch_bounds__(32) k_extract(BatchArgs a, Memo memo)
 {
-    __shared__ __align__(16) char s_memo[HashMemo::kSharedBytes];
+    __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
+    const int qi = blockIdx.x, lane = threadIdx.x;
     memo.setup(s_memo);
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    const int n = q->n;
-    res->n_nodes = 0;
-    res->cost = 0.0;
+    memo.bind(a, qi);
+    __syncwarp();
+    DevOut& o = a.out[qi];
+    DevResult& res = o.result;
+    DevCounters* cnt = &o.counters;
+    const DevQuery* q = a.query + qi;
+    const int n = a.desc[qi].n;
     if (cnt->status != 0 || n < 1) {
-        res->status = cnt->status;
+        if (lane == 0) {
+            res.n_nodes = 0;
+            res.cost = 0.0;
+            res.status = cnt->status;
+        }
         return;
     }
     const uint32_t full = (n == 32) ? kFull : ((1u << n) - 1u);
-    int m = 1;
-    res->nodes[0].set = full;
-    for (int i = 0; i < m; i++) {
-        mpdp_plan_node& nd = res->nodes[i];
-        const uint32_t s = (uint32_t)nd.set;
-        nd.n_leaves = __popc(s);
-        if ((s & (s - 1u)) == 0u) {
-            nd.left = nd.right = -1;
-            nd.rel = lowest(s);
-            nd.card = q->card[nd.rel];
-            nd.cost = 0.0;
-            continue;
+    if (lane == 0) res.nodes[0].set = full;
+    __syncwarp();
+    int lo = 0, hi = 1;  // current depth: nodes [lo, hi)
+    bool bad = false;
+    while (lo < hi) {
+        int next = hi;
+        for (int base = lo; base < hi; base += 32) {
+            const int i = base + lane;
+            bool internal = false;
+            uint32_t s = 0u, l = 0u;
+            double c = 0.0, card = 0.0;
+            if (i < hi) {
+                s = (uint32_t)res.nodes[i].set;
+                internal = (s & (s - 1u)) != 0u;
+                if (internal) {
+                    memo.get(s, c, card, l, cnt);
+                    if (l == 0u || (l & ~s) != 0u || l == s) {
+                        bad = true;
+                        internal = false;
+                    }
+                }
+            }
+            const unsigned bal = __ballot_sync(kFull, internal);
+            const int pos = next + 2 * __popc(bal & ((1u << lane) - 1u));
+            if (i < hi) {
+                mpdp_plan_node& nd = res.nodes[i];
+                nd.n_leaves = __popc(s);
+                if (internal && pos + 1 < kPlanNodes) {
+                    nd.left = pos;
+                    nd.right = pos + 1;
+                    nd.rel = -1;
+                    nd.cost = c;
+                    nd.card = card;
+                    res.nodes[pos].set = l;
+                    res.nodes[pos + 1].set = s ^ l;
+                } else {
+                    nd.left = nd.right = -1;
+                    nd.rel = lowest(s);
+                    nd.card = q->card[nd.rel];
+                    nd.cost = 0.0;
+                }
+            }
+            next += 2 * __popc(bal);
+            __syncwarp();
         }
-        double c;
-        uint32_t l;
-        memo.get(s, c, l, cnt);
-        if (l == 0u || (l & ~s) != 0u || l == s || m + 2 > 2 * kMaxRels - 1) {
-            raise_status(cnt, MPDP_ERR_INTERNAL);
+        lo = hi;
+        hi = next;
+        if (hi > kPlanNodes) {
+            bad = true;
             break;
         }
-        nd.rel = -1;
-        nd.cost = c;
-        nd.card = card_of(s, q->adj, q->card, q->sel);
-        nd.left = m;
-        res->nodes[m].set = l;
-        nd.right = m + 1;
-        res->nodes[m + 1].set = s ^ l;
-        m += 2;
     }
-    res->n_nodes = m;
-    res->cost = res->nodes[0].cost;
-    res->status = cnt->status;
+    if (__any_sync(kFull, bad) && lane == 0) raise_status(cnt, MPDP_ERR_INTERNAL);
+    __syncwarp();
+    if (lane == 0) {
+        res.n_nodes = hi;
+        res.cost = res.nodes[0].cost;
+        res.status = cnt->status;
+    }
 }
 
-// Memo read-back of arbitrary connected sets (parity checks).
+// Memo read-back of arbitrary connected sets of one query (parity checks).
 template <class Memo>
-__global__ void k_memo_lookup(const uint32_t* __restrict__ sets, int count, double* __restrict__ costs,
-                              uint32_t* __restrict__ lefts, DevCounters* __restrict__ cnt, Memo memo)
+__global__ void k_memo_lookup(BatchArgs a, int qi, const uint32_t* __restrict__ sets, int count,
+                              double* __restrict__ costs, uint32_t* __restrict__ lefts, Memo memo)
 {
-    __shared__ __align__(16) char s_memo[HashMemo::kSharedBytes];
+    __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     memo.setup(s_memo);
+    memo.bind(a, qi);
     __syncthreads();
+    DevCounters* cnt = &a.out[qi].counters;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         const uint32_t s = sets[i];
         if ((s & (s - 1u)) == 0u) {
@@ -716,9 +878,9 @@ __global__ void k_memo_lookup(const uint32_t* __restrict__ sets, int count, doub
             lefts[i] = 0u;
             continue;
         }
-        double c;
+        double c, card;
         uint32_t l;
-        memo.get(s, c, l, cnt);
+        memo.get(s, c, card, l, cnt);
         costs[i] = c;
         lefts[i] = l;
     }
@@ -727,7 +889,7 @@ __global__ void k_memo_lookup(const uint32_t* __restrict__ sets, int count, doub
 // ---------------------------------------------------------------------------
 // Host-side launch sequencing.
 
-static unsigned long long binom_host(int n, int k)
+unsigned long long binom_host(int n, int k)
 {
     if (k < 0 || k > n) return 0;
     unsigned long long r = 1;
@@ -735,21 +897,11 @@ static unsigned long long binom_host(int n, int k)
     return r;
 }
 
-void level_layout(int n, uint32_t* list_off /* [kLevels] */)
-{
-    unsigned long long off = 0;
-    for (int k = 0; k < kLevels; k++) list_off[k] = 0;
-    for (int k = 2; k <= n; k++) {
-        list_off[k] = (uint32_t)off;
-        off += binom_host(n, k);
-    }
-}
-
 size_t list_entries(int n)
 {
     unsigned long long off = 0;
     for (int k = 2; k <= n; k++) off += binom_host(n, k);
-    return (size_t)(off ? off : 1);
+    return (size_t)off;
 }
 
 size_t hash_arena_slots(int n)
@@ -760,7 +912,25 @@ size_t hash_arena_slots(int n)
         while (cap < want) cap <<= 1;
         total += cap;
     }
-    return (size_t)(total ? total : 16);
+    return (size_t)total;
+}
+
+void fill_levels(QDesc& d, int run, uint32_t& filter_blocks)
+{
+    const int n = d.n;
+    unsigned long long off = 0, wb = 0;
+    for (int k = 0; k < kLevels; k++) d.list_off[k] = 0;
+    for (int k = 0; k <= kLevels; k++) d.warp_begin[k] = 0;
+    for (int k = 2; k <= n; k++) {
+        const unsigned long long c = binom_host(n, k);
+        d.list_off[k] = (uint32_t)off;
+        off += c;
+        d.warp_begin[k] = (uint32_t)wb;
+        wb += (c + 32ull * run - 1) / (32ull * run);
+    }
+    for (int k = (n >= 2 ? n + 1 : 0); k <= kLevels; k++) d.warp_begin[k] = (uint32_t)wb;
+    const unsigned warps_per_block = kFilterThreads / 32;
+    filter_blocks = (uint32_t)((wb + warps_per_block - 1) / warps_per_block);
 }
 
 struct HookScope {
@@ -778,122 +948,96 @@ struct HookScope {
 };
 
 template <class Memo>
-static void launch_levels(const Workspace& ws, const PipelineCfg& pc, const uint32_t* list_off,
-                          Memo memo, cudaStream_t st, int& launches, LaunchHook* hook)
+static void launch_levels(const BatchArgs& a, const BatchPlan& bp, Memo memo, cudaStream_t st, int& launches,
+                          LaunchHook* hook)
 {
-    const int n = pc.n;
-    const int cap_blocks = pc.num_sms * pc.blocks_per_sm;
-    for (int k = 2; k <= n; k++) {
-        const unsigned long long c = binom_host(n, k);
-        int grid = (int)((c + kEvalThreads - 1) / kEvalThreads);
-        if (grid > cap_blocks) grid = cap_blocks;
-        if (grid < 1) grid = 1;
-        if (pc.enumeration == MPDP_ENUM_TREE) {
+    const int cap_blocks = bp.num_sms * bp.blocks_per_sm;
+    for (int k = 2; k <= a.max_n; k++) {
+        const unsigned long long tree_tiles = bp.tree_tiles[k], block_tiles = bp.block_tiles[k];
+        if (tree_tiles) {
             HookScope hs(hook, MPDP_KC_EVAL, st);
-            k_eval_tree<Memo><<<grid, kEvalThreads, 0, st>>>(k, list_off[k], ws.query, ws.counters,
-                                                             ws.lists, memo);
+            const int grid = (int)(tree_tiles < (unsigned long long)cap_blocks ? tree_tiles : cap_blocks);
+            k_eval_tree<Memo><<<grid, kEvalThreads, 0, st>>>(a, k, memo);
             launches++;
-        } else {
+        }
+        if (block_tiles) {
             {
                 HookScope hs(hook, MPDP_KC_EVAL, st);
-                k_eval_blocks<Memo><<<grid, kEvalThreads, 0, st>>>(
-                    k, list_off[k], (uint32_t)pc.heavy_threshold, ws.query, ws.counters, ws.lists,
-                    ws.heavy, memo);
+                const int grid = (int)(block_tiles < (unsigned long long)cap_blocks ? block_tiles : cap_blocks);
+                k_eval_blocks<Memo><<<grid, kEvalThreads, 0, st>>>(a, k, memo);
             }
-            int hgrid = (int)(c < (unsigned long long)cap_blocks ? c : (unsigned long long)cap_blocks);
-            if (hgrid < 1) hgrid = 1;
             {
                 HookScope hs(hook, MPDP_KC_HEAVY, st);
-                k_eval_heavy<Memo><<<hgrid, kEvalThreads, 0, st>>>(k, list_off[k], pc.use_ccc, ws.query,
-                                                                   ws.counters, ws.heavy, memo);
+                const unsigned long long hs_max = bp.block_sets[k];
+                const int grid = (int)(hs_max < (unsigned long long)cap_blocks ? hs_max : cap_blocks);
+                k_eval_heavy<Memo><<<grid > 0 ? grid : 1, kEvalThreads, 0, st>>>(a, k, memo);
             }
             launches += 2;
         }
     }
-    {
-        HookScope hs(hook, MPDP_KC_EXTRACT, st);
-        k_extract<Memo><<<1, 32, 0, st>>>(ws.query, ws.counters, ws.result, memo);
-    }
+    HookScope hs(hook, MPDP_KC_EXTRACT, st);
+    k_extract<Memo><<<a.nq, 32, 0, st>>>(a, memo);
     launches++;
 }
 
-cudaError_t enqueue_pipeline(const Workspace& ws, const PipelineCfg& pc, cudaStream_t st,
+cudaError_t enqueue_pipeline(const BatchArgs& a, const BatchPlan& bp, int memo_kind, cudaStream_t st,
                              int* launches_out, LaunchHook* hook)
 {
     int launches = 0;
-    const int n = pc.n;
-    const bool dense = pc.memo_kind == MPDP_MEMO_DENSE;
+    const bool dense = memo_kind == MPDP_MEMO_DENSE;
     {
         HookScope hs(hook, MPDP_KC_INGEST, st);
-        k_ingest<<<1, 256, 0, st>>>(ws.staged, ws.query, ws.counters, ws.dcost, ws.dleft, dense ? 1 : 0);
+        k_ingest<<<a.nq, 256, 0, st>>>(a, dense ? 1 : 0);
     }
     launches++;
-
-    FilterParams fp;
-    memset(&fp, 0, sizeof(fp));
-    fp.n = n;
-    fp.run = pc.run_length;
-    level_layout(n, fp.list_off);
-    unsigned long long wb = 0;
-    for (int k = 0; k <= kLevels; k++) fp.warp_begin[k] = 0;
-    for (int k = 2; k <= n; k++) {
-        const unsigned long long c = binom_host(n, k);
-        fp.nranks[k] = (uint32_t)c;
-        fp.warp_begin[k] = (uint32_t)wb;
-        wb += (c + 32ull * pc.run_length - 1) / (32ull * pc.run_length);
-    }
-    for (int k = n + 1; k <= kLevels; k++) fp.warp_begin[k] = (uint32_t)wb;
-    if (n >= 2) fp.warp_begin[n + 1] = (uint32_t)wb;
-    if (wb > 0) {
-        const unsigned long long threads = wb * 32ull;
-        const int blocks = (int)((threads + 255) / 256);
+    if (bp.filter_blocks > 0) {
         HookScope hs(hook, MPDP_KC_FILTER, st);
-        k_filter<<<blocks, 256, 0, st>>>(fp, ws.query, ws.counters, ws.lists);
+        k_filter<<<bp.filter_blocks, kFilterThreads, 0, st>>>(a);
         launches++;
     }
     if (dense) {
-        DenseMemo memo{ws.dcost, ws.dleft};
-        launch_levels(ws, pc, fp.list_off, memo, st, launches, hook);
+        DenseMemo memo{a.memo, a.left, nullptr, nullptr};
+        launch_levels(a, bp, memo, st, launches, hook);
     } else {
         {
             HookScope hs(hook, MPDP_KC_MEMO_INIT, st);
-            k_hash_layout<<<1, 1, 0, st>>>(n, ws.counters, ws.layout, ws.arena_slots);
-            k_hash_clear<<<pc.num_sms * 4, 256, 0, st>>>(ws.layout, ws.counters, ws.arena);
+            k_hash_layout<<<1, 1, 0, st>>>(a);
+            k_hash_clear<<<bp.num_sms * 4, 256, 0, st>>>(a);
         }
         launches += 2;
-        HashMemo memo{ws.arena, ws.layout, nullptr, nullptr};
-        launch_levels(ws, pc, fp.list_off, memo, st, launches, hook);
+        HashMemo memo{a.arena, nullptr, nullptr};
+        launch_levels(a, bp, memo, st, launches, hook);
     }
     if (launches_out) *launches_out = launches;
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_stage_device(const double* card, const mpdp_edge* edges, int n, int m,
-                                 int cost_model, StagedQuery* staged, cudaStream_t st, LaunchHook* hook)
+cudaError_t enqueue_stage_device(const BatchArgs& a, const double* card, const mpdp_edge* edges, cudaStream_t st,
+                                 LaunchHook* hook)
 {
     HookScope hs(hook, MPDP_KC_STAGE, st);
-    k_stage<<<1, 256, 0, st>>>(card, edges, n, m, cost_model, staged);
+    k_stage<<<a.nq, 256, 0, st>>>(a, card, edges);
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_publish(const Workspace& ws, mpdp_plan_node* nodes, double* cost, int32_t* status,
+cudaError_t enqueue_publish(const BatchArgs& a, mpdp_plan_node* nodes, double* cost, int32_t* status,
                             cudaStream_t st, LaunchHook* hook)
 {
     HookScope hs(hook, MPDP_KC_PUBLISH, st);
-    k_publish<<<1, 64, 0, st>>>(ws.result, ws.counters, nodes, cost, status);
+    k_publish<<<a.nq, 64, 0, st>>>(a, nodes, cost, status);
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_memo_lookup(const Workspace& ws, int memo_kind, const uint32_t* d_sets, int count,
+cudaError_t enqueue_memo_lookup(const BatchArgs& a, int memo_kind, int qi, const uint32_t* d_sets, int count,
                                 double* d_costs, uint32_t* d_lefts, cudaStream_t st)
 {
     const int grid = (count + 255) / 256 > 0 ? (count + 255) / 256 : 1;
     if (memo_kind == MPDP_MEMO_DENSE) {
-        DenseMemo memo{ws.dcost, ws.dleft};
-        k_memo_lookup<DenseMemo><<<grid, 256, 0, st>>>(d_sets, count, d_costs, d_lefts, ws.counters, memo);
+        DenseMemo memo{a.memo, a.left, nullptr, nullptr};
+        k_memo_lookup<DenseMemo><<<grid, 256, 0, st>>>(a, qi, d_sets, count, d_costs, d_lefts, memo);
     } else {
-        HashMemo memo{ws.arena, ws.layout, nullptr, nullptr};
-        k_memo_lookup<HashMemo><<<grid, 256, 0, st>>>(d_sets, count, d_costs, d_lefts, ws.counters, memo);
+        HashMemo memo{a.arena, nullptr, nullptr};
+        k_memo_lookup<HashMemo><<<grid, 256, 0, st>>>(a, qi, d_sets, count, d_costs, d_lefts, memo);
     }
     return cudaGetLastError();
 }

@@ -1,4 +1,4 @@
-// Host-side view of the device workspace and the launch sequence of one query.
+// Host-side view of a batch launch: plan (grid sizes) and launch sequence.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -11,41 +11,14 @@
 
 namespace mpdp {
 
-// Device buffers of one query slot.  All pointers are device memory.
-struct Workspace {
-    int n_cap = 0;                 // largest n the buffers were sized for
-    int memo_kind = MPDP_MEMO_DENSE;
-    StagedQuery* staged = nullptr;
-    DevQuery* query = nullptr;
-    DevCounters* counters = nullptr;
-    DevResult* result = nullptr;
-    uint32_t* lists = nullptr;     // per level k: C(n,k) slots (connected k-sets)
-    uint32_t* heavy = nullptr;     // per level k: C(n,k) slots (heavy k-sets)
-    double* dcost = nullptr;       // dense memo: cost[S], S < 2^n
-    uint32_t* dleft = nullptr;     // dense memo: left[S]
-    HashSlot* arena = nullptr;     // hash memo slots
-    unsigned long long arena_slots = 0;
-    HashLayout* layout = nullptr;
-};
-
-struct PipelineCfg {
-    int n = 0;
-    int enumeration = MPDP_ENUM_TREE;  // resolved: TREE or BLOCKS
-    int memo_kind = MPDP_MEMO_DENSE;
-    int heavy_threshold = 64;
-    int use_ccc = 1;
-    int run_length = 32;
+// Grid sizing of one batch, computed on the host from the queries' sizes.
+struct BatchPlan {
     int num_sms = 152;
     int blocks_per_sm = 4;
-};
-
-// Parameters of the unrank + filter launch (passed by value).
-struct FilterParams {
-    int n;
-    int run;                              // consecutive ranks per lane (<= 32)
-    uint32_t nranks[kLevels];             // C(n, k)
-    uint32_t warp_begin[kLevels + 1];     // first warp of level k
-    uint32_t list_off[kLevels];           // level k's region in the list buffer
+    uint32_t filter_blocks = 0;
+    unsigned long long tree_tiles[kLevels] = {};   // upper bound of level-k tiles, tree queries
+    unsigned long long block_tiles[kLevels] = {};  // same, block-mode queries
+    unsigned long long block_sets[kLevels] = {};   // upper bound of level-k sets, block-mode queries
 };
 
 // Hook around every kernel launch (profiling mode): begin/end are called on
@@ -56,18 +29,20 @@ struct LaunchHook {
     virtual void end(int cls, cudaStream_t st) = 0;
 };
 
-void level_layout(int n, uint32_t* list_off);
+unsigned long long binom_host(int n, int k);
 size_t list_entries(int n);
 size_t hash_arena_slots(int n);
+// Per-level list offsets and filter warp ranges of one query; returns the
+// query's filter block count in filter_blocks.
+void fill_levels(QDesc& d, int run, uint32_t& filter_blocks);
 
-cudaError_t enqueue_pipeline(const Workspace& ws, const PipelineCfg& pc, cudaStream_t st,
+cudaError_t enqueue_pipeline(const BatchArgs& a, const BatchPlan& bp, int memo_kind, cudaStream_t st,
                              int* launches, LaunchHook* hook = nullptr);
-cudaError_t enqueue_stage_device(const double* card, const mpdp_edge* edges, int n, int m,
-                                 int cost_model, StagedQuery* staged, cudaStream_t st,
-                                 LaunchHook* hook = nullptr);
-cudaError_t enqueue_publish(const Workspace& ws, mpdp_plan_node* nodes, double* cost,
-                            int32_t* status, cudaStream_t st, LaunchHook* hook = nullptr);
-cudaError_t enqueue_memo_lookup(const Workspace& ws, int memo_kind, const uint32_t* d_sets,
+cudaError_t enqueue_stage_device(const BatchArgs& a, const double* card, const mpdp_edge* edges,
+                                 cudaStream_t st, LaunchHook* hook = nullptr);
+cudaError_t enqueue_publish(const BatchArgs& a, mpdp_plan_node* nodes, double* cost, int32_t* status,
+                            cudaStream_t st, LaunchHook* hook = nullptr);
+cudaError_t enqueue_memo_lookup(const BatchArgs& a, int memo_kind, int qi, const uint32_t* d_sets,
                                 int count, double* d_costs, uint32_t* d_lefts, cudaStream_t st);
 
 }  // namespace mpdp

@@ -91,8 +91,9 @@ EXPORTS = [
     "mpdp_workspace_bytes", "mpdp_optimize", "mpdp_optimize_batch", "mpdp_get_plan",
     "mpdp_release", "mpdp_optimize_device", "mpdp_sync", "mpdp_memo_lookup",
     "mpdp_last_launch_count", "mpdp_strerror", "mpdp_last_error", "mpdp_abi_version",
-    "mpdp_profile", "mpdp_profile_read",
+    "mpdp_profile", "mpdp_profile_read", "mpdp_optimize_batch_device",
 ]
+PLAN_STRIDE = 63
 
 KERNEL_CLASSES = ["stage", "ingest", "filter", "memo_init", "eval", "heavy", "extract", "publish"]
 
@@ -131,6 +132,10 @@ def load(build_if_missing: bool = True):
     L.mpdp_optimize_device.argtypes = [c_ctx, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]
+    L.mpdp_optimize_batch_device.argtypes = [c_ctx, ctypes.c_int32, P(ctypes.c_int32),
+                                             P(ctypes.c_int32), ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]
     L.mpdp_sync.argtypes = [c_ctx]
     L.mpdp_memo_lookup.argtypes = [c_ctx, ctypes.c_int64, P(ctypes.c_uint64), ctypes.c_int32,
                                    P(ctypes.c_double), P(ctypes.c_uint64)]
@@ -143,7 +148,7 @@ def load(build_if_missing: bool = True):
     L.mpdp_abi_version.restype = ctypes.c_int32
     L.mpdp_profile.argtypes = [c_ctx, ctypes.c_int]
     L.mpdp_profile_read.argtypes = [c_ctx, P(ctypes.c_double), P(ctypes.c_uint64)]
-    for f in ("mpdp_profile", "mpdp_profile_read", "mpdp_create", "mpdp_set_config", "mpdp_get_config", "mpdp_optimize",
+    for f in ("mpdp_optimize_batch_device", "mpdp_profile", "mpdp_profile_read", "mpdp_create", "mpdp_set_config", "mpdp_get_config", "mpdp_optimize",
               "mpdp_optimize_batch", "mpdp_get_plan", "mpdp_release", "mpdp_optimize_device",
               "mpdp_sync", "mpdp_memo_lookup"):
         getattr(L, f).restype = ctypes.c_int
@@ -336,6 +341,20 @@ class Optimizer:
                                             ptr(d_edges), 0, ptr(d_nodes), ptr(d_cost),
                                             ptr(d_status))
         self._check(rc, "mpdp_optimize_device")
+
+    def optimize_batch_device(self, n_rels: Sequence[int], n_edges: Sequence[int], d_card, d_edges,
+                              d_nodes, d_cost, d_status):
+        """Enqueue one device batch: d_card / d_edges hold the queries' values
+        back to back in device memory; d_nodes receives PLAN_STRIDE nodes per
+        query, d_cost and d_status one entry per query.  Returns at once."""
+        def ptr(x):
+            return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+        nq = len(n_rels)
+        nr = (ctypes.c_int32 * nq)(*[int(x) for x in n_rels])
+        ne = (ctypes.c_int32 * nq)(*[int(x) for x in n_edges])
+        rc = self._lib.mpdp_optimize_batch_device(self._ctx, nq, nr, ne, ptr(d_card), ptr(d_edges), 0,
+                                                  ptr(d_nodes), ptr(d_cost), ptr(d_status))
+        self._check(rc, "mpdp_optimize_batch_device")
 
     def sync(self) -> int:
         return int(self._lib.mpdp_sync(self._ctx))

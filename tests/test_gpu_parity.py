@@ -286,3 +286,57 @@ def test_device_path_invalid_input_reports_status(opt):
     opt.sync()
     assert int(d_status.item()) == mpdp.ERR["INVALID_ARG"]
     check(opt, W.cyclic(9, seed=1))
+
+
+def test_device_batch_path(opt):
+    """A device-resident batch of mixed queries (tree and block mode, sizes
+    1..20) gives the same plans as the oracle, query by query."""
+    torch = pytest.importorskip("torch")
+    set_cfg(opt)
+    qs = W.mixed_stream(40, seed=11, n_lo=1, n_hi=20)
+    d_card = torch.tensor([c for q in qs for c in q.card], dtype=torch.float64, device="cuda")
+    d_edges = torch.from_numpy(
+        mpdp.pack_edges([e for q in qs for e in q.edges]).view(np.uint8).copy()).cuda()
+    nq = len(qs)
+    d_nodes = torch.zeros((nq, mpdp.PLAN_STRIDE * 40), dtype=torch.uint8, device="cuda")
+    d_cost = torch.zeros(nq, dtype=torch.float64, device="cuda")
+    d_status = torch.full((nq,), 99, dtype=torch.int32, device="cuda")
+    opt.optimize_batch_device([q.n for q in qs], [len(q.edges) for q in qs], d_card, d_edges,
+                              d_nodes, d_cost, d_status)
+    opt.sync()
+    status = d_status.cpu().numpy()
+    costs = d_cost.cpu().numpy()
+    nodes = d_nodes.cpu().numpy()
+    for i, q in enumerate(qs):
+        ref = oracle.dpccp(q)
+        assert status[i] == 0
+        assert costs[i] == ref.opt_cost
+        plan = mpdp.Plan(cost=costs[i], nodes=mpdp.nodes_from_bytes(nodes[i]))
+        assert plan.signature() == oracle.plan_signature(oracle.plan_from_memo(q, ref))
+
+
+def test_batch_split_by_budget():
+    """A small memo budget splits one call into several device batches; every
+    result stays exact, and a query larger than the budget is refused."""
+    small = mpdp.workspace_bytes(16) + mpdp.workspace_bytes(15)
+    with mpdp.Optimizer(0, memo_budget_bytes=small) as o:
+        qs = [W.snowflake(16, seed=s) for s in range(3)] + [W.cyclic(15, seed=2), W.star(14, seed=1)]
+        plans = o.optimize_batch(qs)
+        for q, p in zip(qs, plans):
+            ref = oracle.dpccp(q)
+            assert p.cost == ref.opt_cost
+            assert p.signature() == oracle.plan_signature(oracle.plan_from_memo(q, ref))
+        with pytest.raises(mpdp.MPDPError) as ei:
+            o.optimize(W.snowflake(20, seed=0))
+        assert ei.value.code == mpdp.ERR["ADMISSION"]
+
+
+def test_batch_with_invalid_member_is_rejected_whole(opt):
+    """Host-path batches are validated before anything is enqueued."""
+    set_cfg(opt)
+    q = W.chain(5, 0)
+    bad = W.Query(n=5, card=q.card, edges=q.edges + [(0, 1, 0.5)])
+    with pytest.raises(mpdp.MPDPError) as ei:
+        opt.optimize_batch([W.star(6, 0), bad])
+    assert ei.value.code == mpdp.ERR["INVALID_ARG"]
+    check(opt, W.cyclic(9, seed=3))
