@@ -32,12 +32,13 @@ QUERIES_PER_STEP = 64
 FLUSH_BYTES = 256 << 20
 # Issue-slot peak of the integer filter: 152 SMs x 4 schedulers x 32 lanes x clock.
 SMS, SCHEDULERS, LANES = 152, 4, 32
-# Algorithmic integer operations of the filter (unrank+connectivity), per
-# unranked subset (next-bit-permutation step + loop) and per vertex expanded by
-# the connectivity test (find lowest, clear lowest, load adjacency, and-not,
-# two ors, compare).
-OPS_PER_SUBSET = 9
-OPS_PER_STEP = 8
+# Algorithmic integer operations of the filter (unrank + connectivity):
+# per unranked subset, the next-bit-permutation step (9) and the
+# isolated-vertex test N(S) by four byte-table lookups (4 loads, 3 byte
+# extracts, 3 ors, and-not, compare: 12); per BFS round of the sets that pass
+# it, N(seen) by byte tables (10), or, and, two compares (15 in all).
+OPS_PER_SUBSET = 21
+OPS_PER_STEP = 15
 # Algorithmic memo bytes: two lookups of (4-byte key + 8-byte cost) per CCP pair
 # and one 16-byte entry written per connected set.
 BYTES_PER_CCP = 24
@@ -322,11 +323,14 @@ def run_ours(args):
 
 
 def roofline(kind, timing, stats, prof_steps, peaks, clocks):
+    """Roofline of the dominant kernel class.  `stats` are the per-query
+    counters of one step's queries, `timing` the class's summed event time
+    and launches over `prof_steps` steps."""
     launches = max(timing["launches"], 1)
     avg_s = timing["ms"] / launches / 1000.0
     if kind == "filter":
         ops = sum(OPS_PER_SUBSET * int(s["sets_unranked"]) + OPS_PER_STEP * int(s["filter_steps"])
-                  for s in stats) / len(stats)
+                  for s in stats) * prof_steps / launches
         mhz = 2070.0
         peak = SMS * SCHEDULERS * LANES * mhz * 1e6 / 1e12
         ach = ops / avg_s / 1e12

@@ -132,7 +132,7 @@ typedef struct {
     int32_t memo_kind;         /* MPDP_MEMO_* as run */
     uint64_t h2d_bytes;        /* host -> device bytes copied for this query */
     uint64_t d2h_bytes;        /* device -> host bytes copied for this query */
-    uint64_t filter_steps;     /* vertices expanded by the filter's connectivity tests */
+    uint64_t filter_steps;     /* BFS rounds run by the filter for sets with no isolated vertex */
     uint64_t connected_per_level[MPDP_MAX_LEVELS];
     uint64_t evaluated_per_level[MPDP_MAX_LEVELS];
     uint64_t ccp_per_level[MPDP_MAX_LEVELS];

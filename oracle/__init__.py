@@ -15,7 +15,8 @@ Contents (each restates a definition of arXiv 2202.13511):
     Algorithm 4 visits.
   * ``brute_force`` (pure Python, n <= 7): every bushy join tree without cross
     products (Sec. 2.1.1 "Objective"), costed with C_out, minimised under the
-    recursive (cost, left) order; it pins the DP search of both DPSUB and DPCCP.
+    recursive (x, left) order (x = cost of the two subtrees); it pins the DP
+    search of both DPSUB and DPCCP.
   * ``plan_from_memo``: the recursive plan fetch of Sec. 5 ("the final relation
     is recursively fetched using its left and right join relations").
 
@@ -270,8 +271,10 @@ def brute_force(q, max_n: int = 7):
     """Enumerate every bushy join tree over all relations whose every join has
     at least one predicate between its two inputs (no cross products, Sec. 2.1),
     cost each with C_out, and return the minimum under the recursive key
-    (cost, left mask, key of the subtree on the left mask, key of the other).
-    Returns (cost, signature) with the signature of ``plan_signature``."""
+    (x, left mask, key of the subtree on the left mask, key of the other),
+    where x = cost(left subtree) + cost(right subtree) and the tree's cost is
+    x + card(S).  Returns (cost, signature, number of trees), the signature as
+    in ``plan_signature``."""
     if q.n > max_n:
         raise ValueError("brute force is for tiny queries")
     adj = _adjacency(q)
@@ -310,12 +313,13 @@ def brute_force(q, max_n: int = 7):
             if b and joined(a, b):
                 for (ka, sa, ca) in trees(a):
                     for (kb, sb, cb) in trees(b):
-                        c = (ca + cb) + card_of(s)
+                        x = ca + cb
+                        c = x + card_of(s)
                         if a < b:
-                            key = (c, a, ka, kb)
+                            key = (x, a, ka, kb)
                             sig = (s, sa, sb)
                         else:
-                            key = (c, b, kb, ka)
+                            key = (x, b, kb, ka)
                             sig = (s, sb, sa)
                         out.append((key, sig, c))
             if sub == 0:
@@ -329,4 +333,6 @@ def brute_force(q, max_n: int = 7):
     if not all_trees:
         raise OracleError(OR_DISCONNECTED, "brute_force")
     best = min(all_trees, key=lambda t: t[0])
+    # the minimum x gives the minimum cost (addition is monotone): check it
+    assert best[2] == min(t[2] for t in all_trees)
     return best[2], best[1], len(all_trees)

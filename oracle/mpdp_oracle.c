@@ -27,14 +27,20 @@
  * Readings where the paper is silent (the cost model is unspecified, Sec. 6.1):
  *   - cost model C_out: cost({R_i}) = 0,
  *       cost(L join R) = (cost(L) + cost(R)) + card(L u R);
- *   - card(S) is a product in a fixed order: p = 1; for each relation r of S in
- *     ascending index: p *= card[r], then for each j in S with j < r and an
- *     edge (j, r), in ascending j: p *= sel(j, r).  Every way of building S
+ *   - card(S) is the product of card[r] over the relations of S and sel over
+ *     the edges inside S, taken in one fixed order that depends on S alone
+ *     ("peeling"): card({r}) = card[r]; otherwise let v be the highest-index
+ *     relation of S whose removal does not increase the number of connected
+ *     components of G[S] (for a connected S: its highest non-cut vertex), and
+ *     card(S) = ((card(S \ {v}) * card[v]) * sel(j1, v)) * sel(j2, v) ...
+ *     over the neighbours j1 < j2 < ... of v in S.  Every way of building S
  *     gets the same bits;
- *   - BestPlan(S) is the lexicographic minimum of (cost, left) over the CCP
- *     pairs of S, where left = the numerically smaller of the two masks.  This
- *     replaces Algorithm 1's "first strict improvement wins", whose result would
- *     depend on enumeration order;
+ *   - BestPlan(S) is the split with the lexicographic minimum of
+ *     (x, left), x = cost(S_left) + cost(S_right) and left = the numerically
+ *     smaller of the two masks; cost(S) = x + card(S).  Since card(S) is common
+ *     to every split of S and IEEE addition is monotone, the minimum x gives
+ *     the minimum cost; the rule replaces Algorithm 1's "first strict
+ *     improvement wins", whose result would depend on enumeration order;
  *   - counters: ccp counts each unordered CCP pair once (this is the reading
  *     under which the 2805x ratio printed in Sec. 2.3 and Sec. 6.2.1 holds).
  */
@@ -121,18 +127,59 @@ static int og_connected(const og_graph *g, uint64_t s)
     return og_grow(g, s & (~s + 1), s) == s;
 }
 
-/* card(S) in the fixed order stated in the header. */
+static int count_components(const og_graph *g, uint64_t s)
+{
+    int c = 0;
+    while (s) {
+        uint64_t comp = og_grow(g, s & (~s + 1), s);
+        s &= ~comp;
+        c++;
+    }
+    return c;
+}
+
+/* The peel vertex of S (|S| >= 2): the highest-index member whose removal
+ * does not increase the number of connected components of G[S]. */
+static int peel_vertex(const og_graph *g, uint64_t s)
+{
+    int base = count_components(g, s);
+    for (int v = g->n - 1; v >= 0; v--) {
+        if (!(s & bit(v))) continue;
+        if (count_components(g, s & ~bit(v)) <= base) return v;
+    }
+    return -1; /* not reached: every non-empty graph has such a vertex */
+}
+
+/* The factors of the peel vertex v on top of card(S \ {v}). */
+static double peel_factors(const og_graph *g, uint64_t s, int v, double p)
+{
+    p = p * g->card[v];
+    for (int j = 0; j < g->n; j++)
+        if ((s & bit(j)) && (g->adj[v] & bit(j))) p = p * g->sel[j][v];
+    return p;
+}
+
+/* card(S) by peeling, as stated in the header (plain recursion). */
 static double og_card(const og_graph *g, uint64_t s)
 {
-    double p = 1.0;
-    for (int r = 0; r < g->n; r++) {
-        if (!(s & bit(r))) continue;
-        p = p * g->card[r];
-        for (int j = 0; j < r; j++) {
-            if ((s & bit(j)) && (g->adj[j] & bit(r))) p = p * g->sel[j][r];
-        }
+    if (popcount(s) == 1) return g->card[lowest_index(s)];
+    int v = peel_vertex(g, s);
+    return peel_factors(g, s, v, og_card(g, s & ~bit(v)));
+}
+
+/* The same definition with a per-set cache (NaN = not yet known). */
+static double card_memo(const og_graph *g, double *cache, uint64_t s)
+{
+    double c = cache[s];
+    if (c == c) return c;
+    if (popcount(s) == 1) {
+        c = g->card[lowest_index(s)];
+    } else {
+        int v = peel_vertex(g, s);
+        c = peel_factors(g, s, v, card_memo(g, cache, s & ~bit(v)));
     }
-    return p;
+    cache[s] = c;
+    return c;
 }
 
 /* (c, l) is better than (bc, bl) under the lexicographic rule. */
@@ -191,17 +238,6 @@ static int og_nonseparable(const og_graph *g, uint64_t b)
         if (!og_connected(g, b & ~v)) return 0;
     }
     return 1;
-}
-
-static int count_components(const og_graph *g, uint64_t s)
-{
-    int c = 0;
-    while (s) {
-        uint64_t comp = og_grow(g, s & (~s + 1), s);
-        s &= ~comp;
-        c++;
-    }
-    return c;
 }
 
 /* Blocks of G[S]: the maximal vertex sets B (|B| >= 2) inducing a nonseparable
@@ -322,6 +358,9 @@ int oracle_dpsub(int n, const double *card, int m, const int32_t *eu, const int3
     uint64_t full = (n == 64) ? ~(uint64_t)0 : (bit(n) - 1);
     if (!og_connected(g, full)) { free(g); return OR_DISCONNECTED; }
     int L = n + 1;
+    double *cardc = malloc(sizeof(double) << n);
+    if (!cardc) { free(g); return OR_NOMEM; }
+    for (uint64_t s = 0; s <= full; s++) cardc[s] = NAN;
     memset(counters, 0, sizeof(uint64_t) * 3 * L);
     for (int i = 0; i < n; i++) {       /* BestPlan({R_i}) = R_i */
         best_cost[bit(i)] = 0.0;
@@ -332,8 +371,8 @@ int oracle_dpsub(int n, const double *card, int m, const int32_t *eu, const int3
         for (uint64_t s = 1; s <= full; s++) {  /* every S of size i */
             if (popcount(s) != i || !og_connected(g, s)) continue;
             counters[0 * L + i]++;
-            double card_s = og_card(g, s);
-            double bc = INFINITY;
+            double card_s = card_memo(g, cardc, s);
+            double bx = INFINITY;
             uint64_t bl = UINT64_MAX;
             uint64_t ordered_ccp = 0;
             for (uint64_t sl = s;; sl = (sl - 1) & s) {  /* every S_left subset of S */
@@ -347,17 +386,18 @@ int oracle_dpsub(int n, const double *card, int m, const int32_t *eu, const int3
                 else if (!(neighbours(g, sl) & sr)) ok = 0;
                 if (ok) {
                     ordered_ccp++;
-                    double c = (best_cost[sl] + best_cost[sr]) + card_s;
+                    double x = best_cost[sl] + best_cost[sr];
                     uint64_t l = sl < sr ? sl : sr;
-                    if (better(c, l, bc, bl)) { bc = c; bl = l; }
+                    if (better(x, l, bx, bl)) { bx = x; bl = l; }
                 }
                 if (sl == 0) break;
             }
             counters[2 * L + i] += ordered_ccp / 2;
-            best_cost[s] = bc;
+            best_cost[s] = bx + card_s;
             best_left[s] = (uint32_t)bl;
         }
     }
+    free(cardc);
     free(g);
     return OR_OK;
 }
@@ -376,7 +416,8 @@ int oracle_dpsub(int n, const double *card, int m, const int32_t *eu, const int3
  */
 typedef struct {
     const og_graph *g;
-    double *cost;
+    double *cost;    /* final cost, NaN until the set is first read as an operand */
+    double *xbest;   /* best x = cost(S_left) + cost(S_right) so far */
     uint32_t *left;
     double *cardc;   /* card(S) cache, NaN = not yet computed */
     uint8_t *used;   /* bit per set: plan already read as an operand */
@@ -385,15 +426,21 @@ typedef struct {
     int status;
 } dpccp_state;
 
-static double cached_card(dpccp_state *st, uint64_t s)
-{
-    double c = st->cardc[s];
-    if (c != c) { c = og_card(st->g, s); st->cardc[s] = c; }
-    return c;
-}
-
 static void mark_used(dpccp_state *st, uint64_t s) { st->used[s >> 3] |= (uint8_t)(1u << (s & 7)); }
 static int is_used(dpccp_state *st, uint64_t s) { return (st->used[s >> 3] >> (s & 7)) & 1; }
+
+/* cost(S) of a set whose pairs have all been seen: 0 for a relation,
+ * x + card(S) otherwise (fixed at the first read). */
+static double final_cost(dpccp_state *st, uint64_t s)
+{
+    if ((s & (s - 1)) == 0) return 0.0;
+    double c = st->cost[s];
+    if (c != c) {
+        c = st->xbest[s] + card_memo(st->g, st->cardc, s);
+        st->cost[s] = c;
+    }
+    return c;
+}
 
 static void emit_pair(dpccp_state *st, uint64_t s1, uint64_t s2)
 {
@@ -402,14 +449,14 @@ static void emit_pair(dpccp_state *st, uint64_t s1, uint64_t s2)
     st->counters[2 * st->L + k]++;
     mark_used(st, s1);
     mark_used(st, s2);
-    double c = (st->cost[s1] + st->cost[s2]) + cached_card(st, s);
+    double x = final_cost(st, s1) + final_cost(st, s2);
     uint64_t l = s1 < s2 ? s1 : s2;
-    if (st->left[s] == UINT32_MAX && st->cost[s] == INFINITY) {
+    if (st->left[s] == UINT32_MAX) {
         st->counters[0 * st->L + k]++;   /* first time this set is formed */
     }
-    if (better(c, l, st->cost[s], st->left[s] == UINT32_MAX ? UINT64_MAX : st->left[s])) {
+    if (better(x, l, st->xbest[s], st->left[s] == UINT32_MAX ? UINT64_MAX : st->left[s])) {
         if (is_used(st, s)) st->status = OR_ORDER;
-        st->cost[s] = c;
+        st->xbest[s] = x;
         st->left[s] = (uint32_t)l;
     }
 }
@@ -464,14 +511,18 @@ int oracle_dpccp(int n, const double *card, int m, const int32_t *eu, const int3
     st.g = g;
     st.cost = best_cost;
     st.left = best_left;
+    st.xbest = malloc(sizeof(double) * sz);
     st.cardc = malloc(sizeof(double) * sz);
     st.used = calloc(sz / 8 + 1, 1);
     st.counters = counters;
     st.L = n + 1;
     st.status = OR_OK;
-    if (!st.cardc || !st.used) { free(st.cardc); free(st.used); free(g); return OR_NOMEM; }
+    if (!st.cardc || !st.used || !st.xbest) {
+        free(st.cardc); free(st.used); free(st.xbest); free(g); return OR_NOMEM;
+    }
     for (size_t i = 0; i < sz; i++) {
-        best_cost[i] = INFINITY;
+        best_cost[i] = NAN;
+        st.xbest[i] = INFINITY;
         best_left[i] = UINT32_MAX;
         st.cardc[i] = NAN;
     }
@@ -488,6 +539,14 @@ int oracle_dpccp(int n, const double *card, int m, const int32_t *eu, const int3
     }
     /* pairs evaluated = CCP pairs: DPCCP only ever enumerates CCP pairs */
     for (int k = 0; k <= n; k++) counters[1 * st.L + k] = counters[2 * st.L + k];
+    /* fix the cost of every formed set not read as an operand (the full set
+     * among them); sets never formed (disconnected) keep cost +inf */
+    for (size_t i = 1; i < sz; i++) {
+        if ((i & (i - 1)) == 0) continue;
+        if (best_left[i] == UINT32_MAX) best_cost[i] = INFINITY;
+        else final_cost(&st, i);
+    }
+    free(st.xbest);
     free(st.cardc);
     free(st.used);
     free(g);

@@ -159,9 +159,24 @@ __device__ __forceinline__ uint32_t nbhd(uint32_t s, const uint32_t (*__restrict
     return t[0][s & 255u] | t[1][(s >> 8) & 255u] | t[2][(s >> 16) & 255u] | t[3][s >> 24];
 }
 
-// connected(S) for |S| >= 2 by whole-frontier rounds: first reject S when a
-// member has no neighbour inside S (an isolated vertex of G[S]); otherwise
-// grow from min(S) one BFS layer per round until S is reached or growth stops.
+// connected(S) by whole-frontier rounds, for S (|S| >= 2) with no isolated
+// vertex in G[S]: grow from min(S) one BFS layer per round until S is
+// reached or growth stops.
+__device__ __forceinline__ bool connected_rounds_from(uint32_t s, const uint32_t (*__restrict__ t)[256],
+                                                      uint32_t& rounds)
+{
+    uint32_t seen = s & (0u - s);
+    while (true) {
+        rounds++;
+        const uint32_t nxt = (seen | nbhd(seen, t)) & s;
+        if (nxt == s) return true;
+        if (nxt == seen) return false;
+        seen = nxt;
+    }
+}
+
+// connected(S) for |S| >= 2: first reject S when a member has no neighbour
+// inside S (an isolated vertex of G[S]), then BFS rounds.
 __device__ __forceinline__ bool connected_rounds(uint32_t s, const uint32_t (*__restrict__ t)[256],
                                                  uint32_t& rounds)
 {
@@ -190,31 +205,40 @@ __device__ __forceinline__ double sel_of(const SharedQuery& sq, int j, int r)
     return sq.nsel[sq.nbase[r] + __popc(sq.adj[r] & ((1u << j) - 1u))];
 }
 
-// card(S): product in the fixed order (relations ascending; after each
-// relation r, the selectivities of its edges to smaller members j ascending).
-// __dmul_rn keeps every step a separately rounded IEEE multiply.
-__device__ __forceinline__ double card_of(uint32_t s, const SharedQuery& sq)
+// Highest member of S.
+__device__ __forceinline__ int highest(uint32_t s) { return 31 - __clz(s); }
+
+// Peel vertex of a connected S (|S| >= 2) whose G[S] is a tree: its highest
+// leaf (a vertex of degree 1 in G[S]), i.e. its highest non-cut vertex.
+__device__ __forceinline__ int tree_peel_vertex(uint32_t s, const uint32_t* __restrict__ adj)
 {
-    double p = 1.0;
     uint32_t t = s;
     while (t) {
-        int r = lowest(t);
-        t &= t - 1;
-        p = __dmul_rn(p, sq.card[r]);
-        uint32_t nb = sq.adj[r] & s & ((1u << r) - 1u);
-        while (nb) {
-            int j = lowest(nb);
-            nb &= nb - 1;
-            p = __dmul_rn(p, sel_of(sq, j, r));
-        }
+        const int v = highest(t);
+        if (__popc(adj[v] & s) == 1) return v;
+        t &= ~(1u << v);
     }
-    return p;
+    return highest(s);
 }
 
-// Lexicographic (cost, left) order of candidate plans.
-__device__ __forceinline__ bool better(double c, uint32_t l, double bc, uint32_t bl)
+// Peel vertex of a connected S from its blocks: the highest vertex that lies
+// in exactly one block (a non-cut vertex).
+__device__ __forceinline__ int block_peel_vertex(uint32_t s, const uint32_t* blk, int nb)
 {
-    return c < bc || (c == bc && l < bl);
+    uint32_t once = 0u, twice = 0u;
+    for (int j = 0; j < nb; j++) {
+        twice |= once & blk[j];
+        once |= blk[j];
+    }
+    return highest(s & ~twice);
+}
+
+// Lexicographic order of candidate splits on (x, left), x = cost(S_l) +
+// cost(S_r) >= 0 compared through its IEEE bit pattern (monotone for
+// non-negative doubles, and no FP64 pipe involved).
+__device__ __forceinline__ bool better_x(unsigned long long x, uint32_t l, unsigned long long bx, uint32_t bl)
+{
+    return x < bx || (x == bx && l < bl);
 }
 
 // Murmur3's 32-bit finaliser (fmix32), the hash the paper names for the memo.
@@ -245,6 +269,7 @@ struct DenseMemo {
         left = left0 + a.desc[q].memo_base;
     }
     __device__ __forceinline__ double get_cost(uint32_t s, DevCounters*) const { return __ldg(&cc[s].x); }
+    __device__ __forceinline__ double get_card(uint32_t s, DevCounters*) const { return __ldg(&cc[s].y); }
     __device__ __forceinline__ void get(uint32_t s, double& c, double& card, uint32_t& l, DevCounters*) const
     {
         const double2 v = cc[s];
@@ -301,6 +326,11 @@ struct HashMemo {
         const HashSlot* e = find(s, cnt);
         return e ? __ldg(&e->cost) : __longlong_as_double(0x7ff8000000000000ll);
     }
+    __device__ __forceinline__ double get_card(uint32_t s, DevCounters* cnt) const
+    {
+        const HashSlot* e = find(s, cnt);
+        return e ? __ldg(&e->card) : __longlong_as_double(0x7ff8000000000000ll);
+    }
     __device__ __forceinline__ void get(uint32_t s, double& c, double& card, uint32_t& l, DevCounters* cnt) const
     {
         const HashSlot* e = find(s, cnt);
@@ -331,5 +361,58 @@ struct HashMemo {
         raise_status(cnt, MPDP_ERR_OOM);
     }
 };
+
+}  // namespace mpdp
+
+namespace mpdp {
+
+// card(S) by peeling vertex v: card(S \ {v}) (from the memo; a single
+// relation's card directly), times card[v], times sel(j, v) for the
+// neighbours j of v in S in ascending order.  __dmul_rn keeps every step a
+// separately rounded IEEE multiply.
+template <class Memo>
+__device__ __forceinline__ double peel_card(uint32_t s, int v, const SharedQuery& sq, const Memo& memo,
+                                            DevCounters* cnt)
+{
+    const uint32_t rest = s & ~(1u << v);
+    double p = (rest & (rest - 1u)) ? memo.get_card(rest, cnt) : sq.card[lowest(rest)];
+    p = __dmul_rn(p, sq.card[v]);
+    const uint32_t nv = sq.adj[v];
+    uint32_t nb = nv & s;
+    while (nb) {
+        const int j = lowest(nb);
+        nb &= nb - 1u;
+        p = __dmul_rn(p, sq.nsel[sq.nbase[v] + __popc(nv & ((1u << j) - 1u))]);
+    }
+    return p;
+}
+
+// Fold one CCP pair (S_l, S_r) into the running best (x, left).  x is
+// cost(S_l) + cost(S_r); a single relation costs 0 (C_out base case), so a
+// pair with a single-relation side needs no addition and no memo read for it.
+template <class Memo>
+__device__ __forceinline__ void fold_pair(uint32_t sl, uint32_t sr, const Memo& memo, DevCounters* cnt,
+                                          unsigned long long& bx, uint32_t& bl)
+{
+    const bool ml = (sl & (sl - 1u)) != 0u, mr = (sr & (sr - 1u)) != 0u;
+    double x = 0.0;
+    if (ml && mr) x = __dadd_rn(memo.get_cost(sl, cnt), memo.get_cost(sr, cnt));
+    else if (ml) x = memo.get_cost(sl, cnt);
+    else if (mr) x = memo.get_cost(sr, cnt);
+    const unsigned long long xb = (unsigned long long)__double_as_longlong(x);
+    const uint32_t l = sl < sr ? sl : sr;
+    if (better_x(xb, l, bx, bl)) {
+        bx = xb;
+        bl = l;
+    }
+}
+
+// cost(S) = x* + card(S) for the chosen split.
+__device__ __forceinline__ double set_cost(unsigned long long bx, double card_s)
+{
+    return __dadd_rn(__longlong_as_double((long long)bx), card_s);
+}
+
+constexpr unsigned long long kNoX = 0xffffffffffffffffull;
 
 }  // namespace mpdp

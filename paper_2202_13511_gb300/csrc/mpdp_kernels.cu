@@ -191,14 +191,22 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
 }
 
 // ---------------------------------------------------------------------------
-// Binomial coefficient C(i, j) for i, j <= 32 (exact in 64-bit arithmetic).
-__device__ __forceinline__ uint32_t binom_dev(int i, int j)
+// Binomial coefficients C(i, j), i, j <= 32, built at compile time by
+// Pascal's rule (C(32, 16) < 2^32, so every entry fits 32 bits).
+struct BinomTable {
+    uint32_t v[33 * 33];
+};
+
+constexpr BinomTable make_binom_table()
 {
-    if (j < 0 || j > i) return 0u;
-    unsigned long long r = 1;
-    for (int x = 1; x <= j; x++) r = r * (unsigned long long)(i - j + x) / (unsigned long long)x;
-    return (uint32_t)r;
+    BinomTable t{};
+    for (int i = 0; i <= 32; i++)
+        for (int j = 0; j <= 32; j++)
+            t.v[i * 33 + j] = (j == 0) ? 1u : (i == 0 ? 0u : t.v[(i - 1) * 33 + j - 1] + t.v[(i - 1) * 33 + j]);
+    return t;
 }
+
+__device__ const BinomTable kBinom = make_binom_table();
 
 // Combinatorial number system (colex order): the k-subset of {0..n-1} with
 // rank r is {c_k > ... > c_1} where r = sum_i C(c_i, i); each c_i is the
@@ -250,7 +258,7 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
     const QDesc& d = a.desc[qi];
     const DevQuery* __restrict__ q = a.query + qi;
     DevCounters* __restrict__ cnt = &a.out[qi].counters;
-    for (int t = threadIdx.x; t < 33 * 33; t += blockDim.x) s_binom[t] = binom_dev(t / 33, t % 33);
+    for (int t = threadIdx.x; t < 33 * 33; t += blockDim.x) s_binom[t] = kBinom.v[t];
     for (int t = threadIdx.x; t < 4 * 256; t += blockDim.x) s_nbt[t >> 8][t & 255] = q->nbt[t >> 8][t & 255];
     __syncthreads();
     if (cnt->status != 0) return;
@@ -261,15 +269,23 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
     for (int j = 2; j <= n; j++)
         if (warp >= d.warp_begin[j] && warp < d.warp_begin[j + 1]) k = j;
     if (k < 0) return;  // whole warp: padding past the query's last level
-    const uint32_t nr = binom_dev(n, k);
+    const uint32_t nr = s_binom[n * 33 + k];
     const unsigned long long r0 = (unsigned long long)(warp - d.warp_begin[k]) * 32ull * (unsigned long long)a.run +
                                   (unsigned long long)lane * (unsigned long long)a.run;
     uint32_t len = 0;
     if (r0 < nr) len = (uint32_t)min((unsigned long long)a.run, (unsigned long long)nr - r0);
     const uint32_t s0 = len ? unrank_colex((uint32_t)r0, k, n, s_binom) : 0u;
     uint32_t s = s0, flags = 0u, rounds = 0u;
+    // In colex order the high half of S rarely changes along a run: its part
+    // of N(S) is cached and recomputed only when bits 16..31 change.
+    uint32_t s_hi = 0xffffffffu, nb_hi = 0u;
     for (uint32_t i = 0; i < len; i++) {
-        if (connected_rounds(s, s_nbt, rounds)) flags |= 1u << i;
+        if ((s >> 16) != s_hi) {
+            s_hi = s >> 16;
+            nb_hi = s_nbt[2][s_hi & 255u] | s_nbt[3][s_hi >> 8];
+        }
+        const uint32_t nb = nb_hi | s_nbt[0][s & 255u] | s_nbt[1][(s >> 8) & 255u];
+        if ((s & ~nb) == 0u && connected_rounds_from(s, s_nbt, rounds)) flags |= 1u << i;
         s = next_colex(s);
     }
     const uint32_t c = __popc(flags);
@@ -345,22 +361,6 @@ __global__ void __launch_bounds__(256) k_hash_clear(BatchArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Cost one CCP pair (S_l, S_r) of S and fold it into the running best.
-// Singleton sides cost 0 (C_out base case) and need no memo read.
-template <class Memo>
-__device__ __forceinline__ void cost_pair(uint32_t sl, uint32_t sr, double card_s, const Memo& memo,
-                                          DevCounters* cnt, double& bc, uint32_t& bl)
-{
-    const double cl = (sl & (sl - 1u)) ? memo.get_cost(sl, cnt) : 0.0;
-    const double cr = (sr & (sr - 1u)) ? memo.get_cost(sr, cnt) : 0.0;
-    const double c = __dadd_rn(__dadd_rn(cl, cr), card_s);
-    const uint32_t l = sl < sr ? sl : sr;
-    if (better(c, l, bc, bl)) {
-        bc = c;
-        bl = l;
-    }
-}
-
 // Tiles of kEvalThreads sets of one query at level k for queries in mode `mode`.
 __device__ __forceinline__ uint32_t level_tiles(const BatchArgs& a, int q, int k, int mode)
 {
@@ -412,8 +412,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
         if (idx < cnt->list_count[k]) {
             const QDesc& d = a.desc[qi];
             const uint32_t s = a.lists[d.list_base + d.list_off[k] + idx];
-            const double card_s = card_of(s, sq);
-            double bc = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+            const double card_s = peel_card(s, tree_peel_vertex(s, sq.adj), sq, memo, cnt);
+            unsigned long long bx = kNoX;
             uint32_t bl = kFull;
             uint32_t vis = s & (0u - s), queue = vis;
             while (queue) {
@@ -427,10 +427,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
                     const int v = lowest(ch);
                     ch &= ch - 1u;
                     const uint32_t sl = grow(1u << v, rest, sq.adj);
-                    cost_pair(sl, s ^ sl, card_s, memo, cnt, bc, bl);
+                    fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
                 }
             }
-            memo.put(s, k, bc, card_s, bl, cnt);
+            memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
             sets++;
         }
     }
@@ -587,8 +587,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
             if (pairs > (uint32_t)a.heavy_threshold) {
                 to_heavy = true;
             } else {
-                const double card_s = card_of(s, sq);
-                double bc = __longlong_as_double(0x7ff0000000000000ll);
+                const double card_s = peel_card(s, block_peel_vertex(s, blk, nb), sq, memo, cnt);
+                unsigned long long bx = kNoX;
                 uint32_t bl = kFull;
                 evaluated += pairs;
                 for (int j = 0; j < nb; j++) {
@@ -599,10 +599,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
                         if (!connected(lb, sq.adj) || !connected(rb, sq.adj)) continue;
                         ccp++;
                         const uint32_t sl = grow(lb, s & ~rb, sq.adj);
-                        cost_pair(sl, s ^ sl, card_s, memo, cnt, bc, bl);
+                        fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
                     }
                 }
-                memo.put(s, k, bc, card_s, bl, cnt);
+                memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
             }
         }
         // warp-aggregated append of heavy sets
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
     __shared__ double s_card;
     __shared__ uint32_t s_stash_l[kWarps][64];
     __shared__ uint32_t s_stash_r[kWarps][64];
-    __shared__ double s_bc[kWarps];
+    __shared__ unsigned long long s_bx[kWarps];
     __shared__ uint32_t s_bl[kWarps];
     memo.setup(s_memo);
     const uint32_t total_sets = block_prefix(a.nq, s_pref, [&](int q) -> uint32_t {
@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
             }
             s_bpref[nb] = acc;
             s_nb = nb;
-            s_card = card_of(s, sq);
+            s_card = peel_card(s, block_peel_vertex(s, blk, nb), sq, memo, cnt);
             evaluated += acc;
             heavy++;
         }
@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
         const int nb = s_nb;
         const uint32_t total = s_bpref[nb];
         const double card_s = s_card;
-        double bc = __longlong_as_double(0x7ff0000000000000ll);
+        unsigned long long bx = kNoX;
         uint32_t bl = kFull;
         uint32_t stash = 0u;  // warp-uniform stash fill
         const uint32_t rounds = (total + blockDim.x - 1) / blockDim.x;
@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
             if (!a.use_ccc) {
                 if (valid) {
                     const uint32_t sl = grow(lb, s & ~rb, sq.adj);
-                    cost_pair(sl, s ^ sl, card_s, memo, cnt, bc, bl);
+                    fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
                 }
                 continue;
             }
@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
                 const uint32_t i = stash - 32u + lane;
                 const uint32_t l2 = s_stash_l[warp][i], r2 = s_stash_r[warp][i];
                 const uint32_t sl = grow(l2, s & ~r2, sq.adj);
-                cost_pair(sl, s ^ sl, card_s, memo, cnt, bc, bl);
+                fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
                 stash -= 32u;
             }
             __syncwarp();
@@ -738,30 +738,30 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
         if (a.use_ccc && lane < (int)stash) {
             const uint32_t l2 = s_stash_l[warp][lane], r2 = s_stash_r[warp][lane];
             const uint32_t sl = grow(l2, s & ~r2, sq.adj);
-            cost_pair(sl, s ^ sl, card_s, memo, cnt, bc, bl);
+            fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
         }
-        // prune: warp then block lexicographic min of (cost, left)
+        // prune: warp then block lexicographic min of (x, left)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double oc = __shfl_xor_sync(kFull, bc, o);
+            const unsigned long long ox = __shfl_xor_sync(kFull, bx, o);
             const uint32_t ol = __shfl_xor_sync(kFull, bl, o);
-            if (better(oc, ol, bc, bl)) {
-                bc = oc;
+            if (better_x(ox, ol, bx, bl)) {
+                bx = ox;
                 bl = ol;
             }
         }
         if (lane == 0) {
-            s_bc[warp] = bc;
+            s_bx[warp] = bx;
             s_bl[warp] = bl;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int w = 1; w < kWarps; w++)
-                if (better(s_bc[w], s_bl[w], bc, bl)) {
-                    bc = s_bc[w];
+                if (better_x(s_bx[w], s_bl[w], bx, bl)) {
+                    bx = s_bx[w];
                     bl = s_bl[w];
                 }
-            memo.put(s, k, bc, card_s, bl, cnt);
+            memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
         }
         __syncthreads();
     }
