@@ -33,11 +33,11 @@ FLUSH_BYTES = 256 << 20
 # Issue-slot peak of the integer filter: 152 SMs x 4 schedulers x 32 lanes x clock.
 SMS, SCHEDULERS, LANES = 152, 4, 32
 # Algorithmic integer operations of the filter (unrank + connectivity):
-# per unranked subset, the next-bit-permutation step (9) and the
-# isolated-vertex test N(S) by four byte-table lookups (4 loads, 3 byte
-# extracts, 3 ors, and-not, compare: 12); per BFS round of the sets that pass
-# it, N(seen) by byte tables (10), or, and, two compares (15 in all).
-OPS_PER_SUBSET = 21
+# per unranked subset, the next-bit-permutation step (9) and the spanning-tree
+# test C(S) by byte tables (4 loads, 3 byte extracts, 3 ors, and-not, popc,
+# compare: 13); per BFS round run for the sets of a cyclic graph that neither
+# test settles, N(seen) by byte tables (10), or, and, two compares (15 in all).
+OPS_PER_SUBSET = 22
 OPS_PER_STEP = 15
 # Algorithmic memo bytes: two lookups of (4-byte key + 8-byte cost) per CCP pair
 # and one 16-byte entry written per connected set.

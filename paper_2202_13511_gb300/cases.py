@@ -1,9 +1,11 @@
 """Run one workload shape through the device path (for profiler captures).
 
     python -m paper_2202_13511_gb300.cases --kind star --n 25 --reps 3
+    python -m paper_2202_13511_gb300.cases --kind snowflake --n 25 --queries 4
 
-Builds nothing and checks nothing beyond the device status word; it exists so
-that a profiler can capture the kernels of one shape in isolation.
+All queries of a rep go to the GPU as one device batch.  Nothing is checked
+beyond the device status words; this only exists so that a profiler can
+capture the kernels of one shape in isolation.
 """
 from __future__ import annotations
 
@@ -32,18 +34,18 @@ def main(argv=None) -> int:
                          enumeration={"auto": mpdp.ENUM_AUTO, "tree": mpdp.ENUM_TREE,
                                       "blocks": mpdp.ENUM_BLOCKS}[a.enumeration])
     qs = [W.make(a.kind, a.n, seed=a.seed + i) for i in range(a.queries)]
-    bufs = []
-    for q in qs:
-        bufs.append((torch.tensor(q.card, dtype=torch.float64, device="cuda"),
-                     torch.from_numpy(mpdp.pack_edges(q.edges).view(np.uint8).copy()).cuda(),
-                     torch.zeros((2 * q.n - 1) * 40, dtype=torch.uint8, device="cuda"),
-                     torch.zeros(1, dtype=torch.float64, device="cuda"),
-                     torch.full((1,), -100, dtype=torch.int32, device="cuda")))
+    d_card = torch.tensor([c for q in qs for c in q.card], dtype=torch.float64, device="cuda")
+    d_edges = torch.from_numpy(
+        mpdp.pack_edges([e for q in qs for e in q.edges]).view(np.uint8).copy()).cuda()
+    nq = len(qs)
+    d_nodes = torch.zeros((nq, mpdp.PLAN_STRIDE * 40), dtype=torch.uint8, device="cuda")
+    d_cost = torch.zeros(nq, dtype=torch.float64, device="cuda")
+    d_status = torch.full((nq,), -100, dtype=torch.int32, device="cuda")
     for _ in range(a.reps):
-        for q, (c, e, nd, co, st) in zip(qs, bufs):
-            opt.optimize_device(q.n, len(q.edges), c, e, nd, co, st)
+        opt.optimize_batch_device([q.n for q in qs], [len(q.edges) for q in qs], d_card, d_edges,
+                                  d_nodes, d_cost, d_status)
     torch.cuda.synchronize()
-    bad = [int(b[4].item()) for b in bufs if int(b[4].item()) != 0]
+    bad = [int(x) for x in d_status.cpu().numpy() if x != 0]
     opt.close()
     print(f"{a.kind}-{a.n} x{a.queries} reps={a.reps} status={'ok' if not bad else bad}")
     return 0 if not bad else 1

@@ -125,10 +125,11 @@ struct mpdp_ctx {
     // variable device part
     void* var = nullptr;
     size_t var_bytes = 0;
-    size_t list_words = 0, memo_entries = 0, arena_slots = 0;
+    size_t list_words = 0, heavy_words = 0, memo_entries = 0, arena_slots = 0;
     uint32_t* d_lists = nullptr;
     uint32_t* d_heavy = nullptr;
-    double2* d_memo = nullptr;
+    double* d_cost = nullptr;
+    double* d_card = nullptr;
     uint32_t* d_left = nullptr;
     HashSlot* d_arena = nullptr;
     // host side
@@ -221,7 +222,7 @@ static QuerySize query_size(int n, int enumeration, int memo_kind)
 
 static size_t var_bytes_of(size_t lists, size_t heavy, size_t memo, size_t hash)
 {
-    return align_up(lists * 4) + align_up(heavy * 4) + align_up(memo * sizeof(double2)) +
+    return align_up(lists * 4) + align_up(heavy * 4) + 2 * align_up(memo * sizeof(double)) +
            align_up(memo * sizeof(uint32_t)) + align_up(hash * sizeof(HashSlot));
 }
 
@@ -267,24 +268,25 @@ static int ensure_fixed(mpdp_ctx* ctx)
 // Grow the variable workspace to hold at least the given sizes.
 static int ensure_var(mpdp_ctx* ctx, size_t lists, size_t heavy, size_t memo, size_t hash)
 {
-    const size_t lw = std::max(lists, heavy);
-    if (ctx->var && lw <= ctx->list_words && memo <= ctx->memo_entries && hash <= ctx->arena_slots)
+    if (ctx->var && lists <= ctx->list_words && heavy <= ctx->heavy_words && memo <= ctx->memo_entries &&
+        hash <= ctx->arena_slots)
         return MPDP_OK;
     // grow every part to at least what it had, so alternating shapes do not thrash
-    size_t L = std::max(lw, ctx->list_words), M = std::max(memo, ctx->memo_entries),
-           H = std::max(hash, ctx->arena_slots);
-    if (var_bytes_of(L, L, M, H) + fixed_bytes() > ctx->budget) {
-        L = lw;  // only what this batch needs
+    size_t L = std::max(lists, ctx->list_words), V = std::max(heavy, ctx->heavy_words),
+           M = std::max(memo, ctx->memo_entries), H = std::max(hash, ctx->arena_slots);
+    if (var_bytes_of(L, V, M, H) + fixed_bytes() > ctx->budget) {
+        L = lists;  // only what this batch needs
+        V = heavy;
         M = memo;
         H = hash;
-        if (var_bytes_of(L, L, M, H) + fixed_bytes() > ctx->budget) return MPDP_ERR_ADMISSION;
+        if (var_bytes_of(L, V, M, H) + fixed_bytes() > ctx->budget) return MPDP_ERR_ADMISSION;
     }
-    const size_t bytes = var_bytes_of(L, L, M, H);
+    const size_t bytes = var_bytes_of(L, V, M, H);
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     destroy_graphs(ctx);
     if (ctx->var) cudaFree(ctx->var);
     ctx->var = nullptr;
-    ctx->list_words = ctx->memo_entries = ctx->arena_slots = 0;
+    ctx->list_words = ctx->heavy_words = ctx->memo_entries = ctx->arena_slots = 0;
     ctx->last_seq = 0;
     void* p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
@@ -301,11 +303,13 @@ static int ensure_var(mpdp_ctx* ctx, size_t lists, size_t heavy, size_t memo, si
         return r;
     };
     ctx->d_lists = reinterpret_cast<uint32_t*>(take(L * 4));
-    ctx->d_heavy = reinterpret_cast<uint32_t*>(take(L * 4));
-    ctx->d_memo = reinterpret_cast<double2*>(take(M * sizeof(double2)));
+    ctx->d_heavy = reinterpret_cast<uint32_t*>(take(V * 4));
+    ctx->d_cost = reinterpret_cast<double*>(take(M * sizeof(double)));
+    ctx->d_card = reinterpret_cast<double*>(take(M * sizeof(double)));
     ctx->d_left = reinterpret_cast<uint32_t*>(take(M * sizeof(uint32_t)));
     ctx->d_arena = reinterpret_cast<HashSlot*>(take(H * sizeof(HashSlot)));
     ctx->list_words = L;
+    ctx->heavy_words = V;
     ctx->memo_entries = M;
     ctx->arena_slots = H;
     return MPDP_OK;
@@ -324,7 +328,8 @@ static BatchArgs batch_args(const mpdp_ctx* ctx, int nq, int max_n)
     a.out = ctx->d_out;
     a.lists = ctx->d_lists;
     a.heavy = ctx->d_heavy;
-    a.memo = ctx->d_memo;
+    a.memo_cost = ctx->d_cost;
+    a.memo_card = ctx->d_card;
     a.left = ctx->d_left;
     a.arena = ctx->d_arena;
     a.layout = ctx->d_layout;
@@ -335,28 +340,33 @@ static BatchArgs batch_args(const mpdp_ctx* ctx, int nq, int max_n)
     return a;
 }
 
-// Split [0, count) into consecutive sub-batches that fit the budget.
+// Split [0, count) into consecutive sub-batches that fit the budget.  The
+// heavy-set lists share the list offsets, so once a block-mode query is in a
+// batch its heavy region spans every list word of the batch.
 static int split_batches(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, std::vector<std::pair<int, int>>& out)
 {
     const int kind = ctx->cfg.memo_kind;
-    size_t L = 0, H = 0, M = 0, A = 0;
+    size_t L = 0, M = 0, A = 0;
+    bool blocks = false;
     int start = 0;
     for (int i = 0; i < (int)qs.size(); i++) {
         const QuerySize z = query_size(qs[i].n, qs[i].enumeration, kind);
-        if (var_bytes_of(z.lists, z.heavy, z.memo, z.hash) + fixed_bytes() > ctx->budget)
+        const bool zb = qs[i].enumeration == MPDP_ENUM_BLOCKS;
+        if (var_bytes_of(z.lists, zb ? z.lists : 0, z.memo, z.hash) + fixed_bytes() > ctx->budget)
             return MPDP_ERR_ADMISSION;
         const bool full = (i - start) >= kMaxBatch;
-        const size_t lw = std::max(L + z.lists, H + z.heavy);
-        const size_t need = var_bytes_of(lw, lw, M + z.memo, A + z.hash) + fixed_bytes();
+        const size_t L2 = L + z.lists;
+        const size_t need = var_bytes_of(L2, (blocks || zb) ? L2 : 0, M + z.memo, A + z.hash) + fixed_bytes();
         if (i > start && (full || need > ctx->budget)) {
             out.emplace_back(start, i);
             start = i;
-            L = H = M = A = 0;
+            L = M = A = 0;
+            blocks = false;
         }
         L += z.lists;
-        H += z.heavy;
         M += z.memo;
         A += z.hash;
+        blocks = blocks || zb;
     }
     if (start < (int)qs.size()) out.emplace_back(start, (int)qs.size());
     return MPDP_OK;
@@ -469,15 +479,16 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
     const int kind = ctx->cfg.memo_kind;
     int rc = ensure_fixed(ctx);
     if (rc != MPDP_OK) return rc;
-    size_t L = 0, H = 0, M = 0, A = 0;
+    size_t L = 0, M = 0, A = 0;
+    bool blocks = false;
     for (const auto& q : qs) {
         const QuerySize z = query_size(q.n, q.enumeration, kind);
         L += z.lists;
-        H += z.heavy;
         M += z.memo;
         A += z.hash;
+        blocks = blocks || q.enumeration == MPDP_ENUM_BLOCKS;
     }
-    rc = ensure_var(ctx, L, H, M, A);
+    rc = ensure_var(ctx, L, blocks ? L : 0, M, A);
     if (rc != MPDP_OK) return rc;
     const size_t desc_bytes = sizeof(QDesc) * nq, pref_bytes = sizeof(uint32_t) * (nq + 1);
     const size_t staged_off = align_up(desc_bytes) + align_up(pref_bytes);

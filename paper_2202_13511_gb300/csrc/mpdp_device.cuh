@@ -38,7 +38,23 @@ struct DevQuery {
     // nbt[b][x]: union of the adjacency bitmaps of relations 8b + i for every
     // bit i of the byte x, so N(S) = OR_b nbt[b][byte b of S] (4 lookups)
     uint32_t nbt[4][256];
+    // Spanning tree T of G, rooted at relation 0 (breadth first; T = G when G
+    // is a tree).  ctt[b][x]: union of the children in T of relations 8b + i
+    // for every bit i of the byte x, so C(S) = OR_b ctt[b][byte b of S] is
+    // the set of relations whose T-parent lies in S.
+    uint32_t ctt[4][256];
+    int32_t is_tree;                 // G itself is a tree (n - 1 edges)
+    int32_t pad2[3];
 };
+
+// T[S] has one component per member of S whose T-parent is outside S, so
+// popcount(S & ~C(S)) == 1 exactly when T[S] is connected: connected(S) in
+// a tree join graph, and a sufficient condition in any join graph (T[S] is a
+// spanning subgraph of G[S]).
+__device__ __forceinline__ uint32_t tops_of(uint32_t s, uint32_t children)
+{
+    return s & ~children;
+}
 
 // Per-query device counters and status word.
 struct DevCounters {
@@ -107,8 +123,9 @@ struct BatchArgs {
     DevOut* out;
     uint32_t* lists;
     uint32_t* heavy;
-    double2* memo;       // dense memo {cost, card}
-    uint32_t* left;      // dense memo left masks
+    double* memo_cost;   // dense memo cost[S]
+    double* memo_card;   // dense memo card[S]
+    uint32_t* left;      // dense memo left[S]
     HashSlot* arena;     // hash memo slots
     HashLayout* layout;  // [nq]
     unsigned long long arena_slots;
@@ -252,11 +269,16 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h)
     return h;
 }
 
-// Memo indexed directly by the relation bitmap: entry {cost, card} and left.
+// Memo indexed directly by the relation bitmap, as three arrays: cost[S]
+// (read by every pair), card[S] (read once per set, by peeling) and left[S]
+// (read by the plan fetch only).  A cost lookup then shares its 32-byte
+// sector with three neighbouring bitmaps instead of one.
 struct DenseMemo {
-    double2* cc0;      // batch arena
+    double* cost0;     // batch arena
+    double* card0;
     uint32_t* left0;
-    double2* cc;       // bound to one query
+    double* cost;      // bound to one query
+    double* card;
     uint32_t* left;
 
     static constexpr size_t kSharedBytes = 16;
@@ -265,21 +287,23 @@ struct DenseMemo {
     // per thread; no shared memory involved
     __device__ __forceinline__ void bind(const BatchArgs& a, int q)
     {
-        cc = cc0 + a.desc[q].memo_base;
-        left = left0 + a.desc[q].memo_base;
+        const unsigned long long b = a.desc[q].memo_base;
+        cost = cost0 + b;
+        card = card0 + b;
+        left = left0 + b;
     }
-    __device__ __forceinline__ double get_cost(uint32_t s, DevCounters*) const { return __ldg(&cc[s].x); }
-    __device__ __forceinline__ double get_card(uint32_t s, DevCounters*) const { return __ldg(&cc[s].y); }
-    __device__ __forceinline__ void get(uint32_t s, double& c, double& card, uint32_t& l, DevCounters*) const
+    __device__ __forceinline__ double get_cost(uint32_t s, DevCounters*) const { return __ldg(cost + s); }
+    __device__ __forceinline__ double get_card(uint32_t s, DevCounters*) const { return __ldg(card + s); }
+    __device__ __forceinline__ void get(uint32_t s, double& c, double& cd, uint32_t& l, DevCounters*) const
     {
-        const double2 v = cc[s];
-        c = v.x;
-        card = v.y;
+        c = cost[s];
+        cd = card[s];
         l = left[s];
     }
-    __device__ __forceinline__ void put(uint32_t s, int, double c, double card, uint32_t l, DevCounters*)
+    __device__ __forceinline__ void put(uint32_t s, int, double c, double cd, uint32_t l, DevCounters*)
     {
-        cc[s] = make_double2(c, card);
+        cost[s] = c;
+        card[s] = cd;
         left[s] = l;
     }
 };
@@ -395,11 +419,13 @@ __device__ __forceinline__ void fold_pair(uint32_t sl, uint32_t sr, const Memo& 
                                           unsigned long long& bx, uint32_t& bl)
 {
     const bool ml = (sl & (sl - 1u)) != 0u, mr = (sr & (sr - 1u)) != 0u;
-    double x = 0.0;
-    if (ml && mr) x = __dadd_rn(memo.get_cost(sl, cnt), memo.get_cost(sr, cnt));
-    else if (ml) x = memo.get_cost(sl, cnt);
-    else if (mr) x = memo.get_cost(sr, cnt);
-    const unsigned long long xb = (unsigned long long)__double_as_longlong(x);
+    const double cl = ml ? memo.get_cost(sl, cnt) : 0.0;
+    const double cr = mr ? memo.get_cost(sr, cnt) : 0.0;
+    // with one side a single relation (cost +0.0) the sum is the other cost
+    // exactly: OR of the bit patterns, no FP64 instruction
+    const unsigned long long xb =
+        (ml && mr) ? (unsigned long long)__double_as_longlong(__dadd_rn(cl, cr))
+                   : ((unsigned long long)__double_as_longlong(cl) | (unsigned long long)__double_as_longlong(cr));
     const uint32_t l = sl < sr ? sl : sr;
     if (better_x(xb, l, bx, bl)) {
         bx = xb;

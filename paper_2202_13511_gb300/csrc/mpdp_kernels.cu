@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
     int* cw = reinterpret_cast<int*>(cnt);
     for (int i = tid; i < (int)(sizeof(DevCounters) / sizeof(int)); i += blockDim.x) cw[i] = 0;
     __shared__ int s_status;
+    __shared__ uint32_t s_children[kMaxRels];
     if (tid == 0) {
         const int n = st->n, m = st->n_edges;
         int status = 0;
@@ -169,24 +170,42 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
                 q->nsel[q->nbase[u] + __popc(adj[u] & ((1u << v) - 1u))] = st->edges[e].sel;
                 q->nsel[q->nbase[v] + __popc(adj[v] & ((1u << u) - 1u))] = st->edges[e].sel;
             }
+        // breadth-first spanning tree rooted at relation 0: children bitmaps
+        uint32_t seen = 1u, frontier = 1u;
+        for (int r = 0; r < kMaxRels; r++) s_children[r] = 0u;
+        if (status == 0) {
+            while (frontier) {
+                const int x = lowest(frontier);
+                frontier &= frontier - 1u;
+                const uint32_t ch = adj[x] & ~seen;
+                s_children[x] = ch;
+                seen |= ch;
+                frontier |= ch;
+            }
+        }
         q->n = n;
         q->n_edges = status == 0 ? m : 0;
+        q->is_tree = (status == 0 && m == n - 1) ? 1 : 0;
         s_status = status;
     }
     __syncthreads();
     const int status = s_status;
     if (tid == 0) cnt->status = status;
     if (status == 0 && dense) {
-        DenseMemo memo{a.memo, a.left, nullptr, nullptr};
+        DenseMemo memo{a.memo_cost, a.memo_card, a.left, nullptr, nullptr, nullptr};
         memo.bind(a, qi);
         if (tid < st->n) memo.put(1u << tid, 1, 0.0, q->card[tid], 0u, cnt);
     }
     for (int e = tid; e < 4 * 256; e += blockDim.x) {
         const int b = e >> 8, x = e & 255;
-        uint32_t u = 0u;
+        uint32_t u = 0u, c = 0u;
         for (int i = 0; i < 8; i++)
-            if (x >> i & 1) u |= q->adj[8 * b + i];
+            if (x >> i & 1) {
+                u |= q->adj[8 * b + i];
+                c |= s_children[8 * b + i];
+            }
         q->nbt[b][x] = u;
+        q->ctt[b][x] = c;
     }
 }
 
@@ -247,6 +266,7 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
 {
     __shared__ uint32_t s_binom[33 * 33];
     __shared__ uint32_t s_nbt[4][256];
+    __shared__ uint32_t s_ctt[4][256];
     // query of this block: the largest q with prefix[q] <= blockIdx.x
     int lo = 0, hi = a.nq - 1;
     while (lo < hi) {
@@ -259,9 +279,13 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
     const DevQuery* __restrict__ q = a.query + qi;
     DevCounters* __restrict__ cnt = &a.out[qi].counters;
     for (int t = threadIdx.x; t < 33 * 33; t += blockDim.x) s_binom[t] = kBinom.v[t];
-    for (int t = threadIdx.x; t < 4 * 256; t += blockDim.x) s_nbt[t >> 8][t & 255] = q->nbt[t >> 8][t & 255];
+    for (int t = threadIdx.x; t < 4 * 256; t += blockDim.x) {
+        s_nbt[t >> 8][t & 255] = q->nbt[t >> 8][t & 255];
+        s_ctt[t >> 8][t & 255] = q->ctt[t >> 8][t & 255];
+    }
     __syncthreads();
     if (cnt->status != 0) return;
+    const bool is_tree = q->is_tree != 0;
     const uint32_t warp = (blockIdx.x - a.filter_block_prefix[qi]) * (kFilterThreads / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const int n = d.n;
@@ -277,16 +301,38 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
     const uint32_t s0 = len ? unrank_colex((uint32_t)r0, k, n, s_binom) : 0u;
     uint32_t s = s0, flags = 0u, rounds = 0u;
     // In colex order the high half of S rarely changes along a run: its part
-    // of N(S) is cached and recomputed only when bits 16..31 change.
-    uint32_t s_hi = 0xffffffffu, nb_hi = 0u;
-    for (uint32_t i = 0; i < len; i++) {
-        if ((s >> 16) != s_hi) {
-            s_hi = s >> 16;
-            nb_hi = s_nbt[2][s_hi & 255u] | s_nbt[3][s_hi >> 8];
+    // of the table lookups is cached and redone only when bits 16..31 change.
+    uint32_t s_hi = 0xffffffffu, ch_hi = 0u, nb_hi = 0u;
+    if (is_tree) {
+        // tree join graph: connected(S) iff exactly one member of S has its
+        // parent outside S (one top per component), with no search at all
+        for (uint32_t i = 0; i < len; i++) {
+            if ((s >> 16) != s_hi) {
+                s_hi = s >> 16;
+                ch_hi = s_ctt[2][s_hi & 255u] | s_ctt[3][s_hi >> 8];
+            }
+            const uint32_t ch = ch_hi | s_ctt[0][s & 255u] | s_ctt[1][(s >> 8) & 255u];
+            if (__popc(tops_of(s, ch)) == 1) flags |= 1u << i;
+            s = next_colex(s);
         }
-        const uint32_t nb = nb_hi | s_nbt[0][s & 255u] | s_nbt[1][(s >> 8) & 255u];
-        if ((s & ~nb) == 0u && connected_rounds_from(s, s_nbt, rounds)) flags |= 1u << i;
-        s = next_colex(s);
+    } else {
+        // general join graph: accept when the spanning tree alone connects
+        // S; reject when some member has no neighbour in S; else BFS rounds
+        for (uint32_t i = 0; i < len; i++) {
+            if ((s >> 16) != s_hi) {
+                s_hi = s >> 16;
+                ch_hi = s_ctt[2][s_hi & 255u] | s_ctt[3][s_hi >> 8];
+                nb_hi = s_nbt[2][s_hi & 255u] | s_nbt[3][s_hi >> 8];
+            }
+            const uint32_t ch = ch_hi | s_ctt[0][s & 255u] | s_ctt[1][(s >> 8) & 255u];
+            bool ok = __popc(tops_of(s, ch)) == 1;
+            if (!ok) {
+                const uint32_t nb = nb_hi | s_nbt[0][s & 255u] | s_nbt[1][(s >> 8) & 255u];
+                ok = (s & ~nb) == 0u && connected_rounds_from(s, s_nbt, rounds);
+            }
+            if (ok) flags |= 1u << i;
+            s = next_colex(s);
+        }
     }
     const uint32_t c = __popc(flags);
     uint32_t incl = c;
@@ -412,9 +458,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
         if (idx < cnt->list_count[k]) {
             const QDesc& d = a.desc[qi];
             const uint32_t s = a.lists[d.list_base + d.list_off[k] + idx];
-            const double card_s = peel_card(s, tree_peel_vertex(s, sq.adj), sq, memo, cnt);
-            unsigned long long bx = kNoX;
-            uint32_t bl = kFull;
+            // all k-1 splits first, so that their memo reads below are
+            // independent and issue back to back
+            uint32_t split[kMaxRels];
+            int m = 0;
             uint32_t vis = s & (0u - s), queue = vis;
             while (queue) {
                 const int x = lowest(queue);
@@ -426,10 +473,14 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
                 while (ch) {
                     const int v = lowest(ch);
                     ch &= ch - 1u;
-                    const uint32_t sl = grow(1u << v, rest, sq.adj);
-                    fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
+                    split[m++] = grow(1u << v, rest, sq.adj);
                 }
             }
+            const double card_s = peel_card(s, tree_peel_vertex(s, sq.adj), sq, memo, cnt);
+            unsigned long long bx = kNoX;
+            uint32_t bl = kFull;
+#pragma unroll 4
+            for (int i = 0; i < m; i++) fold_pair(split[i], s ^ split[i], memo, cnt, bx, bl);
             memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
             sets++;
         }
@@ -996,7 +1047,7 @@ cudaError_t enqueue_pipeline(const BatchArgs& a, const BatchPlan& bp, int memo_k
         launches++;
     }
     if (dense) {
-        DenseMemo memo{a.memo, a.left, nullptr, nullptr};
+        DenseMemo memo{a.memo_cost, a.memo_card, a.left, nullptr, nullptr, nullptr};
         launch_levels(a, bp, memo, st, launches, hook);
     } else {
         {
@@ -1033,7 +1084,7 @@ cudaError_t enqueue_memo_lookup(const BatchArgs& a, int memo_kind, int qi, const
 {
     const int grid = (count + 255) / 256 > 0 ? (count + 255) / 256 : 1;
     if (memo_kind == MPDP_MEMO_DENSE) {
-        DenseMemo memo{a.memo, a.left, nullptr, nullptr};
+        DenseMemo memo{a.memo_cost, a.memo_card, a.left, nullptr, nullptr, nullptr};
         k_memo_lookup<DenseMemo><<<grid, 256, 0, st>>>(a, qi, d_sets, count, d_costs, d_lefts, memo);
     } else {
         HashMemo memo{a.arena, nullptr, nullptr};

@@ -14,7 +14,7 @@ namespace mpdp {
 // Grid sizing of one batch, computed on the host from the queries' sizes.
 struct BatchPlan {
     int num_sms = 152;
-    int blocks_per_sm = 4;
+    int blocks_per_sm = 8;  // eval grids: 8 x 256 threads = a full SM's worth of warps
     uint32_t filter_blocks = 0;
     unsigned long long tree_tiles[kLevels] = {};   // upper bound of level-k tiles, tree queries
     unsigned long long block_tiles[kLevels] = {};  // same, block-mode queries

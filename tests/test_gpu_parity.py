@@ -318,7 +318,10 @@ def test_device_batch_path(opt):
 def test_batch_split_by_budget():
     """A small memo budget splits one call into several device batches; every
     result stays exact, and a query larger than the budget is refused."""
-    small = mpdp.workspace_bytes(16) + mpdp.workspace_bytes(15)
+    # room for one 16-relation query (plus the fixed per-context part), so
+    # every query below runs in a device batch of its own
+    small = mpdp.workspace_bytes(16) + 4096
+    assert mpdp.workspace_bytes(20) > small
     with mpdp.Optimizer(0, memo_budget_bytes=small) as o:
         qs = [W.snowflake(16, seed=s) for s in range(3)] + [W.cyclic(15, seed=2), W.star(14, seed=1)]
         plans = o.optimize_batch(qs)
