@@ -81,6 +81,13 @@ enum { MPDP_ENUM_AUTO = 0, MPDP_ENUM_TREE = 1, MPDP_ENUM_BLOCKS = 2 };
  * two >= 2x the level's connected-set count (Sec. 5, memo of "MPDP on GPU"). */
 enum { MPDP_MEMO_DENSE = 0, MPDP_MEMO_HASH = 1 };
 
+/* Connected-set filter.  UNRANK: every k-subset of every level is unranked
+ * with the combinatorial number system and stepped with the next bit
+ * permutation (Sec. 5, "Unrank", "Filter").  BITMAPS: every bitmap below 2^n
+ * is visited in index order (all levels at once, no unranking) and the
+ * connected ones are then sorted into their levels.  Same results. */
+enum { MPDP_FILTER_BITMAPS = 0, MPDP_FILTER_UNRANK = 1 };
+
 typedef struct mpdp_ctx mpdp_ctx; /* opaque, owned by the library */
 
 /* One join predicate between relations u and v (0 <= u, v < n, u != v) with
@@ -148,6 +155,7 @@ typedef struct {
                                  in the warp-per-set kernel (Sec. 5) */
     int32_t use_graphs;       /* 1 (default): replay a captured CUDA graph per shape */
     int32_t run_length;       /* k-subsets unranked per lane (1..32, default 32) */
+    int32_t filter;           /* MPDP_FILTER_BITMAPS (default) or MPDP_FILTER_UNRANK */
 } mpdp_config;
 
 /* Create a context on CUDA device `device`.  memo_budget_bytes caps the device
@@ -225,7 +233,7 @@ int32_t mpdp_last_launch_count(const mpdp_ctx *ctx);
 enum {
     MPDP_KC_STAGE = 0,   /* device-path input gather */
     MPDP_KC_INGEST = 1,  /* graph build and validation */
-    MPDP_KC_FILTER = 2,  /* unrank + connectivity filter, all levels */
+    MPDP_KC_FILTER = 2,  /* connectivity filter, all levels (with the level sort) */
     MPDP_KC_MEMO_INIT = 3, /* hash memo layout and clear */
     MPDP_KC_EVAL = 4,    /* per-level evaluate + prune + scatter (thread per set) */
     MPDP_KC_HEAVY = 5,   /* per-level block-per-set evaluation (block mode) */

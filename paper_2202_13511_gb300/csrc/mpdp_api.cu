@@ -25,7 +25,7 @@ using namespace mpdp;
 
 namespace {
 
-const mpdp_config kDefaultConfig = {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 1, 32};
+const mpdp_config kDefaultConfig = {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 1, 32, MPDP_FILTER_BITMAPS};
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -128,8 +128,7 @@ struct mpdp_ctx {
     size_t list_words = 0, heavy_words = 0, memo_entries = 0, arena_slots = 0;
     uint32_t* d_lists = nullptr;
     uint32_t* d_heavy = nullptr;
-    double* d_cost = nullptr;
-    double* d_card = nullptr;
+    double2* d_memo = nullptr;
     uint32_t* d_left = nullptr;
     HashSlot* d_arena = nullptr;
     // host side
@@ -222,7 +221,7 @@ static QuerySize query_size(int n, int enumeration, int memo_kind)
 
 static size_t var_bytes_of(size_t lists, size_t heavy, size_t memo, size_t hash)
 {
-    return align_up(lists * 4) + align_up(heavy * 4) + 2 * align_up(memo * sizeof(double)) +
+    return align_up(lists * 4) + align_up(heavy * 4) + align_up(memo * sizeof(double2)) +
            align_up(memo * sizeof(uint32_t)) + align_up(hash * sizeof(HashSlot));
 }
 
@@ -304,8 +303,7 @@ static int ensure_var(mpdp_ctx* ctx, size_t lists, size_t heavy, size_t memo, si
     };
     ctx->d_lists = reinterpret_cast<uint32_t*>(take(L * 4));
     ctx->d_heavy = reinterpret_cast<uint32_t*>(take(V * 4));
-    ctx->d_cost = reinterpret_cast<double*>(take(M * sizeof(double)));
-    ctx->d_card = reinterpret_cast<double*>(take(M * sizeof(double)));
+    ctx->d_memo = reinterpret_cast<double2*>(take(M * sizeof(double2)));
     ctx->d_left = reinterpret_cast<uint32_t*>(take(M * sizeof(uint32_t)));
     ctx->d_arena = reinterpret_cast<HashSlot*>(take(H * sizeof(HashSlot)));
     ctx->list_words = L;
@@ -328,8 +326,7 @@ static BatchArgs batch_args(const mpdp_ctx* ctx, int nq, int max_n)
     a.out = ctx->d_out;
     a.lists = ctx->d_lists;
     a.heavy = ctx->d_heavy;
-    a.memo_cost = ctx->d_cost;
-    a.memo_card = ctx->d_card;
+    a.memo = ctx->d_memo;
     a.left = ctx->d_left;
     a.arena = ctx->d_arena;
     a.layout = ctx->d_layout;
@@ -337,6 +334,7 @@ static BatchArgs batch_args(const mpdp_ctx* ctx, int nq, int max_n)
     a.run = ctx->cfg.run_length;
     a.heavy_threshold = ctx->cfg.heavy_threshold;
     a.use_ccc = ctx->cfg.use_ccc;
+    a.filter_mode = ctx->cfg.filter;
     return a;
 }
 
@@ -352,11 +350,12 @@ static int split_batches(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, std::v
     for (int i = 0; i < (int)qs.size(); i++) {
         const QuerySize z = query_size(qs[i].n, qs[i].enumeration, kind);
         const bool zb = qs[i].enumeration == MPDP_ENUM_BLOCKS;
-        if (var_bytes_of(z.lists, zb ? z.lists : 0, z.memo, z.hash) + fixed_bytes() > ctx->budget)
+        const bool zh = zb;
+        if (var_bytes_of(z.lists, zh ? z.lists : 0, z.memo, z.hash) + fixed_bytes() > ctx->budget)
             return MPDP_ERR_ADMISSION;
         const bool full = (i - start) >= kMaxBatch;
         const size_t L2 = L + z.lists;
-        const size_t need = var_bytes_of(L2, (blocks || zb) ? L2 : 0, M + z.memo, A + z.hash) + fixed_bytes();
+        const size_t need = var_bytes_of(L2, (blocks || zh) ? L2 : 0, M + z.memo, A + z.hash) + fixed_bytes();
         if (i > start && (full || need > ctx->budget)) {
             out.emplace_back(start, i);
             start = i;
@@ -366,7 +365,7 @@ static int split_batches(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, std::v
         L += z.lists;
         M += z.memo;
         A += z.hash;
-        blocks = blocks || zb;
+        blocks = blocks || zh;
     }
     if (start < (int)qs.size()) out.emplace_back(start, (int)qs.size());
     return MPDP_OK;
@@ -502,7 +501,8 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
     StagedQuery* hs = reinterpret_cast<StagedQuery*>(h + staged_off);
     BatchPlan bp;
     bp.num_sms = ctx->num_sms;
-    std::vector<int> key = {nq, kind, ctx->cfg.heavy_threshold, ctx->cfg.use_ccc, ctx->cfg.run_length};
+    std::vector<int> key = {nq, kind, ctx->cfg.heavy_threshold, ctx->cfg.use_ccc, ctx->cfg.run_length,
+                            ctx->cfg.filter};
     unsigned long long lbase = 0, mbase = 0;
     uint32_t fblocks = 0;
     int max_n = 0;
@@ -520,7 +520,7 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
         d.card_off = q.card_off;
         d.edge_off = q.edge_off;
         uint32_t qb = 0;
-        fill_levels(d, ctx->cfg.run_length, qb);
+        fill_levels(d, ctx->cfg.run_length, ctx->cfg.filter, qb);
         d.filter_block_base = fblocks;
         hp[i] = fblocks;
         fblocks += qb;
@@ -699,6 +699,7 @@ int mpdp_set_config(mpdp_ctx* ctx, const mpdp_config* cfg)
     if (cfg->memo_kind != MPDP_MEMO_DENSE && cfg->memo_kind != MPDP_MEMO_HASH) return MPDP_ERR_INVALID_ARG;
     if (cfg->enumeration < MPDP_ENUM_AUTO || cfg->enumeration > MPDP_ENUM_BLOCKS) return MPDP_ERR_INVALID_ARG;
     if (cfg->heavy_threshold < 0 || cfg->run_length < 1 || cfg->run_length > 32) return MPDP_ERR_INVALID_ARG;
+    if (cfg->filter != MPDP_FILTER_BITMAPS && cfg->filter != MPDP_FILTER_UNRANK) return MPDP_ERR_INVALID_ARG;
     ctx->cfg = *cfg;
     return MPDP_OK;
 }

@@ -123,8 +123,7 @@ struct BatchArgs {
     DevOut* out;
     uint32_t* lists;
     uint32_t* heavy;
-    double* memo_cost;   // dense memo cost[S]
-    double* memo_card;   // dense memo card[S]
+    double2* memo;       // dense memo {cost, card}[S]
     uint32_t* left;      // dense memo left[S]
     HashSlot* arena;     // hash memo slots
     HashLayout* layout;  // [nq]
@@ -132,6 +131,8 @@ struct BatchArgs {
     int run;             // ranks per lane in the filter (<= 32)
     int heavy_threshold;
     int use_ccc;
+    int filter_mode;     // MPDP_FILTER_BITMAPS or MPDP_FILTER_UNRANK (the filter_block_prefix
+                         // counts the blocks of the chosen filter)
 };
 
 // Record the first device error; later errors keep the first code.
@@ -269,16 +270,14 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h)
     return h;
 }
 
-// Memo indexed directly by the relation bitmap, as three arrays: cost[S]
-// (read by every pair), card[S] (read once per set, by peeling) and left[S]
-// (read by the plan fetch only).  A cost lookup then shares its 32-byte
-// sector with three neighbouring bitmaps instead of one.
+// Memo indexed directly by the relation bitmap: a 16-byte entry {cost, card}
+// (cost read by every pair, card by the peeling of the next level; one
+// sector either way, and one sector written per set) and left[S], read by
+// the plan fetch only.
 struct DenseMemo {
-    double* cost0;     // batch arena
-    double* card0;
+    double2* cc0;      // batch arena
     uint32_t* left0;
-    double* cost;      // bound to one query
-    double* card;
+    double2* cc;       // bound to one query
     uint32_t* left;
 
     static constexpr size_t kSharedBytes = 16;
@@ -288,22 +287,21 @@ struct DenseMemo {
     __device__ __forceinline__ void bind(const BatchArgs& a, int q)
     {
         const unsigned long long b = a.desc[q].memo_base;
-        cost = cost0 + b;
-        card = card0 + b;
+        cc = cc0 + b;
         left = left0 + b;
     }
-    __device__ __forceinline__ double get_cost(uint32_t s, DevCounters*) const { return __ldg(cost + s); }
-    __device__ __forceinline__ double get_card(uint32_t s, DevCounters*) const { return __ldg(card + s); }
+    __device__ __forceinline__ double get_cost(uint32_t s, DevCounters*) const { return __ldg(&cc[s].x); }
+    __device__ __forceinline__ double get_card(uint32_t s, DevCounters*) const { return __ldg(&cc[s].y); }
     __device__ __forceinline__ void get(uint32_t s, double& c, double& cd, uint32_t& l, DevCounters*) const
     {
-        c = cost[s];
-        cd = card[s];
+        const double2 v = cc[s];
+        c = v.x;
+        cd = v.y;
         l = left[s];
     }
     __device__ __forceinline__ void put(uint32_t s, int, double c, double cd, uint32_t l, DevCounters*)
     {
-        cost[s] = c;
-        card[s] = cd;
+        cc[s] = make_double2(c, cd);
         left[s] = l;
     }
 };

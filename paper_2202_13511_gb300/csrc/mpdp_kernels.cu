@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
     const int status = s_status;
     if (tid == 0) cnt->status = status;
     if (status == 0 && dense) {
-        DenseMemo memo{a.memo_cost, a.memo_card, a.left, nullptr, nullptr, nullptr};
+        DenseMemo memo{a.memo, a.left, nullptr, nullptr};
         memo.bind(a, qi);
         if (tid < st->n) memo.put(1u << tid, 1, 0.0, q->card[tid], 0u, cnt);
     }
@@ -366,6 +366,149 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// a2 + a3, bitmap form: every bitmap S < 2^n of every query is tested, in
+// index order, all levels at once (no unranking).  Thread t of a query takes
+// the aligned run of 32 bitmaps 32t .. 32t+31; bits 5..31 are fixed along the
+// run, so their share of the table lookups is done once per run and each
+// bitmap needs one broadcast lookup for its low five bits.  Connected sets
+// (|S| >= 2) go straight into the list of their level, in bitmap order
+// within each warp's slice.
+constexpr uint32_t kBitmapsPerThread = 32;
+constexpr uint32_t kBitmapsPerBlock = kFilterThreads * kBitmapsPerThread;
+
+// kPopcMask.v[j]: the i in [0, 32) with popcount(i) == j, as a 32-bit mask.
+struct PopcMasks {
+    uint32_t v[6];
+};
+
+constexpr PopcMasks make_popc_masks()
+{
+    PopcMasks m{};
+    for (int i = 0; i < 32; i++) {
+        int c = 0;
+        for (int b = 0; b < 5; b++) c += (i >> b) & 1;
+        m.v[c] |= 1u << i;
+    }
+    return m;
+}
+
+__device__ const PopcMasks kPopcMask = make_popc_masks();
+
+__global__ void __launch_bounds__(kFilterThreads) k_filter_bitmaps(BatchArgs a)
+{
+    __shared__ uint32_t s_nbt[4][256];
+    __shared__ uint32_t s_ctt[4][256];
+    int lo = 0, hi = a.nq - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.filter_block_prefix[mid] <= blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const int qi = lo;
+    const QDesc& d = a.desc[qi];
+    const DevQuery* __restrict__ q = a.query + qi;
+    DevCounters* __restrict__ cnt = &a.out[qi].counters;
+    for (int t = threadIdx.x; t < 4 * 256; t += blockDim.x) {
+        s_nbt[t >> 8][t & 255] = q->nbt[t >> 8][t & 255];
+        s_ctt[t >> 8][t & 255] = q->ctt[t >> 8][t & 255];
+    }
+    __syncthreads();
+    if (cnt->status != 0) return;
+    const bool is_tree = q->is_tree != 0;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long base64 =
+        ((unsigned long long)(blockIdx.x - a.filter_block_prefix[qi]) * kFilterThreads + threadIdx.x) *
+        kBitmapsPerThread;
+    const unsigned long long limit = 1ull << d.n;
+    uint32_t flags = 0u, rounds = 0u, examined = 0u;
+    const uint32_t base = (uint32_t)base64;
+    if (base64 < limit) {
+        const uint32_t c_run = s_ctt[0][base & 0xe0u] | s_ctt[1][(base >> 8) & 255u] |
+                               s_ctt[2][(base >> 16) & 255u] | s_ctt[3][base >> 24];
+        if (is_tree) {
+            // tree join graph: connected iff exactly one member's parent is outside S
+#pragma unroll
+            for (uint32_t i = 0; i < kBitmapsPerThread; i++) {
+                const uint32_t s = base | i;
+                flags |= (__popc(s & ~(c_run | s_ctt[0][i])) == 1 ? 1u : 0u) << i;
+            }
+        } else {
+            const uint32_t n_run = s_nbt[0][base & 0xe0u] | s_nbt[1][(base >> 8) & 255u] |
+                                   s_nbt[2][(base >> 16) & 255u] | s_nbt[3][base >> 24];
+            for (uint32_t i = 0; i < kBitmapsPerThread; i++) {
+                const uint32_t s = base | i;
+                bool ok = __popc(s & ~(c_run | s_ctt[0][i])) == 1;
+                if (!ok) ok = (s & ~(n_run | s_nbt[0][i])) == 0u && connected_rounds_from(s, s_nbt, rounds);
+                if (ok) flags |= 1u << i;
+            }
+        }
+        uint32_t valid = 0xffffffffu;
+        if (limit - base64 < kBitmapsPerThread) valid = (1u << (uint32_t)(limit - base64)) - 1u;
+        if (__popc(base) <= 1)  // the empty set and single relations are not DP sets
+            for (uint32_t i = 0; i < kBitmapsPerThread; i++)
+                if (__popc(base | i) < 2) valid &= ~(1u << i);
+        flags &= valid;
+        examined = __popc(valid);
+    }
+    // Ordered output straight into the level lists.  The warp covers the
+    // 1024 bitmaps w0 .. w0+1023 (w0 = its first bitmap), so bitmap
+    // base | i of lane l has level popc(w0) + popc(l) + popc(i): 11 level
+    // bins per warp.  A shuffle scan per bin places every lane's sets in
+    // bitmap order and one atomic per non-empty bin reserves list room.
+    if (__any_sync(kFull, flags != 0u)) {
+        const int pw = __popc((uint32_t)(base64 - (unsigned long long)lane * kBitmapsPerThread));
+        const int pl = __popc((uint32_t)lane);
+        uint32_t cj[6], ex[6];
+#pragma unroll
+        for (int j = 0; j < 6; j++) cj[j] = __popc(flags & kPopcMask.v[j]);
+        uint32_t my_total = 0u;
+#pragma unroll
+        for (int t = 0; t <= 10; t++) {
+            uint32_t v = 0u;
+#pragma unroll
+            for (int j = 0; j < 6; j++) v = (t - pl == j) ? cj[j] : v;
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += u;
+            }
+            const uint32_t tot = __shfl_sync(kFull, incl, 31);
+            if (lane == t) my_total = tot;
+#pragma unroll
+            for (int j = 0; j < 6; j++)
+                if (t - pl == j) ex[j] = incl - v;
+        }
+        uint32_t bpos = 0u;
+        if (lane <= 10 && my_total) bpos = atomicAdd(&cnt->list_count[pw + lane], my_total);
+        uint32_t* lists = a.lists + d.list_base;
+        uint32_t start[6];
+#pragma unroll
+        for (int j = 0; j < 6; j++) start[j] = __shfl_sync(kFull, bpos, pl + j) + ex[j];
+        uint32_t f = flags;
+        while (f) {
+            const int i = lowest(f);
+            f &= f - 1u;
+            const int j = __popc((uint32_t)i);
+            uint32_t pos = 0u;
+#pragma unroll
+            for (int jj = 0; jj < 6; jj++)
+                if (j == jj) pos = start[jj]++;
+            lists[d.list_off[pw + pl + j] + pos] = base | (uint32_t)i;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        examined += __shfl_xor_sync(kFull, examined, o);
+        rounds += __shfl_xor_sync(kFull, rounds, o);
+    }
+    if (lane == 0 && examined) {
+        atomicAdd(&cnt->unranked, (unsigned long long)examined);
+        if (rounds) atomicAdd(&cnt->filter_steps, (unsigned long long)rounds);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Hash memo layout: per query and level k, capacity = the power of two >= 2x
 // the level's connected count (at least 16), carved from one arena.
 __global__ void k_hash_layout(BatchArgs a)
@@ -458,24 +601,38 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
         if (idx < cnt->list_count[k]) {
             const QDesc& d = a.desc[qi];
             const uint32_t s = a.lists[d.list_base + d.list_off[k] + idx];
-            // all k-1 splits first, so that their memo reads below are
-            // independent and issue back to back
+            // All k-1 splits first, so that their memo reads below are
+            // independent and issue back to back.  One search from min(S)
+            // records each vertex's parent in discovery order; walking that
+            // order backwards accumulates every subtree bitmap in O(k):
+            // split[i] = the subtree under the i-th discovered vertex, i.e.
+            // grow({v}, S \ {parent(v)}).
             uint32_t split[kMaxRels];
+            uint8_t par_slot[kMaxRels];  // slot of the parent (0xff: the root)
+            uint8_t slot_of[kMaxRels];   // slot of each discovered vertex
             int m = 0;
-            uint32_t vis = s & (0u - s), queue = vis;
+            const int root = lowest(s);
+            slot_of[root] = 0xff;
+            uint32_t vis = 1u << root, queue = vis;
             while (queue) {
                 const int x = lowest(queue);
                 queue &= queue - 1u;
                 uint32_t ch = sq.adj[x] & s & ~vis;
                 vis |= ch;
                 queue |= ch;
-                const uint32_t rest = s & ~(1u << x);
                 while (ch) {
                     const int v = lowest(ch);
                     ch &= ch - 1u;
-                    split[m++] = grow(1u << v, rest, sq.adj);
+                    slot_of[v] = (uint8_t)m;
+                    par_slot[m] = slot_of[x];
+                    split[m] = 1u << v;
+                    m++;
                 }
             }
+            // a parent is discovered before its children, so one backward
+            // pass adds every subtree into its parent's
+            for (int i = m - 1; i > 0; i--)
+                if (par_slot[i] != 0xff) split[par_slot[i]] |= split[i];
             const double card_s = peel_card(s, tree_peel_vertex(s, sq.adj), sq, memo, cnt);
             unsigned long long bx = kNoX;
             uint32_t bl = kFull;
@@ -966,7 +1123,7 @@ size_t hash_arena_slots(int n)
     return (size_t)total;
 }
 
-void fill_levels(QDesc& d, int run, uint32_t& filter_blocks)
+void fill_levels(QDesc& d, int run, int filter_mode, uint32_t& filter_blocks)
 {
     const int n = d.n;
     unsigned long long off = 0, wb = 0;
@@ -981,7 +1138,10 @@ void fill_levels(QDesc& d, int run, uint32_t& filter_blocks)
     }
     for (int k = (n >= 2 ? n + 1 : 0); k <= kLevels; k++) d.warp_begin[k] = (uint32_t)wb;
     const unsigned warps_per_block = kFilterThreads / 32;
-    filter_blocks = (uint32_t)((wb + warps_per_block - 1) / warps_per_block);
+    if (filter_mode == MPDP_FILTER_BITMAPS)
+        filter_blocks = n >= 2 ? (uint32_t)(((1ull << n) + kBitmapsPerBlock - 1) / kBitmapsPerBlock) : 0u;
+    else
+        filter_blocks = (uint32_t)((wb + warps_per_block - 1) / warps_per_block);
 }
 
 struct HookScope {
@@ -1043,11 +1203,16 @@ cudaError_t enqueue_pipeline(const BatchArgs& a, const BatchPlan& bp, int memo_k
     launches++;
     if (bp.filter_blocks > 0) {
         HookScope hs(hook, MPDP_KC_FILTER, st);
-        k_filter<<<bp.filter_blocks, kFilterThreads, 0, st>>>(a);
-        launches++;
+        if (a.filter_mode == MPDP_FILTER_BITMAPS) {
+            k_filter_bitmaps<<<bp.filter_blocks, kFilterThreads, 0, st>>>(a);
+            launches++;
+        } else {
+            k_filter<<<bp.filter_blocks, kFilterThreads, 0, st>>>(a);
+            launches++;
+        }
     }
     if (dense) {
-        DenseMemo memo{a.memo_cost, a.memo_card, a.left, nullptr, nullptr, nullptr};
+        DenseMemo memo{a.memo, a.left, nullptr, nullptr};
         launch_levels(a, bp, memo, st, launches, hook);
     } else {
         {
@@ -1084,7 +1249,7 @@ cudaError_t enqueue_memo_lookup(const BatchArgs& a, int memo_kind, int qi, const
 {
     const int grid = (count + 255) / 256 > 0 ? (count + 255) / 256 : 1;
     if (memo_kind == MPDP_MEMO_DENSE) {
-        DenseMemo memo{a.memo_cost, a.memo_card, a.left, nullptr, nullptr, nullptr};
+        DenseMemo memo{a.memo, a.left, nullptr, nullptr};
         k_memo_lookup<DenseMemo><<<grid, 256, 0, st>>>(a, qi, d_sets, count, d_costs, d_lefts, memo);
     } else {
         HashMemo memo{a.arena, nullptr, nullptr};

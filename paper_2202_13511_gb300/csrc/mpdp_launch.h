@@ -34,7 +34,7 @@ size_t list_entries(int n);
 size_t hash_arena_slots(int n);
 // Per-level list offsets and filter warp ranges of one query; returns the
 // query's filter block count in filter_blocks.
-void fill_levels(QDesc& d, int run, uint32_t& filter_blocks);
+void fill_levels(QDesc& d, int run, int filter_mode, uint32_t& filter_blocks);
 
 cudaError_t enqueue_pipeline(const BatchArgs& a, const BatchPlan& bp, int memo_kind, cudaStream_t st,
                              int* launches, LaunchHook* hook = nullptr);

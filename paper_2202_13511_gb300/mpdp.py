@@ -30,6 +30,7 @@ ERR = {v: k for k, v in ERRORS.items()}
 MODE_EXACT, MODE_IDP2, MODE_UNIONDP, MODE_IDP2_LEARNED, MODE_UNIONDP_LEARNED = range(5)
 ENUM_AUTO, ENUM_TREE, ENUM_BLOCKS = range(3)
 MEMO_DENSE, MEMO_HASH = range(2)
+FILTER_BITMAPS, FILTER_UNRANK = range(2)
 MAX_LEVELS = 33
 
 
@@ -76,7 +77,8 @@ class StatsC(ctypes.Structure):
 class ConfigC(ctypes.Structure):
     _fields_ = [("memo_kind", ctypes.c_int32), ("enumeration", ctypes.c_int32),
                 ("heavy_threshold", ctypes.c_int32), ("use_ccc", ctypes.c_int32),
-                ("use_graphs", ctypes.c_int32), ("run_length", ctypes.c_int32)]
+                ("use_graphs", ctypes.c_int32), ("run_length", ctypes.c_int32),
+                ("filter", ctypes.c_int32)]
 
 
 EDGE_DTYPE = np.dtype([("u", "<i4"), ("v", "<i4"), ("sel", "<f8")])
@@ -373,7 +375,7 @@ class Optimizer:
 
 def workspace_bytes(n: int, memo_kind: int = MEMO_DENSE) -> int:
     L = load()
-    c = ConfigC(memo_kind, 0, 64, 1, 1, 32)
+    c = ConfigC(memo_kind, 0, 64, 1, 1, 32, FILTER_BITMAPS)
     return int(L.mpdp_workspace_bytes(n, ctypes.byref(c)))
 
 

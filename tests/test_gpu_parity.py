@@ -19,6 +19,9 @@ CONFIGS = {
     "hash_auto": dict(memo_kind=mpdp.MEMO_HASH, enumeration=mpdp.ENUM_AUTO),
     "dense_blocks": dict(memo_kind=mpdp.MEMO_DENSE, enumeration=mpdp.ENUM_BLOCKS),
     "hash_blocks": dict(memo_kind=mpdp.MEMO_HASH, enumeration=mpdp.ENUM_BLOCKS),
+    "unrank_auto": dict(filter=mpdp.FILTER_UNRANK),
+    "unrank_hash_blocks": dict(filter=mpdp.FILTER_UNRANK, memo_kind=mpdp.MEMO_HASH,
+                               enumeration=mpdp.ENUM_BLOCKS),
 }
 
 
@@ -31,7 +34,7 @@ def opt():
 
 def set_cfg(opt, **kw):
     base = dict(memo_kind=mpdp.MEMO_DENSE, enumeration=mpdp.ENUM_AUTO, heavy_threshold=64,
-                use_ccc=1, use_graphs=1, run_length=32)
+                use_ccc=1, use_graphs=1, run_length=32, filter=mpdp.FILTER_BITMAPS)
     base.update(kw)
     opt.set_config(**base)
 
@@ -89,7 +92,7 @@ def test_small_exhaustive(opt, cfg, kind):
 @pytest.mark.parametrize("kind", ["star", "snowflake", "cyclic", "cycle", "chain"])
 @pytest.mark.parametrize("n", [14, 16, 18])
 def test_medium_whole_memo(opt, kind, n):
-    for cfg in ("dense_auto", "hash_auto"):
+    for cfg in ("dense_auto", "hash_auto", "unrank_auto"):
         set_cfg(opt, **CONFIGS[cfg])
         q = W.make(kind, n, seed=n)
         check(opt, q)
@@ -108,11 +111,14 @@ def test_clique_14(opt, cfg):
 
 @pytest.mark.parametrize("n", [20, 25])
 def test_snowflake_full_size(opt, n):
-    """Config: acyclic snowflake queries of 20 and 25 relations (tree mode)."""
-    set_cfg(opt)
+    """Config: acyclic snowflake queries of 20 and 25 relations (tree mode),
+    with both connected-set filters."""
     for seed in range(3):
         q = W.snowflake(n, seed=seed)
-        check(opt, q, memo="sample")
+        ref = oracle.dpccp(q)
+        for flt in (mpdp.FILTER_BITMAPS, mpdp.FILTER_UNRANK):
+            set_cfg(opt, filter=flt)
+            check(opt, q, ref, memo="sample")
 
 
 def test_snowflake_25_blocks_and_hash(opt):
@@ -158,7 +164,7 @@ def test_heavy_path_and_ccc(opt, threshold, ccc):
 @pytest.mark.parametrize("run", [1, 5, 32])
 def test_run_lengths(opt, run):
     """Ragged unrank runs (run lengths that do not divide C(n,k))."""
-    set_cfg(opt, run_length=run)
+    set_cfg(opt, run_length=run, filter=mpdp.FILTER_UNRANK)
     for q in (W.snowflake(13, seed=1), W.cyclic(11, seed=4), W.star(9, seed=2)):
         check(opt, q)
 
