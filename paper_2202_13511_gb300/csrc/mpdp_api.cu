@@ -198,10 +198,12 @@ static int validate_query(const mpdp_query* q, int max_n)
     return MPDP_OK;
 }
 
+// Tree enumeration needs a tree join graph (a connected graph with n - 1
+// edges); BLOCKS is correct for every graph.
 static int resolve_enumeration(const mpdp_config& cfg, int n, int m)
 {
-    if (cfg.enumeration == MPDP_ENUM_TREE || cfg.enumeration == MPDP_ENUM_BLOCKS) return cfg.enumeration;
-    return (m == n - 1) ? MPDP_ENUM_TREE : MPDP_ENUM_BLOCKS;
+    if (cfg.enumeration == MPDP_ENUM_BLOCKS || m != n - 1) return MPDP_ENUM_BLOCKS;
+    return MPDP_ENUM_TREE;
 }
 
 // Variable workspace of one query: list words, heavy words, dense entries, hash slots.

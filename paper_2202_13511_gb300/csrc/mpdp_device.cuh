@@ -43,6 +43,7 @@ struct DevQuery {
     // for every bit i of the byte x, so C(S) = OR_b ctt[b][byte b of S] is
     // the set of relations whose T-parent lies in S.
     uint32_t ctt[4][256];
+    uint32_t desc[kMaxRels];         // desc[v]: v and its descendants in T
     int32_t is_tree;                 // G itself is a tree (n - 1 edges)
     int32_t pad2[3];
 };
@@ -213,6 +214,7 @@ __device__ __forceinline__ bool connected_rounds(uint32_t s, const uint32_t (*__
 struct SharedQuery {
     uint32_t adj[kMaxRels];
     uint32_t nbase[kMaxRels];
+    uint32_t desc[kMaxRels];
     double card[kMaxRels];
     double nsel[2 * kMaxEdges];
 };

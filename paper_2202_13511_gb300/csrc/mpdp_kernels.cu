@@ -80,6 +80,7 @@ __device__ __forceinline__ void load_query(SharedQuery& sq, const DevQuery* __re
         sq.adj[threadIdx.x] = q->adj[threadIdx.x];
         sq.nbase[threadIdx.x] = q->nbase[threadIdx.x];
         sq.card[threadIdx.x] = q->card[threadIdx.x];
+        sq.desc[threadIdx.x] = q->desc[threadIdx.x];
     }
 }
 
@@ -170,10 +171,17 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
                 q->nsel[q->nbase[u] + __popc(adj[u] & ((1u << v) - 1u))] = st->edges[e].sel;
                 q->nsel[q->nbase[v] + __popc(adj[v] & ((1u << u) - 1u))] = st->edges[e].sel;
             }
-        // breadth-first spanning tree rooted at relation 0: children bitmaps
+        // spanning tree T rooted at relation 0: children bitmaps, and the
+        // descendant bitmaps by one backward pass over the discovery order
         uint32_t seen = 1u, frontier = 1u;
-        for (int r = 0; r < kMaxRels; r++) s_children[r] = 0u;
+        uint8_t order[kMaxRels];
+        int cnt_order = 0;
+        for (int r = 0; r < kMaxRels; r++) {
+            s_children[r] = 0u;
+            q->desc[r] = 1u << r;
+        }
         if (status == 0) {
+            order[cnt_order++] = 0;
             while (frontier) {
                 const int x = lowest(frontier);
                 frontier &= frontier - 1u;
@@ -181,6 +189,14 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
                 s_children[x] = ch;
                 seen |= ch;
                 frontier |= ch;
+                for (uint32_t c = ch; c; c &= c - 1u) order[cnt_order++] = (uint8_t)lowest(c);
+            }
+            // every vertex is discovered after its parent
+            for (int i = cnt_order - 1; i >= 0; i--) {
+                const int v = order[i];
+                uint32_t dsc = 1u << v;
+                for (uint32_t c = s_children[v]; c; c &= c - 1u) dsc |= q->desc[lowest(c)];
+                q->desc[v] = dsc;
             }
         }
         q->n = n;
@@ -601,43 +617,27 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
         if (idx < cnt->list_count[k]) {
             const QDesc& d = a.desc[qi];
             const uint32_t s = a.lists[d.list_base + d.list_off[k] + idx];
-            // All k-1 splits first, so that their memo reads below are
-            // independent and issue back to back.  One search from min(S)
-            // records each vertex's parent in discovery order; walking that
-            // order backwards accumulates every subtree bitmap in O(k):
-            // split[i] = the subtree under the i-th discovered vertex, i.e.
-            // grow({v}, S \ {parent(v)}).
-            uint32_t split[kMaxRels];
-            uint8_t par_slot[kMaxRels];  // slot of the parent (0xff: the root)
-            uint8_t slot_of[kMaxRels];   // slot of each discovered vertex
-            int m = 0;
-            const int root = lowest(s);
-            slot_of[root] = 0xff;
-            uint32_t vis = 1u << root, queue = vis;
-            while (queue) {
-                const int x = lowest(queue);
-                queue &= queue - 1u;
-                uint32_t ch = sq.adj[x] & s & ~vis;
-                vis |= ch;
-                queue |= ch;
-                while (ch) {
-                    const int v = lowest(ch);
-                    ch &= ch - 1u;
-                    slot_of[v] = (uint8_t)m;
-                    par_slot[m] = slot_of[x];
-                    split[m] = 1u << v;
-                    m++;
-                }
+            // G[S] is the query tree restricted to S, hanging from its top
+            // vertex (the member whose descendants cover S).  Removing the
+            // edge above any other member v leaves the subtree under v,
+            // desc[v] & S, and the rest: the k-1 CCP pairs of S, one AND each.
+            uint32_t t = s;
+            int top = lowest(t);
+            while ((sq.desc[top] & s) != s) {
+                t &= t - 1u;
+                top = lowest(t);
             }
-            // a parent is discovered before its children, so one backward
-            // pass adds every subtree into its parent's
-            for (int i = m - 1; i > 0; i--)
-                if (par_slot[i] != 0xff) split[par_slot[i]] |= split[i];
             const double card_s = peel_card(s, tree_peel_vertex(s, sq.adj), sq, memo, cnt);
             unsigned long long bx = kNoX;
             uint32_t bl = kFull;
+            uint32_t rest = s & ~(1u << top);
 #pragma unroll 4
-            for (int i = 0; i < m; i++) fold_pair(split[i], s ^ split[i], memo, cnt, bx, bl);
+            for (int i = 1; i < k; i++) {
+                const int v = lowest(rest);
+                rest &= rest - 1u;
+                const uint32_t sl = sq.desc[v] & s;
+                fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
+            }
             memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
             sets++;
         }
