@@ -53,7 +53,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--queries", type=int, default=QUERIES_PER_STEP)
     p.add_argument("--cpu-sample-s", type=float, default=15.0)
-    p.add_argument("--no-star", action="store_true", help="skip the 25-relation star line")
+    p.add_argument("--no-star", action="store_true",
+                   help="skip the extra shapes (star-25, cyclic-20, clique-14)")
     p.add_argument("--no-verify", action="store_true")
     return p.parse_args()
 
@@ -312,7 +313,8 @@ def run_ours(args):
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(queries, args.cpu_sample_s)
     if rank == 0 and not args.no_star:
-        line["star25"] = star_line(opt, torch, mpdp, W, peaks)
+        for name in SHAPES:
+            line[name] = shape_line(name, opt, torch, mpdp, W, peaks)
     opt.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -349,24 +351,35 @@ def roofline(kind, timing, stats, prof_steps, peaks, clocks):
             "bytes_per_launch": nbytes, "avg_launch_ms": avg_s * 1000.0}
 
 
-def star_line(opt, torch, mpdp, W, peaks):
-    """25-relation star (16.8M connected sets, 201M CCP pairs per query)."""
+SHAPES = {
+    # name: (description, generator kind, relations, queries per batch, extra generator args)
+    "star25": ("star join, 25 relations (fact 0 + 24 dimensions), seed 0", "star", 25, 1, {}),
+    "cyclic20": ("cyclic: random spanning tree on 20 relations + 10-30% extra edges, 64 queries",
+                 "cyclic", 20, 64, {}),
+    "clique14": ("clique, 14 relations, 64 queries", "clique", 14, 64, {}),
+}
+
+
+def shape_line(name, opt, torch, mpdp, W, peaks, reps=5):
+    """One extra workload shape: a device batch timed like the main step."""
     import numpy as np
-    q = W.star(N_RELS, seed=0)
-    st = opt.optimize(q).stats
-    d_card = torch.tensor(q.card, dtype=torch.float64, device="cuda")
-    d_edges = torch.from_numpy(mpdp.pack_edges(q.edges).view(np.uint8).copy()).cuda()
-    d_nodes = torch.zeros((2 * N_RELS - 1) * 40, dtype=torch.uint8, device="cuda")
-    d_cost = torch.zeros(1, dtype=torch.float64, device="cuda")
-    d_status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    desc, kind, n, nq, kw = SHAPES[name]
+    qs = [W.make(kind, n, seed=i, **kw) for i in range(nq)]
+    stats = [p.stats for p in opt.optimize_batch(qs)]
+    d_card = torch.tensor([c for q in qs for c in q.card], dtype=torch.float64, device="cuda")
+    d_edges = torch.from_numpy(
+        mpdp.pack_edges([e for q in qs for e in q.edges]).view(np.uint8).copy()).cuda()
+    d_nodes = torch.zeros((nq, mpdp.PLAN_STRIDE * 40), dtype=torch.uint8, device="cuda")
+    d_cost = torch.zeros(nq, dtype=torch.float64, device="cuda")
+    d_status = torch.full((nq,), -100, dtype=torch.int32, device="cuda")
+    ns, ms = [q.n for q in qs], [len(q.edges) for q in qs]
 
     def run():
-        opt.optimize_device(q.n, len(q.edges), d_card, d_edges, d_nodes, d_cost, d_status)
+        opt.optimize_batch_device(ns, ms, d_card, d_edges, d_nodes, d_cost, d_status)
 
     for _ in range(3):
         run()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    reps = 10
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(reps)]
     stream = torch.cuda.current_stream()
@@ -377,8 +390,8 @@ def star_line(opt, torch, mpdp, W, peaks):
         run()
         b.record(stream)
     torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / reps
-    assert int(d_status.item()) == 0
+    ms_batch = sum(a.elapsed_time(b) for a, b in evs) / reps
+    assert int((d_status != 0).sum().item()) == 0
     opt.profile(True)
     for _ in range(3):
         flush.zero_()
@@ -386,11 +399,12 @@ def star_line(opt, torch, mpdp, W, peaks):
     kt = opt.profile_read()
     opt.profile(False)
     dom = max(kt, key=lambda k: kt[k]["ms"])
-    return {"workload": "star join, 25 relations (fact 0 + 24 dimensions), seed 0",
-            "ms_per_query": ms, "queries_per_s": 1000.0 / ms,
-            "ccp_pairs_per_s": int(st["ccp_pairs"]) / (ms / 1000.0),
-            "ccp_pairs": int(st["ccp_pairs"]), "sets_connected": int(st["sets_connected"]),
-            "roofline": roofline(dom, kt[dom], [st], 3, peaks, None),
+    ccp = sum(int(s["ccp_pairs"]) for s in stats)
+    return {"workload": desc, "queries": nq, "ms_per_batch": ms_batch, "ms_per_query": ms_batch / nq,
+            "queries_per_s": nq * 1000.0 / ms_batch, "ccp_pairs_per_s": ccp / (ms_batch / 1000.0),
+            "ccp_pairs_per_query": ccp / nq,
+            "sets_connected_per_query": sum(int(s["sets_connected"]) for s in stats) / nq,
+            "roofline": roofline(dom, kt[dom], stats, 3, peaks, None),
             "kernel_share": {k: round(v["ms"] / max(sum(x["ms"] for x in kt.values()), 1e-12), 4)
                              for k, v in kt.items() if v["launches"]}}
 

@@ -125,9 +125,10 @@ struct mpdp_ctx {
     // variable device part
     void* var = nullptr;
     size_t var_bytes = 0;
-    size_t list_words = 0, heavy_words = 0, memo_entries = 0, arena_slots = 0;
+    size_t list_words = 0, heavy_entries = 0, memo_entries = 0, arena_slots = 0;
     uint32_t* d_lists = nullptr;
-    uint32_t* d_heavy = nullptr;
+    HeavyMain* d_hmain = nullptr;
+    HeavyExtra* d_hextra = nullptr;
     double2* d_memo = nullptr;
     uint32_t* d_left = nullptr;
     HashSlot* d_arena = nullptr;
@@ -206,7 +207,8 @@ static int resolve_enumeration(const mpdp_config& cfg, int n, int m)
     return MPDP_ENUM_TREE;
 }
 
-// Variable workspace of one query: list words, heavy words, dense entries, hash slots.
+// Variable workspace of one query: list words, heavy-set entries (main and
+// extra, reused by every level), dense entries, hash slots.
 struct QuerySize {
     size_t lists = 0, heavy = 0, memo = 0, hash = 0;
 };
@@ -215,7 +217,7 @@ static QuerySize query_size(int n, int enumeration, int memo_kind)
 {
     QuerySize z;
     z.lists = list_entries(n);
-    z.heavy = enumeration == MPDP_ENUM_BLOCKS ? z.lists : 0;
+    z.heavy = enumeration == MPDP_ENUM_BLOCKS ? binom_host(n, n / 2) : 0;
     if (memo_kind == MPDP_MEMO_DENSE) z.memo = (size_t)1 << n;
     else z.hash = hash_arena_slots(n);
     return z;
@@ -223,7 +225,8 @@ static QuerySize query_size(int n, int enumeration, int memo_kind)
 
 static size_t var_bytes_of(size_t lists, size_t heavy, size_t memo, size_t hash)
 {
-    return align_up(lists * 4) + align_up(heavy * 4) + align_up(memo * sizeof(double2)) +
+    return align_up(lists * 4) + align_up(heavy * sizeof(HeavyMain)) + align_up(heavy * sizeof(HeavyExtra)) +
+           align_up(memo * sizeof(double2)) +
            align_up(memo * sizeof(uint32_t)) + align_up(hash * sizeof(HashSlot));
 }
 
@@ -269,11 +272,11 @@ static int ensure_fixed(mpdp_ctx* ctx)
 // Grow the variable workspace to hold at least the given sizes.
 static int ensure_var(mpdp_ctx* ctx, size_t lists, size_t heavy, size_t memo, size_t hash)
 {
-    if (ctx->var && lists <= ctx->list_words && heavy <= ctx->heavy_words && memo <= ctx->memo_entries &&
+    if (ctx->var && lists <= ctx->list_words && heavy <= ctx->heavy_entries && memo <= ctx->memo_entries &&
         hash <= ctx->arena_slots)
         return MPDP_OK;
     // grow every part to at least what it had, so alternating shapes do not thrash
-    size_t L = std::max(lists, ctx->list_words), V = std::max(heavy, ctx->heavy_words),
+    size_t L = std::max(lists, ctx->list_words), V = std::max(heavy, ctx->heavy_entries),
            M = std::max(memo, ctx->memo_entries), H = std::max(hash, ctx->arena_slots);
     if (var_bytes_of(L, V, M, H) + fixed_bytes() > ctx->budget) {
         L = lists;  // only what this batch needs
@@ -287,7 +290,7 @@ static int ensure_var(mpdp_ctx* ctx, size_t lists, size_t heavy, size_t memo, si
     destroy_graphs(ctx);
     if (ctx->var) cudaFree(ctx->var);
     ctx->var = nullptr;
-    ctx->list_words = ctx->heavy_words = ctx->memo_entries = ctx->arena_slots = 0;
+    ctx->list_words = ctx->heavy_entries = ctx->memo_entries = ctx->arena_slots = 0;
     ctx->last_seq = 0;
     void* p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
@@ -304,12 +307,13 @@ static int ensure_var(mpdp_ctx* ctx, size_t lists, size_t heavy, size_t memo, si
         return r;
     };
     ctx->d_lists = reinterpret_cast<uint32_t*>(take(L * 4));
-    ctx->d_heavy = reinterpret_cast<uint32_t*>(take(V * 4));
+    ctx->d_hmain = reinterpret_cast<HeavyMain*>(take(V * sizeof(HeavyMain)));
+    ctx->d_hextra = reinterpret_cast<HeavyExtra*>(take(V * sizeof(HeavyExtra)));
     ctx->d_memo = reinterpret_cast<double2*>(take(M * sizeof(double2)));
     ctx->d_left = reinterpret_cast<uint32_t*>(take(M * sizeof(uint32_t)));
     ctx->d_arena = reinterpret_cast<HashSlot*>(take(H * sizeof(HashSlot)));
     ctx->list_words = L;
-    ctx->heavy_words = V;
+    ctx->heavy_entries = V;
     ctx->memo_entries = M;
     ctx->arena_slots = H;
     return MPDP_OK;
@@ -327,7 +331,8 @@ static BatchArgs batch_args(const mpdp_ctx* ctx, int nq, int max_n)
     a.query = ctx->d_query;
     a.out = ctx->d_out;
     a.lists = ctx->d_lists;
-    a.heavy = ctx->d_heavy;
+    a.hmain = ctx->d_hmain;
+    a.hextra = ctx->d_hextra;
     a.memo = ctx->d_memo;
     a.left = ctx->d_left;
     a.arena = ctx->d_arena;
@@ -340,34 +345,27 @@ static BatchArgs batch_args(const mpdp_ctx* ctx, int nq, int max_n)
     return a;
 }
 
-// Split [0, count) into consecutive sub-batches that fit the budget.  The
-// heavy-set lists share the list offsets, so once a block-mode query is in a
-// batch its heavy region spans every list word of the batch.
+// Split [0, count) into consecutive sub-batches that fit the budget.
 static int split_batches(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, std::vector<std::pair<int, int>>& out)
 {
     const int kind = ctx->cfg.memo_kind;
-    size_t L = 0, M = 0, A = 0;
-    bool blocks = false;
+    size_t L = 0, V = 0, M = 0, A = 0;
     int start = 0;
     for (int i = 0; i < (int)qs.size(); i++) {
         const QuerySize z = query_size(qs[i].n, qs[i].enumeration, kind);
-        const bool zb = qs[i].enumeration == MPDP_ENUM_BLOCKS;
-        const bool zh = zb;
-        if (var_bytes_of(z.lists, zh ? z.lists : 0, z.memo, z.hash) + fixed_bytes() > ctx->budget)
+        if (var_bytes_of(z.lists, z.heavy, z.memo, z.hash) + fixed_bytes() > ctx->budget)
             return MPDP_ERR_ADMISSION;
         const bool full = (i - start) >= kMaxBatch;
-        const size_t L2 = L + z.lists;
-        const size_t need = var_bytes_of(L2, (blocks || zh) ? L2 : 0, M + z.memo, A + z.hash) + fixed_bytes();
+        const size_t need = var_bytes_of(L + z.lists, V + z.heavy, M + z.memo, A + z.hash) + fixed_bytes();
         if (i > start && (full || need > ctx->budget)) {
             out.emplace_back(start, i);
             start = i;
-            L = M = A = 0;
-            blocks = false;
+            L = V = M = A = 0;
         }
         L += z.lists;
+        V += z.heavy;
         M += z.memo;
         A += z.hash;
-        blocks = blocks || zh;
     }
     if (start < (int)qs.size()) out.emplace_back(start, (int)qs.size());
     return MPDP_OK;
@@ -480,16 +478,15 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
     const int kind = ctx->cfg.memo_kind;
     int rc = ensure_fixed(ctx);
     if (rc != MPDP_OK) return rc;
-    size_t L = 0, M = 0, A = 0;
-    bool blocks = false;
+    size_t L = 0, V = 0, M = 0, A = 0;
     for (const auto& q : qs) {
         const QuerySize z = query_size(q.n, q.enumeration, kind);
         L += z.lists;
+        V += z.heavy;
         M += z.memo;
         A += z.hash;
-        blocks = blocks || q.enumeration == MPDP_ENUM_BLOCKS;
     }
-    rc = ensure_var(ctx, L, blocks ? L : 0, M, A);
+    rc = ensure_var(ctx, L, V, M, A);
     if (rc != MPDP_OK) return rc;
     const size_t desc_bytes = sizeof(QDesc) * nq, pref_bytes = sizeof(uint32_t) * (nq + 1);
     const size_t staged_off = align_up(desc_bytes) + align_up(pref_bytes);
@@ -505,7 +502,7 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
     bp.num_sms = ctx->num_sms;
     std::vector<int> key = {nq, kind, ctx->cfg.heavy_threshold, ctx->cfg.use_ccc, ctx->cfg.run_length,
                             ctx->cfg.filter};
-    unsigned long long lbase = 0, mbase = 0;
+    unsigned long long lbase = 0, mbase = 0, hbase = 0;
     uint32_t fblocks = 0;
     int max_n = 0;
     std::vector<unsigned long long> h2d(nq, 0);
@@ -527,8 +524,11 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
         hp[i] = fblocks;
         fblocks += qb;
         const QuerySize z = query_size(q.n, q.enumeration, kind);
+        d.heavy_base = hbase;
+        d.heavy_cap = (uint32_t)z.heavy;
         lbase += z.lists;
         mbase += z.memo;
+        hbase += z.heavy;
         if (q.n > max_n) max_n = q.n;
         for (int k = 2; k <= q.n; k++) {
             const unsigned long long c = binom_host(q.n, k);
@@ -536,7 +536,7 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
                 bp.tree_tiles[k] += (c + kEvalThreads - 1) / kEvalThreads;
             } else {
                 bp.block_tiles[k] += (c + kEvalThreads - 1) / kEvalThreads;
-                bp.block_sets[k] += c;
+                bp.block_sets[k] += (c + z.heavy + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
             }
         }
         key.push_back(q.n);

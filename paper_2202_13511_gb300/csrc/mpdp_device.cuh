@@ -67,7 +67,8 @@ struct DevCounters {
     unsigned long long evaluated[kLevels];
     unsigned long long ccp[kLevels];
     unsigned int list_count[kLevels];   // connected sets of level k in the list
-    unsigned int heavy_count[kLevels];  // sets of level k sent to the block-per-set kernel
+    unsigned int heavy_count[kLevels];  // sets of level k sent to the heavy-set kernel
+    unsigned int extra_count[kLevels];  // extra pair chunks reserved at level k (may exceed the capacity)
     int status;                         // first MPDP_ERR_* raised on the device
     int pad;
 };
@@ -110,7 +111,31 @@ struct QDesc {
     uint32_t list_off[kLevels];        // level k's region, relative to list_base
     uint32_t warp_begin[kLevels + 1];  // first filter warp of level k, relative to the query
     uint32_t filter_block_base;        // first filter block of the query
+    uint32_t heavy_cap;                // heavy-set entries (and extra chunks) of one level: max_k C(n, k)
+    unsigned long long heavy_base;     // first heavy-set entry of the query (block mode only)
+};
+
+// A heavy set (more than heavy_threshold pairs) is cut into nch chunks of
+// its pair index space, each taken by one warp.  Chunk 0 is the main entry;
+// chunks 1..nch-1 are extra entries [ebase, ebase + nch - 1).  Each chunk
+// leaves its best (x, left) in its own entry; the warp whose arrival
+// completes the count folds them and writes the memo.
+constexpr uint32_t kChunkPairs = 2048;   // pairs per chunk (64 rounds of a warp)
+constexpr uint32_t kMaxChunks = 4096;    // chunks per set; with the capacity check before each
+                                         // reservation the extra counter stays below 2^32
+struct HeavyMain {
+    uint32_t set;
+    uint32_t nch;
+    uint32_t ebase;
+    uint32_t arrived;                  // chunks finished; starts at 0
+    unsigned long long x;              // chunk 0's best x
+    uint32_t left;                     // chunk 0's best left
     uint32_t pad;
+};
+struct HeavyExtra {
+    uint32_t main;                     // index of the set's main entry
+    uint32_t left;
+    unsigned long long x;
 };
 
 // Everything a batch launch needs (passed by value).
@@ -123,7 +148,8 @@ struct BatchArgs {
     DevQuery* query;
     DevOut* out;
     uint32_t* lists;
-    uint32_t* heavy;
+    HeavyMain* hmain;
+    HeavyExtra* hextra;
     double2* memo;       // dense memo {cost, card}[S]
     uint32_t* left;      // dense memo left[S]
     HashSlot* arena;     // hash memo slots
@@ -259,6 +285,20 @@ __device__ __forceinline__ int block_peel_vertex(uint32_t s, const uint32_t* blk
 __device__ __forceinline__ bool better_x(unsigned long long x, uint32_t l, unsigned long long bx, uint32_t bl)
 {
     return x < bx || (x == bx && l < bl);
+}
+
+// Warp-wide lexicographic min of (x, left); every lane ends with the min.
+__device__ __forceinline__ void warp_min_x(unsigned long long& bx, uint32_t& bl)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ox = __shfl_xor_sync(0xffffffffu, bx, o);
+        const uint32_t ol = __shfl_xor_sync(0xffffffffu, bl, o);
+        if (better_x(ox, ol, bx, bl)) {
+            bx = ox;
+            bl = ol;
+        }
+    }
 }
 
 // Murmur3's 32-bit finaliser (fmix32), the hash the paper names for the memo.

@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
         const QDesc& d = a.desc[qi];
         const uint32_t idx = (t - s_pref[qi]) * kEvalThreads + threadIdx.x;
         bool to_heavy = false;
-        uint32_t s = 0u;
+        uint32_t s = 0u, want = 0u;  // want: extra chunks asked for
         if (idx < cnt->list_count[k]) {
             s = a.lists[d.list_base + d.list_off[k] + idx];
             uint32_t blk[kMaxRels];
@@ -794,6 +794,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
             for (int j = 0; j < nb; j++) pairs += block_pairs(blk[j]);
             if (pairs > (uint32_t)a.heavy_threshold) {
                 to_heavy = true;
+                const uint32_t nch = (pairs - 1u) / kChunkPairs + 1u;
+                want = (nch < kMaxChunks ? nch : kMaxChunks) - 1u;
             } else {
                 const double card_s = peel_card(s, block_peel_vertex(s, blk, nb), sq, memo, cnt);
                 unsigned long long bx = kNoX;
@@ -813,13 +815,42 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
                 memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
             }
         }
-        // warp-aggregated append of heavy sets
+        // Warp-aggregated append of heavy sets.  The main entries never
+        // overflow (at most C(n, k) sets per level).  Extra chunks are
+        // reserved with one atomicAdd per warp; a reservation that runs past
+        // the capacity keeps only its part below it, so the written extra
+        // entries are exactly [0, min(extra_count, heavy_cap)) and a set
+        // that gets fewer chunks just has longer ones.
         const unsigned bal = __ballot_sync(kFull, to_heavy);
         if (bal) {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&cnt->heavy_count[k], (uint32_t)__popc(bal));
+            uint32_t pre = want;  // inclusive warp scan of the extra chunks asked for
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(kFull, pre, o);
+                if (lane >= o) pre += v;
+            }
+            const uint32_t total = __shfl_sync(kFull, pre, 31);
+            pre -= want;
+            uint32_t base = 0, ebase = 0;
+            if (lane == 0) {
+                base = atomicAdd(&cnt->heavy_count[k], (uint32_t)__popc(bal));
+                // once full, stop adding: keeps the counter far from wrapping
+                const uint32_t seen = *reinterpret_cast<volatile uint32_t*>(&cnt->extra_count[k]);
+                ebase = d.heavy_cap;
+                if (total && seen < d.heavy_cap) ebase = atomicAdd(&cnt->extra_count[k], total);
+            }
             base = __shfl_sync(kFull, base, 0);
-            if (to_heavy) a.heavy[d.list_base + d.list_off[k] + base + __popc(bal & ((1u << lane) - 1u))] = s;
+            ebase = __shfl_sync(kFull, ebase, 0);
+            if (to_heavy) {
+                const uint32_t cap = d.heavy_cap;
+                const uint32_t room = ebase < cap ? cap - ebase : 0u;
+                const uint32_t got = pre >= room ? 0u : (want < room - pre ? want : room - pre);
+                const uint32_t i = base + __popc(bal & ((1u << lane) - 1u));
+                HeavyMain* hm = a.hmain + d.heavy_base;
+                hm[i] = HeavyMain{s, 1u + got, ebase + pre, 0u, kNoX, kFull, 0u};
+                HeavyExtra* he = a.hextra + d.heavy_base + ebase + pre;
+                for (uint32_t c = 0; c < got; c++) he[c] = HeavyExtra{i, kFull, kNoX};
+            }
         }
     }
     if (cur >= 0) {
@@ -832,12 +863,18 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
     }
 }
 
-// Block-per-set evaluation of heavy sets (general mode).  Thread 0 finds the
-// blocks; the block's threads split the set's pair index space.  With
-// Collaborative Context Collection (Sec. 5, "Avoiding 'If' branch
-// divergence") each warp stashes the pairs that pass the CCP block in shared
+// Heavy-set evaluation (general mode).  The work items of level k are the
+// pair chunks reserved by k_eval_blocks: a block takes a tile of 8 items of
+// one query, one per warp (the paper evaluates a set with one warp, Sec. 5
+// "Evaluate"; a set with many pairs is spread over several warps here so that
+// no level waits on one warp working through its largest set).  Lane 0 finds
+// the blocks of the item's set; the lanes split the chunk's pair indices.
+// With Collaborative Context Collection (Sec. 5, "Avoiding 'If' branch
+// divergence") each warp stashes the pairs that pass the CCP test in shared
 // memory and grows/costs them only when 32 are ready, so no lane idles on an
-// invalid pair during the expensive part.
+// invalid pair during the expensive part.  The prune is a warp shuffle
+// reduction of (x, left); a set cut into several chunks is folded by the
+// warp that finishes it last (fence, then an arrival count), with no waiting.
 template <class Memo>
 __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k, Memo memo)
 {
@@ -845,34 +882,31 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
     __shared__ SharedQuery sq;
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
-    __shared__ uint32_t s_blk[kMaxRels];
-    __shared__ uint32_t s_bpref[kMaxRels + 1];
-    __shared__ int s_nb;
-    __shared__ double s_card;
+    __shared__ uint32_t s_blk[kWarps][kMaxRels];
+    __shared__ uint32_t s_bpref[kWarps][kMaxRels + 1];
+    __shared__ int s_nb[kWarps];
     __shared__ uint32_t s_stash_l[kWarps][64];
     __shared__ uint32_t s_stash_r[kWarps][64];
-    __shared__ unsigned long long s_bx[kWarps];
-    __shared__ uint32_t s_bl[kWarps];
     memo.setup(s_memo);
-    const uint32_t total_sets = block_prefix(a.nq, s_pref, [&](int q) -> uint32_t {
+    const uint32_t tiles = block_prefix(a.nq, s_pref, [&](int q) -> uint32_t {
         const QDesc& d = a.desc[q];
-        if (d.n < k || d.enumeration != MPDP_ENUM_BLOCKS || a.out[q].counters.status != 0) return 0u;
-        return a.out[q].counters.heavy_count[k];
+        const DevCounters& c = a.out[q].counters;
+        if (d.n < k || d.enumeration != MPDP_ENUM_BLOCKS || c.status != 0) return 0u;
+        const uint32_t extra = c.extra_count[k] < d.heavy_cap ? c.extra_count[k] : d.heavy_cap;
+        return (c.heavy_count[k] + extra + kWarps - 1) / kWarps;
     });
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int cur = -1;
     unsigned long long ccp = 0, evaluated = 0, heavy = 0;
-    for (uint32_t h = blockIdx.x; h < total_sets; h += gridDim.x) {
-        const int qi = find_q(s_pref, a.nq, h);
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int qi = find_q(s_pref, a.nq, t);
         if (qi != cur) {
-            if (cur >= 0) {
-                if (lane == 0 && ccp) atomicAdd(&a.out[cur].counters.ccp[k], ccp);
-                if (threadIdx.x == 0) {
-                    if (evaluated) atomicAdd(&a.out[cur].counters.evaluated[k], evaluated);
-                    if (heavy) atomicAdd(&a.out[cur].counters.heavy, heavy);
-                }
-                ccp = evaluated = heavy = 0;
+            if (cur >= 0 && lane == 0) {
+                if (ccp) atomicAdd(&a.out[cur].counters.ccp[k], ccp);
+                if (evaluated) atomicAdd(&a.out[cur].counters.evaluated[k], evaluated);
+                if (heavy) atomicAdd(&a.out[cur].counters.heavy, heavy);
             }
+            ccp = evaluated = heavy = 0;
             __syncthreads();
             load_query(sq, a.query + qi);
             memo.bind(a, qi);
@@ -881,40 +915,49 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
         }
         DevCounters* cnt = &a.out[qi].counters;
         const QDesc& d = a.desc[qi];
-        const uint32_t s = a.heavy[d.list_base + d.list_off[k] + (h - s_pref[qi])];
-        if (threadIdx.x == 0) {
-            uint32_t blk[kMaxRels];
-            const int nb = find_blocks(s, sq.adj, blk);
+        const uint32_t nmain = cnt->heavy_count[k];
+        const uint32_t nextra = cnt->extra_count[k] < d.heavy_cap ? cnt->extra_count[k] : d.heavy_cap;
+        const uint32_t item = (t - s_pref[qi]) * kWarps + warp;
+        if (item >= nmain + nextra) continue;  // warp-uniform
+        HeavyMain* hm = a.hmain + d.heavy_base;
+        HeavyExtra* he = a.hextra + d.heavy_base;
+        const uint32_t mi = item < nmain ? item : he[item - nmain].main;
+        const uint32_t s = hm[mi].set, nch = hm[mi].nch, ebase = hm[mi].ebase;
+        const uint32_t chunk = item < nmain ? 0u : item - nmain - ebase + 1u;
+        if (lane == 0) {
+            const int nb = find_blocks(s, sq.adj, s_blk[warp]);
             uint32_t acc = 0u;
             for (int j = 0; j < nb; j++) {
-                s_blk[j] = blk[j];
-                s_bpref[j] = acc;
-                acc += block_pairs(blk[j]);
+                s_bpref[warp][j] = acc;
+                acc += block_pairs(s_blk[warp][j]);
             }
-            s_bpref[nb] = acc;
-            s_nb = nb;
-            s_card = peel_card(s, block_peel_vertex(s, blk, nb), sq, memo, cnt);
-            evaluated += acc;
-            heavy++;
+            s_bpref[warp][nb] = acc;
+            s_nb[warp] = nb;
+            if (chunk == 0u) {
+                evaluated += acc;
+                heavy++;
+            }
         }
-        __syncthreads();
-        const int nb = s_nb;
-        const uint32_t total = s_bpref[nb];
-        const double card_s = s_card;
+        __syncwarp();
+        const int nb = s_nb[warp];
+        const uint32_t* bpref = s_bpref[warp];
+        const uint32_t* blk = s_blk[warp];
+        const uint32_t total = bpref[nb];
+        const uint32_t lo = (uint32_t)((unsigned long long)total * chunk / nch);
+        const uint32_t hi = (uint32_t)((unsigned long long)total * (chunk + 1u) / nch);
         unsigned long long bx = kNoX;
         uint32_t bl = kFull;
         uint32_t stash = 0u;  // warp-uniform stash fill
-        const uint32_t rounds = (total + blockDim.x - 1) / blockDim.x;
-        for (uint32_t rd = 0; rd < rounds; rd++) {
-            const uint32_t p = rd * blockDim.x + threadIdx.x;
+        for (uint32_t p0 = lo; p0 < hi; p0 += 32u) {
+            const uint32_t p = p0 + (uint32_t)lane;
             bool valid = false;
             uint32_t lb = 0u, rb = 0u;
-            if (p < total) {
+            if (p < hi) {
                 int j = 0;
-                while (j + 1 < nb && s_bpref[j + 1] <= p) j++;
-                const uint32_t b = s_blk[j];
+                while (j + 1 < nb && bpref[j + 1] <= p) j++;
+                const uint32_t b = blk[j];
                 const uint32_t mn = b & (0u - b);
-                lb = mn | deposit(p - s_bpref[j], b ^ mn);
+                lb = mn | deposit(p - bpref[j], b ^ mn);
                 rb = b ^ lb;
                 valid = connected(lb, sq.adj) && connected(rb, sq.adj);
             }
@@ -948,37 +991,53 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
             const uint32_t sl = grow(l2, s & ~r2, sq.adj);
             fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
         }
-        // prune: warp then block lexicographic min of (x, left)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ox = __shfl_xor_sync(kFull, bx, o);
-            const uint32_t ol = __shfl_xor_sync(kFull, bl, o);
-            if (better_x(ox, ol, bx, bl)) {
-                bx = ox;
-                bl = ol;
+        warp_min_x(bx, bl);
+        if (nch > 1u) {
+            // leave this chunk's best, then count the arrival; the warp whose
+            // arrival is the last folds every chunk's best
+            uint32_t last = 0u;
+            if (lane == 0) {
+                if (chunk == 0u) {
+                    hm[mi].x = bx;
+                    hm[mi].left = bl;
+                } else {
+                    he[item - nmain].x = bx;
+                    he[item - nmain].left = bl;
+                }
+                __threadfence();
+                last = atomicAdd(&hm[mi].arrived, 1u) == nch - 1u;
+                if (last) __threadfence();
             }
+            if (!__shfl_sync(kFull, last, 0)) continue;
+            bx = kNoX;
+            bl = kFull;
+            for (uint32_t c = (uint32_t)lane; c < nch; c += 32u) {
+                unsigned long long cx;
+                uint32_t cl;
+                if (c == 0u) {
+                    cx = __ldcg(&hm[mi].x);
+                    cl = __ldcg(&hm[mi].left);
+                } else {
+                    cx = __ldcg(&he[ebase + c - 1u].x);
+                    cl = __ldcg(&he[ebase + c - 1u].left);
+                }
+                if (better_x(cx, cl, bx, bl)) {
+                    bx = cx;
+                    bl = cl;
+                }
+            }
+            warp_min_x(bx, bl);
         }
         if (lane == 0) {
-            s_bx[warp] = bx;
-            s_bl[warp] = bl;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < kWarps; w++)
-                if (better_x(s_bx[w], s_bl[w], bx, bl)) {
-                    bx = s_bx[w];
-                    bl = s_bl[w];
-                }
+            const double card_s = peel_card(s, block_peel_vertex(s, blk, nb), sq, memo, cnt);
             memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
         }
-        __syncthreads();
+        __syncwarp();
     }
-    if (cur >= 0) {
-        if (lane == 0 && ccp) atomicAdd(&a.out[cur].counters.ccp[k], ccp);
-        if (threadIdx.x == 0) {
-            if (evaluated) atomicAdd(&a.out[cur].counters.evaluated[k], evaluated);
-            if (heavy) atomicAdd(&a.out[cur].counters.heavy, heavy);
-        }
+    if (cur >= 0 && lane == 0) {
+        if (ccp) atomicAdd(&a.out[cur].counters.ccp[k], ccp);
+        if (evaluated) atomicAdd(&a.out[cur].counters.evaluated[k], evaluated);
+        if (heavy) atomicAdd(&a.out[cur].counters.heavy, heavy);
     }
 }
 

@@ -18,7 +18,7 @@ struct BatchPlan {
     uint32_t filter_blocks = 0;
     unsigned long long tree_tiles[kLevels] = {};   // upper bound of level-k tiles, tree queries
     unsigned long long block_tiles[kLevels] = {};  // same, block-mode queries
-    unsigned long long block_sets[kLevels] = {};   // upper bound of level-k sets, block-mode queries
+    unsigned long long block_sets[kLevels] = {};   // upper bound of level-k heavy tiles (8 chunks), block-mode queries
 };
 
 // Hook around every kernel launch (profiling mode): begin/end are called on
