@@ -215,6 +215,40 @@ int mpdp_optimize_device(mpdp_ctx *ctx, int32_t n_rels, int32_t n_edges, const d
                          const mpdp_edge *d_edges, int32_t cost_model, mpdp_plan_node *d_nodes,
                          double *d_cost, int32_t *d_status);
 
+/* Allocation-free exact optimization of one small query.  The paper has no
+ * counterpart: it is for callers that cannot allocate device memory.  No
+ * context is involved and nothing is allocated: the dense memo is a fixed
+ * device array inside the library of MPDP_NOALLOC_SCRATCH_BYTES
+ * (2^16 sets x 20 bytes), which caps n_rels at MPDP_NOALLOC_MAX_RELS.  One
+ * kernel of one block runs the whole DP (levels 2..n, block enumeration of
+ * Algorithm 4) and the plan fetch; cost, plan and status are bit-identical
+ * to mpdp_optimize_device for the same query.
+ *   n_rels, n_edges: host values; d_card (n_rels doubles), d_edges (n_edges
+ *     edges, may be NULL when 0): device, validated on the device as in the
+ *     batched path; cost_model: MPDP_COST_COUT;
+ *   d_nodes: device, at least 2 * n_rels - 1 plan nodes (breadth-first, as
+ *     mpdp_optimize_device writes them); d_cost: 1 double; d_status: 1 int32
+ *     receiving 0 or an MPDP_ERR_* code (on an error d_cost is 0 and d_nodes
+ *     is not written);
+ *   cuda_stream: a cudaStream_t of the current device (NULL: legacy default).
+ * Returns MPDP_OK once the kernel is enqueued (nothing waits for it),
+ * MPDP_ERR_TOO_LARGE for n_rels > MPDP_NOALLOC_MAX_RELS, MPDP_ERR_INVALID_ARG
+ * for a NULL pointer, n_rels < 1, a bad n_edges or cost model, and
+ * MPDP_ERR_CUDA when a runtime call fails.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Nothing in the array has to start at zero (a
+ * call writes every entry before reading it).  Concurrency: every call on a
+ * device uses the same array, so calls whose kernels can overlap on the GPU
+ * (different streams, unordered host threads) race; order them on one
+ * stream. */
+#define MPDP_NOALLOC_MAX_RELS 16
+#define MPDP_NOALLOC_SCRATCH_BYTES 1310720
+int mpdp_optimize_device_noalloc(int32_t n_rels, int32_t n_edges, const double *d_card,
+                                 const mpdp_edge *d_edges, int32_t cost_model,
+                                 mpdp_plan_node *d_nodes, double *d_cost, int32_t *d_status,
+                                 void *cuda_stream);
+
 /* Wait for all work enqueued on the context's stream.  Device-reported
  * errors are delivered per query (mpdp_get_plan, or the d_status outputs). */
 int mpdp_sync(mpdp_ctx *ctx);

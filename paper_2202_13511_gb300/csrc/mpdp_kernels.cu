@@ -652,100 +652,6 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
 }
 
 // ---------------------------------------------------------------------------
-// Find-Blocks (Sec. 3.2.2; Algorithm 4): the blocks of G[S] as bitmaps.
-// A search from min(S) gives a spanning tree (parent of each vertex; anc[v] =
-// the tree edges on the path root..v, each edge named by its child vertex).
-// Every non-tree edge (x, y) closes the fundamental cycle whose tree edges are
-// anc[x] xor anc[y].  Two tree edges lie in one block exactly when a chain of
-// fundamental cycles sharing tree edges joins them, so merging overlapping
-// cycle edge-sets gives one class per block with a cycle; its vertices are
-// the class's child vertices plus their parents.  A tree edge on no cycle is
-// a bridge, a block of its own two vertices.  Returns the number of blocks.
-__device__ __forceinline__ int find_blocks(uint32_t s, const uint32_t* __restrict__ adj,
-                                           uint32_t* __restrict__ blk)
-{
-    uint8_t par[kMaxRels];
-    uint32_t anc[kMaxRels];
-    const int root = lowest(s);
-    par[root] = 0xff;
-    anc[root] = 0u;
-    uint32_t vis = 1u << root, queue = vis;
-    while (queue) {
-        const int x = lowest(queue);
-        queue &= queue - 1u;
-        uint32_t ch = adj[x] & s & ~vis;
-        vis |= ch;
-        queue |= ch;
-        while (ch) {
-            const int v = lowest(ch);
-            ch &= ch - 1u;
-            par[v] = (uint8_t)x;
-            anc[v] = anc[x] | (1u << v);
-        }
-    }
-    uint32_t cls[kMaxRels];
-    int nc = 0;
-    uint32_t t = s;
-    while (t) {
-        const int x = lowest(t);
-        t &= t - 1u;
-        uint32_t ys = adj[x] & s & ~((2u << x) - 1u);  // neighbours y > x
-        while (ys) {
-            const int y = lowest(ys);
-            ys &= ys - 1u;
-            if (par[y] == x || par[x] == y) continue;  // tree edge
-            uint32_t c = anc[x] ^ anc[y];
-            int j = 0;
-            while (j < nc) {
-                if (cls[j] & c) {
-                    c |= cls[j];
-                    cls[j] = cls[--nc];
-                } else {
-                    j++;
-                }
-            }
-            cls[nc++] = c;
-        }
-    }
-    int nb = 0;
-    uint32_t in_cycle = 0u;
-    for (int j = 0; j < nc; j++) {
-        uint32_t c = cls[j], b = c;
-        in_cycle |= c;
-        while (c) {
-            const int v = lowest(c);
-            c &= c - 1u;
-            b |= 1u << par[v];
-        }
-        blk[nb++] = b;
-    }
-    uint32_t br = s & ~in_cycle & ~(1u << root);
-    while (br) {
-        const int v = lowest(br);
-        br &= br - 1u;
-        blk[nb++] = (1u << v) | (1u << par[v]);
-    }
-    return nb;
-}
-
-// Unordered bipartitions of a block B visited by the enumeration: every lb
-// holding min(B), except lb = B: 2^(|B|-1) - 1.
-__device__ __forceinline__ uint32_t block_pairs(uint32_t b) { return (1u << (__popc(b) - 1)) - 1u; }
-
-// Deposit the low bits of t into the set bits of mask, lowest first.
-__device__ __forceinline__ uint32_t deposit(uint32_t t, uint32_t mask)
-{
-    uint32_t r = 0u;
-    while (t && mask) {
-        const uint32_t low = mask & (0u - mask);
-        if (t & 1u) r |= low;
-        t >>= 1;
-        mask ^= low;
-    }
-    return r;
-}
-
-// ---------------------------------------------------------------------------
 // a4-a8, general join graphs (Algorithm 4), thread per set for light sets.
 // For each block B of G[S] and each lb (min(B) in lb, lb != B): rb = B \ lb;
 // the CCP block keeps the pair when lb and rb both induce connected subgraphs

@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 from dataclasses import dataclass, field
 from typing import Dict, List, Optional, Sequence
 
@@ -94,8 +95,11 @@ EXPORTS = [
     "mpdp_release", "mpdp_optimize_device", "mpdp_sync", "mpdp_memo_lookup",
     "mpdp_last_launch_count", "mpdp_strerror", "mpdp_last_error", "mpdp_abi_version",
     "mpdp_profile", "mpdp_profile_read", "mpdp_optimize_batch_device",
+    "mpdp_optimize_device_noalloc",
 ]
 PLAN_STRIDE = 63
+NOALLOC_MAX_RELS = 16
+NOALLOC_SCRATCH_BYTES = 1310720
 
 KERNEL_CLASSES = ["stage", "ingest", "filter", "memo_init", "eval", "heavy", "extract", "publish"]
 
@@ -138,6 +142,10 @@ def load(build_if_missing: bool = True):
                                              P(ctypes.c_int32), ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p]
+    L.mpdp_optimize_device_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.mpdp_optimize_device_noalloc.restype = ctypes.c_int
     L.mpdp_sync.argtypes = [c_ctx]
     L.mpdp_memo_lookup.argtypes = [c_ctx, ctypes.c_int64, P(ctypes.c_uint64), ctypes.c_int32,
                                    P(ctypes.c_double), P(ctypes.c_uint64)]
@@ -371,6 +379,30 @@ class Optimizer:
         ln = (ctypes.c_uint64 * len(KERNEL_CLASSES))()
         self._check(self._lib.mpdp_profile_read(self._ctx, ms, ln), "mpdp_profile_read")
         return {k: dict(ms=ms[i], launches=int(ln[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def optimize_device_noalloc(n: int, n_edges: int, d_card, d_edges, d_nodes, d_cost, d_status,
+                            stream=None) -> None:
+    """Enqueue the allocation-free optimization of one query of at most
+    NOALLOC_MAX_RELS relations (no context; device tensors or raw device
+    pointers in and out, as in Optimizer.optimize_device; d_nodes needs
+    2n - 1 nodes).  stream: a torch.cuda.Stream, a raw cudaStream_t, or None
+    for the current torch stream when torch is loaded, else the legacy
+    default stream.  Calls on streams that can overlap share the library's
+    fixed memo and race."""
+    def ptr(x):
+        if x is None:
+            return 0
+        return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+    if stream is None:
+        torch = sys.modules.get("torch")
+        stream = torch.cuda.current_stream().cuda_stream if torch is not None else 0
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    rc = load().mpdp_optimize_device_noalloc(int(n), int(n_edges), ptr(d_card), ptr(d_edges), 0,
+                                             ptr(d_nodes), ptr(d_cost), ptr(d_status), int(stream))
+    if rc != 0:
+        raise MPDPError(rc, "mpdp_optimize_device_noalloc", strerror(rc))
 
 
 def workspace_bytes(n: int, memo_kind: int = MEMO_DENSE) -> int:
