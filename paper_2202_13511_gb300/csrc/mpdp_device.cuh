@@ -46,6 +46,12 @@ struct DevQuery {
     uint32_t desc[kMaxRels];         // desc[v]: v and its descendants in T
     int32_t is_tree;                 // G itself is a tree (n - 1 edges)
     int32_t pad2[3];
+    // Bitmap-filter run tables for the low relations r < 5 of T (a run is
+    // the 32 bitmaps base | i, i < 32):  [r] children of r;  [5 + r] the
+    // run mask of "r is in S and its parent is not" when r is the root or
+    // its parent is low;  [10 + r] r's parent when it is a high relation,
+    // else 0xffffffff;  [15] the relations whose parent is low.
+    uint32_t lowrun[16];
 };
 
 // T[S] has one component per member of S whose T-parent is outside S, so
@@ -55,6 +61,14 @@ struct DevQuery {
 __device__ __forceinline__ uint32_t tops_of(uint32_t s, uint32_t children)
 {
     return s & ~children;
+}
+
+// low_bit(r): the i in [0, 32) whose bit r is set, as a 32-bit mask (the
+// membership of relation r < 5 along a run of 32 bitmaps, bit-sliced over i).
+__host__ __device__ constexpr uint32_t low_bit(int r)
+{
+    return r == 0 ? 0xaaaaaaaau
+                  : r == 1 ? 0xccccccccu : r == 2 ? 0xf0f0f0f0u : r == 3 ? 0xff00ff00u : 0xffff0000u;
 }
 
 // Per-query device counters and status word.
@@ -351,30 +365,18 @@ struct DenseMemo {
 // Memo as one open-addressing table per level (linear probing).
 struct HashMemo {
     HashSlot* arena;
-    // the bound query's table bases and masks (shared memory)
-    unsigned long long* s_base;
-    unsigned int* s_mask;
+    const HashLayout* lay;  // the bound query's table bases and masks
 
-    static constexpr size_t kSharedBytes = kLevels * (sizeof(unsigned long long) + sizeof(unsigned int));
+    static constexpr size_t kSharedBytes = 16;
 
-    __device__ __forceinline__ void setup(char* smem)
-    {
-        s_base = reinterpret_cast<unsigned long long*>(smem);
-        s_mask = reinterpret_cast<unsigned int*>(smem + kLevels * sizeof(unsigned long long));
-    }
-    // cooperative: every thread of the block calls it; a barrier must follow
-    __device__ __forceinline__ void bind(const BatchArgs& a, int q)
-    {
-        for (int i = threadIdx.x; i < kLevels; i += blockDim.x) {
-            s_base[i] = a.layout[q].base[i];
-            s_mask[i] = a.layout[q].mask[i];
-        }
-    }
+    __device__ __forceinline__ void setup(char*) {}
+    // per thread; no shared memory involved
+    __device__ __forceinline__ void bind(const BatchArgs& a, int q) { lay = a.layout + q; }
     __device__ __forceinline__ const HashSlot* find(uint32_t s, DevCounters* cnt) const
     {
         const int lvl = __popc(s);
-        const HashSlot* t = arena + s_base[lvl];
-        const uint32_t m = s_mask[lvl];
+        const HashSlot* t = arena + __ldg(&lay->base[lvl]);
+        const uint32_t m = __ldg(&lay->mask[lvl]);
         uint32_t h = fmix32(s) & m;
         for (uint32_t i = 0; i <= m; i++) {
             const uint32_t key = __ldg(&t[h].key);
@@ -410,8 +412,8 @@ struct HashMemo {
     __device__ __forceinline__ void put(uint32_t s, int lvl, double c, double card, uint32_t l,
                                         DevCounters* cnt)
     {
-        HashSlot* t = arena + s_base[lvl];
-        const uint32_t m = s_mask[lvl];
+        HashSlot* t = arena + __ldg(&lay->base[lvl]);
+        const uint32_t m = __ldg(&lay->mask[lvl]);
         uint32_t h = fmix32(s) & m;
         for (uint32_t i = 0; i <= m; i++) {
             if (atomicCAS(&t[h].key, 0u, s) == 0u) {
@@ -431,15 +433,19 @@ struct HashMemo {
 namespace mpdp {
 
 // card(S) by peeling vertex v: card(S \ {v}) (from the memo; a single
-// relation's card directly), times card[v], times sel(j, v) for the
-// neighbours j of v in S in ascending order.  __dmul_rn keeps every step a
-// separately rounded IEEE multiply.
-template <class Memo>
-__device__ __forceinline__ double peel_card(uint32_t s, int v, const SharedQuery& sq, const Memo& memo,
-                                            DevCounters* cnt)
+// relation's card directly; peel_base), times card[v], times sel(j, v) for
+// the neighbours j of v in S in ascending order (peel_finish).  __dmul_rn
+// keeps every step a separately rounded IEEE multiply.
+template <class Memo, class Q>
+__device__ __forceinline__ double peel_base(uint32_t s, int v, const Q& sq, const Memo& memo, DevCounters* cnt)
 {
     const uint32_t rest = s & ~(1u << v);
-    double p = (rest & (rest - 1u)) ? memo.get_card(rest, cnt) : sq.card[lowest(rest)];
+    return (rest & (rest - 1u)) ? memo.get_card(rest, cnt) : sq.card[lowest(rest)];
+}
+
+template <class Q>
+__device__ __forceinline__ double peel_finish(double p, uint32_t s, int v, const Q& sq)
+{
     p = __dmul_rn(p, sq.card[v]);
     const uint32_t nv = sq.adj[v];
     uint32_t nb = nv & s;
@@ -449,6 +455,12 @@ __device__ __forceinline__ double peel_card(uint32_t s, int v, const SharedQuery
         p = __dmul_rn(p, sq.nsel[sq.nbase[v] + __popc(nv & ((1u << j) - 1u))]);
     }
     return p;
+}
+
+template <class Memo, class Q>
+__device__ __forceinline__ double peel_card(uint32_t s, int v, const Q& sq, const Memo& memo, DevCounters* cnt)
+{
+    return peel_finish(peel_base(s, v, sq, memo, cnt), s, v, sq);
 }
 
 // Fold one CCP pair (S_l, S_r) into the running best (x, left).  x is

@@ -199,6 +199,19 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
                 q->desc[v] = dsc;
             }
         }
+        // run tables of the bitmap filter (low relations r < 5 of T)
+        uint32_t lowkids = 0u;
+        for (int r = 0; r < 5; r++) {
+            const bool in = status == 0 && r < n;
+            int par = -1;
+            for (int p = 0; p < n && in; p++)
+                if (s_children[p] >> r & 1u) par = p;
+            q->lowrun[r] = in ? s_children[r] : 0u;
+            q->lowrun[5 + r] = in ? ((par >= 0 && par < 5) ? low_bit(r) & ~low_bit(par) : low_bit(r)) : 0u;
+            q->lowrun[10 + r] = (in && par >= 5) ? (uint32_t)par : 0xffffffffu;
+            if (in) lowkids |= s_children[r];
+        }
+        q->lowrun[15] = lowkids;
         q->n = n;
         q->n_edges = status == 0 ? m : 0;
         q->is_tree = (status == 0 && m == n - 1) ? 1 : 0;
@@ -383,14 +396,15 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
 
 // ---------------------------------------------------------------------------
 // a2 + a3, bitmap form: every bitmap S < 2^n of every query is tested, in
-// index order, all levels at once (no unranking).  Thread t of a query takes
-// the aligned run of 32 bitmaps 32t .. 32t+31; bits 5..31 are fixed along the
-// run, so their share of the table lookups is done once per run and each
-// bitmap needs one broadcast lookup for its low five bits.  Connected sets
-// (|S| >= 2) go straight into the list of their level, in bitmap order
-// within each warp's slice.
+// index order, all levels at once (no unranking).  A thread takes aligned
+// runs of 32 bitmaps base | i, i < 32: bits 5..31 are fixed along a run, so
+// their share of the work is done once per run.  Connected sets (|S| >= 2)
+// go straight into the list of their level, in bitmap order within each
+// warp's slice.  A block covers kFilterRounds consecutive slices of
+// kFilterThreads runs, so its table loads are shared by 8 x 8192 bitmaps.
 constexpr uint32_t kBitmapsPerThread = 32;
-constexpr uint32_t kBitmapsPerBlock = kFilterThreads * kBitmapsPerThread;
+constexpr uint32_t kFilterRounds = 8;
+constexpr uint32_t kBitmapsPerBlock = kFilterThreads * kBitmapsPerThread * kFilterRounds;
 
 // kPopcMask.v[j]: the i in [0, 32) with popcount(i) == j, as a 32-bit mask.
 struct PopcMasks {
@@ -414,6 +428,8 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter_bitmaps(BatchArgs a)
 {
     __shared__ uint32_t s_nbt[4][256];
     __shared__ uint32_t s_ctt[4][256];
+    __shared__ uint32_t s_stage[kFilterThreads / 32][32];
+    __shared__ uint32_t s_run[16];     // DevQuery::lowrun
     int lo = 0, hi = a.nq - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -424,93 +440,159 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter_bitmaps(BatchArgs a)
     const QDesc& d = a.desc[qi];
     const DevQuery* __restrict__ q = a.query + qi;
     DevCounters* __restrict__ cnt = &a.out[qi].counters;
+    const bool is_tree = q->is_tree != 0;
     for (int t = threadIdx.x; t < 4 * 256; t += blockDim.x) {
-        s_nbt[t >> 8][t & 255] = q->nbt[t >> 8][t & 255];
+        if (!is_tree) s_nbt[t >> 8][t & 255] = q->nbt[t >> 8][t & 255];
         s_ctt[t >> 8][t & 255] = q->ctt[t >> 8][t & 255];
     }
+    if (threadIdx.x < 16) s_run[threadIdx.x] = q->lowrun[threadIdx.x];
     __syncthreads();
     if (cnt->status != 0) return;
-    const bool is_tree = q->is_tree != 0;
     const int lane = threadIdx.x & 31;
-    const unsigned long long base64 =
-        ((unsigned long long)(blockIdx.x - a.filter_block_prefix[qi]) * kFilterThreads + threadIdx.x) *
-        kBitmapsPerThread;
     const unsigned long long limit = 1ull << d.n;
-    uint32_t flags = 0u, rounds = 0u, examined = 0u;
-    const uint32_t base = (uint32_t)base64;
-    if (base64 < limit) {
-        const uint32_t c_run = s_ctt[0][base & 0xe0u] | s_ctt[1][(base >> 8) & 255u] |
-                               s_ctt[2][(base >> 16) & 255u] | s_ctt[3][base >> 24];
-        if (is_tree) {
-            // tree join graph: connected iff exactly one member's parent is outside S
+    uint32_t rounds = 0u, examined = 0u;
+    for (uint32_t rd = 0; rd < kFilterRounds; rd++) {
+        const unsigned long long base64 =
+            (((unsigned long long)(blockIdx.x - a.filter_block_prefix[qi]) * kFilterRounds + rd) * kFilterThreads +
+             threadIdx.x) *
+            kBitmapsPerThread;
+        if (base64 - (unsigned long long)lane * kBitmapsPerThread >= limit) break;  // warp-uniform
+        uint32_t flags = 0u;
+        const uint32_t base = (uint32_t)base64;
+        if (base64 < limit) {
+            const uint32_t c_run = s_ctt[0][base & 0xe0u] | s_ctt[1][(base >> 8) & 255u] |
+                                   s_ctt[2][(base >> 16) & 255u] | s_ctt[3][base >> 24];
+            if (is_tree) {
+                // Tree join graph: S is connected iff exactly one member's
+                // parent lies outside S.  Evaluated for the whole run at
+                // once, bit-sliced over i: `one` / `two` collect the runs'
+                // bitmaps with at least one / at least two such members.
+                // High members (bits >= 5) with a high parent outside the
+                // run's high part are a top in every bitmap of the run.
+                const uint32_t fixed = base & ~c_run & ~s_run[15];
+                if ((fixed & (fixed - 1u)) == 0u) {
+                    uint32_t one = fixed ? kFull : 0u, two = 0u;
+                    const uint32_t g = base & s_run[15];  // high members with a low parent
 #pragma unroll
-            for (uint32_t i = 0; i < kBitmapsPerThread; i++) {
-                const uint32_t s = base | i;
-                flags |= (__popc(s & ~(c_run | s_ctt[0][i])) == 1 ? 1u : 0u) << i;
+                    for (int p = 0; p < 5; p++) {
+                        const uint32_t gp = g & s_run[p];
+                        if (gp) {
+                            const uint32_t t = ~low_bit(p);  // a top unless p is in S
+                            two |= (one & t) | ((gp & (gp - 1u)) ? t : 0u);
+                            one |= t;
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < 5; r++) {
+                        const uint32_t hp = s_run[10 + r];
+                        const uint32_t t = (hp < 32u && (base >> hp & 1u)) ? 0u : s_run[5 + r];
+                        two |= one & t;
+                        one |= t;
+                    }
+                    flags = one & ~two;
+                }
+            } else {
+                const uint32_t n_run = s_nbt[0][base & 0xe0u] | s_nbt[1][(base >> 8) & 255u] |
+                                       s_nbt[2][(base >> 16) & 255u] | s_nbt[3][base >> 24];
+                for (uint32_t i = 0; i < kBitmapsPerThread; i++) {
+                    const uint32_t s = base | i;
+                    bool ok = __popc(s & ~(c_run | s_ctt[0][i])) == 1;
+                    if (!ok) ok = (s & ~(n_run | s_nbt[0][i])) == 0u && connected_rounds_from(s, s_nbt, rounds);
+                    if (ok) flags |= 1u << i;
+                }
             }
-        } else {
-            const uint32_t n_run = s_nbt[0][base & 0xe0u] | s_nbt[1][(base >> 8) & 255u] |
-                                   s_nbt[2][(base >> 16) & 255u] | s_nbt[3][base >> 24];
-            for (uint32_t i = 0; i < kBitmapsPerThread; i++) {
-                const uint32_t s = base | i;
-                bool ok = __popc(s & ~(c_run | s_ctt[0][i])) == 1;
-                if (!ok) ok = (s & ~(n_run | s_nbt[0][i])) == 0u && connected_rounds_from(s, s_nbt, rounds);
-                if (ok) flags |= 1u << i;
-            }
+            uint32_t valid = 0xffffffffu;
+            if (limit - base64 < kBitmapsPerThread) valid = (1u << (uint32_t)(limit - base64)) - 1u;
+            if (__popc(base) <= 1)  // the empty set and single relations are not DP sets
+                for (uint32_t i = 0; i < kBitmapsPerThread; i++)
+                    if (__popc(base | i) < 2) valid &= ~(1u << i);
+            flags &= valid;
+            examined += __popc(valid);
         }
-        uint32_t valid = 0xffffffffu;
-        if (limit - base64 < kBitmapsPerThread) valid = (1u << (uint32_t)(limit - base64)) - 1u;
-        if (__popc(base) <= 1)  // the empty set and single relations are not DP sets
-            for (uint32_t i = 0; i < kBitmapsPerThread; i++)
-                if (__popc(base | i) < 2) valid &= ~(1u << i);
-        flags &= valid;
-        examined = __popc(valid);
-    }
-    // Ordered output straight into the level lists.  The warp covers the
-    // 1024 bitmaps w0 .. w0+1023 (w0 = its first bitmap), so bitmap
-    // base | i of lane l has level popc(w0) + popc(l) + popc(i): 11 level
-    // bins per warp.  A shuffle scan per bin places every lane's sets in
-    // bitmap order and one atomic per non-empty bin reserves list room.
-    if (__any_sync(kFull, flags != 0u)) {
+        // Ordered output straight into the level lists.  The warp covers the
+        // 1024 bitmaps w0 .. w0+1023 (w0 = its first bitmap), so bitmap
+        // base | i of lane l has level popc(w0) + popc(l) + popc(i): 11 level
+        // bins per warp.  Sets leave in bitmap order within each level.
+        if (!__any_sync(kFull, flags != 0u)) continue;
+        uint32_t fincl = (uint32_t)__popc(flags);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(kFull, fincl, o);
+            if (lane >= o) fincl += u;
+        }
+        const uint32_t ftotal = __shfl_sync(kFull, fincl, 31);
         const int pw = __popc((uint32_t)(base64 - (unsigned long long)lane * kBitmapsPerThread));
-        const int pl = __popc((uint32_t)lane);
-        uint32_t cj[6], ex[6];
-#pragma unroll
-        for (int j = 0; j < 6; j++) cj[j] = __popc(flags & kPopcMask.v[j]);
-        uint32_t my_total = 0u;
-#pragma unroll
-        for (int t = 0; t <= 10; t++) {
-            uint32_t v = 0u;
-#pragma unroll
-            for (int j = 0; j < 6; j++) v = (t - pl == j) ? cj[j] : v;
-            uint32_t incl = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t u = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += u;
+        if (ftotal != 0u && ftotal <= 32u) {
+            // Sparse warp: compact its sets into one set per lane (bitmap
+            // order), then one ballot per level present places them.
+            uint32_t o = fincl - (uint32_t)__popc(flags), f = flags;
+            while (f) {
+                const int i = lowest(f);
+                f &= f - 1u;
+                s_stage[threadIdx.x >> 5][o++] = base | (uint32_t)i;
             }
-            const uint32_t tot = __shfl_sync(kFull, incl, 31);
-            if (lane == t) my_total = tot;
+            __syncwarp();
+            const bool has = (uint32_t)lane < ftotal;
+            const uint32_t sv = has ? s_stage[threadIdx.x >> 5][lane] : 0u;
+            const int lv = __popc(sv);
+            const int lb = has ? lv - pw : 0;  // level bin, 0..10
+            uint32_t present = __reduce_or_sync(kFull, has ? 1u << lb : 0u);
+            unsigned bin_mask = 0u;  // lane t <= 10: the lanes holding a set of bin t
+            while (present) {
+                const int t = lowest(present);
+                present &= present - 1u;
+                const unsigned m = __ballot_sync(kFull, has && lb == t);
+                if (lane == t) bin_mask = m;
+            }
+            // every bin reserves its list room at once: one atomic latency
+            uint32_t bpos = 0u;
+            if (bin_mask) bpos = atomicAdd(&cnt->list_count[pw + lane], (uint32_t)__popc(bin_mask));
+            const uint32_t b0 = __shfl_sync(kFull, bpos, lb);
+            const unsigned mm = __shfl_sync(kFull, bin_mask, lb);
+            if (has) a.lists[d.list_base + d.list_off[pw + lb] + b0 + __popc(mm & ((1u << lane) - 1u))] = sv;
+            __syncwarp();
+        } else if (ftotal != 0u) {
+            // Dense warp: a shuffle scan per level bin places every lane's sets
+            // and one atomic per non-empty bin reserves list room.
+            const int pl = __popc((uint32_t)lane);
+            uint32_t cj[6], ex[6];
 #pragma unroll
-            for (int j = 0; j < 6; j++)
-                if (t - pl == j) ex[j] = incl - v;
-        }
-        uint32_t bpos = 0u;
-        if (lane <= 10 && my_total) bpos = atomicAdd(&cnt->list_count[pw + lane], my_total);
-        uint32_t* lists = a.lists + d.list_base;
-        uint32_t start[6];
+            for (int j = 0; j < 6; j++) cj[j] = __popc(flags & kPopcMask.v[j]);
+            uint32_t my_total = 0u;
 #pragma unroll
-        for (int j = 0; j < 6; j++) start[j] = __shfl_sync(kFull, bpos, pl + j) + ex[j];
-        uint32_t f = flags;
-        while (f) {
-            const int i = lowest(f);
-            f &= f - 1u;
-            const int j = __popc((uint32_t)i);
-            uint32_t pos = 0u;
+            for (int t = 0; t <= 10; t++) {
+                uint32_t v = 0u;
 #pragma unroll
-            for (int jj = 0; jj < 6; jj++)
-                if (j == jj) pos = start[jj]++;
-            lists[d.list_off[pw + pl + j] + pos] = base | (uint32_t)i;
+                for (int j = 0; j < 6; j++) v = (t - pl == j) ? cj[j] : v;
+                uint32_t incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t u = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += u;
+                }
+                const uint32_t tot = __shfl_sync(kFull, incl, 31);
+                if (lane == t) my_total = tot;
+#pragma unroll
+                for (int j = 0; j < 6; j++)
+                    if (t - pl == j) ex[j] = incl - v;
+            }
+            uint32_t bpos = 0u;
+            if (lane <= 10 && my_total) bpos = atomicAdd(&cnt->list_count[pw + lane], my_total);
+            uint32_t* lists = a.lists + d.list_base;
+            uint32_t start[6];
+#pragma unroll
+            for (int j = 0; j < 6; j++) start[j] = __shfl_sync(kFull, bpos, pl + j) + ex[j];
+            uint32_t f = flags;
+            while (f) {
+                const int i = lowest(f);
+                f &= f - 1u;
+                const int j = __popc((uint32_t)i);
+                uint32_t pos = 0u;
+#pragma unroll
+                for (int jj = 0; jj < 6; jj++)
+                    if (j == jj) pos = start[jj]++;
+                lists[d.list_off[pw + pl + j] + pos] = base | (uint32_t)i;
+            }
         }
     }
 #pragma unroll
@@ -588,16 +670,21 @@ __device__ __forceinline__ uint32_t level_tiles(const BatchArgs& a, int q, int k
 template <class Memo>
 __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, Memo memo)
 {
-    __shared__ SharedQuery sq;
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     memo.setup(s_memo);
     const uint32_t tiles = block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, MPDP_ENUM_TREE); });
+    // Tiles go round-robin over the blocks, so the sets in flight at any
+    // time are neighbours in the level lists (their memo reads are close).
+    // The query is read through the cache, not staged in shared memory:
+    // consecutive tiles of a block belong to different queries and a
+    // switch then costs no block barrier.
     int cur = -1;
+    const DevQuery* __restrict__ q = nullptr;
     unsigned long long sets = 0;
     for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int qi = find_q(s_pref, a.nq, t);
-        if (qi != cur) {
+        if (qi != cur) {  // block-uniform
             if (cur >= 0) {
                 sets = warp_sum(sets);
                 if ((threadIdx.x & 31) == 0 && sets) {
@@ -606,10 +693,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
                 }
                 sets = 0;
             }
-            __syncthreads();
-            load_query(sq, a.query + qi);
+            q = a.query + qi;
             memo.bind(a, qi);
-            __syncthreads();
             cur = qi;
         }
         DevCounters* cnt = &a.out[qi].counters;
@@ -621,23 +706,27 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
             // vertex (the member whose descendants cover S).  Removing the
             // edge above any other member v leaves the subtree under v,
             // desc[v] & S, and the rest: the k-1 CCP pairs of S, one AND each.
-            uint32_t t = s;
-            int top = lowest(t);
-            while ((sq.desc[top] & s) != s) {
-                t &= t - 1u;
-                top = lowest(t);
+            uint32_t t2 = s;
+            int top = lowest(t2);
+            while ((__ldg(&q->desc[top]) & s) != s) {
+                t2 &= t2 - 1u;
+                top = lowest(t2);
             }
-            const double card_s = peel_card(s, tree_peel_vertex(s, sq.adj), sq, memo, cnt);
+            // card(S \ {v}) is loaded before the pairs and used after them,
+            // so its latency overlaps theirs
+            const int pv = tree_peel_vertex(s, q->adj);
+            const double pbase = peel_base(s, pv, *q, memo, cnt);
             unsigned long long bx = kNoX;
             uint32_t bl = kFull;
             uint32_t rest = s & ~(1u << top);
-#pragma unroll 4
+#pragma unroll 8
             for (int i = 1; i < k; i++) {
                 const int v = lowest(rest);
                 rest &= rest - 1u;
-                const uint32_t sl = sq.desc[v] & s;
+                const uint32_t sl = __ldg(&q->desc[v]) & s;
                 fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
             }
+            const double card_s = peel_finish(pbase, s, pv, *q);
             memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
             sets++;
         }
@@ -1186,7 +1275,7 @@ cudaError_t enqueue_pipeline(const BatchArgs& a, const BatchPlan& bp, int memo_k
             k_hash_clear<<<bp.num_sms * 4, 256, 0, st>>>(a);
         }
         launches += 2;
-        HashMemo memo{a.arena, nullptr, nullptr};
+        HashMemo memo{a.arena, nullptr};
         launch_levels(a, bp, memo, st, launches, hook);
     }
     if (launches_out) *launches_out = launches;
@@ -1217,7 +1306,7 @@ cudaError_t enqueue_memo_lookup(const BatchArgs& a, int memo_kind, int qi, const
         DenseMemo memo{a.memo, a.left, nullptr, nullptr};
         k_memo_lookup<DenseMemo><<<grid, 256, 0, st>>>(a, qi, d_sets, count, d_costs, d_lefts, memo);
     } else {
-        HashMemo memo{a.arena, nullptr, nullptr};
+        HashMemo memo{a.arena, nullptr};
         k_memo_lookup<HashMemo><<<grid, 256, 0, st>>>(a, qi, d_sets, count, d_costs, d_lefts, memo);
     }
     return cudaGetLastError();
