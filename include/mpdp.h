@@ -189,6 +189,18 @@ int mpdp_get_plan(mpdp_ctx *ctx, int64_t handle, mpdp_plan_node *nodes, int32_t 
 /* Forget a handle (its host result buffer is reused). */
 int mpdp_release(mpdp_ctx *ctx, int64_t handle);
 
+/* mpdp_get_plan + mpdp_release for `count` handles in one call (no
+ * counterpart in the paper; it saves a host round trip per query when a
+ * batch is collected).  Handle i's plan goes to nodes + i * stride (stride
+ * >= 2n - 1 of every query, or nodes NULL and stride 0 to read only costs
+ * and stats); n_nodes[i], costs[i] and status[i] (0 or that handle's
+ * MPDP_ERR_*) are always written; stats may be NULL, else `count` records.
+ * Every known handle is released, whatever its status.  Returns MPDP_OK,
+ * or MPDP_ERR_BAD_HANDLE if a handle was unknown (its status says so too). */
+int mpdp_get_plans(mpdp_ctx *ctx, const int64_t *handles, int32_t count, mpdp_plan_node *nodes,
+                   int32_t stride, int32_t *n_nodes, double *costs, int32_t *status,
+                   mpdp_stats *stats);
+
 /* Plan nodes reserved per query in the device-path output arrays. */
 #define MPDP_PLAN_STRIDE 63
 

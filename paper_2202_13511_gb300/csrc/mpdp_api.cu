@@ -810,6 +810,29 @@ int mpdp_release(mpdp_ctx* ctx, int64_t handle)
     return MPDP_OK;
 }
 
+int mpdp_get_plans(mpdp_ctx* ctx, const int64_t* handles, int32_t count, mpdp_plan_node* nodes, int32_t stride,
+                   int32_t* n_nodes, double* costs, int32_t* status, mpdp_stats* stats)
+{
+    if (!ctx || count < 0 || (count > 0 && (!handles || !n_nodes || !costs || !status)) || stride < 0 ||
+        (nodes == nullptr && stride != 0))
+        return MPDP_ERR_INVALID_ARG;
+    int rc = MPDP_OK;
+    for (int i = 0; i < count; i++) {
+        n_nodes[i] = 0;
+        costs[i] = 0.0;
+        const int r = mpdp_get_plan(ctx, handles[i], nodes ? nodes + (size_t)i * stride : nullptr, stride,
+                                    &n_nodes[i], &costs[i], stats ? &stats[i] : nullptr);
+        status[i] = r;
+        if (r == MPDP_ERR_BAD_HANDLE) {
+            rc = MPDP_ERR_BAD_HANDLE;
+            continue;
+        }
+        const int rr = mpdp_release(ctx, handles[i]);
+        if (rr != MPDP_OK && status[i] == MPDP_OK) status[i] = rr;
+    }
+    return rc;
+}
+
 int mpdp_optimize_batch_device(mpdp_ctx* ctx, int32_t nq, const int32_t* n_rels, const int32_t* n_edges,
                                const double* d_card, const mpdp_edge* d_edges, int32_t cost_model,
                                mpdp_plan_node* d_nodes, double* d_cost, int32_t* d_status)

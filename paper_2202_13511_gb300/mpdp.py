@@ -11,6 +11,7 @@ tensors resident on the GPU; ``Optimizer(stream=...)`` borrows a CUDA stream).
 from __future__ import annotations
 
 import ctypes
+import itertools
 import os
 import sys
 from dataclasses import dataclass, field
@@ -95,7 +96,7 @@ EXPORTS = [
     "mpdp_release", "mpdp_optimize_device", "mpdp_sync", "mpdp_memo_lookup",
     "mpdp_last_launch_count", "mpdp_strerror", "mpdp_last_error", "mpdp_abi_version",
     "mpdp_profile", "mpdp_profile_read", "mpdp_optimize_batch_device",
-    "mpdp_optimize_device_noalloc",
+    "mpdp_optimize_device_noalloc", "mpdp_get_plans",
 ]
 PLAN_STRIDE = 63
 NOALLOC_MAX_RELS = 16
@@ -135,6 +136,10 @@ def load(build_if_missing: bool = True):
     L.mpdp_get_plan.argtypes = [c_ctx, ctypes.c_int64, P(PlanNode), ctypes.c_int32,
                                 P(ctypes.c_int32), P(ctypes.c_double), P(StatsC)]
     L.mpdp_release.argtypes = [c_ctx, ctypes.c_int64]
+    L.mpdp_get_plans.argtypes = [c_ctx, P(ctypes.c_int64), ctypes.c_int32, ctypes.c_void_p,
+                                 ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_double),
+                                 P(ctypes.c_int32), ctypes.c_void_p]
+    L.mpdp_get_plans.restype = ctypes.c_int
     L.mpdp_optimize_device.argtypes = [c_ctx, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]
@@ -170,8 +175,17 @@ def load(build_if_missing: bool = True):
 class Plan:
     cost: float
     nodes: np.ndarray                 # NODE_DTYPE records, node 0 = root
-    stats: Dict = field(default_factory=dict)
+    raw_stats: Optional["StatsC"] = None
+    n: int = 0
     handle: int = -1
+    _stats: Optional[Dict] = None
+
+    @property
+    def stats(self) -> Dict:
+        """Counters of the run (built from the ABI record on first use)."""
+        if self._stats is None:
+            self._stats = _stats_dict(self.raw_stats, self.n) if self.raw_stats is not None else {}
+        return self._stats
 
     def signature(self, i: int = 0):
         """Nested (set, left-subtree, right-subtree) form; leaves are their set."""
@@ -182,9 +196,14 @@ class Plan:
 
 
 def pack_edges(edges) -> np.ndarray:
-    arr = np.zeros(len(edges), dtype=EDGE_DTYPE)
-    for i, (u, v, s) in enumerate(edges):
-        arr[i] = (u, v, s)
+    """(u, v, sel) triples as mpdp_edge records (relation indices are small
+    integers, exact in a double on the way through)."""
+    flat = np.fromiter(itertools.chain.from_iterable(edges), dtype=np.float64, count=3 * len(edges))
+    flat = flat.reshape(len(edges), 3)
+    arr = np.empty(len(edges), dtype=EDGE_DTYPE)
+    arr["u"] = flat[:, 0]
+    arr["v"] = flat[:, 1]
+    arr["sel"] = flat[:, 2]
     return arr
 
 
@@ -204,6 +223,34 @@ class _Packed:
         self.c.mode = mode
         self.c.k = k
         self.c.reserved = 0
+
+
+QUERY_DTYPE = np.dtype({"names": ["n_rels", "n_edges", "card", "edges", "cost_model", "mode", "k",
+                                   "reserved"],
+                         "formats": ["<i4", "<i4", "<u8", "<u8", "<i4", "<i4", "<i4", "<i4"],
+                         "offsets": [QueryC.n_rels.offset, QueryC.n_edges.offset, QueryC.card.offset,
+                                     QueryC.edges.offset, QueryC.cost_model.offset, QueryC.mode.offset,
+                                     QueryC.k.offset, QueryC.reserved.offset],
+                         "itemsize": ctypes.sizeof(QueryC)})
+
+
+def _pack_batch(queries, mode: int = MODE_EXACT, k: int = 0):
+    """mpdp_query records of a batch over two shared arrays (cards, edges)."""
+    ns = np.fromiter((q.n for q in queries), dtype=np.int64, count=len(queries))
+    ms = np.fromiter((len(q.edges) for q in queries), dtype=np.int64, count=len(queries))
+    card = np.fromiter(itertools.chain.from_iterable(q.card for q in queries), dtype=np.float64,
+                       count=int(ns.sum()))
+    edges = pack_edges([e for q in queries for e in q.edges])
+    recs = np.zeros(len(queries), dtype=QUERY_DTYPE)
+    recs["n_rels"] = ns
+    recs["n_edges"] = ms
+    co = np.concatenate([[0], np.cumsum(ns)[:-1]]) if len(queries) else ns
+    eo = np.concatenate([[0], np.cumsum(ms)[:-1]]) if len(queries) else ms
+    recs["card"] = card.ctypes.data + 8 * co
+    recs["edges"] = np.where(ms > 0, edges.ctypes.data + EDGE_DTYPE.itemsize * eo, 0)
+    recs["mode"] = mode
+    recs["k"] = k
+    return card, edges, recs
 
 
 def _stats_dict(st: StatsC, n: int) -> Dict:
@@ -300,8 +347,7 @@ class Optimizer:
             if release:
                 self.release(handle)
             self._check(rc, "mpdp_get_plan")
-        plan = Plan(cost=cost.value, nodes=nodes[:nn.value].copy(), stats=_stats_dict(st, n),
-                    handle=handle)
+        plan = Plan(cost=cost.value, nodes=nodes[:nn.value].copy(), raw_stats=st, n=n, handle=handle)
         if release:
             self.release(handle)
         return plan
@@ -315,11 +361,14 @@ class Optimizer:
         h = self.submit(q, mode, k)
         return self.get_plan(h, release=not keep)
 
-    def optimize_batch(self, queries: Sequence, mode: int = MODE_EXACT, k: int = 0) -> List[Plan]:
-        packed = [_Packed(q, mode, k) for q in queries]
-        arr = (QueryC * len(packed))(*[p.c for p in packed])
-        hs = (ctypes.c_int64 * len(packed))()
-        rc = self._lib.mpdp_optimize_batch(self._ctx, arr, len(packed), hs)
+    def submit_batch(self, queries: Sequence, mode: int = MODE_EXACT, k: int = 0) -> List[int]:
+        """Enqueue the queries (mpdp_optimize_batch) and return their handles
+        at once; the inputs are copied before this returns."""
+        card, edges, recs = _pack_batch(queries, mode, k)
+        hs = (ctypes.c_int64 * len(queries))()
+        rc = self._lib.mpdp_optimize_batch(self._ctx, recs.ctypes.data_as(ctypes.POINTER(QueryC)),
+                                           len(queries), hs)
+        del card, edges  # copied by the library before it returned
         for q, h in zip(queries, hs):
             if h >= 0:
                 self._n[h] = int(q.n)
@@ -328,7 +377,38 @@ class Optimizer:
                 if h >= 0:
                     self.release(h)
             self._check(rc, "mpdp_optimize_batch")
-        return [self.get_plan(h) for h in hs]
+        return list(hs)
+
+    def collect(self, handles: Sequence[int]) -> List[Plan]:
+        """Plans of submitted handles in one call (mpdp_get_plans: waits for
+        each, releases all); raises the first failing handle's error."""
+        count = len(handles)
+        if count == 0:
+            return []
+        ns = [self._n.get(int(h), 32) for h in handles]
+        stride = max(2 * max(ns) - 1, 1)
+        hs = np.ascontiguousarray(np.asarray(handles, dtype=np.int64))
+        nodes = np.zeros((count, stride), dtype=NODE_DTYPE)
+        nn = np.zeros(count, dtype=np.int32)
+        costs = np.zeros(count, dtype=np.float64)
+        status = np.zeros(count, dtype=np.int32)
+        stats = (StatsC * count)()
+        rc = self._lib.mpdp_get_plans(self._ctx, hs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), count,
+                                      nodes.ctypes.data, stride,
+                                      nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      costs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      status.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), stats)
+        for h in handles:
+            self._n.pop(int(h), None)
+        bad = np.flatnonzero(status != 0)
+        if len(bad):
+            self._check(int(status[bad[0]]), "mpdp_get_plans")
+        self._check(rc, "mpdp_get_plans")
+        return [Plan(cost=float(costs[i]), nodes=nodes[i, :nn[i]], raw_stats=stats[i], n=ns[i],
+                     handle=int(handles[i])) for i in range(count)]
+
+    def optimize_batch(self, queries: Sequence, mode: int = MODE_EXACT, k: int = 0) -> List[Plan]:
+        return self.collect(self.submit_batch(queries, mode, k))
 
     def memo_lookup(self, handle: int, sets) -> (np.ndarray, np.ndarray):
         s = np.ascontiguousarray(np.asarray(sets, dtype=np.uint64))
