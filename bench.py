@@ -32,17 +32,26 @@ QUERIES_PER_STEP = 64
 FLUSH_BYTES = 256 << 20
 # Issue-slot peak of the integer filter: 152 SMs x 4 schedulers x 32 lanes x clock.
 SMS, SCHEDULERS, LANES = 152, 4, 32
-# Algorithmic integer operations of the filter (unrank + connectivity):
-# per unranked subset, the next-bit-permutation step (9) and the spanning-tree
-# test C(S) by byte tables (4 loads, 3 byte extracts, 3 ors, and-not, popc,
-# compare: 13); per BFS round run for the sets of a cyclic graph that neither
-# test settles, N(seen) by byte tables (10), or, and, two compares (15 in all).
-OPS_PER_SUBSET = 22
-OPS_PER_STEP = 15
+# Algorithmic integer operations of the bitmap filter per bitmap examined.
+# Tree join graphs: a run of 32 bitmaps costs C(base) by byte tables (4 loads,
+# 4 byte extracts, 3 ors), the fixed-part test (3) and, when that passes, the
+# bit-sliced count over the 5 low relations (about 40): 2 per bitmap on
+# average.  Other graphs: the spanning-tree test (5), the isolated-vertex test
+# (4) and the compaction (3) per bitmap, plus 15 per BFS round.
+OPS_PER_BITMAP_TREE = 2
+OPS_PER_BITMAP_GRAPH = 12
+OPS_PER_BFS_ROUND = 15
 # Algorithmic memo bytes: two lookups of (4-byte key + 8-byte cost) per CCP pair
 # and one 16-byte entry written per connected set.
 BYTES_PER_CCP = 24
 BYTES_PER_SET = 16
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernels on this bench's 64-query batch, from one ncu capture of
+# this bench command (--cache-control none; profiles/).  They describe the
+# kernel sources whose SHA-1 is given and are reported as null for any other.
+TRAFFIC_SOURCES = ("paper_2202_13511_gb300/csrc/mpdp_kernels.cu", "paper_2202_13511_gb300/csrc/mpdp_device.cuh")
+TRAFFIC = {"sha1": "f7583e67c6dad93afe2095746a122621662e4d58",
+           "eval": 138459685, "filter": 22600137}
 
 
 def parse_args():
@@ -226,8 +235,9 @@ def run_ours(args):
         # one device batch: every kernel launch covers all Q queries
         opt.optimize_batch_device(ns, ms, d_card, d_edges, d_nodes, d_cost, d_status)
 
-    # host-path pass: per-query counters (CCP pairs, filter work, transfer bytes)
-    stats = [opt.optimize(q).stats for q in queries]
+    # host-path pass (one batch): per-query counters (CCP pairs, filter work,
+    # transfer bytes)
+    stats = [p.stats for p in opt.optimize_batch(queries)]
     launches_per_step = None
     for _ in range(max(args.warmup, 3)):
         step()
@@ -296,7 +306,7 @@ def run_ours(args):
     opt.profile(False)
     peaks = read_peaks()
     dom = max(kt, key=lambda k: kt[k]["ms"])
-    roof = roofline(dom, kt[dom], stats, prof_steps, peaks, clocks)
+    roof = roofline(dom, kt[dom], stats, prof_steps, peaks, bench_batch=(Q == QUERIES_PER_STEP))
     kernel_share = {k: round(v["ms"] / max(sum(x["ms"] for x in kt.values()), 1e-12), 4)
                     for k, v in kt.items() if v["launches"]}
 
@@ -330,30 +340,44 @@ def run_ours(args):
     return 0
 
 
-def roofline(kind, timing, stats, prof_steps, peaks, clocks):
+def traffic_for(kind, measured):
+    """ncu DRAM bytes per launch of `kind`, while the kernel sources are the
+    profiled ones and the workload is this bench's own batch."""
+    import hashlib
+    if not measured:
+        return None
+    h = hashlib.sha1()
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return TRAFFIC.get(kind) if h.hexdigest() == TRAFFIC["sha1"] else None
+
+
+def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False):
     """Roofline of the dominant kernel class.  `stats` are the per-query
     counters of one step's queries, `timing` the class's summed event time
     and launches over `prof_steps` steps."""
     launches = max(timing["launches"], 1)
     avg_s = timing["ms"] / launches / 1000.0
     if kind == "filter":
-        ops = sum(OPS_PER_SUBSET * int(s["sets_unranked"]) + OPS_PER_STEP * int(s["filter_steps"])
+        ops = sum((OPS_PER_BITMAP_TREE if s["enumeration"] == 1 else OPS_PER_BITMAP_GRAPH) *
+                  int(s["sets_unranked"]) + OPS_PER_BFS_ROUND * int(s["filter_steps"])
                   for s in stats) * prof_steps / launches
         mhz = 2070.0
         peak = SMS * SCHEDULERS * LANES * mhz * 1e6 / 1e12
         ach = ops / avg_s / 1e12
-        return {"kernel": "k_filter", "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "Tops/s", "frac": ach / peak, "traffic": None,
+        return {"kernel": "k_filter_bitmaps", "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "Tops/s", "frac": ach / peak, "traffic": traffic_for("filter", bench_batch),
                 "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz (issue slots)",
                 "ops_per_launch": ops, "avg_launch_ms": avg_s * 1000.0}
     # memo-traffic kernels: algorithmic bytes per launch
     nbytes = sum(BYTES_PER_CCP * int(s["ccp_pairs"]) + BYTES_PER_SET * int(s["sets_connected"])
-                 for s in stats) * prof_steps / launches / max(prof_steps, 1)
+                 for s in stats) * prof_steps / launches
     peak = (peaks or {}).get("hbm_gbs", 6800.0)
     ach = nbytes / avg_s / 1e9
-    return {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-            "frac": ach / peak, "traffic": None,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s",
+    name = {"eval": "k_eval_tree", "heavy": "k_eval_heavy"}.get(kind, kind)
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "traffic": traffic_for(kind, bench_batch and kind == "eval"),
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst)" if peaks else "fallback 6800 GB/s",
             "bytes_per_launch": nbytes, "avg_launch_ms": avg_s * 1000.0}
 
 
@@ -410,7 +434,7 @@ def shape_line(name, opt, torch, mpdp, W, peaks, reps=5):
             "queries_per_s": nq * 1000.0 / ms_batch, "ccp_pairs_per_s": ccp / (ms_batch / 1000.0),
             "ccp_pairs_per_query": ccp / nq,
             "sets_connected_per_query": sum(int(s["sets_connected"]) for s in stats) / nq,
-            "roofline": roofline(dom, kt[dom], stats, 3, peaks, None),
+            "roofline": roofline(dom, kt[dom], stats, 3, peaks),
             "kernel_share": {k: round(v["ms"] / max(sum(x["ms"] for x in kt.values()), 1e-12), 4)
                              for k, v in kt.items() if v["launches"]}}
 
