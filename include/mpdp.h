@@ -14,13 +14,17 @@
  *   - the plan is fetched recursively from the memo (Sec. 5, last paragraph).
  *
  * Cost model (the paper's own is unspecified, Sec. 6.1): C_out.
- *   cost({R_i}) = 0;  cost(L join R) = (cost(L) + cost(R)) + card(L u R),
- *   card(S) = product, in this fixed order, over the relations r of S in
- *   ascending index of: card[r], then sel(j, r) for every j in S with j < r
- *   and an edge (j, r), in ascending j.  All arithmetic is IEEE-754 binary64,
- *   round to nearest, no fused multiply-add.
- * Ties: the chosen split of S is the lexicographic minimum of (cost, left)
- * where left is the numerically smaller of the two relation bitmaps.
+ *   cost({R_i}) = 0;  cost(L join R) = (cost(L) + cost(R)) + card(L u R).
+ *   card(S) is a product taken in an order fixed by S alone ("peeling"):
+ *   card({r}) = card[r]; otherwise v is the highest-index relation of S
+ *   whose removal leaves G[S] with no more components (for a connected S its
+ *   highest non-cut vertex) and card(S) = ((card(S \ {v}) * card[v]) *
+ *   sel(j1, v)) * sel(j2, v) ... over v's neighbours j1 < j2 < ... in S.
+ *   All arithmetic is IEEE-754 binary64, round to nearest, no fused
+ *   multiply-add.
+ * Ties: the chosen split of S is the lexicographic minimum of (x, left),
+ * x = cost(S_left) + cost(S_right) and left the numerically smaller of the
+ * two relation bitmaps; cost(S) = x + card(S).
  * Results are therefore bit-identical to any exact DP with the same rules.
  *
  * Relation sets are bitmaps: bit i is relation i.
@@ -76,16 +80,18 @@ enum {
 enum { MPDP_ENUM_AUTO = 0, MPDP_ENUM_TREE = 1, MPDP_ENUM_BLOCKS = 2 };
 
 /* Memo layout.  DENSE: arrays indexed directly by the relation bitmap
- * (12 bytes x 2^n).  HASH: one open-addressing table per level, Murmur3 fmix32
- * hash, linear probing, 16-byte slots {key, left, cost}, capacity the power of
- * two >= 2x the level's connected-set count (Sec. 5, memo of "MPDP on GPU"). */
+ * (20 bytes x 2^n: {cost, card} and left).  HASH: one open-addressing table
+ * per level, Murmur3 fmix32 hash, linear probing, 32-byte slots {key, left,
+ * cost, card}, capacity the power of two >= 2x the level's connected-set
+ * count (Sec. 5, memo of "MPDP on GPU"). */
 enum { MPDP_MEMO_DENSE = 0, MPDP_MEMO_HASH = 1 };
 
 /* Connected-set filter.  UNRANK: every k-subset of every level is unranked
  * with the combinatorial number system and stepped with the next bit
  * permutation (Sec. 5, "Unrank", "Filter").  BITMAPS: every bitmap below 2^n
- * is visited in index order (all levels at once, no unranking) and the
- * connected ones are then sorted into their levels.  Same results. */
+ * is visited in index order (all levels at once, no unranking) and each
+ * connected one goes straight into the list of its level.  Same sets and
+ * counters. */
 enum { MPDP_FILTER_BITMAPS = 0, MPDP_FILTER_UNRANK = 1 };
 
 typedef struct mpdp_ctx mpdp_ctx; /* opaque, owned by the library */
@@ -133,7 +139,7 @@ typedef struct {
     uint64_t pairs_evaluated;
     uint64_t ccp_pairs;
     uint64_t memo_bytes;       /* device bytes of the memo used by this query */
-    uint64_t heavy_sets;       /* sets evaluated by the warp-per-set path */
+    uint64_t heavy_sets;       /* block mode: sets evaluated by the chunked heavy-set kernel */
     double device_ms;          /* device time of the DP (CUDA events) */
     int32_t enumeration;       /* MPDP_ENUM_TREE or MPDP_ENUM_BLOCKS as run */
     int32_t memo_kind;         /* MPDP_MEMO_* as run */
@@ -150,11 +156,13 @@ typedef struct {
     int32_t memo_kind;        /* MPDP_MEMO_DENSE (default) or MPDP_MEMO_HASH */
     int32_t enumeration;      /* MPDP_ENUM_AUTO (default), _TREE, _BLOCKS */
     int32_t heavy_threshold;  /* block mode: sets with more pairs than this go to
-                                 the warp-per-set kernel (default 64) */
+                                 the heavy-set kernel, one warp per chunk of at
+                                 most 2048 pairs (default 64) */
     int32_t use_ccc;          /* 1 (default): collaborative context collection
-                                 in the warp-per-set kernel (Sec. 5) */
+                                 in the heavy-set kernel (Sec. 5) */
     int32_t use_graphs;       /* 1 (default): replay a captured CUDA graph per shape */
-    int32_t run_length;       /* k-subsets unranked per lane (1..32, default 32) */
+    int32_t run_length;       /* MPDP_FILTER_UNRANK: k-subsets unranked per lane
+                                 (1..32, default 32) */
     int32_t filter;           /* MPDP_FILTER_BITMAPS (default) or MPDP_FILTER_UNRANK */
 } mpdp_config;
 
