@@ -61,7 +61,8 @@ enum {
     MPDP_ERR_BAD_HANDLE = -10,      /* unknown or released handle */
     MPDP_ERR_NOT_IMPLEMENTED = -11,
     MPDP_ERR_STALE = -12,           /* the handle's memo was overwritten by a later query */
-    MPDP_ERR_INTERNAL = -13         /* an internal consistency check failed */
+    MPDP_ERR_INTERNAL = -13,        /* an internal consistency check failed */
+    MPDP_ERR_NOT_READY = -14        /* the result is not available yet (server) */
 };
 
 enum { MPDP_COST_COUT = 0 };
@@ -164,6 +165,8 @@ typedef struct {
     int32_t run_length;       /* MPDP_FILTER_UNRANK: k-subsets unranked per lane
                                  (1..32, default 32) */
     int32_t filter;           /* MPDP_FILTER_BITMAPS (default) or MPDP_FILTER_UNRANK */
+    int32_t grid_blocks_per_sm; /* evaluate grids: at most this many 256-thread
+                                 blocks per SM (1..32, default 8) */
 } mpdp_config;
 
 /* Create a context on CUDA device `device`.  memo_budget_bytes caps the device
@@ -309,6 +312,62 @@ const char *mpdp_strerror(int code);
 /* Text of the last CUDA error seen by this context (or ""). */
 const char *mpdp_last_error(const mpdp_ctx *ctx);
 int32_t mpdp_abi_version(void);
+
+/* ---------------------------------------------------------------------
+ * Serving loop (no counterpart in the paper): continuous batching of
+ * optimization requests.  A server owns `slots` contexts, each with its own
+ * CUDA stream and device workspace of slot_budget_bytes.  mpdp_server_submit
+ * copies a request and queues it.  Whenever a slot is free, the queue's head
+ * forms that slot's next device batch: requests join in arrival order while
+ * the batch stays within max_batch queries and the slot's budget (admission
+ * by memo memory).  Batches of different slots run concurrently on the GPU.
+ * A request's plan is bit-identical to the same query optimized alone.
+ * Progress happens inside submit / poll / drain; the library runs no
+ * background thread.  A server is used by one host thread at a time. */
+typedef struct mpdp_server mpdp_server; /* opaque, owned by the library */
+
+typedef struct {
+    int32_t slots;                /* concurrent device batches (1..16; default 4) */
+    int32_t max_batch;            /* queries per device batch (1..1024; default 256) */
+    uint64_t slot_budget_bytes;   /* device workspace per slot (0: 16 GiB) */
+    mpdp_config kernel;           /* kernel configuration of every slot (default:
+                                     context defaults with use_graphs = 0, since
+                                     mixed batches rarely repeat a shape) */
+} mpdp_server_config;
+
+/* Fill *cfg with the defaults. */
+int mpdp_server_default_config(mpdp_server_config *cfg);
+
+/* Create a server on CUDA device `device` (cfg NULL: defaults). */
+int mpdp_server_create(mpdp_server **out, int device, const mpdp_server_config *cfg);
+void mpdp_server_destroy(mpdp_server *s);
+
+/* Queue one exact-mode request (inputs copied before return) and make
+ * progress.  *ticket identifies it.  The request is checked here as
+ * mpdp_optimize checks a query (MPDP_ERR_INVALID_ARG, _DISCONNECTED,
+ * _TOO_LARGE), so one bad request never fails a batch;
+ * MPDP_ERR_ADMISSION: the query alone exceeds a slot's budget. */
+int mpdp_server_submit(mpdp_server *s, const mpdp_query *q, int64_t *ticket);
+
+/* Make progress without blocking: collect finished batches, start batches
+ * on free slots.  The tickets finished by this call go to done[0..cap)
+ * (done may be NULL when cap == 0); *count receives how many (count may be
+ * NULL). */
+int mpdp_server_poll(mpdp_server *s, int64_t *done, int32_t cap, int32_t *count);
+
+/* Block until every submitted request has finished. */
+int mpdp_server_drain(mpdp_server *s);
+
+/* Requests waiting in the queue and on the device (either may be NULL). */
+int mpdp_server_pending(const mpdp_server *s, int32_t *queued, int32_t *running);
+
+/* Read and forget a finished request: its plan (cap >= 2n-1 nodes, nodes
+ * may be NULL), cost, and latency from submit to the poll that saw it done,
+ * in microseconds.  Returns the request's status (0 or its MPDP_ERR_*; the
+ * request is forgotten either way), MPDP_ERR_NOT_READY if it has not
+ * finished (it is kept), MPDP_ERR_BAD_HANDLE if unknown. */
+int mpdp_server_result(mpdp_server *s, int64_t ticket, mpdp_plan_node *nodes, int32_t cap,
+                       int32_t *n_nodes, double *cost, double *latency_us);
 
 #ifdef __cplusplus
 }

@@ -25,7 +25,7 @@ using namespace mpdp;
 
 namespace {
 
-const mpdp_config kDefaultConfig = {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 1, 32, MPDP_FILTER_BITMAPS};
+const mpdp_config kDefaultConfig = {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 1, 32, MPDP_FILTER_BITMAPS, 8};
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -500,8 +500,9 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
     StagedQuery* hs = reinterpret_cast<StagedQuery*>(h + staged_off);
     BatchPlan bp;
     bp.num_sms = ctx->num_sms;
+    bp.blocks_per_sm = ctx->cfg.grid_blocks_per_sm;
     std::vector<int> key = {nq, kind, ctx->cfg.heavy_threshold, ctx->cfg.use_ccc, ctx->cfg.run_length,
-                            ctx->cfg.filter};
+                            ctx->cfg.filter, ctx->cfg.grid_blocks_per_sm};
     unsigned long long lbase = 0, mbase = 0, hbase = 0;
     uint32_t fblocks = 0;
     int max_n = 0;
@@ -628,6 +629,7 @@ const char* mpdp_strerror(int code)
     case MPDP_ERR_NOT_IMPLEMENTED: return "not implemented";
     case MPDP_ERR_STALE: return "memo of this handle was overwritten";
     case MPDP_ERR_INTERNAL: return "internal consistency check failed";
+    case MPDP_ERR_NOT_READY: return "result not ready yet";
     default: return "unknown error";
     }
 }
@@ -702,6 +704,7 @@ int mpdp_set_config(mpdp_ctx* ctx, const mpdp_config* cfg)
     if (cfg->enumeration < MPDP_ENUM_AUTO || cfg->enumeration > MPDP_ENUM_BLOCKS) return MPDP_ERR_INVALID_ARG;
     if (cfg->heavy_threshold < 0 || cfg->run_length < 1 || cfg->run_length > 32) return MPDP_ERR_INVALID_ARG;
     if (cfg->filter != MPDP_FILTER_BITMAPS && cfg->filter != MPDP_FILTER_UNRANK) return MPDP_ERR_INVALID_ARG;
+    if (cfg->grid_blocks_per_sm < 1 || cfg->grid_blocks_per_sm > 32) return MPDP_ERR_INVALID_ARG;
     ctx->cfg = *cfg;
     return MPDP_OK;
 }
@@ -972,3 +975,24 @@ int mpdp_memo_lookup(mpdp_ctx* ctx, int64_t handle, const uint64_t* sets, int32_
 }
 
 }  // extern "C"
+
+namespace mpdp {
+
+int validate_host_query(const mpdp_query* q) { return validate_query(q, MPDP_MAX_EXACT_RELS); }
+
+// Workspace of one device batch under the same rules as a context's batch
+// split (for callers that form batches themselves).
+size_t batch_workspace_bytes(const int* n, const int* m, int count, const mpdp_config& cfg)
+{
+    size_t L = 0, V = 0, M = 0, A = 0;
+    for (int i = 0; i < count; i++) {
+        const QuerySize z = query_size(n[i], resolve_enumeration(cfg, n[i], m[i]), cfg.memo_kind);
+        L += z.lists;
+        V += z.heavy;
+        M += z.memo;
+        A += z.hash;
+    }
+    return var_bytes_of(L, V, M, A) + fixed_bytes();
+}
+
+}  // namespace mpdp

@@ -25,7 +25,7 @@ MPDP_OK = 0
 ERRORS = {
     -1: "INVALID_ARG", -2: "DISCONNECTED", -3: "TOO_LARGE", -4: "OOM", -5: "ADMISSION",
     -6: "BUFFER_TOO_SMALL", -7: "TIMEOUT", -8: "PROBE_LIMIT", -9: "CUDA", -10: "BAD_HANDLE",
-    -11: "NOT_IMPLEMENTED", -12: "STALE", -13: "INTERNAL",
+    -11: "NOT_IMPLEMENTED", -12: "STALE", -13: "INTERNAL", -14: "NOT_READY",
 }
 ERR = {v: k for k, v in ERRORS.items()}
 
@@ -80,7 +80,12 @@ class ConfigC(ctypes.Structure):
     _fields_ = [("memo_kind", ctypes.c_int32), ("enumeration", ctypes.c_int32),
                 ("heavy_threshold", ctypes.c_int32), ("use_ccc", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("run_length", ctypes.c_int32),
-                ("filter", ctypes.c_int32)]
+                ("filter", ctypes.c_int32), ("grid_blocks_per_sm", ctypes.c_int32)]
+
+
+class ServerConfigC(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("slot_budget_bytes", ctypes.c_uint64), ("kernel", ConfigC)]
 
 
 EDGE_DTYPE = np.dtype([("u", "<i4"), ("v", "<i4"), ("sel", "<f8")])
@@ -97,6 +102,8 @@ EXPORTS = [
     "mpdp_last_launch_count", "mpdp_strerror", "mpdp_last_error", "mpdp_abi_version",
     "mpdp_profile", "mpdp_profile_read", "mpdp_optimize_batch_device",
     "mpdp_optimize_device_noalloc", "mpdp_get_plans",
+    "mpdp_server_default_config", "mpdp_server_create", "mpdp_server_destroy", "mpdp_server_submit",
+    "mpdp_server_poll", "mpdp_server_drain", "mpdp_server_pending", "mpdp_server_result",
 ]
 PLAN_STRIDE = 63
 NOALLOC_MAX_RELS = 16
@@ -152,6 +159,20 @@ def load(build_if_missing: bool = True):
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.mpdp_optimize_device_noalloc.restype = ctypes.c_int
     L.mpdp_sync.argtypes = [c_ctx]
+    c_srv = ctypes.c_void_p
+    L.mpdp_server_default_config.argtypes = [P(ServerConfigC)]
+    L.mpdp_server_create.argtypes = [P(c_srv), ctypes.c_int, P(ServerConfigC)]
+    L.mpdp_server_destroy.argtypes = [c_srv]
+    L.mpdp_server_destroy.restype = None
+    L.mpdp_server_submit.argtypes = [c_srv, P(QueryC), P(ctypes.c_int64)]
+    L.mpdp_server_poll.argtypes = [c_srv, P(ctypes.c_int64), ctypes.c_int32, P(ctypes.c_int32)]
+    L.mpdp_server_drain.argtypes = [c_srv]
+    L.mpdp_server_pending.argtypes = [c_srv, P(ctypes.c_int32), P(ctypes.c_int32)]
+    L.mpdp_server_result.argtypes = [c_srv, ctypes.c_int64, P(PlanNode), ctypes.c_int32,
+                                     P(ctypes.c_int32), P(ctypes.c_double), P(ctypes.c_double)]
+    for f in ("mpdp_server_default_config", "mpdp_server_create", "mpdp_server_submit",
+              "mpdp_server_poll", "mpdp_server_drain", "mpdp_server_pending", "mpdp_server_result"):
+        getattr(L, f).restype = ctypes.c_int
     L.mpdp_memo_lookup.argtypes = [c_ctx, ctypes.c_int64, P(ctypes.c_uint64), ctypes.c_int32,
                                    P(ctypes.c_double), P(ctypes.c_uint64)]
     L.mpdp_last_launch_count.argtypes = [c_ctx]
@@ -459,6 +480,126 @@ class Optimizer:
         ln = (ctypes.c_uint64 * len(KERNEL_CLASSES))()
         self._check(self._lib.mpdp_profile_read(self._ctx, ms, ln), "mpdp_profile_read")
         return {k: dict(ms=ms[i], launches=int(ln[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+class Server:
+    """Serving loop over the library's native scheduler (mpdp_server_*):
+    continuous batching over `slots` concurrent device batches, admission
+    by memo memory.  Results are bit-identical to optimizing alone."""
+
+    def __init__(self, device: int = 0, slots: Optional[int] = None, max_batch: Optional[int] = None,
+                 slot_budget_bytes: Optional[int] = None, **kernel_config):
+        self._lib = load()
+        cfg = ServerConfigC()
+        self._check(self._lib.mpdp_server_default_config(ctypes.byref(cfg)), "mpdp_server_default_config")
+        if slots is not None:
+            cfg.slots = int(slots)
+        if max_batch is not None:
+            cfg.max_batch = int(max_batch)
+        if slot_budget_bytes is not None:
+            cfg.slot_budget_bytes = int(slot_budget_bytes)
+        for k, v in kernel_config.items():
+            if k not in dict(ConfigC._fields_):
+                raise KeyError(k)
+            setattr(cfg.kernel, k, int(v))
+        self._srv = ctypes.c_void_p()
+        self._check(self._lib.mpdp_server_create(ctypes.byref(self._srv), int(device), ctypes.byref(cfg)),
+                    "mpdp_server_create")
+        self._n: Dict[int, int] = {}
+
+    def _check(self, rc, what):
+        if rc != MPDP_OK:
+            raise MPDPError(rc, what, strerror(rc))
+
+    def close(self):
+        if getattr(self, "_srv", None) and self._srv.value:
+            self._lib.mpdp_server_destroy(self._srv)
+            self._srv = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, q) -> int:
+        p = _Packed(q)
+        t = ctypes.c_int64(-1)
+        self._check(self._lib.mpdp_server_submit(self._srv, ctypes.byref(p.c), ctypes.byref(t)),
+                    "mpdp_server_submit")
+        self._n[t.value] = int(q.n)
+        return t.value
+
+    def poll(self, cap: int = 4096) -> List[int]:
+        buf = (ctypes.c_int64 * cap)()
+        cnt = ctypes.c_int32(0)
+        self._check(self._lib.mpdp_server_poll(self._srv, buf, cap, ctypes.byref(cnt)), "mpdp_server_poll")
+        return list(buf[:cnt.value])
+
+    def drain(self):
+        self._check(self._lib.mpdp_server_drain(self._srv), "mpdp_server_drain")
+
+    def pending(self):
+        a, b = ctypes.c_int32(0), ctypes.c_int32(0)
+        self._check(self._lib.mpdp_server_pending(self._srv, ctypes.byref(a), ctypes.byref(b)),
+                    "mpdp_server_pending")
+        return a.value, b.value
+
+    def result(self, ticket: int):
+        """(Plan, latency in microseconds) of a finished request."""
+        n = self._n.get(ticket, 32)
+        cap = max(2 * n - 1, 1)
+        nodes = np.zeros(cap, dtype=NODE_DTYPE)
+        nn = ctypes.c_int32(0)
+        cost = ctypes.c_double(0.0)
+        lat = ctypes.c_double(0.0)
+        rc = self._lib.mpdp_server_result(self._srv, ticket, nodes.ctypes.data_as(ctypes.POINTER(PlanNode)),
+                                          cap, ctypes.byref(nn), ctypes.byref(cost), ctypes.byref(lat))
+        if rc != ERR["NOT_READY"]:
+            self._n.pop(ticket, None)
+        self._check(rc, "mpdp_server_result")
+        return Plan(cost=cost.value, nodes=nodes[:nn.value].copy(), n=n, handle=ticket), lat.value
+
+    def replay(self, queries: Sequence, arrivals_s: Sequence[float], limit_s: float = 600.0):
+        """Submit queries[i] at arrivals_s[i] seconds after the start (busy
+        waiting on the host clock, polling in between) and collect every
+        result.  Returns (plans, latencies in seconds from each request's
+        arrival time, makespan in seconds).  Raises TimeoutError after
+        limit_s seconds."""
+        import time
+        order = np.argsort(np.asarray(arrivals_s), kind="stable")
+        tickets = [None] * len(queries)
+        lag = [0.0] * len(queries)
+        done_lat: Dict[int, float] = {}
+        t0 = time.perf_counter()
+        nxt = 0
+        outstanding = 0
+        while nxt < len(order) or outstanding:
+            now = time.perf_counter() - t0
+            while nxt < len(order) and arrivals_s[order[nxt]] <= now:
+                i = int(order[nxt])
+                tickets[i] = self.submit(queries[i])
+                lag[i] = (time.perf_counter() - t0) - arrivals_s[i]
+                nxt += 1
+                outstanding += 1
+            for t in self.poll():
+                done_lat[t] = 0.0
+                outstanding -= 1
+            if now > limit_s:
+                raise TimeoutError(f"replay did not finish within {limit_s} s")
+        makespan = time.perf_counter() - t0
+        plans, lats = [], []
+        for i, t in enumerate(tickets):
+            p, lat_us = self.result(t)
+            plans.append(p)
+            lats.append(lag[i] + lat_us * 1e-6)
+        return plans, np.asarray(lats), makespan
 
 
 def optimize_device_noalloc(n: int, n_edges: int, d_card, d_edges, d_nodes, d_cost, d_status,

@@ -34,7 +34,7 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(mpdp.Edge) == 16
     assert ctypes.sizeof(mpdp.PlanNode) == 40
     assert ctypes.sizeof(mpdp.QueryC) == 40
-    assert ctypes.sizeof(mpdp.ConfigC) == 28
+    assert ctypes.sizeof(mpdp.ConfigC) == 32
     assert ctypes.sizeof(mpdp.StatsC) == 6 * 8 + 8 + 8 + 3 * 8 + 3 * 33 * 8
 
 

@@ -34,7 +34,8 @@ def opt():
 
 def set_cfg(opt, **kw):
     base = dict(memo_kind=mpdp.MEMO_DENSE, enumeration=mpdp.ENUM_AUTO, heavy_threshold=64,
-                use_ccc=1, use_graphs=1, run_length=32, filter=mpdp.FILTER_BITMAPS)
+                use_ccc=1, use_graphs=1, run_length=32, filter=mpdp.FILTER_BITMAPS,
+                grid_blocks_per_sm=8)
     base.update(kw)
     opt.set_config(**base)
 
@@ -176,6 +177,15 @@ def test_graphs_on_off(opt, graphs):
         p1 = check(opt, q)
         assert opt.launch_count() > 0
         del p1
+
+
+@pytest.mark.parametrize("grid", [1, 3, 32])
+def test_grid_sizes(opt, grid):
+    """Results do not depend on how many blocks the evaluate grids get."""
+    set_cfg(opt, grid_blocks_per_sm=grid)
+    for q in (W.snowflake(18, seed=6), W.cyclic(15, seed=4), W.clique(12, seed=2)):
+        check(opt, q)
+    set_cfg(opt)
 
 
 @pytest.mark.parametrize("kind", ["star", "clique", "cycle", "chain"])
