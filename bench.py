@@ -344,6 +344,9 @@ def run_ours(args):
     if rank == 0 and not args.no_star:
         for name in SHAPES:
             line[name] = shape_line(name, opt, torch, mpdp, W, peaks)
+    if rank == 0 and world == 1 and not args.no_star:
+        opt.close()
+        line["serving"] = serving_line(mpdp, W)
     opt.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -450,6 +453,44 @@ def shape_line(name, opt, torch, mpdp, W, peaks, reps=5):
             "roofline": roofline(dom, kt[dom], stats, 3, peaks),
             "kernel_share": {k: round(v["ms"] / max(sum(x["ms"] for x in kt.values()), 1e-12), 4)
                              for k, v in kt.items() if v["launches"]}}
+
+
+SERVE_QUERIES = 2000
+
+
+def serving_line(mpdp, W):
+    """Batched/served form: 2,000 mixed queries (star / snowflake / cyclic,
+    8-25 relations, weight 3 on 12-18) through the native serving loop,
+    first all at once (saturated throughput), then as Poisson arrivals at
+    50 / 80 / 95 % of it.  Kernel knobs and the server's slots / batch cap
+    come from the autotuner, run on samples of the same mix."""
+    import numpy as np
+    from paper_2202_13511_gb300 import autotune
+    queries = W.mixed_stream(SERVE_QUERIES, seed=0)
+    t0 = time.perf_counter()
+    kernel, _, khist = autotune.tune_kernels(queries[:256], reps=2)
+    server_cfg, _, shist = autotune.tune_server(queries[:512], kernel=kernel)
+    tune_s = time.perf_counter() - t0
+    out = {"workload": f"{SERVE_QUERIES} mixed queries: star/snowflake/cyclic uniformly, 8-25 relations "
+                       "(weight 3 on 12-18), seed 0",
+           "autotuned": {"kernel": kernel, "server": server_cfg,
+                         "configs_timed": len(khist) + len(shist), "tuning_s": round(tune_s, 2)}}
+    with mpdp.Server(0, slots=server_cfg["slots"], max_batch=server_cfg["max_batch"], **kernel) as srv:
+        srv.replay(queries, [0.0] * len(queries))  # warm-up
+        _, lat, makespan = srv.replay(queries, [0.0] * len(queries))
+        sat = len(queries) / makespan
+        out["saturated"] = {"queries_per_s": sat, "makespan_s": makespan,
+                            "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                            "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+        rng = np.random.default_rng(1)
+        for frac in (0.5, 0.8, 0.95):
+            arrivals = np.cumsum(rng.exponential(1.0 / (frac * sat), size=len(queries)))
+            _, lat, makespan = srv.replay(queries, arrivals)
+            out[f"poisson_{int(frac * 100)}"] = {
+                "offered_queries_per_s": frac * sat, "queries_per_s": len(queries) / makespan,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3)}
+    return out
 
 
 def main():

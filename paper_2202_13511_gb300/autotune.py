@@ -1,0 +1,156 @@
+"""Autotuner for the launch shapes and work splits of a workload.
+
+The DP's results do not depend on any of the knobs below.  Only the speed
+does, and the best setting depends on the workload:
+- the evaluate grids' blocks per SM (`grid_blocks_per_sm`);
+- in block mode, the pair count above which a set leaves the thread-per-set
+  kernel for the chunked warp kernel (`heavy_threshold`), and whether those
+  warps use collaborative context collection (`use_ccc`);
+- the connected-set filter (`filter`);
+- for the serving loop, the number of concurrent device batches (`slots`)
+  and the batch size cap (`max_batch`).
+
+The search is coordinate descent from the defaults. It tries each value of
+one knob with the others fixed, keeps the best, and repeats until a full
+pass changes nothing. Timing comes from a `measure(config) -> seconds`
+callable. The default measures device batches of the sample with CUDA
+events, L2 flushed before each. Tests pass their own.
+"""
+from __future__ import annotations
+
+from typing import Callable, Dict, List, Optional, Sequence
+
+KERNEL_SPACE: Dict[str, List[int]] = {
+    "grid_blocks_per_sm": [2, 4, 8, 16],
+    "heavy_threshold": [16, 64, 256],
+    "use_ccc": [0, 1],
+    "filter": [0, 1],  # MPDP_FILTER_BITMAPS, MPDP_FILTER_UNRANK
+}
+SERVER_SPACE: Dict[str, List[int]] = {
+    "slots": [1, 2, 4, 8],
+    "max_batch": [16, 64, 256],
+}
+
+
+def coordinate_descent(start: Dict[str, int], space: Dict[str, List[int]],
+                       measure: Callable[[Dict[str, int]], float], max_passes: int = 3):
+    """Minimise measure() over the grid `space`, one knob at a time.
+    Returns (best config, its time, every (config, time) measured)."""
+    best = dict(start)
+    cache: Dict[tuple, float] = {}
+
+    def timed(cfg):
+        key = tuple(sorted(cfg.items()))
+        if key not in cache:
+            cache[key] = float(measure(dict(cfg)))
+        return cache[key]
+
+    best_t = timed(best)
+    for _ in range(max_passes):
+        changed = False
+        for knob, values in space.items():
+            for v in values:
+                if v == best[knob]:
+                    continue
+                trial = dict(best)
+                trial[knob] = v
+                t = timed(trial)
+                if t < best_t:
+                    best, best_t, changed = trial, t, True
+        if not changed:
+            break
+    history = [(dict(k), t) for k, t in cache.items()]
+    return best, best_t, history
+
+
+def relevant_space(queries: Sequence) -> Dict[str, List[int]]:
+    """The kernel knobs that can matter for these queries: the block-mode
+    knobs only when some query is not a tree."""
+    space = dict(KERNEL_SPACE)
+    if all(len(q.edges) == q.n - 1 for q in queries):
+        space.pop("heavy_threshold")
+        space.pop("use_ccc")
+    return space
+
+
+def device_batch_timer(queries: Sequence, device: int = 0, reps: int = 3):
+    """measure(config) for the kernel knobs: mean device time of one batch
+    of `queries` (CUDA events around the batch, 256 MiB L2 flush before
+    each rep), through the device-resident entry point."""
+    import numpy as np
+    import torch
+
+    from . import mpdp
+
+    torch.cuda.set_device(device)
+    stream = torch.cuda.current_stream()
+    opt = mpdp.Optimizer(device, stream=stream.cuda_stream)
+    d_card = torch.tensor([c for q in queries for c in q.card], dtype=torch.float64, device="cuda")
+    d_edges = torch.from_numpy(mpdp.pack_edges([e for q in queries for e in q.edges]).view(np.uint8).copy()).cuda()
+    nq = len(queries)
+    d_nodes = torch.zeros((nq, mpdp.PLAN_STRIDE * 40), dtype=torch.uint8, device="cuda")
+    d_cost = torch.zeros(nq, dtype=torch.float64, device="cuda")
+    d_status = torch.zeros(nq, dtype=torch.int32, device="cuda")
+    ns, ms = [q.n for q in queries], [len(q.edges) for q in queries]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def measure(cfg: Dict[str, int]) -> float:
+        opt.set_config(**cfg)
+        run = lambda: opt.optimize_batch_device(ns, ms, d_card, d_edges, d_nodes, d_cost, d_status)
+        run()  # warm-up (graph capture for a new shape)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        total = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a.record(stream)
+            run()
+            b.record(stream)
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b) / 1000.0
+        if int((d_status != 0).sum().item()):
+            raise RuntimeError("device reported an error while tuning")
+        return total / reps
+
+    measure.close = opt.close
+    return measure
+
+
+def tune_kernels(queries: Sequence, device: int = 0, reps: int = 3,
+                 measure: Optional[Callable[[Dict[str, int]], float]] = None):
+    """Best kernel configuration for batches shaped like `queries`.
+    Returns (config dict for Optimizer.set_config / Server kernel config,
+    its time in seconds, the measured history)."""
+    space = relevant_space(queries)
+    start = {"grid_blocks_per_sm": 8, "heavy_threshold": 64, "use_ccc": 1, "filter": 0}
+    start = {k: v for k, v in start.items() if k in space}
+    own = measure is None
+    if own:
+        measure = device_batch_timer(queries, device, reps)
+    try:
+        return coordinate_descent(start, space, measure)
+    finally:
+        if own:
+            measure.close()
+
+
+def server_throughput_timer(queries: Sequence, device: int = 0, kernel: Optional[Dict[str, int]] = None):
+    """measure(config) for the serving knobs: seconds for a server with that
+    many slots and that batch cap to finish `queries` submitted at once."""
+    from . import mpdp
+
+    def measure(cfg: Dict[str, int]) -> float:
+        with mpdp.Server(device, slots=cfg["slots"], max_batch=cfg["max_batch"], **(kernel or {})) as srv:
+            srv.replay(queries, [0.0] * len(queries))  # warm-up: workspaces grow to size
+            _, _, makespan = srv.replay(queries, [0.0] * len(queries))
+        return makespan
+
+    return measure
+
+
+def tune_server(queries: Sequence, device: int = 0, kernel: Optional[Dict[str, int]] = None,
+                measure: Optional[Callable[[Dict[str, int]], float]] = None):
+    """Best (slots, max_batch) for serving a stream shaped like `queries`."""
+    if measure is None:
+        measure = server_throughput_timer(queries, device, kernel)
+    return coordinate_descent({"slots": 4, "max_batch": 256}, SERVER_SPACE, measure)
