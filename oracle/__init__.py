@@ -38,7 +38,7 @@ from typing import Dict, List, Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "mpdp_oracle.c")
+_SRCS = [os.path.join(_HERE, "mpdp_oracle.c"), os.path.join(_HERE, "xd_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
@@ -60,11 +60,11 @@ def build(force: bool = False) -> str:
     """Compile the C oracle (plain gcc, no FMA contraction, no fast-math)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                           "-shared", "-o", tmp, _SRC])
+                           "-shared", "-o", tmp, *_SRCS, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -89,8 +89,15 @@ def _lib():
         lib.oracle_block_enum_counts.argtypes = _GRAPH_ARGS + [_U64, _U64]
         lib.oracle_dpsub.argtypes = _GRAPH_ARGS + [_D, _U32, _U64]
         lib.oracle_dpccp.argtypes = _GRAPH_ARGS + [_D, _U32, _U64]
+        xargs = [ctypes.c_int, _D, _I32, ctypes.c_int, _I32, _I32, _D, _I32, _D, _I32, _U32]
+        lib.oracle_xd_dpsub.argtypes = xargs
+        lib.oracle_xd_dpccp.argtypes = xargs
+        lib.oracle_xd_ops.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                      _D, _I32, _D, _I32, _I32]
+        lib.oracle_xd_ops.restype = None
         for f in ("oracle_card", "oracle_grow", "oracle_connected", "oracle_blocks",
-                  "oracle_block_enum_counts", "oracle_dpsub", "oracle_dpccp"):
+                  "oracle_block_enum_counts", "oracle_dpsub", "oracle_dpccp", "oracle_xd_dpsub",
+                  "oracle_xd_dpccp"):
             getattr(lib, f).restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -336,3 +343,47 @@ def brute_force(q, max_n: int = 7):
     # the minimum x gives the minimum cost (addition is monotone): check it
     assert best[2] == min(t[2] for t in all_trees)
     return best[2], best[1], len(all_trees)
+
+
+# ---------------------------------------------------------------------------
+# Extended range (xd_oracle.c): values m * 2^e, m = 0 or 1 <= m < 2.
+
+def xd_ops(a, b):
+    """(a + b, a * b, compare(a, b)) of two (mantissa, exponent) values,
+    as xd_oracle.c computes them."""
+    sm, se, pm, pe, c = (ctypes.c_double(), ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32(),
+                         ctypes.c_int32())
+    _lib().oracle_xd_ops(float(a[0]), int(a[1]), float(b[0]), int(b[1]), ctypes.byref(sm), ctypes.byref(se),
+                         ctypes.byref(pm), ctypes.byref(pe), ctypes.byref(c))
+    return (sm.value, se.value), (pm.value, pe.value), c.value
+
+
+@dataclass
+class XDResult:
+    cost_m: np.ndarray   # [2^n] mantissa of cost(S) (0 for singletons and unformed sets)
+    cost_e: np.ndarray   # [2^n] exponent
+    left: np.ndarray     # [2^n] left(S); UINT32_MAX for sets never formed
+
+    def cost(self, s: int):
+        return (float(self.cost_m[s]), int(self.cost_e[s]))
+
+
+def xd_dp(n, card, edges, method: str = "dpccp") -> XDResult:
+    """The exact DP in extended range.  card: n (mantissa, exponent) pairs;
+    edges: (u, v, (mantissa, exponent)) with the selectivity in XD."""
+    cm = np.ascontiguousarray([float(c[0]) for c in card], dtype=np.float64)
+    ce = np.ascontiguousarray([int(c[1]) for c in card], dtype=np.int32)
+    eu = np.ascontiguousarray([int(e[0]) for e in edges], dtype=np.int32)
+    ev = np.ascontiguousarray([int(e[1]) for e in edges], dtype=np.int32)
+    sm = np.ascontiguousarray([float(e[2][0]) for e in edges], dtype=np.float64)
+    se = np.ascontiguousarray([int(e[2][1]) for e in edges], dtype=np.int32)
+    size = 1 << n
+    out_m = np.zeros(size, dtype=np.float64)
+    out_e = np.zeros(size, dtype=np.int32)
+    left = np.zeros(size, dtype=np.uint32)
+    fn = _lib().oracle_xd_dpccp if method == "dpccp" else _lib().oracle_xd_dpsub
+    _check(fn(n, cm.ctypes.data_as(_D), ce.ctypes.data_as(_I32), len(edges), eu.ctypes.data_as(_I32),
+              ev.ctypes.data_as(_I32), sm.ctypes.data_as(_D), se.ctypes.data_as(_I32),
+              out_m.ctypes.data_as(_D), out_e.ctypes.data_as(_I32), left.ctypes.data_as(_U32)),
+           "xd_" + method)
+    return XDResult(out_m, out_e, left)
