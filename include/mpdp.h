@@ -45,6 +45,8 @@ extern "C" {
 /* Exact mode uses 32-bit relation bitmaps; memory grows as 2^n (see
  * mpdp_workspace_bytes), so n is further capped by the memo budget. */
 #define MPDP_MAX_EXACT_RELS 30
+/* Heuristic modes (IDP2, UnionDP): relations of one query. */
+#define MPDP_MAX_HEURISTIC_RELS 4096
 #define MPDP_MAX_LEVELS 33
 
 enum {
@@ -113,8 +115,10 @@ typedef struct {
     const mpdp_edge *edges;  /* [n_edges] */
     int32_t cost_model;      /* MPDP_COST_COUT */
     int32_t mode;            /* MPDP_MODE_* */
-    int32_t k;               /* heuristic sub-problem size (IDP2 / UnionDP), <= 25 */
-    int32_t reserved;        /* must be 0 */
+    int32_t k;               /* heuristic sub-problem size (IDP2 / UnionDP), <= 25;
+                                IDP2 with k <= 1 returns GOO's plan */
+    int32_t t;               /* UnionDP partition threshold, 2..k (0: k); 0 in
+                                the other modes */
 } mpdp_query;
 
 /* One node of the result plan.  Node 0 is the root; children have larger
@@ -182,7 +186,15 @@ int mpdp_get_config(const mpdp_ctx *ctx, mpdp_config *cfg);
 size_t mpdp_workspace_bytes(int32_t n_rels, const mpdp_config *cfg);
 
 /* Validate the query on the host, enqueue its optimization on the context's
- * stream and return a handle at once (asynchronous).  Exact mode: n <= 30. */
+ * stream and return a handle at once (asynchronous).  Exact mode: n <= 30.
+ * Heuristic modes (Sec. 4): MPDP_MODE_IDP2 (GOO's plan, then IDP2 with
+ * sub-problems of at most k <= 25 relations) and MPDP_MODE_UNIONDP
+ * (Algorithm 5 with partitions of at most t and a final DP of at most k),
+ * n <= MPDP_MAX_HEURISTIC_RELS.  Every sub-problem is solved exactly on the
+ * device in extended range; these modes run to completion before the call
+ * returns.  Plan nodes of n > 64 relations carry set = 0.  The _LEARNED
+ * modes return MPDP_ERR_NOT_IMPLEMENTED, and so does mpdp_optimize_batch
+ * for any mode but exact. */
 int mpdp_optimize(mpdp_ctx *ctx, const mpdp_query *q, int64_t *handle);
 
 /* Enqueue nq queries as device batches (all queries of a batch share every
@@ -199,6 +211,12 @@ int mpdp_get_plan(mpdp_ctx *ctx, int64_t handle, mpdp_plan_node *nodes, int32_t 
 
 /* Forget a handle (its host result buffer is reused). */
 int mpdp_release(mpdp_ctx *ctx, int64_t handle);
+
+/* The plan cost of a handle in extended range: cost = mant * 2^exp2 with
+ * mant = 0 or 1 <= mant < 2 (heuristic plans of hundreds of relations cost
+ * more than binary64 holds; mpdp_get_plan's cost is then +inf).  No
+ * counterpart in the paper.  Blocks like mpdp_get_plan. */
+int mpdp_get_cost_xd(mpdp_ctx *ctx, int64_t handle, double *mant, int32_t *exp2);
 
 /* mpdp_get_plan + mpdp_release for `count` handles in one call (no
  * counterpart in the paper; it saves a host round trip per query when a

@@ -19,7 +19,9 @@
 #include <vector>
 
 #include "../../include/mpdp.h"
+#include "mpdp_heuristic.h"
 #include "mpdp_launch.h"
+#include "mpdp_xd_exec.h"
 
 using namespace mpdp;
 
@@ -108,6 +110,8 @@ struct PlanQuery {
 }  // namespace
 
 struct mpdp_ctx {
+    mpdp::XdExecutor* xd = nullptr;                      // heuristic sub-problems (created on first use)
+    std::map<int64_t, mpdp::HeuristicResult> heur;      // finished heuristic-mode plans by handle
     int device = 0;
     cudaStream_t stream = nullptr;          // work stream (borrowed; nullptr = default stream)
     cudaStream_t capture_stream = nullptr;  // private, only used to capture graphs
@@ -166,7 +170,7 @@ static int validate_query(const mpdp_query* q, int max_n)
     const int n = q->n_rels, m = q->n_edges;
     if (n < 1) return MPDP_ERR_INVALID_ARG;
     if (n > max_n) return MPDP_ERR_TOO_LARGE;
-    if (q->cost_model != MPDP_COST_COUT || q->reserved != 0) return MPDP_ERR_INVALID_ARG;
+    if (q->cost_model != MPDP_COST_COUT || q->t != 0 || q->mode != MPDP_MODE_EXACT) return MPDP_ERR_INVALID_ARG;
     if (m < 0 || m > edges_max(n)) return MPDP_ERR_INVALID_ARG;
     if (!q->card || (m > 0 && !q->edges)) return MPDP_ERR_INVALID_ARG;
     for (int i = 0; i < n; i++)
@@ -679,6 +683,8 @@ void mpdp_destroy(mpdp_ctx* ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    delete ctx->xd;
+    ctx->xd = nullptr;
     destroy_graphs(ctx);
     for (auto& r : ctx->recs) {
         if (r.host) cudaFreeHost(r.host);
@@ -748,16 +754,117 @@ int mpdp_optimize_batch(mpdp_ctx* ctx, const mpdp_query* qs, int32_t nq, int64_t
     return MPDP_OK;
 }
 
+// Host checks of a heuristic-mode query (any n up to the heuristic limit).
+static int validate_heuristic(const mpdp_query* q)
+{
+    const int n = q->n_rels, m = q->n_edges;
+    if (q->cost_model != MPDP_COST_COUT) return MPDP_ERR_INVALID_ARG;
+    if (q->mode != MPDP_MODE_IDP2 && q->mode != MPDP_MODE_UNIONDP) return MPDP_ERR_INVALID_ARG;
+    if (n < 1 || m < 0 || (long long)m > (long long)n * (n - 1) / 2 || !q->card || (m > 0 && !q->edges))
+        return MPDP_ERR_INVALID_ARG;
+    if (n > MPDP_MAX_HEURISTIC_RELS) return MPDP_ERR_TOO_LARGE;
+    if (q->k > 25) return MPDP_ERR_TOO_LARGE;
+    if (q->mode == MPDP_MODE_IDP2 && q->t != 0) return MPDP_ERR_INVALID_ARG;
+    if (q->mode == MPDP_MODE_UNIONDP && (q->k < 2 || (q->t != 0 && (q->t < 2 || q->t > q->k))))
+        return MPDP_ERR_INVALID_ARG;
+    for (int i = 0; i < n; i++)
+        if (!finite_pos(q->card[i])) return MPDP_ERR_INVALID_ARG;
+    std::vector<int> parent(n);
+    for (int i = 0; i < n; i++) parent[i] = i;
+    auto find = [&](int x) {
+        while (parent[x] != x) x = parent[x] = parent[parent[x]];
+        return x;
+    };
+    std::vector<std::pair<int, int>> seen;
+    seen.reserve(m);
+    int comps = n;
+    for (int e = 0; e < m; e++) {
+        const int u = q->edges[e].u, v = q->edges[e].v;
+        const double s = q->edges[e].sel;
+        if (u < 0 || v < 0 || u >= n || v >= n || u == v || !(s > 0.0) || !(s <= 1.0)) return MPDP_ERR_INVALID_ARG;
+        seen.push_back({std::min(u, v), std::max(u, v)});
+        const int a = find(u), b = find(v);
+        if (a != b) {
+            parent[a] = b;
+            comps--;
+        }
+    }
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return MPDP_ERR_INVALID_ARG;
+    if (comps != 1) return MPDP_ERR_DISCONNECTED;
+    return MPDP_OK;
+}
+
 int mpdp_optimize(mpdp_ctx* ctx, const mpdp_query* q, int64_t* handle)
 {
     if (!ctx || !q || !handle) return MPDP_ERR_INVALID_ARG;
-    return mpdp_optimize_batch(ctx, q, 1, handle);
+    *handle = -1;
+    if (q->mode == MPDP_MODE_EXACT) return mpdp_optimize_batch(ctx, q, 1, handle);
+    if (q->mode == MPDP_MODE_IDP2_LEARNED || q->mode == MPDP_MODE_UNIONDP_LEARNED) return MPDP_ERR_NOT_IMPLEMENTED;
+    const int vrc = validate_heuristic(q);
+    if (vrc != MPDP_OK) return vrc;
+    CK(ctx, cudaSetDevice(ctx->device));
+    if (!ctx->xd) ctx->xd = new mpdp::XdExecutor();
+    mpdp::HeuristicQuery hq;
+    hq.n = q->n_rels;
+    hq.mode = q->mode;
+    hq.k = q->k;
+    hq.t = q->t;
+    hq.card = q->card;
+    for (int e = 0; e < q->n_edges; e++) {
+        hq.eu.push_back(q->edges[e].u);
+        hq.ev.push_back(q->edges[e].v);
+        hq.sel.push_back(q->edges[e].sel);
+    }
+    mpdp::HeuristicResult res;
+    const int rc = mpdp::run_heuristic(hq, *ctx->xd, ctx->stream, ctx->num_sms, res);
+    if (rc != MPDP_OK) {
+        ctx->last_error = "heuristic optimization failed";
+        return rc;
+    }
+    const int64_t h = ctx->next_handle++;
+    ctx->heur[h] = std::move(res);
+    *handle = h;
+    return MPDP_OK;
+}
+
+int mpdp_get_cost_xd(mpdp_ctx* ctx, int64_t handle, double* mant, int32_t* exp2)
+{
+    if (!ctx || !mant || !exp2) return MPDP_ERR_INVALID_ARG;
+    auto hit = ctx->heur.find(handle);
+    if (hit != ctx->heur.end()) {
+        *mant = hit->second.cost.m;
+        *exp2 = hit->second.cost.e;
+        return MPDP_OK;
+    }
+    double c = 0.0;
+    const int rc = mpdp_get_plan(ctx, handle, nullptr, 0, nullptr, &c, nullptr);
+    if (rc != MPDP_OK) return rc;
+    const mpdp::XD x = mpdp::xd_make(c, 0);
+    *mant = x.m;
+    *exp2 = x.e;
+    return MPDP_OK;
 }
 
 int mpdp_get_plan(mpdp_ctx* ctx, int64_t handle, mpdp_plan_node* nodes, int32_t cap, int32_t* n_nodes,
                   double* cost, mpdp_stats* st)
 {
     if (!ctx) return MPDP_ERR_INVALID_ARG;
+    auto hit = ctx->heur.find(handle);
+    if (hit != ctx->heur.end()) {
+        const mpdp::HeuristicResult& r = hit->second;
+        const int nn = (int)r.nodes.size();
+        if (nodes && cap < nn) return MPDP_ERR_BUFFER_TOO_SMALL;
+        if (nodes) memcpy(nodes, r.nodes.data(), sizeof(mpdp_plan_node) * nn);
+        if (n_nodes) *n_nodes = nn;
+        if (cost) *cost = nn ? r.nodes[0].cost : 0.0;
+        if (st) {
+            memset(st, 0, sizeof(*st));
+            st->enumeration = MPDP_ENUM_BLOCKS;
+            st->heavy_sets = (uint64_t)r.subproblems;  // exact sub-problems solved
+        }
+        return MPDP_OK;
+    }
     auto it = ctx->handles.find(handle);
     if (it == ctx->handles.end()) return MPDP_ERR_BAD_HANDLE;
     Record& rec = ctx->recs[it->second.rec];
@@ -804,6 +911,7 @@ int mpdp_get_plan(mpdp_ctx* ctx, int64_t handle, mpdp_plan_node* nodes, int32_t 
 int mpdp_release(mpdp_ctx* ctx, int64_t handle)
 {
     if (!ctx) return MPDP_ERR_INVALID_ARG;
+    if (ctx->heur.erase(handle)) return MPDP_OK;
     auto it = ctx->handles.find(handle);
     if (it == ctx->handles.end()) return MPDP_ERR_BAD_HANDLE;
     Record& rec = ctx->recs[it->second.rec];

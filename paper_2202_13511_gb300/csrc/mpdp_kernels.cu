@@ -1282,6 +1282,13 @@ cudaError_t enqueue_pipeline(const BatchArgs& a, const BatchPlan& bp, int memo_k
     return cudaGetLastError();
 }
 
+cudaError_t enqueue_structure(const BatchArgs& a, const BatchPlan& bp, cudaStream_t st)
+{
+    k_ingest<<<a.nq, 256, 0, st>>>(a, 0);
+    if (bp.filter_blocks > 0) k_filter_bitmaps<<<bp.filter_blocks, kFilterThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t enqueue_stage_device(const BatchArgs& a, const double* card, const mpdp_edge* edges, cudaStream_t st,
                                  LaunchHook* hook)
 {

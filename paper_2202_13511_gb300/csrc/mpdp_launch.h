@@ -45,6 +45,10 @@ cudaError_t enqueue_publish(const BatchArgs& a, mpdp_plan_node* nodes, double* c
 cudaError_t enqueue_memo_lookup(const BatchArgs& a, int memo_kind, int qi, const uint32_t* d_sets,
                                 int count, double* d_costs, uint32_t* d_lefts, cudaStream_t st);
 
+// Ingest and the bitmap filter only (validation, tables, the connected sets
+// of every level): the structure any arithmetic can then evaluate.
+cudaError_t enqueue_structure(const BatchArgs& a, const BatchPlan& bp, cudaStream_t st);
+
 // Device workspace (bytes) a context needs for one batch of these queries
 // under configuration cfg; defined with the context code.
 size_t batch_workspace_bytes(const int* n, const int* m, int count, const mpdp_config& cfg);

@@ -55,7 +55,7 @@ class QueryC(ctypes.Structure):
     _fields_ = [("n_rels", ctypes.c_int32), ("n_edges", ctypes.c_int32),
                 ("card", ctypes.POINTER(ctypes.c_double)), ("edges", ctypes.POINTER(Edge)),
                 ("cost_model", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("k", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("k", ctypes.c_int32), ("t", ctypes.c_int32)]
 
 
 class PlanNode(ctypes.Structure):
@@ -101,7 +101,7 @@ EXPORTS = [
     "mpdp_release", "mpdp_optimize_device", "mpdp_sync", "mpdp_memo_lookup",
     "mpdp_last_launch_count", "mpdp_strerror", "mpdp_last_error", "mpdp_abi_version",
     "mpdp_profile", "mpdp_profile_read", "mpdp_optimize_batch_device",
-    "mpdp_optimize_device_noalloc", "mpdp_get_plans",
+    "mpdp_optimize_device_noalloc", "mpdp_get_plans", "mpdp_get_cost_xd",
     "mpdp_server_default_config", "mpdp_server_create", "mpdp_server_destroy", "mpdp_server_submit",
     "mpdp_server_poll", "mpdp_server_drain", "mpdp_server_pending", "mpdp_server_result",
 ]
@@ -143,6 +143,8 @@ def load(build_if_missing: bool = True):
     L.mpdp_get_plan.argtypes = [c_ctx, ctypes.c_int64, P(PlanNode), ctypes.c_int32,
                                 P(ctypes.c_int32), P(ctypes.c_double), P(StatsC)]
     L.mpdp_release.argtypes = [c_ctx, ctypes.c_int64]
+    L.mpdp_get_cost_xd.argtypes = [c_ctx, ctypes.c_int64, P(ctypes.c_double), P(ctypes.c_int32)]
+    L.mpdp_get_cost_xd.restype = ctypes.c_int
     L.mpdp_get_plans.argtypes = [c_ctx, P(ctypes.c_int64), ctypes.c_int32, ctypes.c_void_p,
                                  ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_double),
                                  P(ctypes.c_int32), ctypes.c_void_p]
@@ -200,6 +202,7 @@ class Plan:
     n: int = 0
     handle: int = -1
     _stats: Optional[Dict] = None
+    cost_xd: Optional[tuple] = None   # heuristic modes: (mantissa, exponent) of the cost
 
     @property
     def stats(self) -> Dict:
@@ -231,7 +234,7 @@ def pack_edges(edges) -> np.ndarray:
 class _Packed:
     """ABI view of one query (keeps its arrays alive)."""
 
-    def __init__(self, q, mode: int = MODE_EXACT, k: int = 0):
+    def __init__(self, q, mode: int = MODE_EXACT, k: int = 0, t: int = 0):
         self.card = np.ascontiguousarray(np.asarray(q.card, dtype=np.float64))
         self.edges = pack_edges(q.edges)
         self.c = QueryC()
@@ -243,15 +246,15 @@ class _Packed:
         self.c.cost_model = 0
         self.c.mode = mode
         self.c.k = k
-        self.c.reserved = 0
+        self.c.t = t
 
 
 QUERY_DTYPE = np.dtype({"names": ["n_rels", "n_edges", "card", "edges", "cost_model", "mode", "k",
-                                   "reserved"],
+                                   "t"],
                          "formats": ["<i4", "<i4", "<u8", "<u8", "<i4", "<i4", "<i4", "<i4"],
                          "offsets": [QueryC.n_rels.offset, QueryC.n_edges.offset, QueryC.card.offset,
                                      QueryC.edges.offset, QueryC.cost_model.offset, QueryC.mode.offset,
-                                     QueryC.k.offset, QueryC.reserved.offset],
+                                     QueryC.k.offset, QueryC.t.offset],
                          "itemsize": ctypes.sizeof(QueryC)})
 
 
@@ -346,8 +349,8 @@ class Optimizer:
         return int(self._lib.mpdp_last_launch_count(self._ctx))
 
     # -- host path --------------------------------------------------------
-    def submit(self, q, mode: int = MODE_EXACT, k: int = 0) -> int:
-        p = _Packed(q, mode, k)
+    def submit(self, q, mode: int = MODE_EXACT, k: int = 0, t: int = 0) -> int:
+        p = _Packed(q, mode, k, t)
         h = ctypes.c_int64(-1)
         self._check(self._lib.mpdp_optimize(self._ctx, ctypes.byref(p.c), ctypes.byref(h)),
                     "mpdp_optimize")
@@ -377,10 +380,20 @@ class Optimizer:
         self._check(self._lib.mpdp_release(self._ctx, handle), "mpdp_release")
         self._n.pop(handle, None)
 
-    def optimize(self, q, mode: int = MODE_EXACT, k: int = 0, keep: bool = False) -> Plan:
-        """Optimize one query through mpdp_optimize + mpdp_get_plan."""
-        h = self.submit(q, mode, k)
-        return self.get_plan(h, release=not keep)
+    def optimize(self, q, mode: int = MODE_EXACT, k: int = 0, keep: bool = False, t: int = 0) -> Plan:
+        """Optimize one query through mpdp_optimize + mpdp_get_plan.  In the
+        heuristic modes (MODE_IDP2, MODE_UNIONDP) the plan also carries
+        cost_xd = (mantissa, exponent): its cost is mantissa * 2^exponent."""
+        h = self.submit(q, mode, k, t)
+        xd = None
+        if mode != MODE_EXACT:
+            m, e = ctypes.c_double(0.0), ctypes.c_int32(0)
+            self._check(self._lib.mpdp_get_cost_xd(self._ctx, h, ctypes.byref(m), ctypes.byref(e)),
+                        "mpdp_get_cost_xd")
+            xd = (m.value, e.value)
+        plan = self.get_plan(h, release=not keep)
+        plan.cost_xd = xd
+        return plan
 
     def submit_batch(self, queries: Sequence, mode: int = MODE_EXACT, k: int = 0) -> List[int]:
         """Enqueue the queries (mpdp_optimize_batch) and return their handles
