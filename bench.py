@@ -345,6 +345,7 @@ def run_ours(args):
         for name in SHAPES:
             line[name] = shape_line(name, opt, torch, mpdp, W, peaks)
     if rank == 0 and world == 1 and not args.no_star:
+        line["large"] = heuristic_line(opt, mpdp, W)
         opt.close()
         line["serving"] = serving_line(mpdp, W)
     opt.close()
@@ -456,6 +457,50 @@ def shape_line(name, opt, torch, mpdp, W, peaks, reps=5):
 
 
 SERVE_QUERIES = 2000
+LARGE_SIZES = (100, 300, 1000)
+LARGE_QUERIES = 10
+
+
+def heuristic_line(opt, mpdp, W):
+    """Large queries (snowflake with fanout 1-5 and no depth cap, plus 5 %
+    extra edges): IDP2 (k = 25, GOO start), UnionDP (k = 25, t = 15) and GOO
+    alone, every sub-problem solved exactly on the GPU in extended range.
+    Wall time per query through mpdp_optimize, and each plan's cost as a
+    ratio to IDP2's (average and 95th percentile, as the paper's tables)."""
+    import math
+    import numpy as np
+    variants = {"idp2_25": (mpdp.MODE_IDP2, 25, 0), "uniondp_25_15": (mpdp.MODE_UNIONDP, 25, 15),
+                "goo": (mpdp.MODE_IDP2, 1, 0)}
+    out = {"workload": f"snowflake with fanout 1-5, depth uncapped, +5 % extra edges; {LARGE_QUERIES} queries "
+                       f"per size, seeds 0..{LARGE_QUERIES - 1}.  'independent': cards 10^U(2,8), sels "
+                       "10^U(-6,-1) (card(S) grows ~10^1.5 per relation, so the last joins dominate every "
+                       "plan's cost); 'pkfk': the same graphs with primary-key/foreign-key sels 1/card(key "
+                       "side), the paper's setting for its heuristic tables",
+           "ratio_to": "idp2_25"}
+    for gen, n in [(g, n) for g in ("independent", "pkfk") for n in LARGE_SIZES]:
+        make = W.snowflake_plus if gen == "independent" else W.snowflake_plus_pkfk
+        qs = [make(n, seed=i) for i in range(LARGE_QUERIES)]
+        opt.optimize(qs[0], mode=mpdp.MODE_IDP2, k=25)  # warm-up: device buffers
+        res = {}
+        for name, (mode, k, t) in variants.items():
+            times, costs = [], []
+            for q in qs:
+                t0 = time.perf_counter()
+                p = opt.optimize(q, mode=mode, k=k, t=t)
+                times.append(time.perf_counter() - t0)
+                costs.append(p.cost_xd)
+            res[name] = (times, costs)
+        line = {}
+        base = res["idp2_25"][1]
+        for name, (times, costs) in res.items():
+            ratios = [m / bm * math.pow(2.0, e - be) for (m, e), (bm, be) in zip(costs, base)]
+            line[name] = {"ms_per_query": 1000.0 * float(np.mean(times)),
+                          "p50_ms": 1000.0 * float(np.median(times)),
+                          "cost_ratio_avg": float(np.mean(ratios)),
+                          "cost_ratio_p95": float(np.percentile(ratios, 95)),
+                          "log2_cost_median": float(np.median([e + math.log2(m) for m, e in costs]))}
+        out[f"{gen}_n{n}"] = line
+    return out
 
 
 def serving_line(mpdp, W):

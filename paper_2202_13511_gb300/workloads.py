@@ -216,6 +216,17 @@ def snowflake_plus(n: int, seed: int = 0, extra_frac: float = 0.05) -> Query:
     return _finish(rng, n, card, pairs, "snowflake_plus", seed)
 
 
+def snowflake_plus_pkfk(n: int, seed: int = 0, extra_frac: float = 0.05) -> Query:
+    """The snowflake_plus graph with primary-key / foreign-key joins, the
+    setting of the paper's heuristic experiments (Sec. 6.3): every edge
+    joins a foreign key to the other relation's primary key, so its
+    selectivity is 1 / card(key side).  A tree edge's key side is the child;
+    an extra edge's is the relation with the larger index."""
+    q = snowflake_plus(n, seed, extra_frac)
+    edges = [(u, v, 1.0 / q.card[v]) for (u, v, _s) in q.edges]
+    return Query(n=n, card=q.card, edges=edges, kind="snowflake_plus_pkfk", seed=seed, meta=q.meta)
+
+
 def uniform_values(n: int, edges_uv, card: float = 1000.0, sel: float = 0.01,
                    kind: str = "uniform") -> Query:
     """All cardinalities and selectivities equal: a case with many exact cost ties."""
@@ -231,6 +242,7 @@ GENERATORS = {
     "snowflake": snowflake,
     "cyclic": cyclic,
     "snowflake_plus": snowflake_plus,
+    "snowflake_plus_pkfk": snowflake_plus_pkfk,
 }
 
 
