@@ -387,6 +387,29 @@ int mpdp_server_pending(const mpdp_server *s, int32_t *queued, int32_t *running)
 int mpdp_server_result(mpdp_server *s, int64_t ticket, mpdp_plan_node *nodes, int32_t cap,
                        int32_t *n_nodes, double *cost, double *latency_us);
 
+/* ---------------------------------------------------------------------
+ * Learned proposal (a project addition; the paper only cites learned
+ * optimizers): a 3 x 256 MLP that scores the edges of a query graph, trained
+ * and run on the GPU by the library's own BF16 kernels (tensor-core
+ * m16n8k16 products, FP32 accumulation, FP32 Adam).  Parameters (f32): W1
+ * [n_in x 256], b1 [256], W2 [256 x 256], b2, W3 [256 x 256], b3, w4 [256],
+ * b4 [1].  x and targets are device arrays of rows x n_in / rows floats. */
+typedef struct mpdp_mlp mpdp_mlp;
+int mpdp_mlp_create(mpdp_mlp **out, int device, int32_t n_in, void *cuda_stream);
+void mpdp_mlp_destroy(mpdp_mlp *m);
+int64_t mpdp_mlp_param_count(const mpdp_mlp *m);
+/* Copy parameters in (resets the optimizer state) / out; host arrays. */
+int mpdp_mlp_set_params(mpdp_mlp *m, const float *host, int64_t count);
+int mpdp_mlp_get_params(mpdp_mlp *m, float *host, int64_t count);
+/* y[rows] = MLP(x); device arrays; enqueued on the model's stream. */
+int mpdp_mlp_forward(mpdp_mlp *m, const float *d_x, int32_t rows, float *d_y);
+/* Gradients of L = sum (y - t)^2 / (2 rows) into host_grads (param_count
+ * floats, may be NULL) and L into *loss (may be NULL); waits. */
+int mpdp_mlp_gradients(mpdp_mlp *m, const float *d_x, const float *d_t, int32_t rows,
+                       float *host_grads, double *loss);
+/* One Adam step (beta 0.9 / 0.999) on L; enqueued. */
+int mpdp_mlp_train_step(mpdp_mlp *m, const float *d_x, const float *d_t, int32_t rows, float lr);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,82 @@
+"""CPU reference of the learned proposal's network, for gradient checks.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Plain numpy in
+float64 with the BF16 rounding points of the GPU kernels made explicit, so
+that a wrong layout, transposition or dropped term in the kernels shows as a
+difference far above the rounding noise:
+  xb = bf16(x); h_l = bf16(relu(h_{l-1} W_l + b_l)) for l = 1..3;
+  y = h_3 . w4 + b4;  L = sum (y - t)^2 / (2 rows);
+  dz_3 = (dy w4^T) masked by h_3 > 0; dW_l = h_{l-1}^T bf16(dz_l);
+  db_l = column sums of dz_l; dh_{l-1} = bf16(dz_l) W_l^T; dz_{l-1} = dh_{l-1}
+  masked by h_{l-1} > 0; dw4 = h_3^T dy; db4 = sum dy, with dy = (y - t) / rows.
+The weights used in products are bf16(W_l) (the GPU's copies of its f32
+masters).  bf16 rounding is round to nearest even on the float32 value.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+H = 256
+
+
+EXACT = False  # tests of the formulas themselves switch the rounding off
+
+
+def bf16(x) -> np.ndarray:
+    """Round to bfloat16 (nearest even) through float32, returned as float64."""
+    if EXACT:
+        return np.asarray(x, dtype=np.float64)
+    f = np.asarray(x, dtype=np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def unpack(p: np.ndarray, n_in: int):
+    sizes = [n_in * H, H, H * H, H, H * H, H, H, 1]
+    out, o = [], 0
+    for s in sizes:
+        out.append(np.asarray(p[o:o + s], dtype=np.float64))
+        o += s
+    W1, b1, W2, b2, W3, b3, w4, b4 = out
+    return [W1.reshape(n_in, H), b1, W2.reshape(H, H), b2, W3.reshape(H, H), b3, w4, b4]
+
+
+def forward(p, x):
+    n_in = x.shape[1]
+    W1, b1, W2, b2, W3, b3, w4, b4 = unpack(p, n_in)
+    h0 = bf16(x)
+    h1 = bf16(np.maximum(h0 @ bf16(W1) + b1, 0.0))
+    h2 = bf16(np.maximum(h1 @ bf16(W2) + b2, 0.0))
+    h3 = bf16(np.maximum(h2 @ bf16(W3) + b3, 0.0))
+    y = h3 @ w4 + b4[0]
+    return y, (h0, h1, h2, h3)
+
+
+def gradients(p, x, t):
+    """(flat gradient in the parameter layout, loss)."""
+    n_in = x.shape[1]
+    W1, b1, W2, b2, W3, b3, w4, b4 = unpack(p, n_in)
+    y, (h0, h1, h2, h3) = forward(p, x)
+    rows = x.shape[0]
+    d = y - t
+    loss = float(np.sum(d * d) / (2 * rows))
+    dy = d / rows
+    dw4 = h3.T @ dy
+    db4 = np.array([dy.sum()])
+    dz3 = np.outer(dy, w4) * (h3 > 0)
+    Ws = [bf16(W1), bf16(W2), bf16(W3)]
+    hs = [h0, h1, h2, h3]
+    grads = {}
+    dz = dz3
+    for l in (3, 2, 1):
+        dzb = bf16(dz)
+        grads[f"b{l}"] = dz.sum(axis=0)
+        grads[f"W{l}"] = hs[l - 1].T @ dzb
+        if l == 1:
+            break
+        dh = dzb @ Ws[l - 1].T
+        dz = dh * (hs[l - 1] > 0)
+    flat = np.concatenate([grads["W1"].ravel(), grads["b1"], grads["W2"].ravel(), grads["b2"],
+                           grads["W3"].ravel(), grads["b3"], dw4, db4])
+    return flat, loss

@@ -102,6 +102,8 @@ EXPORTS = [
     "mpdp_last_launch_count", "mpdp_strerror", "mpdp_last_error", "mpdp_abi_version",
     "mpdp_profile", "mpdp_profile_read", "mpdp_optimize_batch_device",
     "mpdp_optimize_device_noalloc", "mpdp_get_plans", "mpdp_get_cost_xd",
+    "mpdp_mlp_create", "mpdp_mlp_destroy", "mpdp_mlp_param_count", "mpdp_mlp_set_params",
+    "mpdp_mlp_get_params", "mpdp_mlp_forward", "mpdp_mlp_gradients", "mpdp_mlp_train_step",
     "mpdp_server_default_config", "mpdp_server_create", "mpdp_server_destroy", "mpdp_server_submit",
     "mpdp_server_poll", "mpdp_server_drain", "mpdp_server_pending", "mpdp_server_result",
 ]
@@ -161,6 +163,21 @@ def load(build_if_missing: bool = True):
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.mpdp_optimize_device_noalloc.restype = ctypes.c_int
     L.mpdp_sync.argtypes = [c_ctx]
+    c_mlp = ctypes.c_void_p
+    L.mpdp_mlp_create.argtypes = [P(c_mlp), ctypes.c_int, ctypes.c_int32, ctypes.c_void_p]
+    L.mpdp_mlp_destroy.argtypes = [c_mlp]
+    L.mpdp_mlp_destroy.restype = None
+    L.mpdp_mlp_param_count.argtypes = [c_mlp]
+    L.mpdp_mlp_param_count.restype = ctypes.c_int64
+    L.mpdp_mlp_set_params.argtypes = [c_mlp, P(ctypes.c_float), ctypes.c_int64]
+    L.mpdp_mlp_get_params.argtypes = [c_mlp, P(ctypes.c_float), ctypes.c_int64]
+    L.mpdp_mlp_forward.argtypes = [c_mlp, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    L.mpdp_mlp_gradients.argtypes = [c_mlp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                     P(ctypes.c_float), P(ctypes.c_double)]
+    L.mpdp_mlp_train_step.argtypes = [c_mlp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_float]
+    for f in ("mpdp_mlp_create", "mpdp_mlp_set_params", "mpdp_mlp_get_params", "mpdp_mlp_forward",
+              "mpdp_mlp_gradients", "mpdp_mlp_train_step"):
+        getattr(L, f).restype = ctypes.c_int
     c_srv = ctypes.c_void_p
     L.mpdp_server_default_config.argtypes = [P(ServerConfigC)]
     L.mpdp_server_create.argtypes = [P(c_srv), ctypes.c_int, P(ServerConfigC)]
@@ -493,6 +510,85 @@ class Optimizer:
         ln = (ctypes.c_uint64 * len(KERNEL_CLASSES))()
         self._check(self._lib.mpdp_profile_read(self._ctx, ms, ln), "mpdp_profile_read")
         return {k: dict(ms=ms[i], launches=int(ln[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+HIDDEN = 256
+
+
+def _dptr(x):
+    return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+
+
+class Mlp:
+    """The learned proposal's network (mpdp_mlp_*): forward, gradients and
+    Adam steps run in the library's BF16 kernels; x / targets are device
+    tensors (float32, rows x n_in / rows)."""
+
+    def __init__(self, n_in: int, device: int = 0, stream=None):
+        self._lib = load()
+        self.n_in = int(n_in)
+        self._m = ctypes.c_void_p()
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        rc = self._lib.mpdp_mlp_create(ctypes.byref(self._m), int(device), self.n_in, ctypes.c_void_p(int(st)))
+        if rc != MPDP_OK:
+            raise MPDPError(rc, "mpdp_mlp_create", strerror(rc))
+        self.param_count = int(self._lib.mpdp_mlp_param_count(self._m))
+
+    @property
+    def handle(self):
+        return self._m
+
+    def close(self):
+        if getattr(self, "_m", None) and self._m.value:
+            self._lib.mpdp_mlp_destroy(self._m)
+            self._m = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != MPDP_OK:
+            raise MPDPError(rc, what, strerror(rc))
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self._lib.mpdp_mlp_set_params(self._m, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                  p.size), "mpdp_mlp_set_params")
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.param_count, dtype=np.float32)
+        self._check(self._lib.mpdp_mlp_get_params(self._m, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                  p.size), "mpdp_mlp_get_params")
+        return p
+
+    def init_params(self, seed: int = 0) -> np.ndarray:
+        """He-normal weights, zero biases (host draw, then copied in)."""
+        rng = np.random.default_rng(seed)
+        parts = [rng.normal(0, np.sqrt(2.0 / self.n_in), (self.n_in, HIDDEN)), np.zeros(HIDDEN),
+                 rng.normal(0, np.sqrt(2.0 / HIDDEN), (HIDDEN, HIDDEN)), np.zeros(HIDDEN),
+                 rng.normal(0, np.sqrt(2.0 / HIDDEN), (HIDDEN, HIDDEN)), np.zeros(HIDDEN),
+                 rng.normal(0, np.sqrt(1.0 / HIDDEN), HIDDEN), np.zeros(1)]
+        p = np.concatenate([np.ravel(x) for x in parts]).astype(np.float32)
+        self.set_params(p)
+        return p
+
+    def forward(self, d_x, rows: int, d_y):
+        self._check(self._lib.mpdp_mlp_forward(self._m, _dptr(d_x), int(rows), _dptr(d_y)), "mpdp_mlp_forward")
+
+    def gradients(self, d_x, d_t, rows: int):
+        g = np.zeros(self.param_count, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        self._check(self._lib.mpdp_mlp_gradients(self._m, _dptr(d_x), _dptr(d_t), int(rows),
+                                                 g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                 ctypes.byref(loss)), "mpdp_mlp_gradients")
+        return g, loss.value
+
+    def train_step(self, d_x, d_t, rows: int, lr: float):
+        self._check(self._lib.mpdp_mlp_train_step(self._m, _dptr(d_x), _dptr(d_t), int(rows), float(lr)),
+                    "mpdp_mlp_train_step")
 
 
 class Server:
