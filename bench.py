@@ -346,6 +346,7 @@ def run_ours(args):
             line[name] = shape_line(name, opt, torch, mpdp, W, peaks)
     if rank == 0 and world == 1 and not args.no_star:
         line["large"] = heuristic_line(opt, mpdp, W)
+        line["learned"] = learned_line(opt, mpdp, W)
         opt.close()
         line["serving"] = serving_line(mpdp, W)
     opt.close()
@@ -454,6 +455,43 @@ def shape_line(name, opt, torch, mpdp, W, peaks, reps=5):
             "roofline": roofline(dom, kt[dom], stats, 3, peaks),
             "kernel_share": {k: round(v["ms"] / max(sum(x["ms"] for x in kt.values()), 1e-12), 4)
                              for k, v in kt.items() if v["launches"]}}
+
+
+LEARN_QUERIES = 8000
+
+
+def learned_line(opt, mpdp, W):
+    """Learned proposal: a BF16 MLP trained on the GPU by the library's own
+    kernels on the exact plans of LEARN_QUERIES primary-key/foreign-key
+    snowflakes of 10-25 relations, then MODE_UNIONDP_LEARNED against plain
+    UnionDP and IDP2 (k = 25, t = 15) on held-out queries of 100/300/1000
+    relations; plan-cost ratios as geometric means and 95th percentiles."""
+    import math
+    import numpy as np
+    from paper_2202_13511_gb300 import learned as L
+    t0 = time.perf_counter()
+    x, t = L.build_dataset(opt, L.training_queries(LEARN_QUERIES, seed=1))
+    t_data = time.perf_counter() - t0
+    log = []
+    mlp = L.train(x, t, epochs=10, seed=2, log=log)
+    t_train = log[-1][2]
+    out = {"training": {"queries": LEARN_QUERIES, "edges": int(x.shape[0]), "epochs": 10,
+                        "dataset_s": round(t_data, 3), "train_s": round(t_train, 3),
+                        "samples_per_s": 10 * x.shape[0] / t_train, "loss_first": log[0][1],
+                        "loss_last": log[-1][1]},
+           "modes": "uniondp_learned vs uniondp and idp2, k = 25, t = 15"}
+    for n in LARGE_SIZES:
+        qs = [W.snowflake_plus_pkfk(n, seed=5000 + i) for i in range(LARGE_QUERIES)]
+        rows = L.evaluate(opt, mlp, qs, 25, 15)
+        lp = [math.log2(L.cost_ratio(l, p)) for p, l, _ in rows]
+        li = [math.log2(L.cost_ratio(l, i)) for p, l, i in rows]
+        out[f"pkfk_n{n}"] = {"learned_over_plain_geomean": 2.0 ** float(np.mean(lp)),
+                             "learned_over_plain_p95": 2.0 ** float(np.percentile(lp, 95)),
+                             "learned_wins": int(sum(v < 0 for v in lp)), "learned_losses": int(sum(v > 0 for v in lp)),
+                             "learned_over_idp2_geomean": 2.0 ** float(np.mean(li))}
+    opt.set_model(None)
+    mlp.close()
+    return out
 
 
 SERVE_QUERIES = 2000

@@ -192,9 +192,16 @@ size_t mpdp_workspace_bytes(int32_t n_rels, const mpdp_config *cfg);
  * (Algorithm 5 with partitions of at most t and a final DP of at most k),
  * n <= MPDP_MAX_HEURISTIC_RELS.  Every sub-problem is solved exactly on the
  * device in extended range; these modes run to completion before the call
- * returns.  Plan nodes of n > 64 relations carry set = 0.  The _LEARNED
- * modes return MPDP_ERR_NOT_IMPLEMENTED, and so does mpdp_optimize_batch
- * for any mode but exact. */
+ * returns.  Plan nodes of n > 64 relations carry set = 0.
+ * MPDP_MODE_UNIONDP_LEARNED: UnionDP whose partitions follow the learned
+ * proposal set with mpdp_set_model (edges united in the order of the
+ * model's scores), with plain UnionDP as the fallback: both plans are
+ * costed exactly and the cheaper is returned (the plain one on ties, and
+ * always when no model is set).  In the heuristic modes mpdp_stats carries
+ * the number of exact sub-problems in heavy_sets and, for UNIONDP_LEARNED,
+ * filter_steps = 1 when the learned plan was kept.
+ * MPDP_MODE_IDP2_LEARNED returns MPDP_ERR_NOT_IMPLEMENTED, and so does
+ * mpdp_optimize_batch for any mode but exact. */
 int mpdp_optimize(mpdp_ctx *ctx, const mpdp_query *q, int64_t *handle);
 
 /* Enqueue nq queries as device batches (all queries of a batch share every
@@ -409,6 +416,16 @@ int mpdp_mlp_gradients(mpdp_mlp *m, const float *d_x, const float *d_t, int32_t 
                        float *host_grads, double *loss);
 /* One Adam step (beta 0.9 / 0.999) on L; enqueued. */
 int mpdp_mlp_train_step(mpdp_mlp *m, const float *d_x, const float *d_t, int32_t rows, float lr);
+
+/* Use `model` (MPDP_EDGE_FEATURES inputs; borrowed, NULL to detach) for
+ * MPDP_MODE_UNIONDP_LEARNED on this context. */
+#define MPDP_EDGE_FEATURES 12
+int mpdp_set_model(mpdp_ctx *ctx, mpdp_mlp *model);
+/* The model's input rows for the edges of a query graph, in edge order
+ * (MPDP_EDGE_FEATURES floats each; cap_rows >= n_edges): the features the
+ * learned UnionDP computes at every round, here for the base graph, so that
+ * training data uses the same code. */
+int mpdp_edge_features(const mpdp_query *q, float *out, int32_t cap_rows);
 
 #ifdef __cplusplus
 }

@@ -112,6 +112,7 @@ struct PlanQuery {
 struct mpdp_ctx {
     mpdp::XdExecutor* xd = nullptr;                      // heuristic sub-problems (created on first use)
     std::map<int64_t, mpdp::HeuristicResult> heur;      // finished heuristic-mode plans by handle
+    mpdp_mlp* model = nullptr;                          // learned proposal (borrowed)
     int device = 0;
     cudaStream_t stream = nullptr;          // work stream (borrowed; nullptr = default stream)
     cudaStream_t capture_stream = nullptr;  // private, only used to capture graphs
@@ -759,13 +760,14 @@ static int validate_heuristic(const mpdp_query* q)
 {
     const int n = q->n_rels, m = q->n_edges;
     if (q->cost_model != MPDP_COST_COUT) return MPDP_ERR_INVALID_ARG;
-    if (q->mode != MPDP_MODE_IDP2 && q->mode != MPDP_MODE_UNIONDP) return MPDP_ERR_INVALID_ARG;
+    if (q->mode != MPDP_MODE_IDP2 && q->mode != MPDP_MODE_UNIONDP && q->mode != MPDP_MODE_UNIONDP_LEARNED)
+        return MPDP_ERR_INVALID_ARG;
     if (n < 1 || m < 0 || (long long)m > (long long)n * (n - 1) / 2 || !q->card || (m > 0 && !q->edges))
         return MPDP_ERR_INVALID_ARG;
     if (n > MPDP_MAX_HEURISTIC_RELS) return MPDP_ERR_TOO_LARGE;
     if (q->k > 25) return MPDP_ERR_TOO_LARGE;
     if (q->mode == MPDP_MODE_IDP2 && q->t != 0) return MPDP_ERR_INVALID_ARG;
-    if (q->mode == MPDP_MODE_UNIONDP && (q->k < 2 || (q->t != 0 && (q->t < 2 || q->t > q->k))))
+    if (q->mode != MPDP_MODE_IDP2 && (q->k < 2 || (q->t != 0 && (q->t < 2 || q->t > q->k))))
         return MPDP_ERR_INVALID_ARG;
     for (int i = 0; i < n; i++)
         if (!finite_pos(q->card[i])) return MPDP_ERR_INVALID_ARG;
@@ -800,7 +802,7 @@ int mpdp_optimize(mpdp_ctx* ctx, const mpdp_query* q, int64_t* handle)
     if (!ctx || !q || !handle) return MPDP_ERR_INVALID_ARG;
     *handle = -1;
     if (q->mode == MPDP_MODE_EXACT) return mpdp_optimize_batch(ctx, q, 1, handle);
-    if (q->mode == MPDP_MODE_IDP2_LEARNED || q->mode == MPDP_MODE_UNIONDP_LEARNED) return MPDP_ERR_NOT_IMPLEMENTED;
+    if (q->mode == MPDP_MODE_IDP2_LEARNED) return MPDP_ERR_NOT_IMPLEMENTED;
     const int vrc = validate_heuristic(q);
     if (vrc != MPDP_OK) return vrc;
     CK(ctx, cudaSetDevice(ctx->device));
@@ -811,6 +813,7 @@ int mpdp_optimize(mpdp_ctx* ctx, const mpdp_query* q, int64_t* handle)
     hq.k = q->k;
     hq.t = q->t;
     hq.card = q->card;
+    hq.model = ctx->model;
     for (int e = 0; e < q->n_edges; e++) {
         hq.eu.push_back(q->edges[e].u);
         hq.ev.push_back(q->edges[e].v);
@@ -825,6 +828,41 @@ int mpdp_optimize(mpdp_ctx* ctx, const mpdp_query* q, int64_t* handle)
     const int64_t h = ctx->next_handle++;
     ctx->heur[h] = std::move(res);
     *handle = h;
+    return MPDP_OK;
+}
+
+int mpdp_set_model(mpdp_ctx* ctx, mpdp_mlp* model)
+{
+    if (!ctx) return MPDP_ERR_INVALID_ARG;
+    if (model && mpdp_mlp_param_count(model) != (int64_t)mpdp::kEdgeFeatures * 256 + 256 * 3 + 256 * 256 * 2 + 256 + 1)
+        return MPDP_ERR_INVALID_ARG;
+    ctx->model = model;
+    return MPDP_OK;
+}
+
+int mpdp_edge_features(const mpdp_query* q, float* out, int32_t cap_rows)
+{
+    if (!q || !out) return MPDP_ERR_INVALID_ARG;
+    const int n = q->n_rels, m = q->n_edges;
+    if (n < 1 || m < 0 || !q->card || (m > 0 && !q->edges)) return MPDP_ERR_INVALID_ARG;
+    if (cap_rows < m) return MPDP_ERR_BUFFER_TOO_SMALL;
+    std::vector<double> lcard(n), lsel(m);
+    std::vector<int> eu(m), ev(m);
+    for (int i = 0; i < n; i++) {
+        if (!finite_pos(q->card[i])) return MPDP_ERR_INVALID_ARG;
+        lcard[i] = mpdp::xd_log2(mpdp::xd_make(q->card[i], 0));
+    }
+    for (int e = 0; e < m; e++) {
+        const int u = q->edges[e].u, v = q->edges[e].v;
+        if (u < 0 || v < 0 || u >= n || v >= n || u == v || !(q->edges[e].sel > 0.0) || !(q->edges[e].sel <= 1.0))
+            return MPDP_ERR_INVALID_ARG;
+        eu[e] = std::min(u, v);
+        ev[e] = std::max(u, v);
+        lsel[e] = mpdp::xd_log2(mpdp::xd_make(q->edges[e].sel, 0));
+    }
+    std::vector<float> f;
+    mpdp::edge_features(n, lcard, eu, ev, lsel, f);
+    if (!f.empty()) memcpy(out, f.data(), f.size() * sizeof(float));
     return MPDP_OK;
 }
 
@@ -862,6 +900,7 @@ int mpdp_get_plan(mpdp_ctx* ctx, int64_t handle, mpdp_plan_node* nodes, int32_t 
             memset(st, 0, sizeof(*st));
             st->enumeration = MPDP_ENUM_BLOCKS;
             st->heavy_sets = (uint64_t)r.subproblems;  // exact sub-problems solved
+            st->filter_steps = r.learned_won ? 1 : 0;  // UnionDP-learned: the learned plan was kept
         }
         return MPDP_OK;
     }

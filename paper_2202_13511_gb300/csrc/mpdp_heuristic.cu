@@ -183,6 +183,10 @@ public:
     int goo(int& result);
     int idp2(int k, int& result);
     int uniondp(int k, int t, int& result);
+    int scores(int m, const std::vector<int>& cur, const std::vector<std::pair<int, int>>& ij,
+               const std::vector<XD>& sel, std::vector<float>& out);
+
+    mpdp_mlp* model_ = nullptr;
 
     int n_;
     std::vector<PNode> nodes_;
@@ -418,6 +422,31 @@ int Heuristic::uniondp(int k, int t, int& result)
             return x;
         };
         std::vector<char> dropped(es.size(), 0);
+        if (model_) {
+            // learned proposal: edges by predicted score (the share of the
+            // query under the edge's join in an optimal plan), lowest first,
+            // united while the partition stays within t
+            std::vector<std::pair<int, int>> ij;
+            std::vector<XD> sels;
+            for (auto& kv : between) {
+                ij.push_back(kv.first);
+                sels.push_back(sel_product(kv.second));
+            }
+            std::vector<float> sc;
+            const int rc = scores(m, cur, ij, sels, sc);
+            if (rc != MPDP_OK) return rc;
+            std::vector<int> order(es.size());
+            for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sc[a] < sc[b]; });
+            for (int idx : order) {
+                const int a = find(es[idx].i), b = find(es[idx].j);
+                if (a != b && size[a] + size[b] <= t) {
+                    parent[b] = a;
+                    size[a] += size[b];
+                }
+            }
+            std::fill(dropped.begin(), dropped.end(), 1);
+        }
         for (;;) {
             int best = -1, ba = 0, bb = 0, bs = 0;
             for (size_t idx = 0; idx < es.size(); idx++) {
@@ -475,13 +504,149 @@ double xd_to_double(XD x)
 
 }  // namespace
 
+double xd_log2(XD x) { return x.m == 0.0 ? -1e300 : (double)x.e + std::log2(x.m); }
+
+void edge_features(int n, const std::vector<double>& lcard, const std::vector<int>& eu, const std::vector<int>& ev,
+                   const std::vector<double>& lsel, std::vector<float>& out)
+{
+    const int m = (int)eu.size();
+    out.assign((size_t)m * kEdgeFeatures, 0.f);
+    if (m == 0) return;
+    std::vector<int> deg(n, 0);
+    std::vector<std::vector<std::pair<int, int>>> adj(n);  // (neighbour, edge)
+    for (int e = 0; e < m; e++) {
+        deg[eu[e]]++;
+        deg[ev[e]]++;
+        adj[eu[e]].push_back({ev[e], e});
+        adj[ev[e]].push_back({eu[e], e});
+    }
+    std::vector<double> lj(m);
+    for (int e = 0; e < m; e++) lj[e] = lcard[eu[e]] + lcard[ev[e]] + lsel[e];
+    std::vector<double> sorted_lj = lj;
+    std::sort(sorted_lj.begin(), sorted_lj.end());
+    const double median = sorted_lj[m / 2];
+    // bridges (iterative lowlink search)
+    std::vector<char> bridge(m, 0);
+    {
+        std::vector<int> disc(n, -1), low(n, 0), parent_edge(n, -1), it(n, 0);
+        int timer = 0;
+        for (int root = 0; root < n; root++) {
+            if (disc[root] >= 0) continue;
+            std::vector<int> st = {root};
+            disc[root] = low[root] = timer++;
+            while (!st.empty()) {
+                const int v = st.back();
+                if (it[v] < (int)adj[v].size()) {
+                    const auto [w, e] = adj[v][it[v]++];
+                    if (e == parent_edge[v]) continue;
+                    if (disc[w] < 0) {
+                        disc[w] = low[w] = timer++;
+                        parent_edge[w] = e;
+                        st.push_back(w);
+                    } else {
+                        low[v] = std::min(low[v], disc[w]);
+                    }
+                } else {
+                    st.pop_back();
+                    if (!st.empty()) {
+                        const int u = st.back();
+                        low[u] = std::min(low[u], low[v]);
+                        if (low[v] > disc[u]) bridge[parent_edge[v]] = 1;
+                    }
+                }
+            }
+        }
+    }
+    const double ln = std::log2((double)std::max(n, 1));
+    for (int e = 0; e < m; e++) {
+        const int u = eu[e], v = ev[e];
+        double inc_lo = lj[e], inc_hi = lj[e];
+        for (int x : {u, v})
+            for (const auto& nb : adj[x]) {
+                inc_lo = std::min(inc_lo, lj[nb.second]);
+                inc_hi = std::max(inc_hi, lj[nb.second]);
+            }
+        const int rank = (int)(std::lower_bound(sorted_lj.begin(), sorted_lj.end(), lj[e]) - sorted_lj.begin());
+        float* f = &out[(size_t)e * kEdgeFeatures];
+        f[0] = (float)(std::min(lcard[u], lcard[v]) / 32.0);
+        f[1] = (float)(std::max(lcard[u], lcard[v]) / 32.0);
+        f[2] = (float)(lsel[e] / 32.0);
+        f[3] = (float)(lj[e] / 32.0);
+        f[4] = (float)((lj[e] - median) / 32.0);
+        f[5] = (float)(m > 1 ? (double)rank / (double)(m - 1) : 0.0);
+        f[6] = (float)(std::log2(1.0 + std::min(deg[u], deg[v])) / 4.0);
+        f[7] = (float)(std::log2(1.0 + std::max(deg[u], deg[v])) / 4.0);
+        f[8] = (float)((lj[e] - inc_lo) / 32.0);
+        f[9] = (float)((inc_hi - lj[e]) / 32.0);
+        f[10] = bridge[e] ? 1.f : 0.f;
+        f[11] = (float)(ln / 12.0);
+    }
+}
+
+
+namespace {
+
+int Heuristic::scores(int m, const std::vector<int>& cur, const std::vector<std::pair<int, int>>& ij,
+                      const std::vector<XD>& sel, std::vector<float>& out)
+{
+    std::vector<double> lcard(m), lsel(sel.size());
+    std::vector<int> eu(ij.size()), ev(ij.size());
+    for (int i = 0; i < m; i++) lcard[i] = xd_log2(nodes_[cur[i]].card);
+    for (size_t e = 0; e < ij.size(); e++) {
+        eu[e] = ij[e].first;
+        ev[e] = ij[e].second;
+        lsel[e] = xd_log2(sel[e]);
+    }
+    std::vector<float> feat;
+    edge_features(m, lcard, eu, ev, lsel, feat);
+    const int rows = (int)ij.size();
+    out.assign(rows, 0.f);
+    if (rows == 0) return MPDP_OK;
+    float *dx = nullptr, *dy = nullptr;
+    if (cudaMalloc(&dx, feat.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&dy, (size_t)rows * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dx);
+        return MPDP_ERR_OOM;
+    }
+    int rc = MPDP_OK;
+    if (cudaMemcpy(dx, feat.data(), feat.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = MPDP_ERR_CUDA;
+    if (rc == MPDP_OK) rc = mpdp_mlp_forward(model_, dx, rows, dy);
+    if (rc == MPDP_OK && cudaDeviceSynchronize() != cudaSuccess) rc = MPDP_ERR_CUDA;
+    if (rc == MPDP_OK && cudaMemcpy(out.data(), dy, (size_t)rows * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = MPDP_ERR_CUDA;
+    cudaFree(dx);
+    cudaFree(dy);
+    cudaGetLastError();
+    return rc;
+}
+
+}  // namespace
+
 int run_heuristic(const HeuristicQuery& q, XdExecutor& ex, cudaStream_t st, int num_sms, HeuristicResult& res)
 {
     Heuristic h(q, ex, st, num_sms);
     int root = -1, rc;
+    res.learned_won = false;
     if (q.mode == MPDP_MODE_IDP2) rc = h.idp2(q.k, root);
     else if (q.mode == MPDP_MODE_UNIONDP) rc = h.uniondp(q.k, q.t > 0 ? q.t : q.k, root);
-    else return MPDP_ERR_NOT_IMPLEMENTED;
+    else if (q.mode == MPDP_MODE_UNIONDP_LEARNED) {
+        // the learned proposal's plan, with plain UnionDP as the fallback:
+        // both are costed exactly and the cheaper one (plain on ties) wins
+        const int t = q.t > 0 ? q.t : q.k;
+        rc = h.uniondp(q.k, t, root);
+        if (rc == MPDP_OK && q.model) {
+            int learned = -1;
+            h.model_ = q.model;
+            rc = h.uniondp(q.k, t, learned);
+            h.model_ = nullptr;
+            if (rc == MPDP_OK && xd_less(h.nodes_[learned].cost, h.nodes_[root].cost)) {
+                root = learned;
+                res.learned_won = true;
+            }
+        }
+    } else return MPDP_ERR_NOT_IMPLEMENTED;
     if (rc != MPDP_OK) return rc;
     // breadth-first node list from the root
     res.nodes.clear();

@@ -104,6 +104,7 @@ EXPORTS = [
     "mpdp_optimize_device_noalloc", "mpdp_get_plans", "mpdp_get_cost_xd",
     "mpdp_mlp_create", "mpdp_mlp_destroy", "mpdp_mlp_param_count", "mpdp_mlp_set_params",
     "mpdp_mlp_get_params", "mpdp_mlp_forward", "mpdp_mlp_gradients", "mpdp_mlp_train_step",
+    "mpdp_set_model", "mpdp_edge_features",
     "mpdp_server_default_config", "mpdp_server_create", "mpdp_server_destroy", "mpdp_server_submit",
     "mpdp_server_poll", "mpdp_server_drain", "mpdp_server_pending", "mpdp_server_result",
 ]
@@ -178,6 +179,10 @@ def load(build_if_missing: bool = True):
     for f in ("mpdp_mlp_create", "mpdp_mlp_set_params", "mpdp_mlp_get_params", "mpdp_mlp_forward",
               "mpdp_mlp_gradients", "mpdp_mlp_train_step"):
         getattr(L, f).restype = ctypes.c_int
+    L.mpdp_set_model.argtypes = [c_ctx, c_mlp]
+    L.mpdp_set_model.restype = ctypes.c_int
+    L.mpdp_edge_features.argtypes = [P(QueryC), P(ctypes.c_float), ctypes.c_int32]
+    L.mpdp_edge_features.restype = ctypes.c_int
     c_srv = ctypes.c_void_p
     L.mpdp_server_default_config.argtypes = [P(ServerConfigC)]
     L.mpdp_server_create.argtypes = [P(c_srv), ctypes.c_int, P(ServerConfigC)]
@@ -362,6 +367,12 @@ class Optimizer:
         c = ConfigC(**cur)
         self._check(self._lib.mpdp_set_config(self._ctx, ctypes.byref(c)), "mpdp_set_config")
 
+    def set_model(self, mlp: Optional["Mlp"]):
+        """Attach the learned proposal for MODE_UNIONDP_LEARNED (None: detach)."""
+        self._model = mlp
+        self._check(self._lib.mpdp_set_model(self._ctx, mlp.handle if mlp is not None else None),
+                    "mpdp_set_model")
+
     def launch_count(self) -> int:
         return int(self._lib.mpdp_last_launch_count(self._ctx))
 
@@ -513,6 +524,18 @@ class Optimizer:
 
 
 HIDDEN = 256
+EDGE_FEATURES = 12
+
+
+def edge_features(q) -> np.ndarray:
+    """mpdp_edge_features: the learned proposal's input rows for q's edges."""
+    p = _Packed(q)
+    out = np.zeros((max(len(q.edges), 1), EDGE_FEATURES), dtype=np.float32)
+    rc = load().mpdp_edge_features(ctypes.byref(p.c), out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                   len(q.edges))
+    if rc != MPDP_OK:
+        raise MPDPError(rc, "mpdp_edge_features", strerror(rc))
+    return out[:len(q.edges)]
 
 
 def _dptr(x):
