@@ -345,6 +345,7 @@ def run_ours(args):
         for name in SHAPES:
             line[name] = shape_line(name, opt, torch, mpdp, W, peaks)
     if rank == 0 and world == 1 and not args.no_star:
+        line["ablations"] = ablation_line(opt, torch, mpdp, W)
         line["large"] = heuristic_line(opt, mpdp, W)
         line["learned"] = learned_line(opt, mpdp, W)
         opt.close()
@@ -455,6 +456,59 @@ def shape_line(name, opt, torch, mpdp, W, peaks, reps=5):
             "roofline": roofline(dom, kt[dom], stats, 3, peaks),
             "kernel_share": {k: round(v["ms"] / max(sum(x["ms"] for x in kt.values()), 1e-12), 4)
                              for k, v in kt.items() if v["launches"]}}
+
+
+def ablation_line(opt, torch, mpdp, W):
+    """The paper's relative claims on the same kernels: MPDP's block
+    enumeration against DPSUB's vertex-based one (Sec. 6.2: far fewer pairs
+    evaluated), and Collaborative Context Collection on / off (Sec. 6.4).
+    Device time of one batch (CUDA events, L2 flushed, mean of 3)."""
+    import numpy as np
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(qs, **cfg):
+        base = opt.get_config()
+        opt.set_config(**cfg)
+        stats = [p.stats for p in opt.optimize_batch(qs)]
+        d_card = torch.tensor([c for q in qs for c in q.card], dtype=torch.float64, device="cuda")
+        d_edges = torch.from_numpy(mpdp.pack_edges([e for q in qs for e in q.edges]).view(np.uint8).copy()).cuda()
+        nq = len(qs)
+        d_nodes = torch.zeros((nq, mpdp.PLAN_STRIDE * 40), dtype=torch.uint8, device="cuda")
+        d_cost = torch.zeros(nq, dtype=torch.float64, device="cuda")
+        d_status = torch.zeros(nq, dtype=torch.int32, device="cuda")
+        ns, ms = [q.n for q in qs], [len(q.edges) for q in qs]
+        run = lambda: opt.optimize_batch_device(ns, ms, d_card, d_edges, d_nodes, d_cost, d_status)
+        run()
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run()
+            b.record(stream)
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b)
+        assert int((d_status != 0).sum().item()) == 0
+        opt.set_config(**base)
+        return total / 3, sum(int(st["pairs_evaluated"]) for st in stats), d_cost.cpu().numpy()
+
+    out = {}
+    for name, qs in (("star20", [W.star(20, seed=0)]), ("snowflake20_x64", [W.snowflake(20, seed=i) for i in range(64)]),
+                     ("cyclic16_x64", [W.cyclic(16, seed=i) for i in range(64)])):
+        t_m, e_m, c_m = timed(qs)
+        t_d, e_d, c_d = timed(qs, enumeration=mpdp.ENUM_DPSUB)
+        assert np.array_equal(c_m, c_d)
+        out[f"mpdp_vs_dpsub_{name}"] = {"mpdp_ms": t_m, "dpsub_ms": t_d, "speedup": t_d / t_m,
+                                         "pairs_mpdp": e_m, "pairs_dpsub": e_d, "pairs_ratio": e_d / max(e_m, 1)}
+    for name, qs in (("cyclic20_x64", [W.cyclic(20, seed=i) for i in range(64)]),
+                     ("clique14_x64", [W.clique(14, seed=i) for i in range(64)])):
+        t_on, _, c_on = timed(qs, use_ccc=1, enumeration=mpdp.ENUM_BLOCKS)
+        t_off, _, c_off = timed(qs, use_ccc=0, enumeration=mpdp.ENUM_BLOCKS)
+        assert np.array_equal(c_on, c_off)
+        out[f"ccc_{name}"] = {"ccc_on_ms": t_on, "ccc_off_ms": t_off, "gain": t_off / t_on}
+    return out
 
 
 LEARN_QUERIES = 8000

@@ -80,7 +80,11 @@ enum {
 /* CCP enumeration: AUTO picks TREE when the join graph is a tree
  * (connected with n-1 edges), BLOCKS otherwise.  BLOCKS is correct on trees
  * too (every block is one edge). */
-enum { MPDP_ENUM_AUTO = 0, MPDP_ENUM_TREE = 1, MPDP_ENUM_BLOCKS = 2 };
+enum { MPDP_ENUM_AUTO = 0, MPDP_ENUM_TREE = 1, MPDP_ENUM_BLOCKS = 2, MPDP_ENUM_DPSUB = 3 };
+/* MPDP_ENUM_DPSUB (an ablation baseline, not MPDP): the vertex-based
+ * enumeration of DPSUB (Algorithm 1) on the same kernels: every bipartition
+ * of a connected S with min(S) on the left is tested for a CCP, 2^(|S|-1) - 1
+ * per set; same results, more pairs evaluated (reported as such). */
 
 /* Memo layout.  DENSE: arrays indexed directly by the relation bitmap
  * (20 bytes x 2^n: {cost, card} and left).  HASH: one open-addressing table

@@ -208,7 +208,8 @@ static int validate_query(const mpdp_query* q, int max_n)
 // edges); BLOCKS is correct for every graph.
 static int resolve_enumeration(const mpdp_config& cfg, int n, int m)
 {
-    if (cfg.enumeration == MPDP_ENUM_BLOCKS || m != n - 1) return MPDP_ENUM_BLOCKS;
+    if (cfg.enumeration == MPDP_ENUM_BLOCKS || cfg.enumeration == MPDP_ENUM_DPSUB || m != n - 1)
+        return MPDP_ENUM_BLOCKS;
     return MPDP_ENUM_TREE;
 }
 
@@ -346,6 +347,7 @@ static BatchArgs batch_args(const mpdp_ctx* ctx, int nq, int max_n)
     a.run = ctx->cfg.run_length;
     a.heavy_threshold = ctx->cfg.heavy_threshold;
     a.use_ccc = ctx->cfg.use_ccc;
+    a.dpsub = ctx->cfg.enumeration == MPDP_ENUM_DPSUB ? 1 : 0;
     a.filter_mode = ctx->cfg.filter;
     return a;
 }
@@ -507,7 +509,7 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
     bp.num_sms = ctx->num_sms;
     bp.blocks_per_sm = ctx->cfg.grid_blocks_per_sm;
     std::vector<int> key = {nq, kind, ctx->cfg.heavy_threshold, ctx->cfg.use_ccc, ctx->cfg.run_length,
-                            ctx->cfg.filter, ctx->cfg.grid_blocks_per_sm};
+                            ctx->cfg.filter, ctx->cfg.grid_blocks_per_sm, ctx->cfg.enumeration};
     unsigned long long lbase = 0, mbase = 0, hbase = 0;
     uint32_t fblocks = 0;
     int max_n = 0;
@@ -647,7 +649,9 @@ size_t mpdp_workspace_bytes(int32_t n_rels, const mpdp_config* cfg)
 {
     if (n_rels < 1 || n_rels > MPDP_MAX_EXACT_RELS) return 0;
     const int kind = cfg ? cfg->memo_kind : MPDP_MEMO_DENSE;
-    const int en = cfg && cfg->enumeration == MPDP_ENUM_BLOCKS ? MPDP_ENUM_BLOCKS : MPDP_ENUM_TREE;
+    const int en = cfg && (cfg->enumeration == MPDP_ENUM_BLOCKS || cfg->enumeration == MPDP_ENUM_DPSUB)
+                       ? MPDP_ENUM_BLOCKS
+                       : MPDP_ENUM_TREE;
     const QuerySize z = query_size(n_rels, en, kind);
     return var_bytes_of(z.lists, z.heavy, z.memo, z.hash) + fixed_bytes();
 }
@@ -708,7 +712,7 @@ int mpdp_set_config(mpdp_ctx* ctx, const mpdp_config* cfg)
 {
     if (!ctx || !cfg) return MPDP_ERR_INVALID_ARG;
     if (cfg->memo_kind != MPDP_MEMO_DENSE && cfg->memo_kind != MPDP_MEMO_HASH) return MPDP_ERR_INVALID_ARG;
-    if (cfg->enumeration < MPDP_ENUM_AUTO || cfg->enumeration > MPDP_ENUM_BLOCKS) return MPDP_ERR_INVALID_ARG;
+    if (cfg->enumeration < MPDP_ENUM_AUTO || cfg->enumeration > MPDP_ENUM_DPSUB) return MPDP_ERR_INVALID_ARG;
     if (cfg->heavy_threshold < 0 || cfg->run_length < 1 || cfg->run_length > 32) return MPDP_ERR_INVALID_ARG;
     if (cfg->filter != MPDP_FILTER_BITMAPS && cfg->filter != MPDP_FILTER_UNRANK) return MPDP_ERR_INVALID_ARG;
     if (cfg->grid_blocks_per_sm < 1 || cfg->grid_blocks_per_sm > 32) return MPDP_ERR_INVALID_ARG;

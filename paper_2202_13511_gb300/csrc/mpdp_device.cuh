@@ -172,6 +172,7 @@ struct BatchArgs {
     int run;             // ranks per lane in the filter (<= 32)
     int heavy_threshold;
     int use_ccc;
+    int dpsub;           // block mode enumerates each set as one block (DPSUB ablation)
     int filter_mode;     // MPDP_FILTER_BITMAPS or MPDP_FILTER_UNRANK (the filter_block_prefix
                          // counts the blocks of the chosen filter)
 };

@@ -787,6 +787,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
             const int nb = find_blocks(s, sq.adj, blk);
             uint32_t pairs = 0u;
             for (int j = 0; j < nb; j++) pairs += block_pairs(blk[j]);
+            if (a.dpsub) pairs = block_pairs(s);  // the whole set as one block
             if (pairs > (uint32_t)a.heavy_threshold) {
                 to_heavy = true;
                 const uint32_t nch = (pairs - 1u) / kChunkPairs + 1u;
@@ -796,8 +797,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
                 unsigned long long bx = kNoX;
                 uint32_t bl = kFull;
                 evaluated += pairs;
-                for (int j = 0; j < nb; j++) {
-                    const uint32_t b = blk[j];
+                const int enb = a.dpsub ? 1 : nb;
+                for (int j = 0; j < enb; j++) {
+                    const uint32_t b = a.dpsub ? s : blk[j];
                     const uint32_t mn = b & (0u - b), rest = b ^ mn;
                     for (uint32_t sub = 0u; sub != rest; sub = (sub - rest) & rest) {
                         const uint32_t lb = mn | sub, rb = b ^ lb;
@@ -880,6 +882,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
     __shared__ uint32_t s_blk[kWarps][kMaxRels];
     __shared__ uint32_t s_bpref[kWarps][kMaxRels + 1];
     __shared__ int s_nb[kWarps];
+    __shared__ int s_pv[kWarps];
     __shared__ uint32_t s_stash_l[kWarps][64];
     __shared__ uint32_t s_stash_r[kWarps][64];
     memo.setup(s_memo);
@@ -920,7 +923,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
         const uint32_t s = hm[mi].set, nch = hm[mi].nch, ebase = hm[mi].ebase;
         const uint32_t chunk = item < nmain ? 0u : item - nmain - ebase + 1u;
         if (lane == 0) {
-            const int nb = find_blocks(s, sq.adj, s_blk[warp]);
+            int nb = find_blocks(s, sq.adj, s_blk[warp]);
+            s_pv[warp] = block_peel_vertex(s, s_blk[warp], nb);
+            if (a.dpsub) {  // the whole set as one block
+                s_blk[warp][0] = s;
+                nb = 1;
+            }
             uint32_t acc = 0u;
             for (int j = 0; j < nb; j++) {
                 s_bpref[warp][j] = acc;
@@ -1024,7 +1032,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
             warp_min_x(bx, bl);
         }
         if (lane == 0) {
-            const double card_s = peel_card(s, block_peel_vertex(s, blk, nb), sq, memo, cnt);
+            const double card_s = peel_card(s, s_pv[warp], sq, memo, cnt);
             memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
         }
         __syncwarp();

@@ -30,7 +30,7 @@ ERRORS = {
 ERR = {v: k for k, v in ERRORS.items()}
 
 MODE_EXACT, MODE_IDP2, MODE_UNIONDP, MODE_IDP2_LEARNED, MODE_UNIONDP_LEARNED = range(5)
-ENUM_AUTO, ENUM_TREE, ENUM_BLOCKS = range(3)
+ENUM_AUTO, ENUM_TREE, ENUM_BLOCKS, ENUM_DPSUB = range(4)
 MEMO_DENSE, MEMO_HASH = range(2)
 FILTER_BITMAPS, FILTER_UNRANK = range(2)
 MAX_LEVELS = 33

@@ -179,6 +179,29 @@ def test_graphs_on_off(opt, graphs):
         del p1
 
 
+@pytest.mark.parametrize("kind,n,seed", [("snowflake", 14, 1), ("cyclic", 13, 2), ("clique", 10, 3),
+                                         ("star", 12, 4), ("chain", 15, 5)])
+@pytest.mark.parametrize("memo", [mpdp.MEMO_DENSE, mpdp.MEMO_HASH])
+def test_dpsub_enumeration(opt, kind, n, seed, memo):
+    """The DPSUB ablation on the block kernels: same plans, costs and CCP
+    pairs; evaluated = 2^(|S|-1) - 1 per connected set S."""
+    set_cfg(opt, enumeration=mpdp.ENUM_DPSUB, memo_kind=memo)
+    q = W.make(kind, n, seed)
+    ref = oracle.dpccp(q)
+    plan = opt.optimize(q)
+    assert np.float64(plan.cost).tobytes() == np.float64(ref.opt_cost).tobytes()
+    assert plan.signature() == oracle.plan_signature(oracle.plan_from_memo(q, ref))
+    st = plan.stats
+    assert np.array_equal(st["ccp_per_level"][2:], ref.ccp[2:n + 1])
+    want = np.zeros(n + 1, dtype=np.uint64)
+    for s in ref.connected_sets():
+        k = bin(s).count("1")
+        if k >= 2:
+            want[k] += (1 << (k - 1)) - 1
+    assert np.array_equal(st["evaluated_per_level"][2:], want[2:])
+    set_cfg(opt)
+
+
 @pytest.mark.parametrize("grid", [1, 3, 32])
 def test_grid_sizes(opt, grid):
     """Results do not depend on how many blocks the evaluate grids get."""
