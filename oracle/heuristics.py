@@ -252,6 +252,32 @@ def goo(g: Graph) -> Plan:
 
 
 # ---------------------------------------------------------------------------
+# Learned start for IDP2 (a project addition): edges in ascending score
+
+def learned_start(g: Graph, scores: Sequence[float]) -> Plan:
+    """The plan that takes the query's edges (g.edges order) in ascending
+    score, equal scores in edge order, and joins the plans of each edge's two
+    ends while they are still apart.  The scores are the model's outputs,
+    given as inputs here."""
+    assert len(scores) == len(g.edges)
+    order = sorted(range(len(g.edges)), key=lambda e: (scores[e], e))
+    comp = list(range(g.n))          # relation -> component id
+    plans = {r: g.leaf(r) for r in range(g.n)}
+    for e in order:
+        u, v, _ = g.edges[e]
+        a, b = comp[u], comp[v]
+        if a == b:
+            continue
+        j = g.join(plans.pop(a), plans.pop(b))
+        plans[a] = j
+        for r in range(g.n):
+            if comp[r] == b:
+                comp[r] = a
+    assert len(plans) == 1
+    return next(iter(plans.values()))
+
+
+# ---------------------------------------------------------------------------
 # IDP2
 
 def _joins_cost(t: Plan) -> XD:

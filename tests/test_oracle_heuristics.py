@@ -275,3 +275,58 @@ def test_uniondp_partitions_respect_threshold(monkeypatch):
     p = H.uniondp(g, 12, 5)
     assert p.leaves == 50
     assert seen[-1] <= 12 and all(s <= 5 for s in seen[:-1])
+
+
+def _scores_rebuilding(g, p):
+    """Scores for g's edges under which the learned start rebuilds the tree-
+    query plan p: each join's one cut edge scores its post-order rank (a join
+    comes after the joins below it), the other edges score higher."""
+    rank = {}
+
+    def walk(t):
+        if t.is_leaf:
+            return
+        walk(t.left)
+        walk(t.right)
+        cut = g._cut(t.left.rels, t.right.rels, t.left.leaves, t.right.leaves)
+        assert len(cut) == 1
+        rank[cut[0][:2]] = len(rank)
+
+    walk(p)
+    return [float(rank.get((u, v), len(g.edges) + i)) for i, (u, v, _) in enumerate(g.edges)]
+
+
+@pytest.mark.parametrize("kind,n,seed", [("snowflake", 30, 1), ("chain", 20, 2), ("star", 16, 3)])
+def test_learned_start_rebuilds_a_plan_from_its_join_order(kind, n, seed):
+    """On a tree query, joins taken in any children-first order of a plan's
+    joins rebuild that plan: GOO's, and the exact optimum."""
+    q = W.make(kind, n, seed)
+    g = H.Graph(q)
+    for p in (H.goo(g), H.exact_over(g, [g.leaf(r) for r in range(n)]) if n <= 16 else H.idp2(g, 8)):
+        got = H.learned_start(g, _scores_rebuilding(g, p))
+        assert H.canonical(got) == H.canonical(p)
+        assert got.cost == p.cost
+
+
+def test_learned_start_orders_by_score_then_edge():
+    """Chain 0-1-2-3: equal scores keep the edge order, so (0,1) joins
+    before (1,2) and the plan is left-deep; the reverse score order builds
+    the mirror image, and scores making (0,1), (2,3) first give the bushy
+    plan."""
+    q = W.Query(n=4, card=[10.0, 20.0, 30.0, 40.0], edges=[(0, 1, 0.1), (1, 2, 0.1), (2, 3, 0.1)])
+    g = H.Graph(q)
+    assert H.canonical(H.learned_start(g, [0.0, 0.0, 0.0])) == (((0, 1), 2), 3)
+    assert H.canonical(H.learned_start(g, [2.0, 1.0, 0.0])) == (0, (1, (2, 3)))
+    bushy = H.learned_start(g, [0.0, 1.0, 0.0])
+    assert H.canonical(bushy) == ((0, 1), (2, 3))
+    assert bushy.cost == H.plan_cost(g, bushy).cost
+
+
+def test_learned_start_plans_valid():
+    q = W.make("snowflake_plus", 60, 5)
+    g = H.Graph(q)
+    rng = random.Random(5)
+    p = H.learned_start(g, [rng.random() for _ in g.edges])
+    assert p.rels == (1 << 60) - 1 and p.leaves == 60
+    assert cross_product_free(g, p)
+    assert H.plan_cost(g, p).cost == p.cost
