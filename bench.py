@@ -46,12 +46,16 @@ OPS_PER_BFS_ROUND = 15
 BYTES_PER_CCP = 24
 BYTES_PER_SET = 16
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernels on this bench's 64-query batch, from one ncu capture of
-# this bench command (--cache-control none; profiles/).  They describe the
-# kernel sources whose SHA-1 is given and are reported as null for any other.
-TRAFFIC_SOURCES = ("paper_2202_13511_gb300/csrc/mpdp_kernels.cu", "paper_2202_13511_gb300/csrc/mpdp_device.cuh")
-TRAFFIC = {"sha1": "f7583e67c6dad93afe2095746a122621662e4d58",
-           "eval": 138459685, "filter": 22600137}
+# dominant kernels on this bench's 64-query batch (4 lanes of 16 queries), from
+# one ncu capture of this bench command (--cache-control none; profiles/).
+# Each figure describes the kernel whose source fingerprint is given (the
+# kernel's own text plus the device header it includes) and is reported as
+# null once that source changes.
+KERNEL_FILE = "paper_2202_13511_gb300/csrc/mpdp_kernels.cu"
+DEVICE_HEADER = "paper_2202_13511_gb300/csrc/mpdp_device.cuh"
+TRAFFIC = {"eval": {"kernel": "k_eval_tree", "sha1": "7b2401541081565af389a9c4aaf867dfed4ada75", "bytes": 16008593},
+           "filter": {"kernel": "k_filter_bitmaps", "sha1": "6387f98ffbc140f93bd3cf75a6315d19afcbfbb2",
+                      "bytes": 5099008}}
 
 
 def parse_args():
@@ -309,17 +313,13 @@ def run_ours(args):
            "h2d_bytes_per_step": sum(int(s["h2d_bytes"]) for s in stats),
            "d2h_bytes_per_step": sum(int(s["d2h_bytes"]) for s in stats)}
 
-    # kernel timing pass: CUDA events around every launch, on the launch stream
+    # kernel timing passes: CUDA events around every launch, on the launch stream
     prof_steps = min(args.steps, 5)
-    opt.profile(True)
-    for _ in range(prof_steps):
-        flush.zero_()
-        step()
-    kt = opt.profile_read()
-    opt.profile(False)
+    kt, kc = kernel_passes(opt, step, flush, prof_steps, mpdp)
     peaks = read_peaks()
     dom = max(kt, key=lambda k: kt[k]["ms"])
-    roof = roofline(dom, kt[dom], stats, prof_steps, peaks, bench_batch=(Q == QUERIES_PER_STEP))
+    roof = roofline(dom, kc[dom], stats, prof_steps, peaks, bench_batch=(Q == QUERIES_PER_STEP),
+                    serial=kt[dom])
     kernel_share = {k: round(v["ms"] / max(sum(x["ms"] for x in kt.values()), 1e-12), 4)
                     for k, v in kt.items() if v["launches"]}
 
@@ -359,24 +359,63 @@ def run_ours(args):
     return 0
 
 
-def traffic_for(kind, measured):
-    """ncu DRAM bytes per launch of `kind`, while the kernel sources are the
-    profiled ones and the workload is this bench's own batch."""
+def kernel_passes(opt, step, flush, prof_steps, mpdp):
+    """Two profiled passes of prof_steps steps each.  Serial: the batch's
+    lanes one after the other, so that the per-class times add up as in a
+    profiler's serialised launch list (kernel shares).  Concurrent: the lanes
+    as in the timed steps; each class's active wall time (union of its
+    launch intervals) is the time its work took there (roofline)."""
+    out = []
+    for mode in (mpdp.PROFILE_SERIAL, mpdp.PROFILE_CONCURRENT):
+        opt.profile(mode)
+        for _ in range(prof_steps):
+            flush.zero_()
+            step()
+        out.append(opt.profile_read())
+        opt.profile(mpdp.PROFILE_OFF)
+    return out[0], out[1]
+
+
+def kernel_fingerprint(name):
+    """SHA-1 of a kernel's definition in the kernel file (from its template
+    line or signature to the closing brace) and of the device header."""
     import hashlib
-    if not measured:
+    import re
+    src = open(os.path.join(ROOT, KERNEL_FILE)).read()
+    m = re.search(r"(template <class Memo>\n)?__global__ void [^\n]*\b" + name + r"\(", src)
+    if m is None:
         return None
-    h = hashlib.sha1()
-    for f in TRAFFIC_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
-    return TRAFFIC.get(kind) if h.hexdigest() == TRAFFIC["sha1"] else None
+    depth, i = 0, src.index("{", m.end())
+    for j in range(i, len(src)):
+        depth += {"{": 1, "}": -1}.get(src[j], 0)
+        if depth == 0:
+            break
+    h = hashlib.sha1(src[m.start():j + 1].encode())
+    h.update(open(os.path.join(ROOT, DEVICE_HEADER), "rb").read())
+    return h.hexdigest()
 
 
-def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False):
+def traffic_for(kind, measured):
+    """ncu DRAM bytes per launch of `kind`, while the kernel's source is the
+    profiled one and the workload is this bench's own batch."""
+    t = TRAFFIC.get(kind)
+    if not measured or t is None:
+        return None
+    return t["bytes"] if kernel_fingerprint(t["kernel"]) == t["sha1"] else None
+
+
+def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False, serial=None):
     """Roofline of the dominant kernel class.  `stats` are the per-query
-    counters of one step's queries, `timing` the class's summed event time
-    and launches over `prof_steps` steps."""
+    counters of one step's queries, `timing` the class's launches and active
+    wall time over `prof_steps` steps with the lanes concurrent (the timed
+    configuration); the average launch duration is that time over the
+    launches.  `serial`, when given, is the same class timed with the lanes
+    one after the other (each launch alone)."""
     launches = max(timing["launches"], 1)
-    avg_s = timing["ms"] / launches / 1000.0
+    avg_s = timing["active_ms"] / launches / 1000.0
+    extra = {}
+    if serial is not None and serial["launches"]:
+        extra["avg_launch_ms_alone"] = serial["ms"] / serial["launches"]
     if kind == "filter":
         ops = sum((OPS_PER_BITMAP_TREE if s["enumeration"] == 1 else OPS_PER_BITMAP_GRAPH) *
                   int(s["sets_unranked"]) + OPS_PER_BFS_ROUND * int(s["filter_steps"])
@@ -387,7 +426,7 @@ def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False):
         return {"kernel": "k_filter_bitmaps", "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "Tops/s", "frac": ach / peak, "traffic": traffic_for("filter", bench_batch),
                 "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz (issue slots)",
-                "ops_per_launch": ops, "avg_launch_ms": avg_s * 1000.0}
+                "ops_per_launch": ops, "avg_launch_ms": avg_s * 1000.0, **extra}
     # memo-traffic kernels: algorithmic bytes per launch
     nbytes = sum(BYTES_PER_CCP * int(s["ccp_pairs"]) + BYTES_PER_SET * int(s["sets_connected"])
                  for s in stats) * prof_steps / launches
@@ -397,7 +436,7 @@ def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False):
     return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "traffic": traffic_for(kind, bench_batch and kind == "eval"),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst)" if peaks else "fallback 6800 GB/s",
-            "bytes_per_launch": nbytes, "avg_launch_ms": avg_s * 1000.0}
+            "bytes_per_launch": nbytes, "avg_launch_ms": avg_s * 1000.0, **extra}
 
 
 SHAPES = {
@@ -441,19 +480,14 @@ def shape_line(name, opt, torch, mpdp, W, peaks, reps=5):
     torch.cuda.synchronize()
     ms_batch = sum(a.elapsed_time(b) for a, b in evs) / reps
     assert int((d_status != 0).sum().item()) == 0
-    opt.profile(True)
-    for _ in range(3):
-        flush.zero_()
-        run()
-    kt = opt.profile_read()
-    opt.profile(False)
+    kt, kc = kernel_passes(opt, run, flush, 3, mpdp)
     dom = max(kt, key=lambda k: kt[k]["ms"])
     ccp = sum(int(s["ccp_pairs"]) for s in stats)
     return {"workload": desc, "queries": nq, "ms_per_batch": ms_batch, "ms_per_query": ms_batch / nq,
             "queries_per_s": nq * 1000.0 / ms_batch, "ccp_pairs_per_s": ccp / (ms_batch / 1000.0),
             "ccp_pairs_per_query": ccp / nq,
             "sets_connected_per_query": sum(int(s["sets_connected"]) for s in stats) / nq,
-            "roofline": roofline(dom, kt[dom], stats, 3, peaks),
+            "roofline": roofline(dom, kc[dom], stats, 3, peaks, serial=kt[dom]),
             "kernel_share": {k: round(v["ms"] / max(sum(x["ms"] for x in kt.values()), 1e-12), 4)
                              for k, v in kt.items() if v["launches"]}}
 
@@ -461,8 +495,9 @@ def shape_line(name, opt, torch, mpdp, W, peaks, reps=5):
 def ablation_line(opt, torch, mpdp, W):
     """The paper's relative claims on the same kernels: MPDP's block
     enumeration against DPSUB's vertex-based one (Sec. 6.2: far fewer pairs
-    evaluated), and Collaborative Context Collection on / off (Sec. 6.4).
-    Device time of one batch (CUDA events, L2 flushed, mean of 3)."""
+    evaluated), and Collaborative Context Collection on / off (Sec. 6.4);
+    and the batch split into 1/2/4/8 concurrent lanes.  Device time of one
+    batch (CUDA events, L2 flushed, mean of 3)."""
     import numpy as np
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -508,6 +543,16 @@ def ablation_line(opt, torch, mpdp, W):
         t_off, _, c_off = timed(qs, use_ccc=0, enumeration=mpdp.ENUM_BLOCKS)
         assert np.array_equal(c_on, c_off)
         out[f"ccc_{name}"] = {"ccc_on_ms": t_on, "ccc_off_ms": t_off, "gain": t_off / t_on}
+    # lanes: one device batch as concurrent sub-batches (a project addition)
+    for name, qs in (("snowflake25_x64", [W.snowflake(25, seed=i) for i in range(64)]),
+                     ("cyclic20_x64", [W.cyclic(20, seed=i) for i in range(64)])):
+        t_1, _, c_1 = timed(qs, lanes=1)
+        res = {"lanes_1_ms": t_1}
+        for lanes in (2, 4, 8):
+            t_l, _, c_l = timed(qs, lanes=lanes)
+            assert np.array_equal(c_1, c_l)
+            res[f"lanes_{lanes}_ms"] = t_l
+        out[f"lanes_{name}"] = res
     return out
 
 
@@ -517,9 +562,11 @@ LEARN_QUERIES = 8000
 def learned_line(opt, mpdp, W):
     """Learned proposal: a BF16 MLP trained on the GPU by the library's own
     kernels on the exact plans of LEARN_QUERIES primary-key/foreign-key
-    snowflakes of 10-25 relations, then MODE_UNIONDP_LEARNED against plain
-    UnionDP and IDP2 (k = 25, t = 15) on held-out queries of 100/300/1000
-    relations; plan-cost ratios as geometric means and 95th percentiles."""
+    snowflakes of 10-25 relations, then MODE_IDP2_LEARNED against plain IDP2
+    (k = 25; the learned-IDP plan-cost ratio) and MODE_UNIONDP_LEARNED
+    against plain UnionDP and IDP2 (k = 25, t = 15) on held-out queries of
+    100/300/1000 relations; plan-cost ratios as geometric means and 95th
+    percentiles."""
     import math
     import numpy as np
     from paper_2202_13511_gb300 import learned as L
@@ -533,13 +580,21 @@ def learned_line(opt, mpdp, W):
                         "dataset_s": round(t_data, 3), "train_s": round(t_train, 3),
                         "samples_per_s": 10 * x.shape[0] / t_train, "loss_first": log[0][1],
                         "loss_last": log[-1][1]},
-           "modes": "uniondp_learned vs uniondp and idp2, k = 25, t = 15"}
+           "modes": "idp2_learned vs idp2 (k = 25); uniondp_learned vs uniondp and idp2 (k = 25, t = 15)"}
     for n in LARGE_SIZES:
         qs = [W.snowflake_plus_pkfk(n, seed=5000 + i) for i in range(LARGE_QUERIES)]
         rows = L.evaluate(opt, mlp, qs, 25, 15)
         lp = [math.log2(L.cost_ratio(l, p)) for p, l, _ in rows]
         li = [math.log2(L.cost_ratio(l, i)) for p, l, i in rows]
-        out[f"pkfk_n{n}"] = {"learned_over_plain_geomean": 2.0 ** float(np.mean(lp)),
+        t1 = time.perf_counter()
+        irows = L.evaluate_idp2(opt, mlp, qs, 25)
+        t_idp = (time.perf_counter() - t1) / len(qs)
+        ll = [math.log2(L.cost_ratio(l, p)) for p, l in irows]
+        out[f"pkfk_n{n}"] = {"idp2_learned_over_idp2_geomean": 2.0 ** float(np.mean(ll)),
+                             "idp2_learned_over_idp2_p95": 2.0 ** float(np.percentile(ll, 95)),
+                             "idp2_learned_wins": int(sum(v < 0 for v in ll)),
+                             "idp2_pair_s_per_query": round(t_idp, 4),
+                             "learned_over_plain_geomean": 2.0 ** float(np.mean(lp)),
                              "learned_over_plain_p95": 2.0 ** float(np.percentile(lp, 95)),
                              "learned_wins": int(sum(v < 0 for v in lp)), "learned_losses": int(sum(v > 0 for v in lp)),
                              "learned_over_idp2_geomean": 2.0 ** float(np.mean(li))}

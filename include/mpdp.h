@@ -41,13 +41,15 @@
 extern "C" {
 #endif
 
-#define MPDP_ABI_VERSION 1
+#define MPDP_ABI_VERSION 2
 /* Exact mode uses 32-bit relation bitmaps; memory grows as 2^n (see
  * mpdp_workspace_bytes), so n is further capped by the memo budget. */
 #define MPDP_MAX_EXACT_RELS 30
 /* Heuristic modes (IDP2, UnionDP): relations of one query. */
 #define MPDP_MAX_HEURISTIC_RELS 4096
 #define MPDP_MAX_LEVELS 33
+/* Concurrent sub-batches of one device batch (mpdp_config.lanes). */
+#define MPDP_MAX_LANES 8
 
 enum {
     MPDP_OK = 0,
@@ -175,6 +177,13 @@ typedef struct {
     int32_t filter;           /* MPDP_FILTER_BITMAPS (default) or MPDP_FILTER_UNRANK */
     int32_t grid_blocks_per_sm; /* evaluate grids: at most this many 256-thread
                                  blocks per SM (1..32, default 8) */
+    int32_t lanes;            /* a device batch runs as up to this many
+                                 sub-batches of consecutive queries, balanced
+                                 by 2^n, on concurrent streams, so that one
+                                 sub-batch's filter (integer-issue bound)
+                                 overlaps another's evaluation (memo-traffic
+                                 bound); 1..MPDP_MAX_LANES, default 4.
+                                 Results do not depend on it. */
 } mpdp_config;
 
 /* Create a context on CUDA device `device`.  memo_budget_bytes caps the device
@@ -202,10 +211,16 @@ size_t mpdp_workspace_bytes(int32_t n_rels, const mpdp_config *cfg);
  * model's scores), with plain UnionDP as the fallback: both plans are
  * costed exactly and the cheaper is returned (the plain one on ties, and
  * always when no model is set).  In the heuristic modes mpdp_stats carries
- * the number of exact sub-problems in heavy_sets and, for UNIONDP_LEARNED,
- * filter_steps = 1 when the learned plan was kept.
- * MPDP_MODE_IDP2_LEARNED returns MPDP_ERR_NOT_IMPLEMENTED, and so does
- * mpdp_optimize_batch for any mode but exact. */
+ * the number of exact sub-problems in heavy_sets and, for the learned
+ * modes, filter_steps = 1 when the learned plan was kept.
+ * MPDP_MODE_IDP2_LEARNED: IDP2 started from the learned proposal's plan
+ * instead of GOO's (the query's edges in ascending score, each joining the
+ * plans of its two ends while they are apart; equal scores in edge order
+ * (min(u, v), max(u, v))), with IDP2 from GOO's plan as the fallback: the
+ * cheaper plan is returned (GOO's on ties, and always when no model is
+ * set).  t must be 0, as for MPDP_MODE_IDP2.
+ * mpdp_optimize_batch returns MPDP_ERR_NOT_IMPLEMENTED for any mode but
+ * exact. */
 int mpdp_optimize(mpdp_ctx *ctx, const mpdp_query *q, int64_t *handle);
 
 /* Enqueue nq queries as device batches (all queries of a batch share every
@@ -328,13 +343,23 @@ enum {
     MPDP_KC_COUNT = 8
 };
 
-/* Profiling mode (off by default).  While on, work is launched kernel by
- * kernel (no graph replay) with a pair of CUDA events on the context's stream
- * around every launch.  mpdp_profile_read waits for the stream, adds the
- * elapsed times per kernel class since the previous read into ms[MPDP_KC_COUNT]
- * and the launch counts into launches[MPDP_KC_COUNT], and resets them. */
-int mpdp_profile(mpdp_ctx *ctx, int enable);
+/* Profiling modes (off by default).  While on, work is launched kernel by
+ * kernel (no graph replay) with a pair of CUDA events around every launch, on
+ * the stream it is launched on.  SERIAL runs a batch's lanes one after the
+ * other on the context's stream, so that per-class times add up to the batch
+ * (as a profiler's serialised launch list does); CONCURRENT runs them on
+ * their own streams as in normal operation.  Any nonzero `mode` other than
+ * these is invalid; 1 is SERIAL.
+ * mpdp_profile_read waits for the stream, adds the elapsed times per kernel
+ * class since the previous read into ms[MPDP_KC_COUNT] and the launch counts
+ * into launches[MPDP_KC_COUNT], and resets them.  mpdp_profile_read_active
+ * also returns, per class, the wall time during which at least one of its
+ * launches was in flight (the union of the launch intervals within each
+ * batch; equal to ms in SERIAL mode). */
+enum { MPDP_PROFILE_OFF = 0, MPDP_PROFILE_SERIAL = 1, MPDP_PROFILE_CONCURRENT = 2 };
+int mpdp_profile(mpdp_ctx *ctx, int mode);
 int mpdp_profile_read(mpdp_ctx *ctx, double *ms, uint64_t *launches);
+int mpdp_profile_read_active(mpdp_ctx *ctx, double *ms, double *active_ms, uint64_t *launches);
 
 /* Static text for an error code. */
 const char *mpdp_strerror(int code);
@@ -422,13 +447,14 @@ int mpdp_mlp_gradients(mpdp_mlp *m, const float *d_x, const float *d_t, int32_t 
 int mpdp_mlp_train_step(mpdp_mlp *m, const float *d_x, const float *d_t, int32_t rows, float lr);
 
 /* Use `model` (MPDP_EDGE_FEATURES inputs; borrowed, NULL to detach) for
- * MPDP_MODE_UNIONDP_LEARNED on this context. */
+ * MPDP_MODE_UNIONDP_LEARNED and MPDP_MODE_IDP2_LEARNED on this context. */
 #define MPDP_EDGE_FEATURES 12
 int mpdp_set_model(mpdp_ctx *ctx, mpdp_mlp *model);
 /* The model's input rows for the edges of a query graph, in edge order
  * (MPDP_EDGE_FEATURES floats each; cap_rows >= n_edges): the features the
- * learned UnionDP computes at every round, here for the base graph, so that
- * training data uses the same code. */
+ * learned UnionDP computes at every round and the learned IDP2 start
+ * computes once, here for the base graph, so that training data uses the
+ * same code. */
 int mpdp_edge_features(const mpdp_query *q, float *out, int32_t cap_rows);
 
 #ifdef __cplusplus

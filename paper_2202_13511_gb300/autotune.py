@@ -7,6 +7,7 @@ does, and the best setting depends on the workload:
   kernel for the chunked warp kernel (`heavy_threshold`), and whether those
   warps use collaborative context collection (`use_ccc`);
 - the connected-set filter (`filter`);
+- the concurrent sub-batches of a device batch (`lanes`);
 - for the serving loop, the number of concurrent device batches (`slots`)
   and the batch size cap (`max_batch`).
 
@@ -25,6 +26,7 @@ KERNEL_SPACE: Dict[str, List[int]] = {
     "heavy_threshold": [16, 64, 256],
     "use_ccc": [0, 1],
     "filter": [0, 1],  # MPDP_FILTER_BITMAPS, MPDP_FILTER_UNRANK
+    "lanes": [1, 2, 4, 8],
 }
 SERVER_SPACE: Dict[str, List[int]] = {
     "slots": [1, 2, 4, 8],
@@ -122,7 +124,7 @@ def tune_kernels(queries: Sequence, device: int = 0, reps: int = 3,
     Returns (config dict for Optimizer.set_config / Server kernel config,
     its time in seconds, the measured history)."""
     space = relevant_space(queries)
-    start = {"grid_blocks_per_sm": 8, "heavy_threshold": 64, "use_ccc": 1, "filter": 0}
+    start = {"grid_blocks_per_sm": 8, "heavy_threshold": 64, "use_ccc": 1, "filter": 0, "lanes": 4}
     start = {k: v for k, v in start.items() if k in space}
     own = measure is None
     if own:

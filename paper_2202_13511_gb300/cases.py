@@ -1,7 +1,7 @@
 """Run one workload shape through the device path (for profiler captures).
 
     python -m paper_2202_13511_gb300.cases --kind star --n 25 --reps 3
-    python -m paper_2202_13511_gb300.cases --kind snowflake --n 25 --queries 4
+    python -m paper_2202_13511_gb300.cases --kind snowflake --n 25 --queries 4 --lanes 1
 
 All queries of a rep go to the GPU as one device batch.  Nothing is checked
 beyond the device status words; this only exists so that a profiler can
@@ -24,6 +24,7 @@ def main(argv=None) -> int:
     p.add_argument("--reps", type=int, default=2)
     p.add_argument("--memo", choices=["dense", "hash"], default="dense")
     p.add_argument("--enumeration", choices=["auto", "tree", "blocks"], default="auto")
+    p.add_argument("--lanes", type=int, default=0, help="concurrent sub-batches (0: library default)")
     a = p.parse_args(argv)
     import torch
     from . import mpdp
@@ -33,6 +34,8 @@ def main(argv=None) -> int:
                          memo_kind={"dense": mpdp.MEMO_DENSE, "hash": mpdp.MEMO_HASH}[a.memo],
                          enumeration={"auto": mpdp.ENUM_AUTO, "tree": mpdp.ENUM_TREE,
                                       "blocks": mpdp.ENUM_BLOCKS}[a.enumeration])
+    if a.lanes:
+        opt.set_config(lanes=a.lanes)
     qs = [W.make(a.kind, a.n, seed=a.seed + i) for i in range(a.queries)]
     d_card = torch.tensor([c for q in qs for c in q.card], dtype=torch.float64, device="cuda")
     d_edges = torch.from_numpy(

@@ -27,7 +27,7 @@ using namespace mpdp;
 
 namespace {
 
-const mpdp_config kDefaultConfig = {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 1, 32, MPDP_FILTER_BITMAPS, 8};
+const mpdp_config kDefaultConfig = {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 1, 32, MPDP_FILTER_BITMAPS, 8, 4};
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -65,9 +65,18 @@ struct GraphEntry {
 };
 
 // Profiling mode: a pair of events around every launch, summed per class.
+// Every batch also records an origin event before its first launch, so that
+// launches of one batch on different streams share a time line: the union of
+// a class's launch intervals is the wall time during which it was active.
 struct EventHook : LaunchHook {
+    struct Rec {
+        int cls;
+        size_t begin;  // index of the begin event (the end event follows)
+        int group;     // batch (index into origins), -1 before the first mark
+    };
     std::vector<cudaEvent_t> pool;
-    std::vector<std::pair<int, size_t>> recs;  // (class, index of the begin event)
+    std::vector<Rec> recs;
+    std::vector<size_t> origins;  // event index of each batch's origin
     size_t next = 0;
     cudaError_t err = cudaSuccess;
 
@@ -81,9 +90,15 @@ struct EventHook : LaunchHook {
         }
         return pool[next++];
     }
+    void mark(cudaStream_t st)
+    {
+        origins.push_back(next);
+        cudaError_t r = cudaEventRecord(take(), st);
+        if (r != cudaSuccess) err = r;
+    }
     void begin(int cls, cudaStream_t st) override
     {
-        recs.emplace_back(cls, next);
+        recs.push_back(Rec{cls, next, (int)origins.size() - 1});
         cudaError_t r = cudaEventRecord(take(), st);
         if (r != cudaSuccess) err = r;
     }
@@ -91,6 +106,12 @@ struct EventHook : LaunchHook {
     {
         cudaError_t r = cudaEventRecord(take(), st);
         if (r != cudaSuccess) err = r;
+    }
+    void reset()
+    {
+        recs.clear();
+        origins.clear();
+        next = 0;
     }
     ~EventHook()
     {
@@ -116,6 +137,11 @@ struct mpdp_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;          // work stream (borrowed; nullptr = default stream)
     cudaStream_t capture_stream = nullptr;  // private, only used to capture graphs
+    // lanes: private streams of the concurrent sub-batches, forked from and
+    // joined back into the work (or capture) stream by events
+    cudaStream_t lane_stream[MPDP_MAX_LANES] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[MPDP_MAX_LANES] = {};
     size_t budget = 0;
     mpdp_config cfg = kDefaultConfig;
     int num_sms = 152;
@@ -148,7 +174,7 @@ struct mpdp_ctx {
     unsigned long long last_seq = 0;  // seq of the batch whose memo is in the workspace
     std::map<std::vector<int>, GraphEntry> graphs;
     int last_launches = 0;
-    bool profiling = false;
+    int profiling = 0;  // MPDP_PROFILE_*
     EventHook hook;
     std::string last_error;
 };
@@ -238,7 +264,7 @@ static size_t var_bytes_of(size_t lists, size_t heavy, size_t memo, size_t hash)
 
 static size_t fixed_bytes()
 {
-    return align_up(sizeof(QDesc) * kMaxBatch) + align_up(sizeof(uint32_t) * (kMaxBatch + 1)) +
+    return align_up(sizeof(QDesc) * kMaxBatch) + align_up(sizeof(uint32_t) * (kMaxBatch + MPDP_MAX_LANES + 1)) +
            align_up(sizeof(StagedQuery) * kMaxBatch) + align_up(sizeof(DevQuery) * kMaxBatch) +
            align_up(sizeof(DevOut) * kMaxBatch) + align_up(sizeof(HashLayout) * kMaxBatch);
 }
@@ -266,7 +292,7 @@ static int ensure_fixed(mpdp_ctx* ctx)
         return r;
     };
     ctx->d_desc = reinterpret_cast<QDesc*>(take(sizeof(QDesc) * kMaxBatch));
-    ctx->d_prefix = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (kMaxBatch + 1)));
+    ctx->d_prefix = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (kMaxBatch + MPDP_MAX_LANES + 1)));
     ctx->d_staged = reinterpret_cast<StagedQuery*>(take(sizeof(StagedQuery) * kMaxBatch));
     ctx->d_query = reinterpret_cast<DevQuery*>(take(sizeof(DevQuery) * kMaxBatch));
     ctx->d_out = reinterpret_cast<DevOut*>(take(sizeof(DevOut) * kMaxBatch));
@@ -440,13 +466,68 @@ static int acquire_stage(mpdp_ctx* ctx, size_t bytes, char** host, int* slot)
     return MPDP_OK;
 }
 
-// Enqueue the DP pipeline of a planned batch: graph replay or direct launches.
-static int run_pipeline(mpdp_ctx* ctx, const BatchArgs& a, const BatchPlan& bp, const std::vector<int>& key,
-                        int* launches)
+// One sub-batch of a device batch: queries [q0, q1), their arguments (query
+// arrays offset by q0, own filter-block prefix, own hash-arena range) and
+// launch plan.
+struct Lane {
+    int q0 = 0, q1 = 0;
+    BatchArgs a;
+    BatchPlan bp;
+};
+
+static int ensure_lane_streams(mpdp_ctx* ctx, int lanes)
 {
+    if (!ctx->fork_ev) CK(ctx, cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+    for (int l = 0; l < lanes; l++) {
+        if (!ctx->lane_stream[l]) CK(ctx, cudaStreamCreateWithFlags(&ctx->lane_stream[l], cudaStreamNonBlocking));
+        if (!ctx->join_ev[l]) CK(ctx, cudaEventCreateWithFlags(&ctx->join_ev[l], cudaEventDisableTiming));
+    }
+    return MPDP_OK;
+}
+
+// Enqueue every lane's pipeline on `st`: one lane directly; several on the
+// lane streams, forked from and joined back into `st` (inside a capture this
+// makes parallel branches of one graph).  In serial profiling the lanes run
+// one after the other on `st`, so that per-kernel-class times add up; in
+// concurrent profiling they run as in normal operation.
+static cudaError_t enqueue_lanes(mpdp_ctx* ctx, const std::vector<Lane>& lanes, cudaStream_t st, int* launches,
+                                 LaunchHook* hook)
+{
+    int total = 0;
+    cudaError_t e = cudaSuccess;
+    if (lanes.size() == 1 || (hook && ctx->profiling != MPDP_PROFILE_CONCURRENT)) {
+        for (const Lane& ln : lanes) {
+            int c = 0;
+            e = enqueue_pipeline(ln.a, ln.bp, ctx->cfg.memo_kind, st, &c, hook);
+            if (e != cudaSuccess) return e;
+            total += c;
+        }
+    } else {
+        if ((e = cudaEventRecord(ctx->fork_ev, st)) != cudaSuccess) return e;
+        for (size_t l = 0; l < lanes.size(); l++) {
+            cudaStream_t ls = ctx->lane_stream[l];
+            int c = 0;
+            if ((e = cudaStreamWaitEvent(ls, ctx->fork_ev, 0)) != cudaSuccess) return e;
+            if ((e = enqueue_pipeline(lanes[l].a, lanes[l].bp, ctx->cfg.memo_kind, ls, &c, hook)) != cudaSuccess)
+                return e;
+            total += c;
+            if ((e = cudaEventRecord(ctx->join_ev[l], ls)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(st, ctx->join_ev[l], 0)) != cudaSuccess) return e;
+        }
+    }
+    if (launches) *launches = total;
+    return cudaSuccess;
+}
+
+// Enqueue the DP pipeline of a planned batch: graph replay or direct launches.
+static int run_pipeline(mpdp_ctx* ctx, const std::vector<Lane>& lanes, const std::vector<int>& key, int* launches)
+{
+    if (lanes.size() > 1) {
+        const int rc = ensure_lane_streams(ctx, (int)lanes.size());
+        if (rc != MPDP_OK) return rc;
+    }
     if (ctx->profiling || !ctx->cfg.use_graphs) {
-        CK(ctx, enqueue_pipeline(a, bp, ctx->cfg.memo_kind, ctx->stream, launches,
-                                 ctx->profiling ? &ctx->hook : nullptr));
+        CK(ctx, enqueue_lanes(ctx, lanes, ctx->stream, launches, ctx->profiling ? &ctx->hook : nullptr));
         return MPDP_OK;
     }
     auto it = ctx->graphs.find(key);
@@ -455,10 +536,11 @@ static int run_pipeline(mpdp_ctx* ctx, const BatchArgs& a, const BatchPlan& bp, 
         GraphEntry g;
         cudaGraph_t graph = nullptr;
         CK(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = enqueue_pipeline(a, bp, ctx->cfg.memo_kind, ctx->capture_stream, &g.launches);
+        cudaError_t e = enqueue_lanes(ctx, lanes, ctx->capture_stream, &g.launches, nullptr);
         cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
             ctx->last_error = std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
             return MPDP_ERR_CUDA;
         }
@@ -473,6 +555,27 @@ static int run_pipeline(mpdp_ctx* ctx, const BatchArgs& a, const BatchPlan& bp, 
     CK(ctx, cudaGraphLaunch(it->second.exec, ctx->stream));
     if (launches) *launches = it->second.launches;
     return MPDP_OK;
+}
+
+// Split queries [0, nq) into at most `lanes` runs of consecutive queries with
+// about equal sums of 2^n (the filter's work; the evaluation's grows with it
+// too).  Returns the run starts followed by nq.
+static std::vector<int> lane_bounds(const std::vector<PlanQuery>& qs, int lanes)
+{
+    const int nq = (int)qs.size();
+    lanes = std::max(1, std::min(lanes, nq));
+    double total = 0.0;
+    for (const auto& q : qs) total += std::ldexp(1.0, q.n);
+    std::vector<int> b = {0};
+    double acc = 0.0;
+    for (int i = 0; i < nq && (int)b.size() < lanes; i++) {
+        acc += std::ldexp(1.0, qs[i].n);
+        // close this run once it holds its share, leaving a query for each later run
+        if (acc >= total * (double)b.size() / lanes && i + 1 < nq && nq - (i + 1) >= lanes - (int)b.size())
+            b.push_back(i + 1);
+    }
+    b.push_back(nq);
+    return b;
 }
 
 // Plan, upload and enqueue one device batch.  host_path: queries come from
@@ -495,7 +598,10 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
     }
     rc = ensure_var(ctx, L, V, M, A);
     if (rc != MPDP_OK) return rc;
-    const size_t desc_bytes = sizeof(QDesc) * nq, pref_bytes = sizeof(uint32_t) * (nq + 1);
+    const std::vector<int> bounds = lane_bounds(qs, ctx->cfg.lanes);
+    const int n_lanes = (int)bounds.size() - 1;
+    std::vector<Lane> lanes(n_lanes);
+    const size_t desc_bytes = sizeof(QDesc) * nq, pref_bytes = sizeof(uint32_t) * (nq + n_lanes);
     const size_t staged_off = align_up(desc_bytes) + align_up(pref_bytes);
     const size_t stage_bytes = staged_off + (host_path ? sizeof(StagedQuery) * nq : 0);
     char* h = nullptr;
@@ -505,18 +611,34 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
     QDesc* hd = reinterpret_cast<QDesc*>(h);
     uint32_t* hp = reinterpret_cast<uint32_t*>(h + align_up(desc_bytes));
     StagedQuery* hs = reinterpret_cast<StagedQuery*>(h + staged_off);
-    BatchPlan bp;
-    bp.num_sms = ctx->num_sms;
-    bp.blocks_per_sm = ctx->cfg.grid_blocks_per_sm;
-    std::vector<int> key = {nq, kind, ctx->cfg.heavy_threshold, ctx->cfg.use_ccc, ctx->cfg.run_length,
-                            ctx->cfg.filter, ctx->cfg.grid_blocks_per_sm, ctx->cfg.enumeration};
-    unsigned long long lbase = 0, mbase = 0, hbase = 0;
+    std::vector<int> key = {nq,
+                            kind,
+                            ctx->cfg.heavy_threshold,
+                            ctx->cfg.use_ccc,
+                            ctx->cfg.run_length,
+                            ctx->cfg.filter,
+                            ctx->cfg.grid_blocks_per_sm,
+                            ctx->cfg.enumeration,
+                            n_lanes};
+    unsigned long long lbase = 0, mbase = 0, hbase = 0, abase = 0;
     uint32_t fblocks = 0;
-    int max_n = 0;
+    int max_n = 0, lane = 0, lane_max_n = 0;
     std::vector<unsigned long long> h2d(nq, 0);
     for (int i = 0; i < nq; i++) {
         const PlanQuery& q = qs[i];
         QDesc& d = hd[i];
+        if (i == bounds[lane]) {  // first query of a lane
+            Lane& ln = lanes[lane];
+            ln.q0 = i;
+            ln.q1 = bounds[lane + 1];
+            ln.bp.num_sms = ctx->num_sms;
+            ln.bp.blocks_per_sm = ctx->cfg.grid_blocks_per_sm;
+            ln.a.arena_begin = abase;
+            fblocks = 0;
+            lane_max_n = 0;
+            lane++;
+        }
+        BatchPlan& bp = lanes[lane - 1].bp;
         memset(&d, 0, sizeof(d));
         d.n = q.n;
         d.n_edges = q.m;
@@ -529,7 +651,7 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
         uint32_t qb = 0;
         fill_levels(d, ctx->cfg.run_length, ctx->cfg.filter, qb);
         d.filter_block_base = fblocks;
-        hp[i] = fblocks;
+        hp[i + lane - 1] = fblocks;  // the lane's own prefix: lane l's starts at q0 + l
         fblocks += qb;
         const QuerySize z = query_size(q.n, q.enumeration, kind);
         d.heavy_base = hbase;
@@ -537,7 +659,26 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
         lbase += z.lists;
         mbase += z.memo;
         hbase += z.heavy;
+        abase += z.hash;
         if (q.n > max_n) max_n = q.n;
+        if (q.n > lane_max_n) lane_max_n = q.n;
+        if (i + 1 == bounds[lane]) {  // last query of the lane
+            Lane& ln = lanes[lane - 1];
+            hp[i + lane] = fblocks;
+            bp.filter_blocks = fblocks;
+            const BatchArgs whole = batch_args(ctx, nq, max_n);
+            const unsigned long long begin = ln.a.arena_begin;
+            ln.a = batch_args(ctx, ln.q1 - ln.q0, lane_max_n);
+            ln.a.desc = whole.desc + ln.q0;
+            ln.a.filter_block_prefix = ctx->d_prefix + ln.q0 + (lane - 1);
+            ln.a.staged = whole.staged + ln.q0;
+            ln.a.query = whole.query + ln.q0;
+            ln.a.out = whole.out + ln.q0;
+            ln.a.layout = whole.layout + ln.q0;
+            // hash memo: every lane has its own arena range (the last one the rest)
+            ln.a.arena_begin = n_lanes == 1 ? 0 : begin;
+            ln.a.arena_slots = lane == n_lanes ? ctx->arena_slots : abase;
+        }
         for (int k = 2; k <= q.n; k++) {
             const unsigned long long c = binom_host(q.n, k);
             if (q.enumeration == MPDP_ENUM_TREE) {
@@ -559,8 +700,6 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
             for (int e = 0; e < q.m; e++) sq.edges[e] = q.edges[e];
         }
     }
-    hp[nq] = fblocks;
-    bp.filter_blocks = fblocks;
     CK(ctx, cudaMemcpyAsync(ctx->d_desc, hd, desc_bytes, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->d_prefix, hp, pref_bytes, cudaMemcpyHostToDevice, ctx->stream));
     if (host_path) {
@@ -573,6 +712,7 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
     CK(ctx, cudaEventRecord(ctx->ring[slot].free_ev, ctx->stream));
     const BatchArgs a = batch_args(ctx, nq, max_n);
     LaunchHook* hook = ctx->profiling ? &ctx->hook : nullptr;
+    if (ctx->profiling) ctx->hook.mark(ctx->stream);
     int launches = 0;
     if (!host_path) {
         CK(ctx, enqueue_stage_device(a, d_card, d_edges, ctx->stream, hook));
@@ -585,7 +725,7 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
         CK(ctx, cudaEventRecord(ctx->recs[ri].t0, ctx->stream));
     }
     int pl = 0;
-    rc = run_pipeline(ctx, a, bp, key, &pl);
+    rc = run_pipeline(ctx, lanes, key, &pl);
     if (rc != MPDP_OK) {
         if (ri >= 0) ctx->recs[ri].in_use = false;
         return rc;
@@ -704,6 +844,11 @@ void mpdp_destroy(mpdp_ctx* ctx)
     if (ctx->var) cudaFree(ctx->var);
     if (ctx->fixed) cudaFree(ctx->fixed);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    for (int l = 0; l < MPDP_MAX_LANES; l++) {
+        if (ctx->lane_stream[l]) cudaStreamDestroy(ctx->lane_stream[l]);
+        if (ctx->join_ev[l]) cudaEventDestroy(ctx->join_ev[l]);
+    }
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     cudaGetLastError();
     delete ctx;
 }
@@ -716,6 +861,7 @@ int mpdp_set_config(mpdp_ctx* ctx, const mpdp_config* cfg)
     if (cfg->heavy_threshold < 0 || cfg->run_length < 1 || cfg->run_length > 32) return MPDP_ERR_INVALID_ARG;
     if (cfg->filter != MPDP_FILTER_BITMAPS && cfg->filter != MPDP_FILTER_UNRANK) return MPDP_ERR_INVALID_ARG;
     if (cfg->grid_blocks_per_sm < 1 || cfg->grid_blocks_per_sm > 32) return MPDP_ERR_INVALID_ARG;
+    if (cfg->lanes < 1 || cfg->lanes > MPDP_MAX_LANES) return MPDP_ERR_INVALID_ARG;
     ctx->cfg = *cfg;
     return MPDP_OK;
 }
@@ -764,14 +910,14 @@ static int validate_heuristic(const mpdp_query* q)
 {
     const int n = q->n_rels, m = q->n_edges;
     if (q->cost_model != MPDP_COST_COUT) return MPDP_ERR_INVALID_ARG;
-    if (q->mode != MPDP_MODE_IDP2 && q->mode != MPDP_MODE_UNIONDP && q->mode != MPDP_MODE_UNIONDP_LEARNED)
-        return MPDP_ERR_INVALID_ARG;
+    const bool idp = q->mode == MPDP_MODE_IDP2 || q->mode == MPDP_MODE_IDP2_LEARNED;
+    if (!idp && q->mode != MPDP_MODE_UNIONDP && q->mode != MPDP_MODE_UNIONDP_LEARNED) return MPDP_ERR_INVALID_ARG;
     if (n < 1 || m < 0 || (long long)m > (long long)n * (n - 1) / 2 || !q->card || (m > 0 && !q->edges))
         return MPDP_ERR_INVALID_ARG;
     if (n > MPDP_MAX_HEURISTIC_RELS) return MPDP_ERR_TOO_LARGE;
     if (q->k > 25) return MPDP_ERR_TOO_LARGE;
-    if (q->mode == MPDP_MODE_IDP2 && q->t != 0) return MPDP_ERR_INVALID_ARG;
-    if (q->mode != MPDP_MODE_IDP2 && (q->k < 2 || (q->t != 0 && (q->t < 2 || q->t > q->k))))
+    if (idp && q->t != 0) return MPDP_ERR_INVALID_ARG;
+    if (!idp && (q->k < 2 || (q->t != 0 && (q->t < 2 || q->t > q->k))))
         return MPDP_ERR_INVALID_ARG;
     for (int i = 0; i < n; i++)
         if (!finite_pos(q->card[i])) return MPDP_ERR_INVALID_ARG;
@@ -806,7 +952,6 @@ int mpdp_optimize(mpdp_ctx* ctx, const mpdp_query* q, int64_t* handle)
     if (!ctx || !q || !handle) return MPDP_ERR_INVALID_ARG;
     *handle = -1;
     if (q->mode == MPDP_MODE_EXACT) return mpdp_optimize_batch(ctx, q, 1, handle);
-    if (q->mode == MPDP_MODE_IDP2_LEARNED) return MPDP_ERR_NOT_IMPLEMENTED;
     const int vrc = validate_heuristic(q);
     if (vrc != MPDP_OK) return vrc;
     CK(ctx, cudaSetDevice(ctx->device));
@@ -904,7 +1049,7 @@ int mpdp_get_plan(mpdp_ctx* ctx, int64_t handle, mpdp_plan_node* nodes, int32_t 
             memset(st, 0, sizeof(*st));
             st->enumeration = MPDP_ENUM_BLOCKS;
             st->heavy_sets = (uint64_t)r.subproblems;  // exact sub-problems solved
-            st->filter_steps = r.learned_won ? 1 : 0;  // UnionDP-learned: the learned plan was kept
+            st->filter_steps = r.learned_won ? 1 : 0;  // learned modes: the learned plan was kept
         }
         return MPDP_OK;
     }
@@ -1024,42 +1169,71 @@ int mpdp_optimize_device(mpdp_ctx* ctx, int32_t n_rels, int32_t n_edges, const d
                                       d_status);
 }
 
-int mpdp_profile(mpdp_ctx* ctx, int enable)
+int mpdp_profile(mpdp_ctx* ctx, int mode)
 {
     if (!ctx) return MPDP_ERR_INVALID_ARG;
+    if (mode != MPDP_PROFILE_OFF && mode != MPDP_PROFILE_SERIAL && mode != MPDP_PROFILE_CONCURRENT)
+        return MPDP_ERR_INVALID_ARG;
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    ctx->profiling = enable != 0;
-    ctx->hook.recs.clear();
-    ctx->hook.next = 0;
+    ctx->profiling = mode;
+    ctx->hook.reset();
     return MPDP_OK;
 }
 
 int mpdp_profile_read(mpdp_ctx* ctx, double* ms, uint64_t* launches)
 {
-    if (!ctx || !ms || !launches) return MPDP_ERR_INVALID_ARG;
+    std::vector<double> active(MPDP_KC_COUNT);
+    return mpdp_profile_read_active(ctx, ms, active.data(), launches);
+}
+
+int mpdp_profile_read_active(mpdp_ctx* ctx, double* ms, double* active_ms, uint64_t* launches)
+{
+    if (!ctx || !ms || !active_ms || !launches) return MPDP_ERR_INVALID_ARG;
     for (int i = 0; i < MPDP_KC_COUNT; i++) {
         ms[i] = 0.0;
+        active_ms[i] = 0.0;
         launches[i] = 0;
     }
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));  // the lanes join back into it
     EventHook& h = ctx->hook;
     if (h.err != cudaSuccess) {
         ctx->last_error = std::string("profiling events: ") + cudaGetErrorString(h.err);
         h.err = cudaSuccess;
-        h.recs.clear();
-        h.next = 0;
+        h.reset();
         return MPDP_ERR_CUDA;
     }
-    for (auto& r : h.recs) {
+    // per (batch, class): launch intervals on the batch's time line
+    std::map<std::pair<int, int>, std::vector<std::pair<float, float>>> spans;
+    for (const auto& r : h.recs) {
         float t = 0.f;
-        CK(ctx, cudaEventElapsedTime(&t, h.pool[r.second], h.pool[r.second + 1]));
-        if (r.first >= 0 && r.first < MPDP_KC_COUNT) {
-            ms[r.first] += t;
-            launches[r.first] += 1;
+        CK(ctx, cudaEventElapsedTime(&t, h.pool[r.begin], h.pool[r.begin + 1]));
+        if (r.cls < 0 || r.cls >= MPDP_KC_COUNT) continue;
+        ms[r.cls] += t;
+        launches[r.cls] += 1;
+        if (r.group < 0) {
+            active_ms[r.cls] += t;
+            continue;
         }
+        float t0 = 0.f;
+        CK(ctx, cudaEventElapsedTime(&t0, h.pool[h.origins[r.group]], h.pool[r.begin]));
+        spans[{r.group, r.cls}].emplace_back(t0, t0 + t);
     }
-    h.recs.clear();
-    h.next = 0;
+    for (auto& kv : spans) {
+        auto& v = kv.second;
+        std::sort(v.begin(), v.end());
+        double total = 0.0, lo = v[0].first, hi = v[0].second;
+        for (size_t i = 1; i < v.size(); i++) {
+            if (v[i].first > hi) {
+                total += hi - lo;
+                lo = v[i].first;
+                hi = v[i].second;
+            } else if (v[i].second > hi) {
+                hi = v[i].second;
+            }
+        }
+        active_ms[kv.first.second] += total + (hi - lo);
+    }
+    h.reset();
     return MPDP_OK;
 }
 

@@ -168,6 +168,7 @@ struct BatchArgs {
     uint32_t* left;      // dense memo left[S]
     HashSlot* arena;     // hash memo slots
     HashLayout* layout;  // [nq]
+    unsigned long long arena_begin;  // hash memo: this batch's slots are [arena_begin, arena_slots)
     unsigned long long arena_slots;
     int run;             // ranks per lane in the filter (<= 32)
     int heavy_threshold;

@@ -181,7 +181,8 @@ public:
     }
 
     int goo(int& result);
-    int idp2(int k, int& result);
+    int learned_start(int& result);
+    int idp2(int k, int& result, bool learned = false);
     int uniondp(int k, int t, int& result);
     int scores(int m, const std::vector<int>& cur, const std::vector<std::pair<int, int>>& ij,
                const std::vector<XD>& sel, std::vector<float>& out);
@@ -275,11 +276,56 @@ int Heuristic::goo(int& result)
 }
 
 // --------------------------------------------------------------------------
+// Learned start for IDP2: the query's edges in ascending predicted score
+// (the share of the query under the edge's join in an optimal plan), each
+// joining the plans of its two ends when they are still apart (union-find):
+// the plan that joins first what the model expects an optimal plan to join
+// first.  Equal scores keep the edge order (min(u, v), max(u, v)).
+
+int Heuristic::learned_start(int& result)
+{
+    std::vector<int> cur(n_), plan(n_), parent(n_);
+    for (int r = 0; r < n_; r++) {
+        cur[r] = leaf(r);
+        plan[r] = cur[r];
+        parent[r] = r;
+    }
+    std::vector<std::pair<int, int>> ij;
+    std::vector<XD> sels;
+    for (const CutEdge& e : edges_) {
+        ij.push_back({e.u, e.v});
+        sels.push_back(xd_make(e.sel, 0));
+    }
+    std::vector<float> sc;
+    const int rc = scores(n_, cur, ij, sels, sc);
+    if (rc != MPDP_OK) return rc;
+    std::vector<int> order(ij.size());
+    for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sc[a] < sc[b]; });
+    auto find = [&](int x) {
+        while (parent[x] != x) x = parent[x] = parent[parent[x]];
+        return x;
+    };
+    int trees = n_;
+    for (int idx : order) {
+        const int a = find(ij[idx].first), b = find(ij[idx].second);
+        if (a == b) continue;
+        const int lo = std::min(a, b), hi = std::max(a, b);
+        plan[lo] = join(plan[lo], plan[hi]);
+        parent[hi] = lo;
+        trees--;
+    }
+    if (trees != 1) return MPDP_ERR_DISCONNECTED;
+    result = plan[find(0)];
+    return MPDP_OK;
+}
+
+// --------------------------------------------------------------------------
 // IDP2
 
-int Heuristic::idp2(int k, int& result)
+int Heuristic::idp2(int k, int& result, bool learned)
 {
-    int rc = goo(result);
+    int rc = learned ? learned_start(result) : goo(result);
     if (rc != MPDP_OK || k <= 1) return rc;
     // working tree: leaves hold plan nodes; internal nodes are joins of the
     // working tree whose cards are recomputed every round
@@ -640,6 +686,20 @@ int run_heuristic(const HeuristicQuery& q, XdExecutor& ex, cudaStream_t st, int 
             int learned = -1;
             h.model_ = q.model;
             rc = h.uniondp(q.k, t, learned);
+            h.model_ = nullptr;
+            if (rc == MPDP_OK && xd_less(h.nodes_[learned].cost, h.nodes_[root].cost)) {
+                root = learned;
+                res.learned_won = true;
+            }
+        }
+    } else if (q.mode == MPDP_MODE_IDP2_LEARNED) {
+        // IDP2 from the learned start, with IDP2 from GOO's plan as the
+        // fallback: the cheaper plan wins (GOO's on ties)
+        rc = h.idp2(q.k, root);
+        if (rc == MPDP_OK && q.model) {
+            int learned = -1;
+            h.model_ = q.model;
+            rc = h.idp2(q.k, learned, true);
             h.model_ = nullptr;
             if (rc == MPDP_OK && xd_less(h.nodes_[learned].cost, h.nodes_[root].cost)) {
                 root = learned;

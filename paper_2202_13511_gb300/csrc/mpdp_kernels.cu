@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter_bitmaps(BatchArgs a)
 __global__ void k_hash_layout(BatchArgs a)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    unsigned long long base = 0;
+    unsigned long long base = a.arena_begin;
     for (int qi = 0; qi < a.nq; qi++) {
         DevCounters* cnt = &a.out[qi].counters;
         HashLayout* lay = a.layout + qi;
@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(256) k_hash_clear(BatchArgs a)
     const unsigned long long total = a.layout[a.nq - 1].total_slots;
     const unsigned long long lim = total < a.arena_slots ? total : a.arena_slots;
     const double4_32a z = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < lim;
+    for (unsigned long long i = a.arena_begin + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < lim;
          i += (unsigned long long)gridDim.x * blockDim.x)
         reinterpret_cast<double4_32a*>(a.arena)[i] = z;
 }

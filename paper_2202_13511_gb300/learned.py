@@ -1,13 +1,14 @@
-"""Learned proposal for UnionDP (a project addition; the paper cites learned
-optimizers only as related work).
+"""Learned proposal for UnionDP and IDP2 (a project addition; the paper cites
+learned optimizers only as related work).
 
 A 3 x 256 MLP (mpdp_mlp_*: the library's own BF16 forward/backward kernels)
 scores every edge of a query graph with a prediction of how much of the query
 lies under that edge's join in an optimal plan.  UnionDP in
 MODE_UNIONDP_LEARNED then unites edges in ascending score, so the joins an
 optimal plan makes early stay inside partitions and the late ones become cut
-edges.  Plain UnionDP is the proposal's fallback: the optimizer costs both
-plans exactly and keeps the cheaper one.
+edges.  IDP2 in MODE_IDP2_LEARNED starts from the plan that joins the edges
+in ascending score instead of GOO's.  The plain heuristic is each proposal's
+fallback: the optimizer costs both plans exactly and keeps the cheaper one.
 
 Training data are exact MPDP plans of <= 25-relation queries: for an edge
 (u, v), the label is n_leaves(LCA(u, v)) / n, where LCA(u, v) is the plan
@@ -109,4 +110,18 @@ def evaluate(opt: "mpdp.Optimizer", mlp: "mpdp.Mlp", queries: Sequence, k: int =
         opt.set_model(None)
         idp2 = opt.optimize(q, mode=mpdp.MODE_IDP2, k=k).cost_xd
         rows.append((plain, learned, idp2))
+    return rows
+
+
+def evaluate_idp2(opt: "mpdp.Optimizer", mlp: "mpdp.Mlp", queries: Sequence, k: int = 25):
+    """Per query: costs of plain IDP2(k) (GOO start) and learned IDP2(k)
+    (learned start, plain IDP2 as its fallback)."""
+    rows = []
+    for q in queries:
+        opt.set_model(None)
+        plain = opt.optimize(q, mode=mpdp.MODE_IDP2, k=k).cost_xd
+        opt.set_model(mlp)
+        learned = opt.optimize(q, mode=mpdp.MODE_IDP2_LEARNED, k=k).cost_xd
+        opt.set_model(None)
+        rows.append((plain, learned))
     return rows

@@ -30,6 +30,7 @@ ERRORS = {
 ERR = {v: k for k, v in ERRORS.items()}
 
 MODE_EXACT, MODE_IDP2, MODE_UNIONDP, MODE_IDP2_LEARNED, MODE_UNIONDP_LEARNED = range(5)
+PROFILE_OFF, PROFILE_SERIAL, PROFILE_CONCURRENT = range(3)
 ENUM_AUTO, ENUM_TREE, ENUM_BLOCKS, ENUM_DPSUB = range(4)
 MEMO_DENSE, MEMO_HASH = range(2)
 FILTER_BITMAPS, FILTER_UNRANK = range(2)
@@ -80,7 +81,8 @@ class ConfigC(ctypes.Structure):
     _fields_ = [("memo_kind", ctypes.c_int32), ("enumeration", ctypes.c_int32),
                 ("heavy_threshold", ctypes.c_int32), ("use_ccc", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("run_length", ctypes.c_int32),
-                ("filter", ctypes.c_int32), ("grid_blocks_per_sm", ctypes.c_int32)]
+                ("filter", ctypes.c_int32), ("grid_blocks_per_sm", ctypes.c_int32),
+                ("lanes", ctypes.c_int32)]
 
 
 class ServerConfigC(ctypes.Structure):
@@ -100,7 +102,7 @@ EXPORTS = [
     "mpdp_workspace_bytes", "mpdp_optimize", "mpdp_optimize_batch", "mpdp_get_plan",
     "mpdp_release", "mpdp_optimize_device", "mpdp_sync", "mpdp_memo_lookup",
     "mpdp_last_launch_count", "mpdp_strerror", "mpdp_last_error", "mpdp_abi_version",
-    "mpdp_profile", "mpdp_profile_read", "mpdp_optimize_batch_device",
+    "mpdp_profile", "mpdp_profile_read", "mpdp_profile_read_active", "mpdp_optimize_batch_device",
     "mpdp_optimize_device_noalloc", "mpdp_get_plans", "mpdp_get_cost_xd",
     "mpdp_mlp_create", "mpdp_mlp_destroy", "mpdp_mlp_param_count", "mpdp_mlp_set_params",
     "mpdp_mlp_get_params", "mpdp_mlp_forward", "mpdp_mlp_gradients", "mpdp_mlp_train_step",
@@ -208,7 +210,9 @@ def load(build_if_missing: bool = True):
     L.mpdp_abi_version.restype = ctypes.c_int32
     L.mpdp_profile.argtypes = [c_ctx, ctypes.c_int]
     L.mpdp_profile_read.argtypes = [c_ctx, P(ctypes.c_double), P(ctypes.c_uint64)]
-    for f in ("mpdp_optimize_batch_device", "mpdp_profile", "mpdp_profile_read", "mpdp_create", "mpdp_set_config", "mpdp_get_config", "mpdp_optimize",
+    L.mpdp_profile_read_active.argtypes = [c_ctx, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_uint64)]
+    for f in ("mpdp_optimize_batch_device", "mpdp_profile", "mpdp_profile_read", "mpdp_profile_read_active",
+              "mpdp_create", "mpdp_set_config", "mpdp_get_config", "mpdp_optimize",
               "mpdp_optimize_batch", "mpdp_get_plan", "mpdp_release", "mpdp_optimize_device",
               "mpdp_sync", "mpdp_memo_lookup"):
         getattr(L, f).restype = ctypes.c_int
@@ -512,15 +516,19 @@ class Optimizer:
         return int(self._lib.mpdp_sync(self._ctx))
 
     # -- profiling ----------------------------------------------------------
-    def profile(self, enable: bool):
-        self._check(self._lib.mpdp_profile(self._ctx, int(bool(enable))), "mpdp_profile")
+    def profile(self, mode):
+        """PROFILE_OFF / PROFILE_SERIAL / PROFILE_CONCURRENT (True: serial)."""
+        self._check(self._lib.mpdp_profile(self._ctx, int(mode)), "mpdp_profile")
 
     def profile_read(self) -> Dict[str, Dict]:
-        """Per kernel class: summed device ms and launches since the last read."""
+        """Per kernel class since the last read: summed device ms of its
+        launches, their count, and active_ms, the wall time during which at
+        least one of them was in flight."""
         ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+        act = (ctypes.c_double * len(KERNEL_CLASSES))()
         ln = (ctypes.c_uint64 * len(KERNEL_CLASSES))()
-        self._check(self._lib.mpdp_profile_read(self._ctx, ms, ln), "mpdp_profile_read")
-        return {k: dict(ms=ms[i], launches=int(ln[i])) for i, k in enumerate(KERNEL_CLASSES)}
+        self._check(self._lib.mpdp_profile_read_active(self._ctx, ms, act, ln), "mpdp_profile_read_active")
+        return {k: dict(ms=ms[i], active_ms=act[i], launches=int(ln[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
 
 HIDDEN = 256

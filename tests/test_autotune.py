@@ -30,7 +30,7 @@ def test_coordinate_descent_keeps_start_on_ties():
 
 def test_relevant_space_drops_block_knobs_for_trees():
     trees = [W.snowflake(10, seed=s) for s in range(3)]
-    assert set(autotune.relevant_space(trees)) == {"grid_blocks_per_sm", "filter"}
+    assert set(autotune.relevant_space(trees)) == {"grid_blocks_per_sm", "filter", "lanes"}
     mixed = trees + [W.cyclic(10, seed=1)]
     assert set(autotune.relevant_space(mixed)) == set(autotune.KERNEL_SPACE)
 

@@ -105,7 +105,8 @@ def test_heuristic_errors(opt):
     for kw, code in ((dict(mode=mpdp.MODE_IDP2, k=26), "TOO_LARGE"),
                      (dict(mode=mpdp.MODE_UNIONDP, k=1), "INVALID_ARG"),
                      (dict(mode=mpdp.MODE_UNIONDP, k=10, t=11), "INVALID_ARG"),
-                     (dict(mode=mpdp.MODE_IDP2_LEARNED, k=10), "NOT_IMPLEMENTED")):
+                     (dict(mode=mpdp.MODE_IDP2_LEARNED, k=10, t=3), "INVALID_ARG"),
+                     (dict(mode=mpdp.MODE_IDP2_LEARNED, k=26), "TOO_LARGE")):
         with pytest.raises(mpdp.MPDPError) as ei:
             opt.optimize(q, **kw)
         assert ei.value.code == mpdp.ERR[code]

@@ -35,7 +35,7 @@ def opt():
 def set_cfg(opt, **kw):
     base = dict(memo_kind=mpdp.MEMO_DENSE, enumeration=mpdp.ENUM_AUTO, heavy_threshold=64,
                 use_ccc=1, use_graphs=1, run_length=32, filter=mpdp.FILTER_BITMAPS,
-                grid_blocks_per_sm=8)
+                grid_blocks_per_sm=8, lanes=4)
     base.update(kw)
     opt.set_config(**base)
 
@@ -208,6 +208,40 @@ def test_grid_sizes(opt, grid):
     set_cfg(opt, grid_blocks_per_sm=grid)
     for q in (W.snowflake(18, seed=6), W.cyclic(15, seed=4), W.clique(12, seed=2)):
         check(opt, q)
+    set_cfg(opt)
+
+
+@pytest.mark.parametrize("graphs", [1, 0])
+@pytest.mark.parametrize("memo", ["dense", "hash"])
+@pytest.mark.parametrize("lanes", [1, 2, 3, 8])
+def test_lanes(opt, lanes, memo, graphs):
+    """A batch run as concurrent sub-batches of consecutive queries (lanes):
+    every query's cost, plan and whole memo (read back for the queries of
+    every lane) equal the oracle's, whatever the lane count."""
+    set_cfg(opt, lanes=lanes, use_graphs=graphs,
+            memo_kind=mpdp.MEMO_DENSE if memo == "dense" else mpdp.MEMO_HASH)
+    qs = W.mixed_stream(11, seed=31, n_lo=3, n_hi=15)
+    refs = [oracle.dpccp(q) for q in qs]
+    hs = opt.submit_batch(qs)
+    try:
+        for q, h, ref in zip(qs, hs, refs):
+            sets = ref.connected_sets()
+            costs, lefts = opt.memo_lookup(h, sets)
+            assert np.array_equal(costs.view(np.uint64), ref.cost[sets].view(np.uint64))
+            assert np.array_equal(lefts, ref.left[sets].astype(np.uint64))
+    finally:
+        plans = opt.collect(hs)
+    for q, p, ref in zip(qs, plans, refs):
+        assert p.cost == ref.opt_cost
+        assert p.signature() == oracle.plan_signature(oracle.plan_from_memo(q, ref))
+    set_cfg(opt)
+
+
+def test_lanes_bad_config(opt):
+    for bad in (0, 9):
+        with pytest.raises(mpdp.MPDPError) as ei:
+            opt.set_config(lanes=bad)
+        assert ei.value.code == mpdp.ERR["INVALID_ARG"]
     set_cfg(opt)
 
 
