@@ -41,6 +41,11 @@ SMS, SCHEDULERS, LANES = 152, 4, 32
 OPS_PER_BITMAP_TREE = 2
 OPS_PER_BITMAP_GRAPH = 12
 OPS_PER_BFS_ROUND = 15
+# Connected-set unranking (tree join graphs, the default filter): per set
+# formed, the top search (5 steps of 3), one step per member and per child
+# considered (about 3 each, a mixed-radix digit about 20), and the output
+# (match, atomic, scan, store: about 10): 40 on average on the snowflakes.
+OPS_PER_CONNECTED_SET = 40
 # Algorithmic memo bytes: two lookups of (4-byte key + 8-byte cost) per CCP pair
 # and one 16-byte entry written per connected set.
 BYTES_PER_CCP = 24
@@ -338,6 +343,8 @@ def run_ours(args):
         "clocks": clocks,
         "roofline": roof,
         "kernel_share": kernel_share,
+        "kernel_active_ms_per_step": {k: round(v["active_ms"] / prof_steps, 4) for k, v in kc.items()
+                                      if v["launches"]},
     }
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(queries, args.cpu_sample_s)
@@ -404,7 +411,7 @@ def traffic_for(kind, measured):
     return t["bytes"] if kernel_fingerprint(t["kernel"]) == t["sha1"] else None
 
 
-def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False, serial=None):
+def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False, serial=None, filter_mode=2):
     """Roofline of the dominant kernel class.  `stats` are the per-query
     counters of one step's queries, `timing` the class's launches and active
     wall time over `prof_steps` steps with the lanes concurrent (the timed
@@ -417,8 +424,11 @@ def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False, serial=N
     if serial is not None and serial["launches"]:
         extra["avg_launch_ms_alone"] = serial["ms"] / serial["launches"]
     if kind == "filter":
-        ops = sum((OPS_PER_BITMAP_TREE if s["enumeration"] == 1 else OPS_PER_BITMAP_GRAPH) *
-                  int(s["sets_unranked"]) + OPS_PER_BFS_ROUND * int(s["filter_steps"])
+        def per_set(s):
+            if s["enumeration"] != 1:
+                return OPS_PER_BITMAP_GRAPH
+            return OPS_PER_CONNECTED_SET if filter_mode == 2 else OPS_PER_BITMAP_TREE
+        ops = sum(per_set(s) * int(s["sets_unranked"]) + OPS_PER_BFS_ROUND * int(s["filter_steps"])
                   for s in stats) * prof_steps / launches
         mhz = 2070.0
         peak = SMS * SCHEDULERS * LANES * mhz * 1e6 / 1e12
@@ -495,9 +505,10 @@ def shape_line(name, opt, torch, mpdp, W, peaks, reps=5):
 def ablation_line(opt, torch, mpdp, W):
     """The paper's relative claims on the same kernels: MPDP's block
     enumeration against DPSUB's vertex-based one (Sec. 6.2: far fewer pairs
-    evaluated), and Collaborative Context Collection on / off (Sec. 6.4);
-    and the batch split into 1/2/4/8 concurrent lanes.  Device time of one
-    batch (CUDA events, L2 flushed, mean of 3)."""
+    evaluated), Collaborative Context Collection on / off (Sec. 6.4), the
+    fusion of evaluate, prune and scatter on / off (Sec. 5), and the batch
+    split into 1/2/4/8 concurrent lanes.  Device time of one batch (CUDA
+    events, L2 flushed, mean of 3)."""
     import numpy as np
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -543,6 +554,13 @@ def ablation_line(opt, torch, mpdp, W):
         t_off, _, c_off = timed(qs, use_ccc=0, enumeration=mpdp.ENUM_BLOCKS)
         assert np.array_equal(c_on, c_off)
         out[f"ccc_{name}"] = {"ccc_on_ms": t_on, "ccc_off_ms": t_off, "gain": t_off / t_on}
+    # fusion of evaluate, prune and scatter (Sec. 5) on / off, tree mode
+    for name, qs in (("star20", [W.star(20, seed=0)]),
+                     ("snowflake20_x64", [W.snowflake(20, seed=i) for i in range(64)])):
+        t_on, _, c_on = timed(qs, fuse_prune=1, lanes=1)
+        t_off, _, c_off = timed(qs, fuse_prune=0, lanes=1)
+        assert np.array_equal(c_on, c_off)
+        out[f"fusion_{name}"] = {"fused_ms": t_on, "unfused_ms": t_off, "gain": t_off / t_on}
     # lanes: one device batch as concurrent sub-batches (a project addition)
     for name, qs in (("snowflake25_x64", [W.snowflake(25, seed=i) for i in range(64)]),
                      ("cyclic20_x64", [W.cyclic(20, seed=i) for i in range(64)])):

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define MPDP_ABI_VERSION 2
+#define MPDP_ABI_VERSION 4
 /* Exact mode uses 32-bit relation bitmaps; memory grows as 2^n (see
  * mpdp_workspace_bytes), so n is further capped by the memo budget. */
 #define MPDP_MAX_EXACT_RELS 30
@@ -99,9 +99,13 @@ enum { MPDP_MEMO_DENSE = 0, MPDP_MEMO_HASH = 1 };
  * with the combinatorial number system and stepped with the next bit
  * permutation (Sec. 5, "Unrank", "Filter").  BITMAPS: every bitmap below 2^n
  * is visited in index order (all levels at once, no unranking) and each
- * connected one goes straight into the list of its level.  Same sets and
- * counters. */
-enum { MPDP_FILTER_BITMAPS = 0, MPDP_FILTER_UNRANK = 1 };
+ * connected one goes straight into the list of its level.  CONNECTED
+ * (default): tree join graphs unrank their connected sets themselves (no
+ * disconnected set is ever formed); other join graphs as BITMAPS.  The same
+ * sets reach the level lists in every mode.  sets_unranked counts the sets of
+ * two or more relations each mode forms: 2^n - n - 1 for UNRANK and BITMAPS,
+ * the connected ones for CONNECTED on a tree. */
+enum { MPDP_FILTER_BITMAPS = 0, MPDP_FILTER_UNRANK = 1, MPDP_FILTER_CONNECTED = 2 };
 
 typedef struct mpdp_ctx mpdp_ctx; /* opaque, owned by the library */
 
@@ -145,7 +149,7 @@ typedef struct {
  * non-empty proper lb visits each of these twice).  ccp_pairs counts each
  * unordered CCP pair once. */
 typedef struct {
-    uint64_t sets_unranked;    /* k-subsets unranked, k = 2..n */
+    uint64_t sets_unranked;    /* sets of k = 2..n relations formed by the filter */
     uint64_t sets_connected;   /* connected sets, k = 2..n */
     uint64_t pairs_evaluated;
     uint64_t ccp_pairs;
@@ -174,7 +178,7 @@ typedef struct {
     int32_t use_graphs;       /* 1 (default): replay a captured CUDA graph per shape */
     int32_t run_length;       /* MPDP_FILTER_UNRANK: k-subsets unranked per lane
                                  (1..32, default 32) */
-    int32_t filter;           /* MPDP_FILTER_BITMAPS (default) or MPDP_FILTER_UNRANK */
+    int32_t filter;           /* MPDP_FILTER_CONNECTED (default), _BITMAPS or _UNRANK */
     int32_t grid_blocks_per_sm; /* evaluate grids: at most this many 256-thread
                                  blocks per SM (1..32, default 8) */
     int32_t lanes;            /* a device batch runs as up to this many
@@ -184,6 +188,12 @@ typedef struct {
                                  overlaps another's evaluation (memo-traffic
                                  bound); 1..MPDP_MAX_LANES, default 4.
                                  Results do not depend on it. */
+    int32_t fuse_prune;       /* 1 (default): tree-mode levels evaluate, prune
+                                 and scatter in one kernel.  0: an ablation of
+                                 that fusion (Sec. 5): one kernel writes every
+                                 CCP pair's (cost sum, left) to a buffer of
+                                 16 B x the largest level's sets x (k - 1),
+                                 a second prunes and scatters.  Same results. */
 } mpdp_config;
 
 /* Create a context on CUDA device `device`.  memo_budget_bytes caps the device

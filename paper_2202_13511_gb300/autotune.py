@@ -25,7 +25,7 @@ KERNEL_SPACE: Dict[str, List[int]] = {
     "grid_blocks_per_sm": [2, 4, 8, 16],
     "heavy_threshold": [16, 64, 256],
     "use_ccc": [0, 1],
-    "filter": [0, 1],  # MPDP_FILTER_BITMAPS, MPDP_FILTER_UNRANK
+    "filter": [2, 0, 1],  # MPDP_FILTER_CONNECTED, _BITMAPS, _UNRANK
     "lanes": [1, 2, 4, 8],
 }
 SERVER_SPACE: Dict[str, List[int]] = {
@@ -124,7 +124,7 @@ def tune_kernels(queries: Sequence, device: int = 0, reps: int = 3,
     Returns (config dict for Optimizer.set_config / Server kernel config,
     its time in seconds, the measured history)."""
     space = relevant_space(queries)
-    start = {"grid_blocks_per_sm": 8, "heavy_threshold": 64, "use_ccc": 1, "filter": 0, "lanes": 4}
+    start = {"grid_blocks_per_sm": 8, "heavy_threshold": 64, "use_ccc": 1, "filter": 2, "lanes": 4}
     start = {k: v for k, v in start.items() if k in space}
     own = measure is None
     if own:

@@ -27,7 +27,7 @@ using namespace mpdp;
 
 namespace {
 
-const mpdp_config kDefaultConfig = {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 1, 32, MPDP_FILTER_BITMAPS, 8, 4};
+const mpdp_config kDefaultConfig = {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 1, 32, MPDP_FILTER_CONNECTED, 8, 4, 1};
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -163,6 +163,8 @@ struct mpdp_ctx {
     double2* d_memo = nullptr;
     uint32_t* d_left = nullptr;
     HashSlot* d_arena = nullptr;
+    PairRec* d_pairs = nullptr;  // unfused ablation only
+    size_t pair_records = 0;
     // host side
     static constexpr int kRing = 4;
     StageSlot ring[kRing];
@@ -557,6 +559,35 @@ static int run_pipeline(mpdp_ctx* ctx, const std::vector<Lane>& lanes, const std
     return MPDP_OK;
 }
 
+// Unfused ablation: pair records for every lane (each lane its own range),
+// grown on demand inside the memo budget; a move invalidates the graphs.
+static int ensure_pairs(mpdp_ctx* ctx, std::vector<Lane>& lanes)
+{
+    size_t need = 0;
+    for (const Lane& ln : lanes) need += unfused_pair_records(ln.bp);
+    if (need > ctx->pair_records) {
+        if (ctx->var_bytes + fixed_bytes() + need * sizeof(PairRec) > ctx->budget) return MPDP_ERR_ADMISSION;
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        destroy_graphs(ctx);
+        if (ctx->d_pairs) cudaFree(ctx->d_pairs);
+        ctx->d_pairs = nullptr;
+        ctx->pair_records = 0;
+        if (cudaMalloc(&ctx->d_pairs, need * sizeof(PairRec)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->d_pairs = nullptr;
+            ctx->last_error = "cudaMalloc of the unfused pair buffer failed";
+            return MPDP_ERR_OOM;
+        }
+        ctx->pair_records = need;
+    }
+    size_t off = 0;
+    for (Lane& ln : lanes) {
+        ln.bp.pairs = ctx->d_pairs + off;
+        off += unfused_pair_records(ln.bp);
+    }
+    return MPDP_OK;
+}
+
 // Split queries [0, nq) into at most `lanes` runs of consecutive queries with
 // about equal sums of 2^n (the filter's work; the evaluation's grows with it
 // too).  Returns the run starts followed by nq.
@@ -619,10 +650,12 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
                             ctx->cfg.filter,
                             ctx->cfg.grid_blocks_per_sm,
                             ctx->cfg.enumeration,
+                            ctx->cfg.fuse_prune,
                             n_lanes};
     unsigned long long lbase = 0, mbase = 0, hbase = 0, abase = 0;
     uint32_t fblocks = 0;
     int max_n = 0, lane = 0, lane_max_n = 0;
+    unsigned long long conn_blocks = 0;  // k_filter_connected blocks the lane's tree queries could use
     std::vector<unsigned long long> h2d(nq, 0);
     for (int i = 0; i < nq; i++) {
         const PlanQuery& q = qs[i];
@@ -636,6 +669,7 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
             ln.a.arena_begin = abase;
             fblocks = 0;
             lane_max_n = 0;
+            conn_blocks = 0;
             lane++;
         }
         BatchPlan& bp = lanes[lane - 1].bp;
@@ -653,6 +687,11 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
         d.filter_block_base = fblocks;
         hp[i + lane - 1] = fblocks;  // the lane's own prefix: lane l's starts at q0 + l
         fblocks += qb;
+        if (ctx->cfg.filter == MPDP_FILTER_CONNECTED && q.m == q.n - 1 && q.n >= 2) {
+            // at most 2^(n-1) + n - 1 connected sets (a star): warps of 32 ranks, 8 per block
+            const unsigned long long warps = ((1ull << (q.n - 1)) + (unsigned long long)q.n + 31ull) / 32ull;
+            conn_blocks += (warps + kFilterThreads / 32 - 1) / (kFilterThreads / 32);
+        }
         const QuerySize z = query_size(q.n, q.enumeration, kind);
         d.heavy_base = hbase;
         d.heavy_cap = (uint32_t)z.heavy;
@@ -666,6 +705,8 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
             Lane& ln = lanes[lane - 1];
             hp[i + lane] = fblocks;
             bp.filter_blocks = fblocks;
+            const unsigned long long cap = (unsigned long long)ctx->num_sms * 8ull;  // grid-stride beyond
+            bp.connected_blocks = (uint32_t)(conn_blocks < cap ? conn_blocks : cap);
             const BatchArgs whole = batch_args(ctx, nq, max_n);
             const unsigned long long begin = ln.a.arena_begin;
             ln.a = batch_args(ctx, ln.q1 - ln.q0, lane_max_n);
@@ -690,6 +731,7 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
         }
         key.push_back(q.n);
         key.push_back(q.enumeration);
+        key.push_back(q.m == q.n - 1 ? 1 : 0);  // trees take another filter kernel
         if (host_path) {
             StagedQuery& sq = hs[i];
             sq.n = q.n;
@@ -699,6 +741,10 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
             for (int r = 0; r < kMaxRels; r++) sq.card[r] = r < q.n ? q.card[r] : 1.0;
             for (int e = 0; e < q.m; e++) sq.edges[e] = q.edges[e];
         }
+    }
+    if (!ctx->cfg.fuse_prune) {
+        rc = ensure_pairs(ctx, lanes);
+        if (rc != MPDP_OK) return rc;
     }
     CK(ctx, cudaMemcpyAsync(ctx->d_desc, hd, desc_bytes, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaMemcpyAsync(ctx->d_prefix, hp, pref_bytes, cudaMemcpyHostToDevice, ctx->stream));
@@ -844,6 +890,7 @@ void mpdp_destroy(mpdp_ctx* ctx)
     if (ctx->var) cudaFree(ctx->var);
     if (ctx->fixed) cudaFree(ctx->fixed);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->d_pairs) cudaFree(ctx->d_pairs);
     for (int l = 0; l < MPDP_MAX_LANES; l++) {
         if (ctx->lane_stream[l]) cudaStreamDestroy(ctx->lane_stream[l]);
         if (ctx->join_ev[l]) cudaEventDestroy(ctx->join_ev[l]);
@@ -859,9 +906,12 @@ int mpdp_set_config(mpdp_ctx* ctx, const mpdp_config* cfg)
     if (cfg->memo_kind != MPDP_MEMO_DENSE && cfg->memo_kind != MPDP_MEMO_HASH) return MPDP_ERR_INVALID_ARG;
     if (cfg->enumeration < MPDP_ENUM_AUTO || cfg->enumeration > MPDP_ENUM_DPSUB) return MPDP_ERR_INVALID_ARG;
     if (cfg->heavy_threshold < 0 || cfg->run_length < 1 || cfg->run_length > 32) return MPDP_ERR_INVALID_ARG;
-    if (cfg->filter != MPDP_FILTER_BITMAPS && cfg->filter != MPDP_FILTER_UNRANK) return MPDP_ERR_INVALID_ARG;
+    if (cfg->filter != MPDP_FILTER_BITMAPS && cfg->filter != MPDP_FILTER_UNRANK &&
+        cfg->filter != MPDP_FILTER_CONNECTED)
+        return MPDP_ERR_INVALID_ARG;
     if (cfg->grid_blocks_per_sm < 1 || cfg->grid_blocks_per_sm > 32) return MPDP_ERR_INVALID_ARG;
     if (cfg->lanes < 1 || cfg->lanes > MPDP_MAX_LANES) return MPDP_ERR_INVALID_ARG;
+    if (cfg->fuse_prune != 0 && cfg->fuse_prune != 1) return MPDP_ERR_INVALID_ARG;
     ctx->cfg = *cfg;
     return MPDP_OK;
 }

@@ -52,6 +52,16 @@ struct DevQuery {
     // its parent is low;  [10 + r] r's parent when it is a high relation,
     // else 0xffffffff;  [15] the relations whose parent is low.
     uint32_t lowrun[16];
+    // Connected-set unranking for tree join graphs (zero otherwise).  The
+    // connected sets whose top (the member nearest the root) is v are {v}
+    // with, for each child c of v, nothing or a connected set whose top is c:
+    // nsub[v] = prod over children c of (1 + nsub[c]) of them.  top_pref[v]
+    // = sum of nsub[u] for u < v, top_pref[n] = every connected set.
+    uint32_t chmask[kMaxRels];       // children of v in T
+    uint32_t nsub[kMaxRels];
+    uint32_t top_pref[kMaxRels + 1];
+    uint32_t leaves;                 // relations without children in T
+    uint32_t pad3[2];
 };
 
 // T[S] has one component per member of S whose T-parent is outside S, so

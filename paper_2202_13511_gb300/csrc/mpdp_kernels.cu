@@ -212,6 +212,29 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
             if (in) lowkids |= s_children[r];
         }
         q->lowrun[15] = lowkids;
+        // connected-set unranking tables (tree join graphs): nsub bottom-up
+        // over the discovery order; a subtree of t relations has at most
+        // 2^(t-1) connected sets with its root on top, so 32 bits suffice
+        const bool tree = status == 0 && m == n - 1;
+        uint32_t leaves = 0u;
+        for (int r = 0; r < kMaxRels; r++) {
+            q->chmask[r] = tree ? s_children[r] : 0u;
+            q->nsub[r] = 0u;
+            if (tree && r < n && s_children[r] == 0u) leaves |= 1u << r;
+        }
+        if (tree)
+            for (int i = cnt_order - 1; i >= 0; i--) {
+                const int v = order[i];
+                uint32_t prod = 1u;
+                for (uint32_t c = s_children[v]; c; c &= c - 1u) prod *= 1u + q->nsub[lowest(c)];
+                q->nsub[v] = prod;
+            }
+        uint32_t acc = 0u;
+        for (int r = 0; r <= kMaxRels; r++) {
+            q->top_pref[r] = acc;
+            if (tree && r < n) acc += q->nsub[r];
+        }
+        q->leaves = leaves;
         q->n = n;
         q->n_edges = status == 0 ? m : 0;
         q->is_tree = (status == 0 && m == n - 1) ? 1 : 0;
@@ -391,6 +414,111 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
     if (lane == 0 && done) {
         atomicAdd(&cnt->unranked, (unsigned long long)done);
         atomicAdd(&cnt->filter_steps, (unsigned long long)rounds);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a2 + a3 for tree join graphs (filter mode CONNECTED): the connected sets
+// themselves are unranked, so no disconnected set is ever formed.  A query's
+// ranks r < top_pref[n] cover its connected sets: the top is the v with
+// top_pref[v] <= r < top_pref[v + 1], and x = r - top_pref[v] < nsub[v]
+// decodes over v's children: the leaf children first, one bit of x each (in
+// or out, ascending), then every other child c in ascending order with digit
+// d = x mod (1 + nsub[c]), x /= 1 + nsub[c]; d = 0 leaves c's subtree out,
+// d > 0 takes c's connected set of rank d - 1, decoded the same way.
+__device__ __forceinline__ uint32_t unrank_connected(const DevQuery* __restrict__ q, int v, uint32_t x)
+{
+    uint8_t st_v[kMaxRels];
+    uint32_t st_x[kMaxRels];
+    int sp = 1;
+    st_v[0] = (uint8_t)v;
+    st_x[0] = x;
+    const uint32_t leaves = __ldg(&q->leaves);
+    uint32_t s = 0u;
+    while (sp > 0) {
+        --sp;
+        const int u = st_v[sp];
+        uint32_t r = st_x[sp];
+        s |= 1u << u;
+        const uint32_t ch = __ldg(&q->chmask[u]);
+        for (uint32_t c = ch & leaves; c; c &= c - 1u) {
+            if (r & 1u) s |= c & (0u - c);
+            r >>= 1;
+        }
+        for (uint32_t c = ch & ~leaves; c; c &= c - 1u) {
+            const int w = lowest(c);
+            const uint32_t radix = __ldg(&q->nsub[w]) + 1u;
+            const uint32_t dgt = r % radix;
+            r /= radix;
+            if (dgt) {
+                st_v[sp] = (uint8_t)w;
+                st_x[sp] = dgt - 1u;
+                sp++;
+            }
+        }
+    }
+    return s;
+}
+
+// Warps of 32 consecutive ranks of a tree query in mode CONNECTED (0 for
+// the other queries and after an error).
+__device__ __forceinline__ uint32_t connected_warps(const BatchArgs& a, int q)
+{
+    const DevQuery& dq = a.query[q];
+    if (a.out[q].counters.status != 0 || !dq.is_tree) return 0u;
+    return (dq.top_pref[dq.n] + 31u) / 32u;
+}
+
+// A warp takes 32 consecutive ranks of one query (grid-stride over all the
+// batch's warps of ranks); its sets of two or more relations go to their
+// level's list with one atomic per level present.
+__global__ void __launch_bounds__(kFilterThreads) k_filter_connected(BatchArgs a)
+{
+    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    const uint32_t items = block_prefix(a.nq, s_pref, [&](int q) { return connected_warps(a, q); });
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * (blockDim.x / 32);
+    int cur = -1;
+    unsigned long long formed = 0;
+    for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w < items; w += stride) {
+        const int qi = find_q(s_pref, a.nq, w);  // warp-uniform
+        if (qi != cur) {
+            if (cur >= 0) {
+                formed = warp_sum(formed);
+                if (lane == 0 && formed) atomicAdd(&a.out[cur].counters.unranked, formed);
+                formed = 0;
+            }
+            cur = qi;
+        }
+        const DevQuery* __restrict__ q = a.query + qi;
+        const int n = q->n;
+        const uint32_t r = (w - s_pref[qi]) * 32u + (uint32_t)lane;
+        uint32_t s = 0u;
+        if (r < __ldg(&q->top_pref[n])) {
+            int lo = 0, hi = n - 1;  // largest v with top_pref[v] <= r
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(&q->top_pref[mid]) <= r) lo = mid;
+                else hi = mid - 1;
+            }
+            s = unrank_connected(q, lo, r - __ldg(&q->top_pref[lo]));
+        }
+        const int lv = __popc(s);
+        const bool keep = lv >= 2;  // the empty set and single relations are not DP sets
+        const unsigned same = __match_any_sync(kFull, keep ? lv : 0);
+        const int leader = __ffs(same) - 1;
+        uint32_t base = 0u;
+        if (keep && lane == leader) base = atomicAdd(&a.out[qi].counters.list_count[lv], (uint32_t)__popc(same));
+        base = __shfl_sync(kFull, base, leader);
+        if (keep) {
+            const QDesc& d = a.desc[qi];
+            a.lists[d.list_base + d.list_off[lv] + base + __popc(same & ((1u << lane) - 1u))] = s;
+            formed++;
+        }
+    }
+    if (cur >= 0) {
+        formed = warp_sum(formed);
+        if (lane == 0 && formed) atomicAdd(&a.out[cur].counters.unranked, formed);
     }
 }
 
@@ -736,6 +864,111 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
         if ((threadIdx.x & 31) == 0 && sets) {
             atomicAdd(&a.out[cur].counters.evaluated[k], sets * (unsigned long long)(k - 1));
             atomicAdd(&a.out[cur].counters.ccp[k], sets * (unsigned long long)(k - 1));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Ablation of the fusion (Sec. 5: evaluate and prune in one kernel): the same
+// tree-mode work as k_eval_tree in two kernels.  The first writes every CCP
+// pair's (x, left) to global memory, slot (tile * 256 + thread) * (k - 1) + i;
+// the second reads a set's k - 1 records back, keeps the (x, left) minimum,
+// computes card(S) and writes the memo.  Same tiles, same results.
+template <class Memo>
+__global__ void __launch_bounds__(kEvalThreads) k_eval_tree_pairs(BatchArgs a, int k, Memo memo,
+                                                                  PairRec* __restrict__ pairs)
+{
+    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
+    memo.setup(s_memo);
+    const uint32_t tiles = block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, MPDP_ENUM_TREE); });
+    int cur = -1;
+    unsigned long long sets = 0;
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int qi = find_q(s_pref, a.nq, t);
+        if (qi != cur) {
+            if (cur >= 0) {
+                sets = warp_sum(sets);
+                if ((threadIdx.x & 31) == 0 && sets) {
+                    atomicAdd(&a.out[cur].counters.evaluated[k], sets * (unsigned long long)(k - 1));
+                    atomicAdd(&a.out[cur].counters.ccp[k], sets * (unsigned long long)(k - 1));
+                }
+                sets = 0;
+            }
+            memo.bind(a, qi);
+            cur = qi;
+        }
+        const DevQuery* __restrict__ q = a.query + qi;
+        DevCounters* cnt = &a.out[qi].counters;
+        const uint32_t idx = (t - s_pref[qi]) * kEvalThreads + threadIdx.x;
+        if (idx < cnt->list_count[k]) {
+            const QDesc& d = a.desc[qi];
+            const uint32_t s = a.lists[d.list_base + d.list_off[k] + idx];
+            uint32_t t2 = s;
+            int top = lowest(t2);
+            while ((__ldg(&q->desc[top]) & s) != s) {
+                t2 &= t2 - 1u;
+                top = lowest(t2);
+            }
+            PairRec* out = pairs + ((unsigned long long)t * kEvalThreads + threadIdx.x) * (unsigned long long)(k - 1);
+            uint32_t rest = s & ~(1u << top);
+            for (int i = 1; i < k; i++) {
+                const int v = lowest(rest);
+                rest &= rest - 1u;
+                const uint32_t sl = __ldg(&q->desc[v]) & s;
+                unsigned long long bx = kNoX;
+                uint32_t bl = kFull;
+                fold_pair(sl, s ^ sl, memo, cnt, bx, bl);  // one pair: its own (x, left)
+                out[i - 1].x = bx;
+                out[i - 1].left = bl;
+            }
+            sets++;
+        }
+    }
+    if (cur >= 0) {
+        sets = warp_sum(sets);
+        if ((threadIdx.x & 31) == 0 && sets) {
+            atomicAdd(&a.out[cur].counters.evaluated[k], sets * (unsigned long long)(k - 1));
+            atomicAdd(&a.out[cur].counters.ccp[k], sets * (unsigned long long)(k - 1));
+        }
+    }
+}
+
+template <class Memo>
+__global__ void __launch_bounds__(kEvalThreads) k_prune_tree(BatchArgs a, int k, Memo memo,
+                                                             const PairRec* __restrict__ pairs)
+{
+    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
+    memo.setup(s_memo);
+    const uint32_t tiles = block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, MPDP_ENUM_TREE); });
+    int cur = -1;
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int qi = find_q(s_pref, a.nq, t);
+        if (qi != cur) {
+            memo.bind(a, qi);
+            cur = qi;
+        }
+        const DevQuery* __restrict__ q = a.query + qi;
+        DevCounters* cnt = &a.out[qi].counters;
+        const uint32_t idx = (t - s_pref[qi]) * kEvalThreads + threadIdx.x;
+        if (idx < cnt->list_count[k]) {
+            const QDesc& d = a.desc[qi];
+            const uint32_t s = a.lists[d.list_base + d.list_off[k] + idx];
+            const int pv = tree_peel_vertex(s, q->adj);
+            const double pbase = peel_base(s, pv, *q, memo, cnt);
+            const PairRec* in = pairs + ((unsigned long long)t * kEvalThreads + threadIdx.x) * (unsigned long long)(k - 1);
+            unsigned long long bx = kNoX;
+            uint32_t bl = kFull;
+            for (int i = 0; i < k - 1; i++) {
+                const PairRec r = in[i];
+                if (better_x(r.x, r.left, bx, bl)) {
+                    bx = r.x;
+                    bl = r.left;
+                }
+            }
+            const double card_s = peel_finish(pbase, s, pv, *q);
+            memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
         }
     }
 }
@@ -1185,6 +1418,16 @@ size_t hash_arena_slots(int n)
     return (size_t)total;
 }
 
+unsigned long long unfused_pair_records(const BatchPlan& bp)
+{
+    unsigned long long most = 0;
+    for (int k = 2; k < kLevels; k++) {
+        const unsigned long long r = bp.tree_tiles[k] * (unsigned long long)kEvalThreads * (unsigned long long)(k - 1);
+        if (r > most) most = r;
+    }
+    return most;
+}
+
 void fill_levels(QDesc& d, int run, int filter_mode, uint32_t& filter_blocks)
 {
     const int n = d.n;
@@ -1200,7 +1443,9 @@ void fill_levels(QDesc& d, int run, int filter_mode, uint32_t& filter_blocks)
     }
     for (int k = (n >= 2 ? n + 1 : 0); k <= kLevels; k++) d.warp_begin[k] = (uint32_t)wb;
     const unsigned warps_per_block = kFilterThreads / 32;
-    if (filter_mode == MPDP_FILTER_BITMAPS)
+    if (filter_mode == MPDP_FILTER_CONNECTED && d.n_edges == n - 1)
+        filter_blocks = 0u;  // a tree: k_filter_connected
+    else if (filter_mode != MPDP_FILTER_UNRANK)
         filter_blocks = n >= 2 ? (uint32_t)(((1ull << n) + kBitmapsPerBlock - 1) / kBitmapsPerBlock) : 0u;
     else
         filter_blocks = (uint32_t)((wb + warps_per_block - 1) / warps_per_block);
@@ -1228,10 +1473,20 @@ static void launch_levels(const BatchArgs& a, const BatchPlan& bp, Memo memo, cu
     for (int k = 2; k <= a.max_n; k++) {
         const unsigned long long tree_tiles = bp.tree_tiles[k], block_tiles = bp.block_tiles[k];
         if (tree_tiles) {
-            HookScope hs(hook, MPDP_KC_EVAL, st);
             const int grid = (int)(tree_tiles < (unsigned long long)cap_blocks ? tree_tiles : cap_blocks);
-            k_eval_tree<Memo><<<grid, kEvalThreads, 0, st>>>(a, k, memo);
-            launches++;
+            if (bp.pairs) {
+                {
+                    HookScope hs(hook, MPDP_KC_EVAL, st);
+                    k_eval_tree_pairs<Memo><<<grid, kEvalThreads, 0, st>>>(a, k, memo, bp.pairs);
+                }
+                HookScope hs(hook, MPDP_KC_EVAL, st);
+                k_prune_tree<Memo><<<grid, kEvalThreads, 0, st>>>(a, k, memo, bp.pairs);
+                launches += 2;
+            } else {
+                HookScope hs(hook, MPDP_KC_EVAL, st);
+                k_eval_tree<Memo><<<grid, kEvalThreads, 0, st>>>(a, k, memo);
+                launches++;
+            }
         }
         if (block_tiles) {
             {
@@ -1263,13 +1518,18 @@ cudaError_t enqueue_pipeline(const BatchArgs& a, const BatchPlan& bp, int memo_k
         k_ingest<<<a.nq, 256, 0, st>>>(a, dense ? 1 : 0);
     }
     launches++;
+    if (bp.connected_blocks > 0) {
+        HookScope hs(hook, MPDP_KC_FILTER, st);
+        k_filter_connected<<<bp.connected_blocks, kFilterThreads, 0, st>>>(a);
+        launches++;
+    }
     if (bp.filter_blocks > 0) {
         HookScope hs(hook, MPDP_KC_FILTER, st);
-        if (a.filter_mode == MPDP_FILTER_BITMAPS) {
-            k_filter_bitmaps<<<bp.filter_blocks, kFilterThreads, 0, st>>>(a);
+        if (a.filter_mode == MPDP_FILTER_UNRANK) {
+            k_filter<<<bp.filter_blocks, kFilterThreads, 0, st>>>(a);
             launches++;
         } else {
-            k_filter<<<bp.filter_blocks, kFilterThreads, 0, st>>>(a);
+            k_filter_bitmaps<<<bp.filter_blocks, kFilterThreads, 0, st>>>(a);
             launches++;
         }
     }

@@ -12,10 +12,20 @@
 namespace mpdp {
 
 // Grid sizing of one batch, computed on the host from the queries' sizes.
+// One evaluated CCP pair of the unfused ablation path: (x, left) as the
+// fused kernels fold them (x = bit pattern of cost(S_l) + cost(S_r)).
+struct PairRec {
+    unsigned long long x;
+    uint32_t left;
+    uint32_t pad;
+};
+
 struct BatchPlan {
     int num_sms = 152;
     int blocks_per_sm = 8;  // eval grids: 8 x 256 threads = a full SM's worth of warps
-    uint32_t filter_blocks = 0;
+    uint32_t filter_blocks = 0;     // bitmap / unrank filter blocks
+    uint32_t connected_blocks = 0;  // k_filter_connected grid (tree queries in mode CONNECTED)
+    PairRec* pairs = nullptr;  // non-null: tree levels run unfused (evaluate, then prune + scatter)
     unsigned long long tree_tiles[kLevels] = {};   // upper bound of level-k tiles, tree queries
     unsigned long long block_tiles[kLevels] = {};  // same, block-mode queries
     unsigned long long block_sets[kLevels] = {};   // upper bound of level-k heavy tiles (8 chunks), block-mode queries
@@ -30,6 +40,9 @@ struct LaunchHook {
 };
 
 unsigned long long binom_host(int n, int k);
+// Pair records the unfused tree path needs for a plan: the largest level's
+// tiles x 256 sets x (k - 1) pairs.
+unsigned long long unfused_pair_records(const BatchPlan& bp);
 size_t list_entries(int n);
 size_t hash_arena_slots(int n);
 // Per-level list offsets and filter warp ranges of one query; returns the

@@ -33,7 +33,7 @@ MODE_EXACT, MODE_IDP2, MODE_UNIONDP, MODE_IDP2_LEARNED, MODE_UNIONDP_LEARNED = r
 PROFILE_OFF, PROFILE_SERIAL, PROFILE_CONCURRENT = range(3)
 ENUM_AUTO, ENUM_TREE, ENUM_BLOCKS, ENUM_DPSUB = range(4)
 MEMO_DENSE, MEMO_HASH = range(2)
-FILTER_BITMAPS, FILTER_UNRANK = range(2)
+FILTER_BITMAPS, FILTER_UNRANK, FILTER_CONNECTED = range(3)
 MAX_LEVELS = 33
 
 
@@ -82,7 +82,7 @@ class ConfigC(ctypes.Structure):
                 ("heavy_threshold", ctypes.c_int32), ("use_ccc", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("run_length", ctypes.c_int32),
                 ("filter", ctypes.c_int32), ("grid_blocks_per_sm", ctypes.c_int32),
-                ("lanes", ctypes.c_int32)]
+                ("lanes", ctypes.c_int32), ("fuse_prune", ctypes.c_int32)]
 
 
 class ServerConfigC(ctypes.Structure):
@@ -768,7 +768,7 @@ def optimize_device_noalloc(n: int, n_edges: int, d_card, d_edges, d_nodes, d_co
 
 def workspace_bytes(n: int, memo_kind: int = MEMO_DENSE) -> int:
     L = load()
-    c = ConfigC(memo_kind, 0, 64, 1, 1, 32, FILTER_BITMAPS)
+    c = ConfigC(memo_kind, 0, 64, 1, 1, 32, FILTER_CONNECTED, 8, 4, 1)
     return int(L.mpdp_workspace_bytes(n, ctypes.byref(c)))
 
 

@@ -22,6 +22,9 @@ CONFIGS = {
     "unrank_auto": dict(filter=mpdp.FILTER_UNRANK),
     "unrank_hash_blocks": dict(filter=mpdp.FILTER_UNRANK, memo_kind=mpdp.MEMO_HASH,
                                enumeration=mpdp.ENUM_BLOCKS),
+    "bitmaps_auto": dict(filter=mpdp.FILTER_BITMAPS),
+    "dense_unfused": dict(fuse_prune=0),
+    "hash_unfused": dict(memo_kind=mpdp.MEMO_HASH, fuse_prune=0),
 }
 
 
@@ -34,8 +37,8 @@ def opt():
 
 def set_cfg(opt, **kw):
     base = dict(memo_kind=mpdp.MEMO_DENSE, enumeration=mpdp.ENUM_AUTO, heavy_threshold=64,
-                use_ccc=1, use_graphs=1, run_length=32, filter=mpdp.FILTER_BITMAPS,
-                grid_blocks_per_sm=8, lanes=4)
+                use_ccc=1, use_graphs=1, run_length=32, filter=mpdp.FILTER_CONNECTED,
+                grid_blocks_per_sm=8, lanes=4, fuse_prune=1)
     base.update(kw)
     opt.set_config(**base)
 
@@ -56,7 +59,11 @@ def check(opt, q, ref=None, memo="all", sample=20000, block_counts=None):
         n = q.n
         assert np.array_equal(st["connected_per_level"][2:], ref.connected[2:n + 1])
         assert np.array_equal(st["ccp_per_level"][2:], ref.ccp[2:n + 1])
-        assert st["sets_unranked"] == 2 ** n - n - 1
+        if opt.get_config()["filter"] == mpdp.FILTER_CONNECTED and is_tree(q):
+            # tree join graph: only its connected sets are ever formed
+            assert st["sets_unranked"] == int(np.sum(ref.connected[2:n + 1]))
+        else:
+            assert st["sets_unranked"] == 2 ** n - n - 1
         tree_mode = st["enumeration"] == mpdp.ENUM_TREE
         if tree_mode:
             assert np.array_equal(st["evaluated_per_level"], st["ccp_per_level"])
@@ -113,11 +120,11 @@ def test_clique_14(opt, cfg):
 @pytest.mark.parametrize("n", [20, 25])
 def test_snowflake_full_size(opt, n):
     """Config: acyclic snowflake queries of 20 and 25 relations (tree mode),
-    with both connected-set filters."""
+    with all three connected-set filters."""
     for seed in range(3):
         q = W.snowflake(n, seed=seed)
         ref = oracle.dpccp(q)
-        for flt in (mpdp.FILTER_BITMAPS, mpdp.FILTER_UNRANK):
+        for flt in (mpdp.FILTER_CONNECTED, mpdp.FILTER_BITMAPS, mpdp.FILTER_UNRANK):
             set_cfg(opt, filter=flt)
             check(opt, q, ref, memo="sample")
 
@@ -237,10 +244,25 @@ def test_lanes(opt, lanes, memo, graphs):
     set_cfg(opt)
 
 
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_unfused_ablation(opt, lanes):
+    """The unfused tree path (pairs to a buffer, then prune + scatter) gives
+    the fused path's costs, plans and memo at full tree sizes."""
+    set_cfg(opt, fuse_prune=0, lanes=lanes)
+    for q in (W.snowflake(20, seed=5), W.star(16, seed=2), W.chain(22, seed=1)):
+        check(opt, q, memo="sample")
+    qs = [W.snowflake(18, seed=s) for s in range(6)]
+    for q, p in zip(qs, opt.optimize_batch(qs)):
+        ref = oracle.dpccp(q)
+        assert p.cost == ref.opt_cost
+        assert p.signature() == oracle.plan_signature(oracle.plan_from_memo(q, ref))
+    set_cfg(opt)
+
+
 def test_lanes_bad_config(opt):
-    for bad in (0, 9):
+    for kw in (dict(lanes=0), dict(lanes=9), dict(fuse_prune=2)):
         with pytest.raises(mpdp.MPDPError) as ei:
-            opt.set_config(lanes=bad)
+            opt.set_config(**kw)
         assert ei.value.code == mpdp.ERR["INVALID_ARG"]
     set_cfg(opt)
 
@@ -266,15 +288,19 @@ def test_max_size_chain(opt):
     assert plan.stats["ccp_pairs"] == (28 ** 3 - 28) // 6
 
 
-def test_max_size_30_counts(opt):
-    """n = 30, the exact-mode maximum: closed-form counts on a chain."""
-    set_cfg(opt)
+@pytest.mark.parametrize("filt", ["connected", "bitmaps"])
+def test_max_size_30_counts(opt, filt):
+    """n = 30, the exact-mode maximum: closed-form counts on a chain.  The
+    bitmap sweep forms every one of the 2^30 - 31 sets of two or more
+    relations; the connected-set unranking forms only the connected ones."""
+    set_cfg(opt, filter=mpdp.FILTER_CONNECTED if filt == "connected" else mpdp.FILTER_BITMAPS)
     q = W.chain(30, seed=0)
     plan = opt.optimize(q)
     assert plan.stats["sets_connected"] == 30 * 31 // 2 - 30
     assert plan.stats["ccp_pairs"] == (30 ** 3 - 30) // 6
-    assert plan.stats["sets_unranked"] == 2 ** 30 - 31
+    assert plan.stats["sets_unranked"] == (2 ** 30 - 31 if filt == "bitmaps" else 30 * 31 // 2 - 30)
     assert len(plan.nodes) == 59
+    set_cfg(opt)
 
 
 def test_single_relation(opt):

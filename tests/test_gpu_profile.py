@@ -21,7 +21,9 @@ def test_profile_modes():
             got[mode] = o.profile_read()
             o.profile(mpdp.PROFILE_OFF)
         s, c = got[mpdp.PROFILE_SERIAL], got[mpdp.PROFILE_CONCURRENT]
-        assert s["filter"]["launches"] == 4  # one filter launch per lane
+        # per lane one filter launch per kind present: the connected-set
+        # unranking for the trees, the bitmap sweep for the cyclic queries
+        assert 4 <= s["filter"]["launches"] <= 8
         for k in s:
             assert s[k]["launches"] == c[k]["launches"]
             assert s[k]["active_ms"] == pytest.approx(s[k]["ms"], rel=1e-3, abs=1e-3)
