@@ -100,11 +100,11 @@ enum { MPDP_MEMO_DENSE = 0, MPDP_MEMO_HASH = 1 };
  * permutation (Sec. 5, "Unrank", "Filter").  BITMAPS: every bitmap below 2^n
  * is visited in index order (all levels at once, no unranking) and each
  * connected one goes straight into the list of its level.  CONNECTED
- * (default): tree join graphs unrank their connected sets themselves (no
- * disconnected set is ever formed); other join graphs as BITMAPS.  The same
- * sets reach the level lists in every mode.  sets_unranked counts the sets of
- * two or more relations each mode forms: 2^n - n - 1 for UNRANK and BITMAPS,
- * the connected ones for CONNECTED on a tree. */
+ * (default): a tree join graph whose connected sets number at most 2^n / 4
+ * unranks them themselves (no disconnected set is ever formed); other
+ * queries as BITMAPS.  The same sets reach the level lists in every mode.
+ * sets_unranked counts the sets of two or more relations the filter forms:
+ * 2^n - n - 1 for a sweep, the connected ones for the unranking. */
 enum { MPDP_FILTER_BITMAPS = 0, MPDP_FILTER_UNRANK = 1, MPDP_FILTER_CONNECTED = 2 };
 
 typedef struct mpdp_ctx mpdp_ctx; /* opaque, owned by the library */

@@ -704,7 +704,12 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
         if (i + 1 == bounds[lane]) {  // last query of the lane
             Lane& ln = lanes[lane - 1];
             hp[i + lane] = fblocks;
-            bp.filter_blocks = fblocks;
+            // the bitmap sweep strides over the blocks the device assigns it
+            // (trees may go to the connected-set unranking): one resident
+            // wave of 6 blocks per SM; the unranking filter maps blocks to
+            // queries by this prefix and takes all of them
+            const uint32_t sweep_cap = (uint32_t)ctx->num_sms * 6u;
+            bp.filter_blocks = (ctx->cfg.filter == MPDP_FILTER_UNRANK || fblocks < sweep_cap) ? fblocks : sweep_cap;
             const unsigned long long cap = (unsigned long long)ctx->num_sms * 8ull;  // grid-stride beyond
             bp.connected_blocks = (uint32_t)(conn_blocks < cap ? conn_blocks : cap);
             const BatchArgs whole = batch_args(ctx, nq, max_n);

@@ -61,7 +61,8 @@ struct DevQuery {
     uint32_t nsub[kMaxRels];
     uint32_t top_pref[kMaxRels + 1];
     uint32_t leaves;                 // relations without children in T
-    uint32_t pad3[2];
+    uint32_t use_connected;          // filter CONNECTED chose unranking for this query
+    uint32_t pad3;
 };
 
 // T[S] has one component per member of S whose T-parent is outside S, so

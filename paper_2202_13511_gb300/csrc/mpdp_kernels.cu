@@ -235,6 +235,11 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
             if (tree && r < n) acc += q->nsub[r];
         }
         q->leaves = leaves;
+        // filter CONNECTED: unrank a tree's connected sets when they are at
+        // most a quarter of the 2^n bitmaps (forming a set costs a few times
+        // testing a bitmap); denser trees such as stars take the sweep
+        q->use_connected =
+            (a.filter_mode == MPDP_FILTER_CONNECTED && tree && 4ull * (unsigned long long)acc <= (1ull << n)) ? 1u : 0u;
         q->n = n;
         q->n_edges = status == 0 ? m : 0;
         q->is_tree = (status == 0 && m == n - 1) ? 1 : 0;
@@ -460,66 +465,79 @@ __device__ __forceinline__ uint32_t unrank_connected(const DevQuery* __restrict_
     return s;
 }
 
-// Warps of 32 consecutive ranks of a tree query in mode CONNECTED (0 for
-// the other queries and after an error).
-__device__ __forceinline__ uint32_t connected_warps(const BatchArgs& a, int q)
+// Ranks per thread and per block item of the connected-set filter.
+constexpr int kConnPerThread = 4;
+constexpr uint32_t kConnPerItem = kFilterThreads * kConnPerThread;
+
+// Items of kConnPerItem consecutive ranks of a tree query in mode CONNECTED
+// (0 for the other queries and after an error).
+__device__ __forceinline__ uint32_t connected_items(const BatchArgs& a, int q)
 {
     const DevQuery& dq = a.query[q];
-    if (a.out[q].counters.status != 0 || !dq.is_tree) return 0u;
-    return (dq.top_pref[dq.n] + 31u) / 32u;
+    if (a.out[q].counters.status != 0 || !dq.use_connected) return 0u;
+    return (dq.top_pref[dq.n] + kConnPerItem - 1u) / kConnPerItem;
 }
 
-// A warp takes 32 consecutive ranks of one query (grid-stride over all the
-// batch's warps of ranks); its sets of two or more relations go to their
-// level's list with one atomic per level present.
+// A block takes an item of kConnPerItem consecutive ranks of one query
+// (grid-stride over the batch's items); thread t decodes ranks
+// item * kConnPerItem + j * blockDim + t.  Places within the block come from
+// shared-memory counters per level, and one global atomic per level present
+// reserves the block's room in that level's list.
 __global__ void __launch_bounds__(kFilterThreads) k_filter_connected(BatchArgs a)
 {
     __shared__ uint32_t s_pref[kMaxBatch + 1];
-    const uint32_t items = block_prefix(a.nq, s_pref, [&](int q) { return connected_warps(a, q); });
-    const int lane = threadIdx.x & 31;
-    const uint32_t stride = gridDim.x * (blockDim.x / 32);
+    __shared__ uint32_t s_cnt[kLevels];
+    __shared__ uint32_t s_base[kLevels];
+    const uint32_t items = block_prefix(a.nq, s_pref, [&](int q) { return connected_items(a, q); });
+    const int tid = threadIdx.x;
     int cur = -1;
-    unsigned long long formed = 0;
-    for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w < items; w += stride) {
-        const int qi = find_q(s_pref, a.nq, w);  // warp-uniform
+    unsigned long long formed = 0;  // threads tid < kLevels: sets of level tid formed for query cur
+    for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int qi = find_q(s_pref, a.nq, it);  // block-uniform
         if (qi != cur) {
-            if (cur >= 0) {
-                formed = warp_sum(formed);
-                if (lane == 0 && formed) atomicAdd(&a.out[cur].counters.unranked, formed);
-                formed = 0;
-            }
+            if (cur >= 0 && tid < kLevels && formed) atomicAdd(&a.out[cur].counters.unranked, formed);
+            formed = 0;
             cur = qi;
         }
+        if (tid < kLevels) s_cnt[tid] = 0u;
+        __syncthreads();
         const DevQuery* __restrict__ q = a.query + qi;
         const int n = q->n;
-        const uint32_t r = (w - s_pref[qi]) * 32u + (uint32_t)lane;
-        uint32_t s = 0u;
-        if (r < __ldg(&q->top_pref[n])) {
-            int lo = 0, hi = n - 1;  // largest v with top_pref[v] <= r
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(&q->top_pref[mid]) <= r) lo = mid;
-                else hi = mid - 1;
+        const uint32_t total = __ldg(&q->top_pref[n]);
+        const uint32_t r0 = (it - s_pref[qi]) * kConnPerItem + (uint32_t)tid;
+        uint32_t sv[kConnPerThread], off[kConnPerThread];
+#pragma unroll 1
+        for (int j = 0; j < kConnPerThread; j++) {
+            const uint32_t r = r0 + (uint32_t)j * kFilterThreads;
+            uint32_t s = 0u;
+            if (r < total) {
+                int lo = 0, hi = n - 1;  // largest v with top_pref[v] <= r
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (__ldg(&q->top_pref[mid]) <= r) lo = mid;
+                    else hi = mid - 1;
+                }
+                s = unrank_connected(q, lo, r - __ldg(&q->top_pref[lo]));
             }
-            s = unrank_connected(q, lo, r - __ldg(&q->top_pref[lo]));
+            sv[j] = s;
+            const int lv = __popc(s);
+            off[j] = lv >= 2 ? atomicAdd(&s_cnt[lv], 1u) : 0u;  // the empty set and single relations are not DP sets
         }
-        const int lv = __popc(s);
-        const bool keep = lv >= 2;  // the empty set and single relations are not DP sets
-        const unsigned same = __match_any_sync(kFull, keep ? lv : 0);
-        const int leader = __ffs(same) - 1;
-        uint32_t base = 0u;
-        if (keep && lane == leader) base = atomicAdd(&a.out[qi].counters.list_count[lv], (uint32_t)__popc(same));
-        base = __shfl_sync(kFull, base, leader);
-        if (keep) {
-            const QDesc& d = a.desc[qi];
-            a.lists[d.list_base + d.list_off[lv] + base + __popc(same & ((1u << lane) - 1u))] = s;
-            formed++;
+        __syncthreads();
+        if (tid < kLevels) {
+            const uint32_t c = s_cnt[tid];
+            s_base[tid] = c ? atomicAdd(&a.out[qi].counters.list_count[tid], c) : 0u;
+            formed += c;
+        }
+        __syncthreads();
+        const QDesc& d = a.desc[qi];
+#pragma unroll
+        for (int j = 0; j < kConnPerThread; j++) {
+            const int lv = __popc(sv[j]);
+            if (lv >= 2) a.lists[d.list_base + d.list_off[lv] + s_base[lv] + off[j]] = sv[j];
         }
     }
-    if (cur >= 0) {
-        formed = warp_sum(formed);
-        if (lane == 0 && formed) atomicAdd(&a.out[cur].counters.unranked, formed);
-    }
+    if (cur >= 0 && tid < kLevels && formed) atomicAdd(&a.out[cur].counters.unranked, formed);
 }
 
 // ---------------------------------------------------------------------------
@@ -552,186 +570,212 @@ constexpr PopcMasks make_popc_masks()
 
 __device__ const PopcMasks kPopcMask = make_popc_masks();
 
-__global__ void __launch_bounds__(kFilterThreads) k_filter_bitmaps(BatchArgs a)
+// Items of kBitmapsPerBlock bitmaps of a query the bitmap sweep serves: all
+// queries but the trees whose connected sets are unranked directly.
+__device__ __forceinline__ uint32_t bitmap_items(const BatchArgs& a, int q)
 {
-    __shared__ uint32_t s_nbt[4][256];
-    __shared__ uint32_t s_ctt[4][256];
-    __shared__ uint32_t s_stage[kFilterThreads / 32][32];
-    __shared__ uint32_t s_run[16];     // DevQuery::lowrun
-    int lo = 0, hi = a.nq - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.filter_block_prefix[mid] <= blockIdx.x) lo = mid;
-        else hi = mid - 1;
-    }
-    const int qi = lo;
-    const QDesc& d = a.desc[qi];
-    const DevQuery* __restrict__ q = a.query + qi;
-    DevCounters* __restrict__ cnt = &a.out[qi].counters;
-    const bool is_tree = q->is_tree != 0;
-    for (int t = threadIdx.x; t < 4 * 256; t += blockDim.x) {
-        if (!is_tree) s_nbt[t >> 8][t & 255] = q->nbt[t >> 8][t & 255];
-        s_ctt[t >> 8][t & 255] = q->ctt[t >> 8][t & 255];
-    }
-    if (threadIdx.x < 16) s_run[threadIdx.x] = q->lowrun[threadIdx.x];
-    __syncthreads();
-    if (cnt->status != 0) return;
-    const int lane = threadIdx.x & 31;
-    const unsigned long long limit = 1ull << d.n;
-    uint32_t rounds = 0u, examined = 0u;
-    for (uint32_t rd = 0; rd < kFilterRounds; rd++) {
-        const unsigned long long base64 =
-            (((unsigned long long)(blockIdx.x - a.filter_block_prefix[qi]) * kFilterRounds + rd) * kFilterThreads +
-             threadIdx.x) *
-            kBitmapsPerThread;
-        if (base64 - (unsigned long long)lane * kBitmapsPerThread >= limit) break;  // warp-uniform
-        uint32_t flags = 0u;
-        const uint32_t base = (uint32_t)base64;
-        if (base64 < limit) {
-            const uint32_t c_run = s_ctt[0][base & 0xe0u] | s_ctt[1][(base >> 8) & 255u] |
-                                   s_ctt[2][(base >> 16) & 255u] | s_ctt[3][base >> 24];
-            if (is_tree) {
-                // Tree join graph: S is connected iff exactly one member's
-                // parent lies outside S.  Evaluated for the whole run at
-                // once, bit-sliced over i: `one` / `two` collect the runs'
-                // bitmaps with at least one / at least two such members.
-                // High members (bits >= 5) with a high parent outside the
-                // run's high part are a top in every bitmap of the run.
-                const uint32_t fixed = base & ~c_run & ~s_run[15];
-                if ((fixed & (fixed - 1u)) == 0u) {
-                    uint32_t one = fixed ? kFull : 0u, two = 0u;
-                    const uint32_t g = base & s_run[15];  // high members with a low parent
-#pragma unroll
-                    for (int p = 0; p < 5; p++) {
-                        const uint32_t gp = g & s_run[p];
-                        if (gp) {
-                            const uint32_t t = ~low_bit(p);  // a top unless p is in S
-                            two |= (one & t) | ((gp & (gp - 1u)) ? t : 0u);
-                            one |= t;
-                        }
-                    }
-#pragma unroll
-                    for (int r = 0; r < 5; r++) {
-                        const uint32_t hp = s_run[10 + r];
-                        const uint32_t t = (hp < 32u && (base >> hp & 1u)) ? 0u : s_run[5 + r];
-                        two |= one & t;
-                        one |= t;
-                    }
-                    flags = one & ~two;
-                }
-            } else {
-                const uint32_t n_run = s_nbt[0][base & 0xe0u] | s_nbt[1][(base >> 8) & 255u] |
-                                       s_nbt[2][(base >> 16) & 255u] | s_nbt[3][base >> 24];
-                for (uint32_t i = 0; i < kBitmapsPerThread; i++) {
-                    const uint32_t s = base | i;
-                    bool ok = __popc(s & ~(c_run | s_ctt[0][i])) == 1;
-                    if (!ok) ok = (s & ~(n_run | s_nbt[0][i])) == 0u && connected_rounds_from(s, s_nbt, rounds);
-                    if (ok) flags |= 1u << i;
-                }
-            }
-            uint32_t valid = 0xffffffffu;
-            if (limit - base64 < kBitmapsPerThread) valid = (1u << (uint32_t)(limit - base64)) - 1u;
-            if (__popc(base) <= 1)  // the empty set and single relations are not DP sets
-                for (uint32_t i = 0; i < kBitmapsPerThread; i++)
-                    if (__popc(base | i) < 2) valid &= ~(1u << i);
-            flags &= valid;
-            examined += __popc(valid);
-        }
-        // Ordered output straight into the level lists.  The warp covers the
-        // 1024 bitmaps w0 .. w0+1023 (w0 = its first bitmap), so bitmap
-        // base | i of lane l has level popc(w0) + popc(l) + popc(i): 11 level
-        // bins per warp.  Sets leave in bitmap order within each level.
-        if (!__any_sync(kFull, flags != 0u)) continue;
-        uint32_t fincl = (uint32_t)__popc(flags);
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t u = __shfl_up_sync(kFull, fincl, o);
-            if (lane >= o) fincl += u;
-        }
-        const uint32_t ftotal = __shfl_sync(kFull, fincl, 31);
-        const int pw = __popc((uint32_t)(base64 - (unsigned long long)lane * kBitmapsPerThread));
-        if (ftotal != 0u && ftotal <= 32u) {
-            // Sparse warp: compact its sets into one set per lane (bitmap
-            // order), then one ballot per level present places them.
-            uint32_t o = fincl - (uint32_t)__popc(flags), f = flags;
-            while (f) {
-                const int i = lowest(f);
-                f &= f - 1u;
-                s_stage[threadIdx.x >> 5][o++] = base | (uint32_t)i;
-            }
-            __syncwarp();
-            const bool has = (uint32_t)lane < ftotal;
-            const uint32_t sv = has ? s_stage[threadIdx.x >> 5][lane] : 0u;
-            const int lv = __popc(sv);
-            const int lb = has ? lv - pw : 0;  // level bin, 0..10
-            uint32_t present = __reduce_or_sync(kFull, has ? 1u << lb : 0u);
-            unsigned bin_mask = 0u;  // lane t <= 10: the lanes holding a set of bin t
-            while (present) {
-                const int t = lowest(present);
-                present &= present - 1u;
-                const unsigned m = __ballot_sync(kFull, has && lb == t);
-                if (lane == t) bin_mask = m;
-            }
-            // every bin reserves its list room at once: one atomic latency
-            uint32_t bpos = 0u;
-            if (bin_mask) bpos = atomicAdd(&cnt->list_count[pw + lane], (uint32_t)__popc(bin_mask));
-            const uint32_t b0 = __shfl_sync(kFull, bpos, lb);
-            const unsigned mm = __shfl_sync(kFull, bin_mask, lb);
-            if (has) a.lists[d.list_base + d.list_off[pw + lb] + b0 + __popc(mm & ((1u << lane) - 1u))] = sv;
-            __syncwarp();
-        } else if (ftotal != 0u) {
-            // Dense warp: a shuffle scan per level bin places every lane's sets
-            // and one atomic per non-empty bin reserves list room.
-            const int pl = __popc((uint32_t)lane);
-            uint32_t cj[6], ex[6];
-#pragma unroll
-            for (int j = 0; j < 6; j++) cj[j] = __popc(flags & kPopcMask.v[j]);
-            uint32_t my_total = 0u;
-#pragma unroll
-            for (int t = 0; t <= 10; t++) {
-                uint32_t v = 0u;
-#pragma unroll
-                for (int j = 0; j < 6; j++) v = (t - pl == j) ? cj[j] : v;
-                uint32_t incl = v;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t u = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += u;
-                }
-                const uint32_t tot = __shfl_sync(kFull, incl, 31);
-                if (lane == t) my_total = tot;
-#pragma unroll
-                for (int j = 0; j < 6; j++)
-                    if (t - pl == j) ex[j] = incl - v;
-            }
-            uint32_t bpos = 0u;
-            if (lane <= 10 && my_total) bpos = atomicAdd(&cnt->list_count[pw + lane], my_total);
-            uint32_t* lists = a.lists + d.list_base;
-            uint32_t start[6];
-#pragma unroll
-            for (int j = 0; j < 6; j++) start[j] = __shfl_sync(kFull, bpos, pl + j) + ex[j];
-            uint32_t f = flags;
-            while (f) {
-                const int i = lowest(f);
-                f &= f - 1u;
-                const int j = __popc((uint32_t)i);
-                uint32_t pos = 0u;
-#pragma unroll
-                for (int jj = 0; jj < 6; jj++)
-                    if (j == jj) pos = start[jj]++;
-                lists[d.list_off[pw + pl + j] + pos] = base | (uint32_t)i;
-            }
-        }
-    }
+    const DevQuery& dq = a.query[q];
+    if (a.out[q].counters.status != 0 || dq.use_connected || dq.n < 2) return 0u;
+    return (uint32_t)(((1ull << dq.n) + kBitmapsPerBlock - 1) / kBitmapsPerBlock);
+}
+
+__device__ __forceinline__ void flush_filter_counts(DevCounters* cnt, uint32_t& examined, uint32_t& rounds)
+{
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         examined += __shfl_xor_sync(kFull, examined, o);
         rounds += __shfl_xor_sync(kFull, rounds, o);
     }
-    if (lane == 0 && examined) {
+    if ((threadIdx.x & 31) == 0 && examined) {
         atomicAdd(&cnt->unranked, (unsigned long long)examined);
         if (rounds) atomicAdd(&cnt->filter_steps, (unsigned long long)rounds);
     }
+    examined = 0u;
+    rounds = 0u;
+}
+
+__global__ void __launch_bounds__(kFilterThreads, 6) k_filter_bitmaps(BatchArgs a)
+{
+    __shared__ uint32_t s_nbt[4][256];
+    __shared__ uint32_t s_ctt[4][256];
+    __shared__ uint32_t s_stage[kFilterThreads / 32][32];
+    __shared__ uint32_t s_run[16];     // DevQuery::lowrun
+    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    // items of kBitmapsPerBlock bitmaps of every query this filter serves,
+    // grid-stride; a block reloads the tables when its query changes
+    const uint32_t items = block_prefix(a.nq, s_pref, [&](int q) { return bitmap_items(a, q); });
+    const int lane = threadIdx.x & 31;
+    int cur = -1;
+    const QDesc* d = nullptr;
+    DevCounters* cnt = nullptr;
+    bool is_tree = false;
+    unsigned long long limit = 0;
+    uint32_t rounds = 0u, examined = 0u;
+    for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int qi = find_q(s_pref, a.nq, it);  // block-uniform
+        if (qi != cur) {
+            if (cur >= 0) flush_filter_counts(cnt, examined, rounds);
+            __syncthreads();  // every warp is done with the previous tables
+            const DevQuery* __restrict__ q = a.query + qi;
+            d = a.desc + qi;
+            cnt = &a.out[qi].counters;
+            is_tree = q->is_tree != 0;
+            for (int t = threadIdx.x; t < 4 * 256; t += blockDim.x) {
+                if (!is_tree) s_nbt[t >> 8][t & 255] = q->nbt[t >> 8][t & 255];
+                s_ctt[t >> 8][t & 255] = q->ctt[t >> 8][t & 255];
+            }
+            if (threadIdx.x < 16) s_run[threadIdx.x] = q->lowrun[threadIdx.x];
+            __syncthreads();
+            limit = 1ull << d->n;
+            cur = qi;
+        }
+        const uint32_t blk = it - s_pref[qi];
+        for (uint32_t rd = 0; rd < kFilterRounds; rd++) {
+            const unsigned long long base64 =
+                (((unsigned long long)blk * kFilterRounds + rd) * kFilterThreads +
+                 threadIdx.x) *
+                kBitmapsPerThread;
+            if (base64 - (unsigned long long)lane * kBitmapsPerThread >= limit) break;  // warp-uniform
+            uint32_t flags = 0u;
+            const uint32_t base = (uint32_t)base64;
+            if (base64 < limit) {
+                const uint32_t c_run = s_ctt[0][base & 0xe0u] | s_ctt[1][(base >> 8) & 255u] |
+                                       s_ctt[2][(base >> 16) & 255u] | s_ctt[3][base >> 24];
+                if (is_tree) {
+                    // Tree join graph: S is connected iff exactly one member's
+                    // parent lies outside S.  Evaluated for the whole run at
+                    // once, bit-sliced over i: `one` / `two` collect the runs'
+                    // bitmaps with at least one / at least two such members.
+                    // High members (bits >= 5) with a high parent outside the
+                    // run's high part are a top in every bitmap of the run.
+                    const uint32_t fixed = base & ~c_run & ~s_run[15];
+                    if ((fixed & (fixed - 1u)) == 0u) {
+                        uint32_t one = fixed ? kFull : 0u, two = 0u;
+                        const uint32_t g = base & s_run[15];  // high members with a low parent
+#pragma unroll
+                        for (int p = 0; p < 5; p++) {
+                            const uint32_t gp = g & s_run[p];
+                            if (gp) {
+                                const uint32_t t = ~low_bit(p);  // a top unless p is in S
+                                two |= (one & t) | ((gp & (gp - 1u)) ? t : 0u);
+                                one |= t;
+                            }
+                        }
+#pragma unroll
+                        for (int r = 0; r < 5; r++) {
+                            const uint32_t hp = s_run[10 + r];
+                            const uint32_t t = (hp < 32u && (base >> hp & 1u)) ? 0u : s_run[5 + r];
+                            two |= one & t;
+                            one |= t;
+                        }
+                        flags = one & ~two;
+                    }
+                } else {
+                    const uint32_t n_run = s_nbt[0][base & 0xe0u] | s_nbt[1][(base >> 8) & 255u] |
+                                           s_nbt[2][(base >> 16) & 255u] | s_nbt[3][base >> 24];
+                    for (uint32_t i = 0; i < kBitmapsPerThread; i++) {
+                        const uint32_t s = base | i;
+                        bool ok = __popc(s & ~(c_run | s_ctt[0][i])) == 1;
+                        if (!ok) ok = (s & ~(n_run | s_nbt[0][i])) == 0u && connected_rounds_from(s, s_nbt, rounds);
+                        if (ok) flags |= 1u << i;
+                    }
+                }
+                uint32_t valid = 0xffffffffu;
+                if (limit - base64 < kBitmapsPerThread) valid = (1u << (uint32_t)(limit - base64)) - 1u;
+                if (__popc(base) <= 1)  // the empty set and single relations are not DP sets
+                    for (uint32_t i = 0; i < kBitmapsPerThread; i++)
+                        if (__popc(base | i) < 2) valid &= ~(1u << i);
+                flags &= valid;
+                examined += __popc(valid);
+            }
+            // Ordered output straight into the level lists.  The warp covers the
+            // 1024 bitmaps w0 .. w0+1023 (w0 = its first bitmap), so bitmap
+            // base | i of lane l has level popc(w0) + popc(l) + popc(i): 11 level
+            // bins per warp.  Sets leave in bitmap order within each level.
+            if (!__any_sync(kFull, flags != 0u)) continue;
+            uint32_t fincl = (uint32_t)__popc(flags);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(kFull, fincl, o);
+                if (lane >= o) fincl += u;
+            }
+            const uint32_t ftotal = __shfl_sync(kFull, fincl, 31);
+            const int pw = __popc((uint32_t)(base64 - (unsigned long long)lane * kBitmapsPerThread));
+            if (ftotal != 0u && ftotal <= 32u) {
+                // Sparse warp: compact its sets into one set per lane (bitmap
+                // order), then one ballot per level present places them.
+                uint32_t o = fincl - (uint32_t)__popc(flags), f = flags;
+                while (f) {
+                    const int i = lowest(f);
+                    f &= f - 1u;
+                    s_stage[threadIdx.x >> 5][o++] = base | (uint32_t)i;
+                }
+                __syncwarp();
+                const bool has = (uint32_t)lane < ftotal;
+                const uint32_t sv = has ? s_stage[threadIdx.x >> 5][lane] : 0u;
+                const int lv = __popc(sv);
+                const int lb = has ? lv - pw : 0;  // level bin, 0..10
+                uint32_t present = __reduce_or_sync(kFull, has ? 1u << lb : 0u);
+                unsigned bin_mask = 0u;  // lane t <= 10: the lanes holding a set of bin t
+                while (present) {
+                    const int t = lowest(present);
+                    present &= present - 1u;
+                    const unsigned m = __ballot_sync(kFull, has && lb == t);
+                    if (lane == t) bin_mask = m;
+                }
+                // every bin reserves its list room at once: one atomic latency
+                uint32_t bpos = 0u;
+                if (bin_mask) bpos = atomicAdd(&cnt->list_count[pw + lane], (uint32_t)__popc(bin_mask));
+                const uint32_t b0 = __shfl_sync(kFull, bpos, lb);
+                const unsigned mm = __shfl_sync(kFull, bin_mask, lb);
+                if (has) a.lists[d->list_base + d->list_off[pw + lb] + b0 + __popc(mm & ((1u << lane) - 1u))] = sv;
+                __syncwarp();
+            } else if (ftotal != 0u) {
+                // Dense warp: a shuffle scan per level bin places every lane's sets
+                // and one atomic per non-empty bin reserves list room.
+                const int pl = __popc((uint32_t)lane);
+                uint32_t cj[6], ex[6];
+#pragma unroll
+                for (int j = 0; j < 6; j++) cj[j] = __popc(flags & kPopcMask.v[j]);
+                uint32_t my_total = 0u;
+#pragma unroll
+                for (int t = 0; t <= 10; t++) {
+                    uint32_t v = 0u;
+#pragma unroll
+                    for (int j = 0; j < 6; j++) v = (t - pl == j) ? cj[j] : v;
+                    uint32_t incl = v;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t u = __shfl_up_sync(kFull, incl, o);
+                        if (lane >= o) incl += u;
+                    }
+                    const uint32_t tot = __shfl_sync(kFull, incl, 31);
+                    if (lane == t) my_total = tot;
+#pragma unroll
+                    for (int j = 0; j < 6; j++)
+                        if (t - pl == j) ex[j] = incl - v;
+                }
+                uint32_t bpos = 0u;
+                if (lane <= 10 && my_total) bpos = atomicAdd(&cnt->list_count[pw + lane], my_total);
+                uint32_t* lists = a.lists + d->list_base;
+                uint32_t start[6];
+#pragma unroll
+                for (int j = 0; j < 6; j++) start[j] = __shfl_sync(kFull, bpos, pl + j) + ex[j];
+                uint32_t f = flags;
+                while (f) {
+                    const int i = lowest(f);
+                    f &= f - 1u;
+                    const int j = __popc((uint32_t)i);
+                    uint32_t pos = 0u;
+#pragma unroll
+                    for (int jj = 0; jj < 6; jj++)
+                        if (j == jj) pos = start[jj]++;
+                    lists[d->list_off[pw + pl + j] + pos] = base | (uint32_t)i;
+                }
+            }
+        }
+    }
+    if (cur >= 0) flush_filter_counts(cnt, examined, rounds);
 }
 
 // ---------------------------------------------------------------------------
@@ -1443,9 +1487,7 @@ void fill_levels(QDesc& d, int run, int filter_mode, uint32_t& filter_blocks)
     }
     for (int k = (n >= 2 ? n + 1 : 0); k <= kLevels; k++) d.warp_begin[k] = (uint32_t)wb;
     const unsigned warps_per_block = kFilterThreads / 32;
-    if (filter_mode == MPDP_FILTER_CONNECTED && d.n_edges == n - 1)
-        filter_blocks = 0u;  // a tree: k_filter_connected
-    else if (filter_mode != MPDP_FILTER_UNRANK)
+    if (filter_mode != MPDP_FILTER_UNRANK)
         filter_blocks = n >= 2 ? (uint32_t)(((1ull << n) + kBitmapsPerBlock - 1) / kBitmapsPerBlock) : 0u;
     else
         filter_blocks = (uint32_t)((wb + warps_per_block - 1) / warps_per_block);
