@@ -424,16 +424,20 @@ def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False, serial=N
     if serial is not None and serial["launches"]:
         extra["avg_launch_ms_alone"] = serial["ms"] / serial["launches"]
     if kind == "filter":
+        def unranked_connected(s):  # the filter formed only the connected sets
+            return filter_mode == 2 and s["enumeration"] == 1 and int(s["sets_unranked"]) == int(s["sets_connected"])
+
         def per_set(s):
             if s["enumeration"] != 1:
                 return OPS_PER_BITMAP_GRAPH
-            return OPS_PER_CONNECTED_SET if filter_mode == 2 else OPS_PER_BITMAP_TREE
+            return OPS_PER_CONNECTED_SET if unranked_connected(s) else OPS_PER_BITMAP_TREE
         ops = sum(per_set(s) * int(s["sets_unranked"]) + OPS_PER_BFS_ROUND * int(s["filter_steps"])
                   for s in stats) * prof_steps / launches
         mhz = 2070.0
         peak = SMS * SCHEDULERS * LANES * mhz * 1e6 / 1e12
         ach = ops / avg_s / 1e12
-        return {"kernel": "k_filter_bitmaps", "bound": "alu", "achieved": ach, "peak": peak,
+        kname = "k_filter_connected" if all(unranked_connected(s) for s in stats) else "k_filter_bitmaps"
+        return {"kernel": kname, "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "Tops/s", "frac": ach / peak, "traffic": traffic_for("filter", bench_batch),
                 "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz (issue slots)",
                 "ops_per_launch": ops, "avg_launch_ms": avg_s * 1000.0, **extra}

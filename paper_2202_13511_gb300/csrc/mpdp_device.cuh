@@ -479,13 +479,11 @@ __device__ __forceinline__ double peel_card(uint32_t s, int v, const Q& sq, cons
 // Fold one CCP pair (S_l, S_r) into the running best (x, left).  x is
 // cost(S_l) + cost(S_r); a single relation costs 0 (C_out base case), so a
 // pair with a single-relation side needs no addition and no memo read for it.
-template <class Memo>
-__device__ __forceinline__ void fold_pair(uint32_t sl, uint32_t sr, const Memo& memo, DevCounters* cnt,
-                                          unsigned long long& bx, uint32_t& bl)
+// Fold one split whose side costs are loaded (cost 0 for a single relation).
+__device__ __forceinline__ void fold_costs(uint32_t sl, uint32_t sr, double cl, double cr, unsigned long long& bx,
+                                           uint32_t& bl)
 {
     const bool ml = (sl & (sl - 1u)) != 0u, mr = (sr & (sr - 1u)) != 0u;
-    const double cl = ml ? memo.get_cost(sl, cnt) : 0.0;
-    const double cr = mr ? memo.get_cost(sr, cnt) : 0.0;
     // with one side a single relation (cost +0.0) the sum is the other cost
     // exactly: OR of the bit patterns, no FP64 instruction
     const unsigned long long xb =
@@ -496,6 +494,15 @@ __device__ __forceinline__ void fold_pair(uint32_t sl, uint32_t sr, const Memo& 
         bx = xb;
         bl = l;
     }
+}
+
+template <class Memo>
+__device__ __forceinline__ void fold_pair(uint32_t sl, uint32_t sr, const Memo& memo, DevCounters* cnt,
+                                          unsigned long long& bx, uint32_t& bl)
+{
+    const double cl = (sl & (sl - 1u)) ? memo.get_cost(sl, cnt) : 0.0;
+    const double cr = (sr & (sr - 1u)) ? memo.get_cost(sr, cnt) : 0.0;
+    fold_costs(sl, sr, cl, cr, bx, bl);
 }
 
 // cost(S) = x* + card(S) for the chosen split.

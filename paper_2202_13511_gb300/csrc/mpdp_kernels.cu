@@ -891,12 +891,26 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
             unsigned long long bx = kNoX;
             uint32_t bl = kFull;
             uint32_t rest = s & ~(1u << top);
-#pragma unroll 8
-            for (int i = 1; i < k; i++) {
-                const int v = lowest(rest);
+            // two splits at a time: both left sides, then their four cost
+            // loads together, then the fold (one more load in flight per
+            // thread without raising the register count)
+            for (int i = 1; i < k; i += 2) {
+                const int v0 = lowest(rest);
                 rest &= rest - 1u;
-                const uint32_t sl = __ldg(&q->desc[v]) & s;
-                fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
+                const uint32_t sl0 = __ldg(&q->desc[v0]) & s;
+                uint32_t sl1 = 0u;
+                if (i + 1 < k) {
+                    const int v1 = lowest(rest);
+                    rest &= rest - 1u;
+                    sl1 = __ldg(&q->desc[v1]) & s;
+                }
+                const uint32_t sr0 = s ^ sl0, sr1 = s ^ sl1;
+                const double cl0 = (sl0 & (sl0 - 1u)) ? memo.get_cost(sl0, cnt) : 0.0;
+                const double cr0 = (sr0 & (sr0 - 1u)) ? memo.get_cost(sr0, cnt) : 0.0;
+                const double cl1 = (sl1 & (sl1 - 1u)) ? memo.get_cost(sl1, cnt) : 0.0;
+                const double cr1 = (sl1 != 0u && (sr1 & (sr1 - 1u))) ? memo.get_cost(sr1, cnt) : 0.0;
+                fold_costs(sl0, sr0, cl0, cr0, bx, bl);
+                if (sl1 != 0u) fold_costs(sl1, sr1, cl1, cr1, bx, bl);
             }
             const double card_s = peel_finish(pbase, s, pv, *q);
             memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
