@@ -58,9 +58,9 @@ BYTES_PER_SET = 16
 # null once that source changes.
 KERNEL_FILE = "paper_2202_13511_gb300/csrc/mpdp_kernels.cu"
 DEVICE_HEADER = "paper_2202_13511_gb300/csrc/mpdp_device.cuh"
-TRAFFIC = {"eval": {"kernel": "k_eval_tree", "sha1": "7b2401541081565af389a9c4aaf867dfed4ada75", "bytes": 16008593},
-           "filter": {"kernel": "k_filter_bitmaps", "sha1": "6387f98ffbc140f93bd3cf75a6315d19afcbfbb2",
-                      "bytes": 5099008}}
+TRAFFIC = {"eval": {"kernel": "k_eval_tree", "sha1": "22d66191895fe41068eacd1350d647a473fab7f4", "bytes": 16279321},
+           "filter": {"kernel": "k_filter_connected", "sha1": "ebefad6b0981ffc90e44e7698b6d6830244996f3",
+                      "bytes": 8946443}}
 
 
 def parse_args():
