@@ -348,11 +348,55 @@ struct DenseMemo {
     uint32_t* left0;
     double2* cc;       // bound to one query
     uint32_t* left;
+    int shift;         // bound query: 32 - n when its entries sit at bit-reversed bitmaps, else -1
+
+    static constexpr size_t kSharedBytes = 16;
+
+    // Entry of set S.  A tree-mode query whose connected sets are unranked
+    // keeps them at the bit-reversed bitmap (relation 0 the top bit): the
+    // unranking lists them with the high-numbered relations varying fastest,
+    // so sets evaluated side by side then read and write neighbouring
+    // entries.  The bitmap sweep lists sets in bitmap order, which the plain
+    // bitmap keeps.
+    __device__ __forceinline__ uint32_t at(uint32_t s) const { return shift >= 0 ? __brev(s) >> shift : s; }
+    __device__ __forceinline__ void setup(char*) {}
+    // per thread; no shared memory involved
+    __device__ __forceinline__ void bind(const BatchArgs& a, int q)
+    {
+        const unsigned long long b = a.desc[q].memo_base;
+        cc = cc0 + b;
+        left = left0 + b;
+        shift = (a.query[q].use_connected && a.desc[q].enumeration == MPDP_ENUM_TREE) ? 32 - a.desc[q].n : -1;
+    }
+    __device__ __forceinline__ double get_cost(uint32_t s, DevCounters*) const { return __ldg(&cc[at(s)].x); }
+    __device__ __forceinline__ double get_card(uint32_t s, DevCounters*) const { return __ldg(&cc[at(s)].y); }
+    __device__ __forceinline__ void get(uint32_t s, double& c, double& cd, uint32_t& l, DevCounters*) const
+    {
+        const uint32_t i = at(s);
+        const double2 v = cc[i];
+        c = v.x;
+        cd = v.y;
+        l = left[i];
+    }
+    __device__ __forceinline__ void put(uint32_t s, int, double c, double cd, uint32_t l, DevCounters*)
+    {
+        const uint32_t i = at(s);
+        cc[i] = make_double2(c, cd);
+        left[i] = l;
+    }
+};
+
+// The dense memo as the block-mode kernels see it: their queries (block
+// enumeration) always keep entries at the plain bitmap.
+struct DensePlainMemo {
+    double2* cc0;
+    uint32_t* left0;
+    double2* cc;
+    uint32_t* left;
 
     static constexpr size_t kSharedBytes = 16;
 
     __device__ __forceinline__ void setup(char*) {}
-    // per thread; no shared memory involved
     __device__ __forceinline__ void bind(const BatchArgs& a, int q)
     {
         const unsigned long long b = a.desc[q].memo_base;

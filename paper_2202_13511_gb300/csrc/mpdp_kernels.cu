@@ -1522,9 +1522,23 @@ struct HookScope {
 };
 
 template <class Memo>
+struct BlockMemoOf {
+    using type = Memo;
+};
+template <>
+struct BlockMemoOf<DenseMemo> {
+    using type = DensePlainMemo;
+};
+static inline HashMemo block_memo(const HashMemo& m) { return m; }
+static inline DensePlainMemo block_memo(const DenseMemo& m) { return DensePlainMemo{m.cc0, m.left0, nullptr, nullptr}; }
+
+template <class Memo>
 static void launch_levels(const BatchArgs& a, const BatchPlan& bp, Memo memo, cudaStream_t st, int& launches,
                           LaunchHook* hook)
 {
+    // block-mode kernels: plain-bitmap entries (see DensePlainMemo)
+    using BlockMemo = typename BlockMemoOf<Memo>::type;
+
     const int cap_blocks = bp.num_sms * bp.blocks_per_sm;
     for (int k = 2; k <= a.max_n; k++) {
         const unsigned long long tree_tiles = bp.tree_tiles[k], block_tiles = bp.block_tiles[k];
@@ -1548,13 +1562,13 @@ static void launch_levels(const BatchArgs& a, const BatchPlan& bp, Memo memo, cu
             {
                 HookScope hs(hook, MPDP_KC_EVAL, st);
                 const int grid = (int)(block_tiles < (unsigned long long)cap_blocks ? block_tiles : cap_blocks);
-                k_eval_blocks<Memo><<<grid, kEvalThreads, 0, st>>>(a, k, memo);
+                k_eval_blocks<BlockMemo><<<grid, kEvalThreads, 0, st>>>(a, k, block_memo(memo));
             }
             {
                 HookScope hs(hook, MPDP_KC_HEAVY, st);
                 const unsigned long long hs_max = bp.block_sets[k];
                 const int grid = (int)(hs_max < (unsigned long long)cap_blocks ? hs_max : cap_blocks);
-                k_eval_heavy<Memo><<<grid > 0 ? grid : 1, kEvalThreads, 0, st>>>(a, k, memo);
+                k_eval_heavy<BlockMemo><<<grid > 0 ? grid : 1, kEvalThreads, 0, st>>>(a, k, block_memo(memo));
             }
             launches += 2;
         }
