@@ -58,9 +58,9 @@ BYTES_PER_SET = 16
 # null once that source changes.
 KERNEL_FILE = "paper_2202_13511_gb300/csrc/mpdp_kernels.cu"
 DEVICE_HEADER = "paper_2202_13511_gb300/csrc/mpdp_device.cuh"
-TRAFFIC = {"eval": {"kernel": "k_eval_tree", "sha1": "22d66191895fe41068eacd1350d647a473fab7f4", "bytes": 16279321},
-           "filter": {"kernel": "k_filter_connected", "sha1": "ebefad6b0981ffc90e44e7698b6d6830244996f3",
-                      "bytes": 8946443}}
+TRAFFIC = {"eval": {"kernel": "k_eval_tree", "sha1": "36c6b891aca0d682fecf4f9d4d89f204dceca9b2", "bytes": 5334931},
+           "filter": {"kernel": "k_filter_connected", "sha1": "356842f3d0cb40bc4416e8aadd0b1fb77b0670f9",
+                      "bytes": 14302382}}
 
 
 def parse_args():
