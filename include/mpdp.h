@@ -89,7 +89,10 @@ enum { MPDP_ENUM_AUTO = 0, MPDP_ENUM_TREE = 1, MPDP_ENUM_BLOCKS = 2, MPDP_ENUM_D
  * per set; same results, more pairs evaluated (reported as such). */
 
 /* Memo layout.  DENSE: arrays indexed directly by the relation bitmap
- * (20 bytes x 2^n: {cost, card} and left).  HASH: one open-addressing table
+ * (20 bytes x 2^n: {cost, card} and left); a tree-mode query whose connected
+ * sets the filter unranks uses the bit-reversed bitmap instead (relation 0
+ * the top bit), so that the sets the unranking lists side by side sit side
+ * by side (an address permutation only).  HASH: one open-addressing table
  * per level, Murmur3 fmix32 hash, linear probing, 32-byte slots {key, left,
  * cost, card}, capacity the power of two >= 2x the level's connected-set
  * count (Sec. 5, memo of "MPDP on GPU"). */

@@ -63,6 +63,11 @@ struct DevQuery {
     uint32_t leaves;                 // relations without children in T
     uint32_t use_connected;          // filter CONNECTED chose unranking for this query
     uint32_t pad3;
+    // x / (1 + nsub[c]) as (t + ((x - t) >> s1)) >> s2 with t = umulhi(x,
+    // dmag[c]), s1 = dsh[c] & 1, s2 = dsh[c] >> 1 (Granlund and Montgomery,
+    // "Division by invariant integers using multiplication", 1994, Fig. 4.1)
+    uint32_t dmag[kMaxRels];
+    uint8_t dsh[kMaxRels];
 };
 
 // T[S] has one component per member of S whose T-parent is outside S, so

@@ -131,6 +131,18 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
     for (int i = tid; i < (int)(sizeof(DevCounters) / sizeof(int)); i += blockDim.x) cw[i] = 0;
     __shared__ int s_status;
     __shared__ uint32_t s_children[kMaxRels];
+    // the query's edges and cards, staged by all threads at once: the
+    // serial checks below then read shared memory, not a chain of global
+    // loads
+    __shared__ mpdp_edge s_edges[kMaxEdges];
+    __shared__ double s_card[kMaxRels];
+    {
+        const int m0 = st->n_edges;
+        const int mm = (m0 > 0 && m0 <= kMaxEdges) ? m0 : 0;
+        for (int e = tid; e < mm; e += blockDim.x) s_edges[e] = st->edges[e];
+        if (tid < kMaxRels) s_card[tid] = st->card[tid];
+    }
+    __syncthreads();
     if (tid == 0) {
         const int n = st->n, m = st->n_edges;
         int status = 0;
@@ -138,14 +150,14 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
         else if (m < 0 || m > kMaxEdges || st->cost_model != MPDP_COST_COUT) status = MPDP_ERR_INVALID_ARG;
         if (status == 0)
             for (int i = 0; i < n; i++) {
-                const double c = st->card[i];
+                const double c = s_card[i];
                 if (!(c > 0.0) || !(c <= 1.7976931348623157e308)) status = MPDP_ERR_INVALID_ARG;
             }
         uint32_t adj[kMaxRels];
         for (int i = 0; i < kMaxRels; i++) adj[i] = 0u;
         for (int e = 0; e < m && status == 0; e++) {
-            const int u = st->edges[e].u, v = st->edges[e].v;
-            const double s = st->edges[e].sel;
+            const int u = s_edges[e].u, v = s_edges[e].v;
+            const double s = s_edges[e].sel;
             if (u < 0 || v < 0 || u >= n || v >= n || u == v || !(s > 0.0) || !(s <= 1.0) ||
                 (adj[u] >> v & 1u)) {
                 status = MPDP_ERR_INVALID_ARG;
@@ -158,27 +170,33 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
             const uint32_t full = (n == 32) ? kFull : ((1u << n) - 1u);
             if (grow(1u, full, adj) != full) status = MPDP_ERR_DISCONNECTED;
         }
+        // this thread's working copies live in registers / local memory:
+        // reading back its own global stores would cost an L2 round trip each
+        uint32_t nbase[kMaxRels];
         uint32_t base = 0;
         for (int r = 0; r < kMaxRels; r++) {
             q->adj[r] = status == 0 ? adj[r] : 0u;
+            nbase[r] = base;
             q->nbase[r] = base;
-            q->card[r] = (status == 0 && r < n) ? st->card[r] : 1.0;
+            q->card[r] = (status == 0 && r < n) ? s_card[r] : 1.0;
             if (status == 0) base += __popc(adj[r]);
         }
         if (status == 0)
             for (int e = 0; e < m; e++) {
-                const int u = st->edges[e].u, v = st->edges[e].v;
-                q->nsel[q->nbase[u] + __popc(adj[u] & ((1u << v) - 1u))] = st->edges[e].sel;
-                q->nsel[q->nbase[v] + __popc(adj[v] & ((1u << u) - 1u))] = st->edges[e].sel;
+                const int u = s_edges[e].u, v = s_edges[e].v;
+                const double sel = s_edges[e].sel;
+                q->nsel[nbase[u] + __popc(adj[u] & ((1u << v) - 1u))] = sel;
+                q->nsel[nbase[v] + __popc(adj[v] & ((1u << u) - 1u))] = sel;
             }
         // spanning tree T rooted at relation 0: children bitmaps, and the
         // descendant bitmaps by one backward pass over the discovery order
         uint32_t seen = 1u, frontier = 1u;
         uint8_t order[kMaxRels];
         int cnt_order = 0;
+        uint32_t desc[kMaxRels];
         for (int r = 0; r < kMaxRels; r++) {
             s_children[r] = 0u;
-            q->desc[r] = 1u << r;
+            desc[r] = 1u << r;
         }
         if (status == 0) {
             order[cnt_order++] = 0;
@@ -195,10 +213,11 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
             for (int i = cnt_order - 1; i >= 0; i--) {
                 const int v = order[i];
                 uint32_t dsc = 1u << v;
-                for (uint32_t c = s_children[v]; c; c &= c - 1u) dsc |= q->desc[lowest(c)];
-                q->desc[v] = dsc;
+                for (uint32_t c = s_children[v]; c; c &= c - 1u) dsc |= desc[lowest(c)];
+                desc[v] = dsc;
             }
         }
+        for (int r = 0; r < kMaxRels; r++) q->desc[r] = desc[r];
         // run tables of the bitmap filter (low relations r < 5 of T)
         uint32_t lowkids = 0u;
         for (int r = 0; r < 5; r++) {
@@ -216,23 +235,24 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
         // over the discovery order; a subtree of t relations has at most
         // 2^(t-1) connected sets with its root on top, so 32 bits suffice
         const bool tree = status == 0 && m == n - 1;
-        uint32_t leaves = 0u;
+        uint32_t leaves = 0u, nsub[kMaxRels];
         for (int r = 0; r < kMaxRels; r++) {
             q->chmask[r] = tree ? s_children[r] : 0u;
-            q->nsub[r] = 0u;
+            nsub[r] = 0u;
             if (tree && r < n && s_children[r] == 0u) leaves |= 1u << r;
         }
         if (tree)
             for (int i = cnt_order - 1; i >= 0; i--) {
                 const int v = order[i];
                 uint32_t prod = 1u;
-                for (uint32_t c = s_children[v]; c; c &= c - 1u) prod *= 1u + q->nsub[lowest(c)];
-                q->nsub[v] = prod;
+                for (uint32_t c = s_children[v]; c; c &= c - 1u) prod *= 1u + nsub[lowest(c)];
+                nsub[v] = prod;
             }
         uint32_t acc = 0u;
         for (int r = 0; r <= kMaxRels; r++) {
             q->top_pref[r] = acc;
-            if (tree && r < n) acc += q->nsub[r];
+            if (r < kMaxRels) q->nsub[r] = nsub[r];
+            if (tree && r < n) acc += nsub[r];
         }
         q->leaves = leaves;
         // filter CONNECTED: unrank a tree's connected sets when they are at
@@ -248,6 +268,13 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
     __syncthreads();
     const int status = s_status;
     if (tid == 0) cnt->status = status;
+    if (tid < kMaxRels) {  // the divisors 1 + nsub[r] of the unranking's mixed-radix digits
+        const unsigned long long d = 1ull + q->nsub[tid];
+        int l = 0;
+        while ((1ull << l) < d) l++;
+        q->dmag[tid] = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1ull);
+        q->dsh[tid] = (uint8_t)((l > 0 ? 1 : 0) | ((l > 0 ? l - 1 : 0) << 1));
+    }
     if (status == 0 && dense) {
         DenseMemo memo{a.memo, a.left, nullptr, nullptr};
         memo.bind(a, qi);
@@ -453,8 +480,11 @@ __device__ __forceinline__ uint32_t unrank_connected(const DevQuery* __restrict_
         for (uint32_t c = ch & ~leaves; c; c &= c - 1u) {
             const int w = lowest(c);
             const uint32_t radix = __ldg(&q->nsub[w]) + 1u;
-            const uint32_t dgt = r % radix;
-            r /= radix;
+            const uint32_t t = __umulhi(r, __ldg(&q->dmag[w]));
+            const uint32_t sh = __ldg(&q->dsh[w]);
+            const uint32_t quo = (t + ((r - t) >> (sh & 1u))) >> (sh >> 1);
+            const uint32_t dgt = r - quo * radix;
+            r = quo;
             if (dgt) {
                 st_v[sp] = (uint8_t)w;
                 st_x[sp] = dgt - 1u;
