@@ -58,9 +58,9 @@ BYTES_PER_SET = 16
 # null once that source changes.
 KERNEL_FILE = "paper_2202_13511_gb300/csrc/mpdp_kernels.cu"
 DEVICE_HEADER = "paper_2202_13511_gb300/csrc/mpdp_device.cuh"
-TRAFFIC = {"eval": {"kernel": "k_eval_tree", "sha1": "36c6b891aca0d682fecf4f9d4d89f204dceca9b2", "bytes": 5334931},
-           "filter": {"kernel": "k_filter_connected", "sha1": "356842f3d0cb40bc4416e8aadd0b1fb77b0670f9",
-                      "bytes": 14302382}}
+TRAFFIC = {"eval": {"kernel": "k_eval_tree", "sha1": "f0387f41c3068717b83374b47303c5d127f4d806", "bytes": 5338696},
+           "filter": {"kernel": "k_filter_connected", "sha1": "0516ed8ef9a7bba748b4ca0e7cc80a54ad9ccca0",
+                      "bytes": 14392196}}
 
 
 def parse_args():
@@ -694,7 +694,7 @@ def serving_line(mpdp, W):
     queries = W.mixed_stream(SERVE_QUERIES, seed=0)
     t0 = time.perf_counter()
     kernel, _, khist = autotune.tune_kernels(queries[:256], reps=2)
-    server_cfg, _, shist = autotune.tune_server(queries[:512], kernel=kernel)
+    server_cfg, _, shist = autotune.tune_server(queries[:1000], kernel=kernel)
     tune_s = time.perf_counter() - t0
     out = {"workload": f"{SERVE_QUERIES} mixed queries: star/snowflake/cyclic uniformly, 8-25 relations "
                        "(weight 3 on 12-18), seed 0",
