@@ -861,6 +861,20 @@ __device__ __forceinline__ uint32_t level_tiles(const BatchArgs& a, int q, int k
 }
 
 // ---------------------------------------------------------------------------
+// Tile prefix of every level over the lane's tree queries, once after the
+// filter (a block per level): each evaluate launch then loads its row
+// instead of recomputing it from the queries' counters.
+constexpr int kPrefStride = kMaxBatch + 1;
+
+__global__ void __launch_bounds__(256) k_level_prefix(BatchArgs a, uint32_t* __restrict__ pref)
+{
+    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    const int k = blockIdx.x + 2;
+    block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, MPDP_ENUM_TREE); });
+    for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) pref[k * kPrefStride + i] = s_pref[i];
+}
+
+// ---------------------------------------------------------------------------
 // a4-a8, tree join graphs (Algorithm 2, MPDP:Tree).  One thread per connected
 // set S of level k (tiles of 256 sets of one query per block iteration).
 // Every connected S induces a tree; its CCP pairs are the k-1 splits made by
@@ -870,12 +884,14 @@ __device__ __forceinline__ uint32_t level_tiles(const BatchArgs& a, int q, int k
 // (cost, left) over the k-1 splits is written to the memo: evaluate, prune
 // and scatter fused in one pass, one memo write per set.
 template <class Memo>
-__global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, Memo memo)
+__global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, Memo memo, const uint32_t* __restrict__ level_pref)
 {
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     memo.setup(s_memo);
-    const uint32_t tiles = block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, MPDP_ENUM_TREE); });
+    for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) s_pref[i] = level_pref[k * kPrefStride + i];
+    __syncthreads();
+    const uint32_t tiles = s_pref[a.nq];
     // Tiles go round-robin over the blocks, so the sets in flight at any
     // time are neighbours in the level lists (their memo reads are close).
     // The query is read through the cache, not staged in shared memory:
@@ -1570,6 +1586,13 @@ static void launch_levels(const BatchArgs& a, const BatchPlan& bp, Memo memo, cu
     using BlockMemo = typename BlockMemoOf<Memo>::type;
 
     const int cap_blocks = bp.num_sms * bp.blocks_per_sm;
+    bool any_tree = false;
+    for (int k = 2; k <= a.max_n; k++) any_tree = any_tree || bp.tree_tiles[k] != 0;
+    if (any_tree && !bp.pairs) {
+        HookScope hs(hook, MPDP_KC_EVAL, st);
+        k_level_prefix<<<a.max_n - 1, 256, 0, st>>>(a, bp.level_pref);
+        launches++;
+    }
     for (int k = 2; k <= a.max_n; k++) {
         const unsigned long long tree_tiles = bp.tree_tiles[k], block_tiles = bp.block_tiles[k];
         if (tree_tiles) {
@@ -1584,7 +1607,7 @@ static void launch_levels(const BatchArgs& a, const BatchPlan& bp, Memo memo, cu
                 launches += 2;
             } else {
                 HookScope hs(hook, MPDP_KC_EVAL, st);
-                k_eval_tree<Memo><<<grid, kEvalThreads, 0, st>>>(a, k, memo);
+                k_eval_tree<Memo><<<grid, kEvalThreads, 0, st>>>(a, k, memo, bp.level_pref);
                 launches++;
             }
         }
