@@ -861,17 +861,19 @@ __device__ __forceinline__ uint32_t level_tiles(const BatchArgs& a, int q, int k
 }
 
 // ---------------------------------------------------------------------------
-// Tile prefix of every level over the lane's tree queries, once after the
-// filter (a block per level): each evaluate launch then loads its row
-// instead of recomputing it from the queries' counters.
+// Tile prefix of every level over the lane's tree queries and, in a second
+// table, over its block-mode queries, once after the filter (a block per
+// level and mode): each evaluate launch then loads its row instead of
+// recomputing it from the queries' counters.
 constexpr int kPrefStride = kMaxBatch + 1;
 
 __global__ void __launch_bounds__(256) k_level_prefix(BatchArgs a, uint32_t* __restrict__ pref)
 {
     __shared__ uint32_t s_pref[kMaxBatch + 1];
-    const int k = blockIdx.x + 2;
-    block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, MPDP_ENUM_TREE); });
-    for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) pref[k * kPrefStride + i] = s_pref[i];
+    const int k = blockIdx.x / 2 + 2, mode = (blockIdx.x & 1) ? MPDP_ENUM_BLOCKS : MPDP_ENUM_TREE;
+    block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, mode); });
+    uint32_t* row = pref + ((mode == MPDP_ENUM_BLOCKS ? kLevels : 0) + k) * kPrefStride;
+    for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) row[i] = s_pref[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -1085,13 +1087,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_prune_tree(BatchArgs a, int k,
 // S_r = S \ S_l.  Sets whose pair count exceeds the heavy threshold go to the
 // block-per-set kernel instead.
 template <class Memo>
-__global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k, Memo memo)
+__global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k, Memo memo, const uint32_t* __restrict__ level_pref)
 {
     __shared__ SharedQuery sq;
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     memo.setup(s_memo);
-    const uint32_t tiles = block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, MPDP_ENUM_BLOCKS); });
+    for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) s_pref[i] = level_pref[(kLevels + k) * kPrefStride + i];
+    __syncthreads();
+    const uint32_t tiles = s_pref[a.nq];
     int cur = -1;
     unsigned long long evaluated = 0, ccp = 0;
     const int lane = threadIdx.x & 31;
@@ -1586,11 +1590,11 @@ static void launch_levels(const BatchArgs& a, const BatchPlan& bp, Memo memo, cu
     using BlockMemo = typename BlockMemoOf<Memo>::type;
 
     const int cap_blocks = bp.num_sms * bp.blocks_per_sm;
-    bool any_tree = false;
-    for (int k = 2; k <= a.max_n; k++) any_tree = any_tree || bp.tree_tiles[k] != 0;
-    if (any_tree && !bp.pairs) {
+    bool any = false;  // levels to evaluate (k >= 2)
+    for (int k = 2; k <= a.max_n; k++) any = any || bp.tree_tiles[k] != 0 || bp.block_tiles[k] != 0;
+    if (any) {
         HookScope hs(hook, MPDP_KC_EVAL, st);
-        k_level_prefix<<<a.max_n - 1, 256, 0, st>>>(a, bp.level_pref);
+        k_level_prefix<<<2 * (a.max_n - 1), 256, 0, st>>>(a, bp.level_pref);
         launches++;
     }
     for (int k = 2; k <= a.max_n; k++) {
@@ -1615,7 +1619,7 @@ static void launch_levels(const BatchArgs& a, const BatchPlan& bp, Memo memo, cu
             {
                 HookScope hs(hook, MPDP_KC_EVAL, st);
                 const int grid = (int)(block_tiles < (unsigned long long)cap_blocks ? block_tiles : cap_blocks);
-                k_eval_blocks<BlockMemo><<<grid, kEvalThreads, 0, st>>>(a, k, block_memo(memo));
+                k_eval_blocks<BlockMemo><<<grid, kEvalThreads, 0, st>>>(a, k, block_memo(memo), bp.level_pref);
             }
             {
                 HookScope hs(hook, MPDP_KC_HEAVY, st);

@@ -26,7 +26,7 @@ struct BatchPlan {
     uint32_t filter_blocks = 0;     // bitmap / unrank filter blocks
     uint32_t connected_blocks = 0;  // k_filter_connected grid (tree queries in mode CONNECTED)
     PairRec* pairs = nullptr;  // non-null: tree levels run unfused (evaluate, then prune + scatter)
-    uint32_t* level_pref = nullptr;  // [kLevels][kMaxBatch + 1]: per-level tile prefix of the tree queries
+    uint32_t* level_pref = nullptr;  // [2][kLevels][kMaxBatch + 1]: per-level tile prefix, tree then block mode
     unsigned long long tree_tiles[kLevels] = {};   // upper bound of level-k tiles, tree queries
     unsigned long long block_tiles[kLevels] = {};  // same, block-mode queries
     unsigned long long block_sets[kLevels] = {};   // upper bound of level-k heavy tiles (8 chunks), block-mode queries
