@@ -348,7 +348,7 @@ enum {
     MPDP_KC_STAGE = 0,   /* device-path input gather */
     MPDP_KC_INGEST = 1,  /* graph build and validation */
     MPDP_KC_FILTER = 2,  /* connectivity filter, all levels (with the level sort) */
-    MPDP_KC_MEMO_INIT = 3, /* hash memo layout and clear */
+    MPDP_KC_MEMO_INIT = 3, /* hash memo layout and clear; per-level tile prefixes */
     MPDP_KC_EVAL = 4,    /* per-level evaluate + prune + scatter (thread per set) */
     MPDP_KC_HEAVY = 5,   /* per-level block-per-set evaluation (block mode) */
     MPDP_KC_EXTRACT = 6, /* plan fetch */

@@ -1593,7 +1593,7 @@ static void launch_levels(const BatchArgs& a, const BatchPlan& bp, Memo memo, cu
     bool any = false;  // levels to evaluate (k >= 2)
     for (int k = 2; k <= a.max_n; k++) any = any || bp.tree_tiles[k] != 0 || bp.block_tiles[k] != 0;
     if (any) {
-        HookScope hs(hook, MPDP_KC_EVAL, st);
+        HookScope hs(hook, MPDP_KC_MEMO_INIT, st);
         k_level_prefix<<<2 * (a.max_n - 1), 256, 0, st>>>(a, bp.level_pref);
         launches++;
     }
