@@ -693,7 +693,7 @@ def serving_line(mpdp, W):
     from paper_2202_13511_gb300 import autotune
     queries = W.mixed_stream(SERVE_QUERIES, seed=0)
     t0 = time.perf_counter()
-    kernel, _, khist = autotune.tune_kernels(queries[:256], reps=2)
+    kernel, _, khist = autotune.tune_kernels(queries[:512], reps=3)
     server_cfg, _, shist = autotune.tune_server(queries[:1000], kernel=kernel)
     tune_s = time.perf_counter() - t0
     out = {"workload": f"{SERVE_QUERIES} mixed queries: star/snowflake/cyclic uniformly, 8-25 relations "
