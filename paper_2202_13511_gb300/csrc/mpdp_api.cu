@@ -270,7 +270,7 @@ static size_t fixed_bytes()
     return align_up(sizeof(QDesc) * kMaxBatch) + align_up(sizeof(uint32_t) * (kMaxBatch + MPDP_MAX_LANES + 1)) +
            align_up(sizeof(StagedQuery) * kMaxBatch) + align_up(sizeof(DevQuery) * kMaxBatch) +
            align_up(sizeof(DevOut) * kMaxBatch) + align_up(sizeof(HashLayout) * kMaxBatch) +
-           align_up(sizeof(uint32_t) * MPDP_MAX_LANES * 2 * kLevels * (kMaxBatch + 1));
+           align_up(sizeof(uint32_t) * MPDP_MAX_LANES * 2 * kLevels * (kMaxBatch + 2));
 }
 
 static void destroy_graphs(mpdp_ctx* ctx)
@@ -302,7 +302,7 @@ static int ensure_fixed(mpdp_ctx* ctx)
     ctx->d_out = reinterpret_cast<DevOut*>(take(sizeof(DevOut) * kMaxBatch));
     ctx->d_layout = reinterpret_cast<HashLayout*>(take(sizeof(HashLayout) * kMaxBatch));
     ctx->d_level_pref =
-        reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * MPDP_MAX_LANES * 2 * kLevels * (kMaxBatch + 1)));
+        reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * MPDP_MAX_LANES * 2 * kLevels * (kMaxBatch + 2)));
     CK(ctx, cudaMemsetAsync(ctx->d_out, 0, sizeof(DevOut) * kMaxBatch, ctx->stream));
     return MPDP_OK;
 }
@@ -670,7 +670,7 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
             ln.q1 = bounds[lane + 1];
             ln.bp.num_sms = ctx->num_sms;
             ln.bp.blocks_per_sm = ctx->cfg.grid_blocks_per_sm;
-            ln.bp.level_pref = ctx->d_level_pref + (size_t)lane * 2 * kLevels * (kMaxBatch + 1);
+            ln.bp.level_pref = ctx->d_level_pref + (size_t)lane * 2 * kLevels * (kMaxBatch + 2);
             ln.a.arena_begin = abase;
             fblocks = 0;
             lane_max_n = 0;

@@ -864,16 +864,42 @@ __device__ __forceinline__ uint32_t level_tiles(const BatchArgs& a, int q, int k
 // Tile prefix of every level over the lane's tree queries and, in a second
 // table, over its block-mode queries, once after the filter (a block per
 // level and mode): each evaluate launch then loads its row instead of
-// recomputing it from the queries' counters.
-constexpr int kPrefStride = kMaxBatch + 1;
+// recomputing it from the queries' counters.  A tree level with few sets
+// gets a set prefix instead and is evaluated a warp per set.
+// Top of a connected set in a tree query: the member whose descendants cover it.
+__device__ __forceinline__ int set_top_of(const DevQuery* __restrict__ q, uint32_t s)
+{
+    uint32_t t = s;
+    int top = lowest(t);
+    while ((__ldg(&q->desc[top]) & s) != s) {
+        t &= t - 1u;
+        top = lowest(t);
+    }
+    return top;
+}
+
+constexpr int kPrefStride = kMaxBatch + 2;  // prefix [0, nq], then the level's mapping flag
+// Tree levels with at most this many sets (and k >= kWarpLevelMin) map a
+// warp to a set: each lane takes one split, so the set's k - 1 cost pairs
+// cost one round of memory latency instead of (k - 1) / 2.
+constexpr uint32_t kWarpLevelSets = 1024;
+constexpr int kWarpLevelMin = 8;
 
 __global__ void __launch_bounds__(256) k_level_prefix(BatchArgs a, uint32_t* __restrict__ pref)
 {
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     const int k = blockIdx.x / 2 + 2, mode = (blockIdx.x & 1) ? MPDP_ENUM_BLOCKS : MPDP_ENUM_TREE;
-    block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, mode); });
     uint32_t* row = pref + ((mode == MPDP_ENUM_BLOCKS ? kLevels : 0) + k) * kPrefStride;
+    uint32_t warp_mode = 0u;
+    if (mode == MPDP_ENUM_TREE && k >= kWarpLevelMin) {
+        const uint32_t sets = block_prefix(a.nq, s_pref, [&](int q) {
+            return level_tiles(a, q, k, mode) ? a.out[q].counters.list_count[k] : 0u;
+        });
+        warp_mode = sets <= kWarpLevelSets ? 1u : 0u;  // block-uniform
+    }
+    if (!warp_mode) block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, mode); });
     for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) row[i] = s_pref[i];
+    if (threadIdx.x == 0) row[kMaxBatch + 1] = warp_mode;
 }
 
 // ---------------------------------------------------------------------------
@@ -893,6 +919,37 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
     memo.setup(s_memo);
     for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) s_pref[i] = level_pref[k * kPrefStride + i];
     __syncthreads();
+    if (level_pref[k * kPrefStride + kMaxBatch + 1]) {  // a warp per set (s_pref: set prefix)
+        const uint32_t nsets = s_pref[a.nq];
+        const int lane = threadIdx.x & 31;
+        const uint32_t stride = gridDim.x * (kEvalThreads / 32);
+        for (uint32_t g = blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5); g < nsets; g += stride) {
+            const int qi = find_q(s_pref, a.nq, g);
+            const DevQuery* __restrict__ q = a.query + qi;
+            DevCounters* cnt = &a.out[qi].counters;
+            memo.bind(a, qi);
+            const QDesc& d = a.desc[qi];
+            const uint32_t s = a.lists[d.list_base + d.list_off[k] + (g - s_pref[qi])];
+            const int top = set_top_of(q, s);
+            const int pv = tree_peel_vertex(s, q->adj);
+            const double pbase = lane == 0 ? peel_base(s, pv, *q, memo, cnt) : 0.0;
+            unsigned long long bx = kNoX;
+            uint32_t bl = kFull;
+            if (lane < k - 1) {
+                const int v = (int)__fns(s & ~(1u << top), 0u, lane + 1);
+                const uint32_t sl = __ldg(&q->desc[v]) & s;
+                fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
+            }
+            warp_min_x(bx, bl);
+            if (lane == 0) {
+                const double card_s = peel_finish(pbase, s, pv, *q);
+                memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
+                atomicAdd(&cnt->evaluated[k], (unsigned long long)(k - 1));
+                atomicAdd(&cnt->ccp[k], (unsigned long long)(k - 1));
+            }
+        }
+        return;
+    }
     const uint32_t tiles = s_pref[a.nq];
     // Tiles go round-robin over the blocks, so the sets in flight at any
     // time are neighbours in the level lists (their memo reads are close).
