@@ -130,81 +130,71 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
     int* cw = reinterpret_cast<int*>(cnt);
     for (int i = tid; i < (int)(sizeof(DevCounters) / sizeof(int)); i += blockDim.x) cw[i] = 0;
     __shared__ int s_status;
-    __shared__ uint32_t s_children[kMaxRels];
-    // the query's edges and cards, staged by all threads at once: the
-    // serial checks below then read shared memory, not a chain of global
-    // loads
+    __shared__ uint32_t s_adj[kMaxRels], s_children[kMaxRels], s_desc[kMaxRels], s_nsub[kMaxRels], s_nbase[kMaxRels];
+    __shared__ uint32_t s_top_pref[kMaxRels + 1], s_lowrun[16], s_leaves, s_flags;
+    // the query's edges and cards, staged by all threads at once
     __shared__ mpdp_edge s_edges[kMaxEdges];
     __shared__ double s_card[kMaxRels];
-    {
-        const int m0 = st->n_edges;
-        const int mm = (m0 > 0 && m0 <= kMaxEdges) ? m0 : 0;
-        for (int e = tid; e < mm; e += blockDim.x) s_edges[e] = st->edges[e];
-        if (tid < kMaxRels) s_card[tid] = st->card[tid];
+    const int n = st->n, m = st->n_edges;
+    const bool shape_ok = n >= 1 && n <= MPDP_MAX_EXACT_RELS && m >= 0 && m <= kMaxEdges;
+    if (shape_ok)
+        for (int e = tid; e < m; e += blockDim.x) s_edges[e] = st->edges[e];
+    if (tid < kMaxRels) {
+        s_card[tid] = st->card[tid];
+        s_adj[tid] = 0u;
     }
-    __syncthreads();
     if (tid == 0) {
-        const int n = st->n, m = st->n_edges;
         int status = 0;
         if (n < 1 || n > MPDP_MAX_EXACT_RELS) status = MPDP_ERR_TOO_LARGE;
         else if (m < 0 || m > kMaxEdges || st->cost_model != MPDP_COST_COUT) status = MPDP_ERR_INVALID_ARG;
-        if (status == 0)
-            for (int i = 0; i < n; i++) {
-                const double c = s_card[i];
-                if (!(c > 0.0) || !(c <= 1.7976931348623157e308)) status = MPDP_ERR_INVALID_ARG;
-            }
-        uint32_t adj[kMaxRels];
-        for (int i = 0; i < kMaxRels; i++) adj[i] = 0u;
-        for (int e = 0; e < m && status == 0; e++) {
-            const int u = s_edges[e].u, v = s_edges[e].v;
-            const double s = s_edges[e].sel;
-            if (u < 0 || v < 0 || u >= n || v >= n || u == v || !(s > 0.0) || !(s <= 1.0) ||
-                (adj[u] >> v & 1u)) {
-                status = MPDP_ERR_INVALID_ARG;
-                break;
-            }
-            adj[u] |= 1u << v;
-            adj[v] |= 1u << u;
+        s_status = status;
+    }
+    __syncthreads();
+    // values and edges, in parallel: a duplicate pair shows as a bit that
+    // another edge's atomic OR already set in one of the pair's two words
+    if (s_status == 0) {
+        if (tid < n) {
+            const double c = s_card[tid];
+            if (!(c > 0.0) || !(c <= 1.7976931348623157e308)) atomicCAS(&s_status, 0, MPDP_ERR_INVALID_ARG);
         }
+        for (int e = tid; e < m; e += blockDim.x) {
+            const int u = s_edges[e].u, v = s_edges[e].v;
+            const double sel = s_edges[e].sel;
+            if (u < 0 || v < 0 || u >= n || v >= n || u == v || !(sel > 0.0) || !(sel <= 1.0)) {
+                atomicCAS(&s_status, 0, MPDP_ERR_INVALID_ARG);
+                continue;
+            }
+            const uint32_t o1 = atomicOr(&s_adj[u], 1u << v), o2 = atomicOr(&s_adj[v], 1u << u);
+            if ((o1 >> v & 1u) || (o2 >> u & 1u)) atomicCAS(&s_status, 0, MPDP_ERR_INVALID_ARG);
+        }
+    }
+    __syncthreads();
+    // the short serial walks: connectivity, spanning tree T rooted at
+    // relation 0 (children, discovery order, descendants), the bitmap
+    // filter's run tables and the unranking's subtree counts
+    uint8_t order[kMaxRels];
+    int cnt_order = 0;
+    if (tid == 0) {
+        int status = s_status;
+        uint32_t adj[kMaxRels];
+        for (int r = 0; r < kMaxRels; r++) adj[r] = status == 0 ? s_adj[r] : 0u;
         if (status == 0) {
             const uint32_t full = (n == 32) ? kFull : ((1u << n) - 1u);
             if (grow(1u, full, adj) != full) status = MPDP_ERR_DISCONNECTED;
         }
-        // this thread's working copies live in registers / local memory:
-        // reading back its own global stores would cost an L2 round trip each
-        uint32_t nbase[kMaxRels];
-        uint32_t base = 0;
+        uint32_t desc[kMaxRels], children[kMaxRels];
         for (int r = 0; r < kMaxRels; r++) {
-            q->adj[r] = status == 0 ? adj[r] : 0u;
-            nbase[r] = base;
-            q->nbase[r] = base;
-            q->card[r] = (status == 0 && r < n) ? s_card[r] : 1.0;
-            if (status == 0) base += __popc(adj[r]);
-        }
-        if (status == 0)
-            for (int e = 0; e < m; e++) {
-                const int u = s_edges[e].u, v = s_edges[e].v;
-                const double sel = s_edges[e].sel;
-                q->nsel[nbase[u] + __popc(adj[u] & ((1u << v) - 1u))] = sel;
-                q->nsel[nbase[v] + __popc(adj[v] & ((1u << u) - 1u))] = sel;
-            }
-        // spanning tree T rooted at relation 0: children bitmaps, and the
-        // descendant bitmaps by one backward pass over the discovery order
-        uint32_t seen = 1u, frontier = 1u;
-        uint8_t order[kMaxRels];
-        int cnt_order = 0;
-        uint32_t desc[kMaxRels];
-        for (int r = 0; r < kMaxRels; r++) {
-            s_children[r] = 0u;
+            children[r] = 0u;
             desc[r] = 1u << r;
         }
         if (status == 0) {
+            uint32_t seen = 1u, frontier = 1u;
             order[cnt_order++] = 0;
             while (frontier) {
                 const int x = lowest(frontier);
                 frontier &= frontier - 1u;
                 const uint32_t ch = adj[x] & ~seen;
-                s_children[x] = ch;
+                children[x] = ch;
                 seen |= ch;
                 frontier |= ch;
                 for (uint32_t c = ch; c; c &= c - 1u) order[cnt_order++] = (uint8_t)lowest(c);
@@ -213,79 +203,116 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
             for (int i = cnt_order - 1; i >= 0; i--) {
                 const int v = order[i];
                 uint32_t dsc = 1u << v;
-                for (uint32_t c = s_children[v]; c; c &= c - 1u) dsc |= desc[lowest(c)];
+                for (uint32_t c = children[v]; c; c &= c - 1u) dsc |= desc[lowest(c)];
                 desc[v] = dsc;
             }
         }
-        for (int r = 0; r < kMaxRels; r++) q->desc[r] = desc[r];
         // run tables of the bitmap filter (low relations r < 5 of T)
         uint32_t lowkids = 0u;
         for (int r = 0; r < 5; r++) {
             const bool in = status == 0 && r < n;
             int par = -1;
             for (int p = 0; p < n && in; p++)
-                if (s_children[p] >> r & 1u) par = p;
-            q->lowrun[r] = in ? s_children[r] : 0u;
-            q->lowrun[5 + r] = in ? ((par >= 0 && par < 5) ? low_bit(r) & ~low_bit(par) : low_bit(r)) : 0u;
-            q->lowrun[10 + r] = (in && par >= 5) ? (uint32_t)par : 0xffffffffu;
-            if (in) lowkids |= s_children[r];
+                if (children[p] >> r & 1u) par = p;
+            s_lowrun[r] = in ? children[r] : 0u;
+            s_lowrun[5 + r] = in ? ((par >= 0 && par < 5) ? low_bit(r) & ~low_bit(par) : low_bit(r)) : 0u;
+            s_lowrun[10 + r] = (in && par >= 5) ? (uint32_t)par : 0xffffffffu;
+            if (in) lowkids |= children[r];
         }
-        q->lowrun[15] = lowkids;
+        s_lowrun[15] = lowkids;
         // connected-set unranking tables (tree join graphs): nsub bottom-up
         // over the discovery order; a subtree of t relations has at most
         // 2^(t-1) connected sets with its root on top, so 32 bits suffice
         const bool tree = status == 0 && m == n - 1;
         uint32_t leaves = 0u, nsub[kMaxRels];
         for (int r = 0; r < kMaxRels; r++) {
-            q->chmask[r] = tree ? s_children[r] : 0u;
             nsub[r] = 0u;
-            if (tree && r < n && s_children[r] == 0u) leaves |= 1u << r;
+            if (tree && r < n && children[r] == 0u) leaves |= 1u << r;
         }
         if (tree)
             for (int i = cnt_order - 1; i >= 0; i--) {
                 const int v = order[i];
                 uint32_t prod = 1u;
-                for (uint32_t c = s_children[v]; c; c &= c - 1u) prod *= 1u + nsub[lowest(c)];
+                for (uint32_t c = children[v]; c; c &= c - 1u) prod *= 1u + nsub[lowest(c)];
                 nsub[v] = prod;
             }
         uint32_t acc = 0u;
         for (int r = 0; r <= kMaxRels; r++) {
-            q->top_pref[r] = acc;
-            if (r < kMaxRels) q->nsub[r] = nsub[r];
+            s_top_pref[r] = acc;
+            if (r < kMaxRels) {
+                s_nsub[r] = nsub[r];
+                s_desc[r] = desc[r];
+                s_children[r] = children[r];
+            }
             if (tree && r < n) acc += nsub[r];
         }
-        q->leaves = leaves;
+        s_leaves = leaves;
         // filter CONNECTED: unrank a tree's connected sets when they are at
         // most a quarter of the 2^n bitmaps (forming a set costs a few times
         // testing a bitmap); denser trees such as stars take the sweep
-        q->use_connected =
-            (a.filter_mode == MPDP_FILTER_CONNECTED && tree && 4ull * (unsigned long long)acc <= (1ull << n)) ? 1u : 0u;
-        q->n = n;
-        q->n_edges = status == 0 ? m : 0;
-        q->is_tree = (status == 0 && m == n - 1) ? 1 : 0;
+        const bool use_connected =
+            a.filter_mode == MPDP_FILTER_CONNECTED && tree && 4ull * (unsigned long long)acc <= (1ull << n);
+        s_flags = (tree ? 1u : 0u) | (use_connected ? 2u : 0u);
         s_status = status;
     }
     __syncthreads();
     const int status = s_status;
-    if (tid == 0) cnt->status = status;
-    if (tid < kMaxRels) {  // the divisors 1 + nsub[r] of the unranking's mixed-radix digits
-        const unsigned long long d = 1ull + q->nsub[tid];
+    const bool tree = (s_flags & 1u) != 0u;
+    // the device record, in parallel
+    if (tid < kMaxRels) {
+        const uint32_t adj = status == 0 ? s_adj[tid] : 0u;
+        // neighbour-list bases: exclusive prefix of the degrees over the warp
+        const uint32_t deg = __popc(adj);
+        uint32_t incl = deg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (tid >= o) incl += t;
+        }
+        s_nbase[tid] = incl - deg;
+        q->nbase[tid] = incl - deg;
+        q->adj[tid] = adj;
+        q->card[tid] = (status == 0 && tid < n) ? s_card[tid] : 1.0;
+        q->desc[tid] = s_desc[tid];
+        q->chmask[tid] = tree ? s_children[tid] : 0u;
+        q->nsub[tid] = s_nsub[tid];
+        q->top_pref[tid] = s_top_pref[tid];
+        if (tid < 16) q->lowrun[tid] = s_lowrun[tid];
+        if (tid == 0) {
+            q->top_pref[kMaxRels] = s_top_pref[kMaxRels];
+            q->leaves = s_leaves;
+            q->use_connected = (s_flags & 2u) ? 1u : 0u;
+            q->n = n;
+            q->n_edges = status == 0 ? m : 0;
+            q->is_tree = tree ? 1 : 0;
+            cnt->status = status;
+        }
+        // the divisors 1 + nsub[r] of the unranking's mixed-radix digits
+        const unsigned long long d = 1ull + s_nsub[tid];
         int l = 0;
         while ((1ull << l) < d) l++;
         q->dmag[tid] = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1ull);
         q->dsh[tid] = (uint8_t)((l > 0 ? 1 : 0) | ((l > 0 ? l - 1 : 0) << 1));
     }
+    __syncthreads();
+    if (status == 0)
+        for (int e = tid; e < m; e += blockDim.x) {  // neighbour selectivities, ascending by neighbour
+            const int u = s_edges[e].u, v = s_edges[e].v;
+            const double sel = s_edges[e].sel;
+            q->nsel[s_nbase[u] + __popc(s_adj[u] & ((1u << v) - 1u))] = sel;
+            q->nsel[s_nbase[v] + __popc(s_adj[v] & ((1u << u) - 1u))] = sel;
+        }
     if (status == 0 && dense) {
         DenseMemo memo{a.memo, a.left, nullptr, nullptr};
         memo.bind(a, qi);
-        if (tid < st->n) memo.put(1u << tid, 1, 0.0, q->card[tid], 0u, cnt);
+        if (tid < n) memo.put(1u << tid, 1, 0.0, s_card[tid], 0u, cnt);
     }
     for (int e = tid; e < 4 * 256; e += blockDim.x) {
         const int b = e >> 8, x = e & 255;
         uint32_t u = 0u, c = 0u;
         for (int i = 0; i < 8; i++)
             if (x >> i & 1) {
-                u |= q->adj[8 * b + i];
+                u |= status == 0 ? s_adj[8 * b + i] : 0u;
                 c |= s_children[8 * b + i];
             }
         q->nbt[b][x] = u;
