@@ -147,6 +147,7 @@ struct mpdp_ctx {
     int num_sms = 152;
     // fixed device part (kMaxBatch queries)
     void* fixed = nullptr;
+    char* d_upload = nullptr;  // [prefixes | descriptors | packed cards and edges]
     QDesc* d_desc = nullptr;
     uint32_t* d_prefix = nullptr;
     StagedQuery* d_staged = nullptr;
@@ -265,10 +266,22 @@ static size_t var_bytes_of(size_t lists, size_t heavy, size_t memo, size_t hash)
            align_up(memo * sizeof(uint32_t)) + align_up(hash * sizeof(HashSlot));
 }
 
+// Upload region: one host-to-device copy per batch carries the filter-block
+// prefixes, the query descriptors and (host path) the packed cardinalities
+// and predicates, laid out as [prefixes | descriptors | cards | edges].  The
+// prefixes and descriptors sit at fixed offsets (captured graphs read them);
+// the packed arrays follow the batch's descriptors.
+constexpr size_t kUploadPrefixBytes = ((sizeof(uint32_t) * (kMaxBatch + MPDP_MAX_LANES + 1)) + 255) & ~(size_t)255;
+
+static size_t upload_bytes_max()
+{
+    return kUploadPrefixBytes + align_up(sizeof(QDesc) * kMaxBatch) + align_up(sizeof(double) * kMaxRels * kMaxBatch) +
+           align_up(sizeof(mpdp_edge) * kMaxEdges * kMaxBatch);
+}
+
 static size_t fixed_bytes()
 {
-    return align_up(sizeof(QDesc) * kMaxBatch) + align_up(sizeof(uint32_t) * (kMaxBatch + MPDP_MAX_LANES + 1)) +
-           align_up(sizeof(StagedQuery) * kMaxBatch) + align_up(sizeof(DevQuery) * kMaxBatch) +
+    return upload_bytes_max() + align_up(sizeof(StagedQuery) * kMaxBatch) + align_up(sizeof(DevQuery) * kMaxBatch) +
            align_up(sizeof(DevOut) * kMaxBatch) + align_up(sizeof(HashLayout) * kMaxBatch) +
            align_up(sizeof(uint32_t) * MPDP_MAX_LANES * 2 * kLevels * (kMaxBatch + 2));
 }
@@ -295,8 +308,9 @@ static int ensure_fixed(mpdp_ctx* ctx)
         c += align_up(sz);
         return r;
     };
-    ctx->d_desc = reinterpret_cast<QDesc*>(take(sizeof(QDesc) * kMaxBatch));
-    ctx->d_prefix = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (kMaxBatch + MPDP_MAX_LANES + 1)));
+    ctx->d_upload = take(upload_bytes_max());
+    ctx->d_prefix = reinterpret_cast<uint32_t*>(ctx->d_upload);
+    ctx->d_desc = reinterpret_cast<QDesc*>(ctx->d_upload + kUploadPrefixBytes);
     ctx->d_staged = reinterpret_cast<StagedQuery*>(take(sizeof(StagedQuery) * kMaxBatch));
     ctx->d_query = reinterpret_cast<DevQuery*>(take(sizeof(DevQuery) * kMaxBatch));
     ctx->d_out = reinterpret_cast<DevOut*>(take(sizeof(DevOut) * kMaxBatch));
@@ -636,16 +650,27 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
     const std::vector<int> bounds = lane_bounds(qs, ctx->cfg.lanes);
     const int n_lanes = (int)bounds.size() - 1;
     std::vector<Lane> lanes(n_lanes);
-    const size_t desc_bytes = sizeof(QDesc) * nq, pref_bytes = sizeof(uint32_t) * (nq + n_lanes);
-    const size_t staged_off = align_up(desc_bytes) + align_up(pref_bytes);
-    const size_t stage_bytes = staged_off + (host_path ? sizeof(StagedQuery) * nq : 0);
+    // one copy: [prefixes | descriptors | cards | edges], the same layout as
+    // the device upload region (cards and edges on the host path only)
+    const size_t desc_bytes = sizeof(QDesc) * nq;
+    size_t sum_n = 0, sum_m = 0;
+    if (host_path)
+        for (const auto& q : qs) {
+            sum_n += (size_t)q.n;
+            sum_m += (size_t)q.m;
+        }
+    const size_t card_at = kUploadPrefixBytes + align_up(desc_bytes);
+    const size_t edge_at = card_at + align_up(sizeof(double) * sum_n);
+    const size_t stage_bytes = host_path ? edge_at + sizeof(mpdp_edge) * sum_m : kUploadPrefixBytes + desc_bytes;
     char* h = nullptr;
     int slot = 0;
     rc = acquire_stage(ctx, stage_bytes, &h, &slot);
     if (rc != MPDP_OK) return rc;
-    QDesc* hd = reinterpret_cast<QDesc*>(h);
-    uint32_t* hp = reinterpret_cast<uint32_t*>(h + align_up(desc_bytes));
-    StagedQuery* hs = reinterpret_cast<StagedQuery*>(h + staged_off);
+    uint32_t* hp = reinterpret_cast<uint32_t*>(h);
+    QDesc* hd = reinterpret_cast<QDesc*>(h + kUploadPrefixBytes);
+    double* hcard = reinterpret_cast<double*>(h + card_at);
+    mpdp_edge* hedge = reinterpret_cast<mpdp_edge*>(h + edge_at);
+    unsigned long long pack_card = 0, pack_edge = 0;
     std::vector<int> key = {nq,
                             kind,
                             ctx->cfg.heavy_threshold,
@@ -685,8 +710,17 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
         d.cost_model = MPDP_COST_COUT;
         d.memo_base = mbase;
         d.list_base = lbase;
-        d.card_off = q.card_off;
-        d.edge_off = q.edge_off;
+        if (host_path) {  // packed behind the descriptors
+            d.card_off = pack_card;
+            d.edge_off = pack_edge;
+            memcpy(hcard + pack_card, q.card, sizeof(double) * q.n);
+            if (q.m > 0) memcpy(hedge + pack_edge, q.edges, sizeof(mpdp_edge) * q.m);
+            pack_card += (unsigned long long)q.n;
+            pack_edge += (unsigned long long)q.m;
+        } else {
+            d.card_off = q.card_off;
+            d.edge_off = q.edge_off;
+        }
         uint32_t qb = 0;
         fill_levels(d, ctx->cfg.run_length, ctx->cfg.filter, qb);
         d.filter_block_base = fblocks;
@@ -742,38 +776,33 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
         key.push_back(q.n);
         key.push_back(q.enumeration);
         key.push_back(q.m == q.n - 1 ? 1 : 0);  // trees take another filter kernel
-        if (host_path) {
-            StagedQuery& sq = hs[i];
-            sq.n = q.n;
-            sq.n_edges = q.m;
-            sq.cost_model = MPDP_COST_COUT;
-            sq.pad = 0;
-            for (int r = 0; r < kMaxRels; r++) sq.card[r] = r < q.n ? q.card[r] : 1.0;
-            for (int e = 0; e < q.m; e++) sq.edges[e] = q.edges[e];
-        }
     }
     if (!ctx->cfg.fuse_prune) {
         rc = ensure_pairs(ctx, lanes);
         if (rc != MPDP_OK) return rc;
     }
-    CK(ctx, cudaMemcpyAsync(ctx->d_desc, hd, desc_bytes, cudaMemcpyHostToDevice, ctx->stream));
-    CK(ctx, cudaMemcpyAsync(ctx->d_prefix, hp, pref_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->d_upload, h, stage_bytes, cudaMemcpyHostToDevice, ctx->stream));
     if (host_path) {
+        // bytes copied per query: its descriptor, cards and edges; the first
+        // query also carries the prefixes and the alignment padding
+        unsigned long long rest = stage_bytes;
         for (int i = 0; i < nq; i++) {
-            const size_t bytes = offsetof(StagedQuery, edges) + (size_t)qs[i].m * sizeof(mpdp_edge);
-            h2d[i] = bytes;
-            CK(ctx, cudaMemcpyAsync(ctx->d_staged + i, hs + i, bytes, cudaMemcpyHostToDevice, ctx->stream));
+            h2d[i] = sizeof(QDesc) + sizeof(double) * qs[i].n + sizeof(mpdp_edge) * qs[i].m;
+            rest -= h2d[i];
         }
+        h2d[0] += rest;
     }
     CK(ctx, cudaEventRecord(ctx->ring[slot].free_ev, ctx->stream));
     const BatchArgs a = batch_args(ctx, nq, max_n);
     LaunchHook* hook = ctx->profiling ? &ctx->hook : nullptr;
     if (ctx->profiling) ctx->hook.mark(ctx->stream);
     int launches = 0;
-    if (!host_path) {
-        CK(ctx, enqueue_stage_device(a, d_card, d_edges, ctx->stream, hook));
-        launches++;
+    if (host_path) {
+        d_card = reinterpret_cast<const double*>(ctx->d_upload + card_at);
+        d_edges = reinterpret_cast<const mpdp_edge*>(ctx->d_upload + edge_at);
     }
+    CK(ctx, enqueue_stage_device(a, d_card, d_edges, ctx->stream, hook));
+    launches++;
     int ri = -1;
     if (host_path) {
         ri = acquire_record(ctx, nq);

@@ -245,6 +245,27 @@ def test_lanes(opt, lanes, memo, graphs):
     set_cfg(opt)
 
 
+def test_host_upload(opt):
+    """The host path packs a batch's cardinalities and predicates behind the
+    descriptors and sends them in one copy: a mixed batch (single relations
+    without edges, trees, cycles, a clique) gets the oracle's costs and plans
+    back, and the bytes charged to each query cover at least its own values."""
+    set_cfg(opt)
+    qs = [W.Query(n=1, card=[42.0], edges=[]), W.chain(2, seed=3), W.snowflake(17, seed=8),
+          W.Query(n=1, card=[7.0], edges=[]), W.cyclic(13, seed=5), W.clique(9, seed=1),
+          W.star(12, seed=4)]
+    plans = opt.optimize_batch(qs)
+    for q, p in zip(qs, plans):
+        ref = oracle.dpccp(q)
+        assert p.cost == ref.opt_cost
+        assert p.signature() == oracle.plan_signature(oracle.plan_from_memo(q, ref))
+    own = [8 * q.n + 16 * len(q.edges) for q in qs]
+    got = [int(p.stats["h2d_bytes"]) for p in plans]
+    assert all(g >= o for g, o in zip(got, own))
+    # the rest is one descriptor per query, the prefix slot and alignment
+    assert sum(got) - sum(own) < 1024 * len(qs) + 8192
+
+
 @pytest.mark.parametrize("lanes", [1, 4])
 def test_unfused_ablation(opt, lanes):
     """The unfused tree path (pairs to a buffer, then prune + scatter) gives
