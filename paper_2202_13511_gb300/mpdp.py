@@ -303,6 +303,25 @@ def _pack_batch(queries, mode: int = MODE_EXACT, k: int = 0):
     return card, edges, recs
 
 
+class PackedBatch:
+    """A batch already in the ABI's columnar form: every query's cards back to
+    back in one float64 array, its predicates in one mpdp_edge array, and one
+    mpdp_query record per query pointing into them.  Callers that hold their
+    queries as arrays submit this directly and skip the per-tuple conversion
+    of Query objects; the library copies the values on every submit."""
+
+    def __init__(self, queries: Sequence, mode: int = MODE_EXACT, k: int = 0):
+        self.card, self.edges, self.recs = _pack_batch(queries, mode, k)
+        self.n = [int(q.n) for q in queries]
+
+    def __len__(self) -> int:
+        return len(self.n)
+
+
+def pack_batch(queries: Sequence, mode: int = MODE_EXACT, k: int = 0) -> PackedBatch:
+    return PackedBatch(queries, mode, k)
+
+
 def _stats_dict(st: StatsC, n: int) -> Dict:
     L = n + 1
     return dict(
@@ -427,17 +446,19 @@ class Optimizer:
         plan.cost_xd = xd
         return plan
 
-    def submit_batch(self, queries: Sequence, mode: int = MODE_EXACT, k: int = 0) -> List[int]:
+    def submit_batch(self, queries, mode: int = MODE_EXACT, k: int = 0) -> List[int]:
         """Enqueue the queries (mpdp_optimize_batch) and return their handles
-        at once; the inputs are copied before this returns."""
-        card, edges, recs = _pack_batch(queries, mode, k)
-        hs = (ctypes.c_int64 * len(queries))()
-        rc = self._lib.mpdp_optimize_batch(self._ctx, recs.ctypes.data_as(ctypes.POINTER(QueryC)),
-                                           len(queries), hs)
-        del card, edges  # copied by the library before it returned
-        for q, h in zip(queries, hs):
+        at once; the inputs are copied before this returns.  `queries` is a
+        sequence of Query objects or a PackedBatch (whose own mode and k
+        apply)."""
+        pb = queries if isinstance(queries, PackedBatch) else PackedBatch(queries, mode, k)
+        count = len(pb)
+        hs = (ctypes.c_int64 * count)()
+        rc = self._lib.mpdp_optimize_batch(self._ctx, pb.recs.ctypes.data_as(ctypes.POINTER(QueryC)),
+                                           count, hs)
+        for n, h in zip(pb.n, hs):
             if h >= 0:
-                self._n[h] = int(q.n)
+                self._n[h] = n
         if rc != MPDP_OK:
             for h in hs:
                 if h >= 0:
@@ -473,7 +494,7 @@ class Optimizer:
         return [Plan(cost=float(costs[i]), nodes=nodes[i, :nn[i]], raw_stats=stats[i], n=ns[i],
                      handle=int(handles[i])) for i in range(count)]
 
-    def optimize_batch(self, queries: Sequence, mode: int = MODE_EXACT, k: int = 0) -> List[Plan]:
+    def optimize_batch(self, queries, mode: int = MODE_EXACT, k: int = 0) -> List[Plan]:
         return self.collect(self.submit_batch(queries, mode, k))
 
     def memo_lookup(self, handle: int, sets) -> (np.ndarray, np.ndarray):

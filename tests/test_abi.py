@@ -65,3 +65,21 @@ def test_create_without_gpu_fails_cleanly():
     with pytest.raises(mpdp.MPDPError) as ei:
         mpdp.Optimizer(0)
     assert ei.value.code == mpdp.ERR["CUDA"]
+
+
+def test_packed_batch_layout():
+    """The columnar batch: cards and predicates back to back, one record per
+    query pointing at its own slice (no edge pointer for an edgeless query)."""
+    import numpy as np
+    from paper_2202_13511_gb300 import workloads as W
+    qs = [W.chain(3, seed=1), W.Query(n=1, card=[5.0], edges=[]), W.star(4, seed=2)]
+    pb = mpdp.pack_batch(qs)
+    assert len(pb) == 3 and pb.n == [3, 1, 4]
+    assert pb.card.tolist() == qs[0].card + qs[1].card + qs[2].card
+    flat = [e for q in qs for e in q.edges]
+    assert [(int(e["u"]), int(e["v"]), float(e["sel"])) for e in pb.edges] == \
+        [(u, v, s) for u, v, s in flat]
+    assert pb.recs["n_rels"].tolist() == [3, 1, 4]
+    assert pb.recs["n_edges"].tolist() == [2, 0, 3]
+    assert pb.recs["card"].tolist() == [pb.card.ctypes.data + 8 * o for o in (0, 3, 4)]
+    assert pb.recs["edges"].tolist() == [pb.edges.ctypes.data, 0, pb.edges.ctypes.data + 16 * 2]

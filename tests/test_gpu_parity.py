@@ -264,6 +264,13 @@ def test_host_upload(opt):
     assert all(g >= o for g, o in zip(got, own))
     # the rest is one descriptor per query, the prefix slot and alignment
     assert sum(got) - sum(own) < 1024 * len(qs) + 8192
+    # the same batch in columnar form, submitted twice while in flight
+    packed = mpdp.pack_batch(qs)
+    h1 = opt.submit_batch(packed)
+    h2 = opt.submit_batch(packed)
+    for again in (opt.collect(h1), opt.collect(h2)):
+        for p, a in zip(plans, again):
+            assert a.cost == p.cost and a.signature() == p.signature()
 
 
 @pytest.mark.parametrize("lanes", [1, 4])
