@@ -891,8 +891,8 @@ __device__ __forceinline__ uint32_t level_tiles(const BatchArgs& a, int q, int k
 // Tile prefix of every level over the lane's tree queries and, in a second
 // table, over its block-mode queries, once after the filter (a block per
 // level and mode): each evaluate launch then loads its row instead of
-// recomputing it from the queries' counters.  A tree level with few sets
-// gets a set prefix instead and is evaluated a warp per set.
+// recomputing it from the queries' counters.  A tree level evaluated by
+// groups of lanes (see group_size) gets a set prefix instead.
 // Top of a connected set in a tree query: the member whose descendants cover it.
 __device__ __forceinline__ int set_top_of(const DevQuery* __restrict__ q, uint32_t s)
 {
@@ -906,27 +906,89 @@ __device__ __forceinline__ int set_top_of(const DevQuery* __restrict__ q, uint32
 }
 
 constexpr int kPrefStride = kMaxBatch + 2;  // prefix [0, nq], then the level's mapping flag
-// Tree levels with at most this many sets (and k >= kWarpLevelMin) map a
-// warp to a set: each lane takes one split, so the set's k - 1 cost pairs
-// cost one round of memory latency instead of (k - 1) / 2.
-constexpr uint32_t kWarpLevelSets = 1024;
-constexpr int kWarpLevelMin = 8;
+// A tree level may be evaluated by groups of G lanes per set, G the power
+// of two at or above the set's k - 1 splits (2..32): each lane takes one
+// split, so a set's cost pairs cost one round of memory latency instead of a
+// thread's ceil((k - 1) / 2).  A level goes to groups when its sets x G stay
+// within kGroupThreads, else it runs a thread per set.
+constexpr uint32_t kGroupThreads = 1u << 18;
+
+__device__ __forceinline__ uint32_t group_size(uint32_t sets, int k)
+{
+    if (k < 4) return 1u;  // one or two splits: a thread takes them in one round
+    uint32_t g = 2u;
+    while (g < (uint32_t)(k - 1)) g <<= 1;
+    return (unsigned long long)sets * g <= kGroupThreads ? g : 1u;
+}
 
 __global__ void __launch_bounds__(256) k_level_prefix(BatchArgs a, uint32_t* __restrict__ pref)
 {
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     const int k = blockIdx.x / 2 + 2, mode = (blockIdx.x & 1) ? MPDP_ENUM_BLOCKS : MPDP_ENUM_TREE;
     uint32_t* row = pref + ((mode == MPDP_ENUM_BLOCKS ? kLevels : 0) + k) * kPrefStride;
-    uint32_t warp_mode = 0u;
-    if (mode == MPDP_ENUM_TREE && k >= kWarpLevelMin) {
+    uint32_t group = 0u;
+    if (mode == MPDP_ENUM_TREE) {
         const uint32_t sets = block_prefix(a.nq, s_pref, [&](int q) {
             return level_tiles(a, q, k, mode) ? a.out[q].counters.list_count[k] : 0u;
         });
-        warp_mode = sets <= kWarpLevelSets ? 1u : 0u;  // block-uniform
+        const uint32_t g = group_size(sets, k);  // block-uniform
+        group = g > 1u ? g : 0u;
     }
-    if (!warp_mode) block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, mode); });
+    if (!group) block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, mode); });
     for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) row[i] = s_pref[i];
-    if (threadIdx.x == 0) row[kMaxBatch + 1] = warp_mode;
+    if (threadIdx.x == 0) row[kMaxBatch + 1] = group;
+}
+
+// (x, left) minimum over the g lanes of a group (g a power of two <= 32,
+// groups aligned within the warp; mask: the group's lanes).
+__device__ __forceinline__ void group_min_x(unsigned long long& bx, uint32_t& bl, uint32_t g, unsigned mask)
+{
+    for (uint32_t o = g >> 1; o > 0u; o >>= 1) {
+        const unsigned long long ox = __shfl_xor_sync(mask, bx, o);
+        const uint32_t ol = __shfl_xor_sync(mask, bl, o);
+        if (better_x(ox, ol, bx, bl)) {
+            bx = ox;
+            bl = ol;
+        }
+    }
+}
+
+// One tree level by groups of G lanes per set (set g of the level's set
+// prefix s_pref, grid-stride): lane j of a group forms the split below the
+// member of rank j of S minus its top; the group's (x, left) minimum goes to
+// its first lane, which writes the memo and counts the set in s_sets.
+template <class Memo>
+__device__ __forceinline__ void eval_tree_groups(const BatchArgs& a, int k, uint32_t G, Memo& memo,
+                                                 const uint32_t* s_pref, uint32_t* s_sets)
+{
+    const uint32_t nsets = s_pref[a.nq];
+    const uint32_t gl = threadIdx.x & (G - 1u);
+    const unsigned gmask = G == 32u ? kFull : ((1u << G) - 1u) << ((threadIdx.x & 31u) & ~(G - 1u));
+    for (uint32_t g = (blockIdx.x * kEvalThreads + threadIdx.x) / G; g < nsets; g += gridDim.x * (kEvalThreads / G)) {
+        const int qi = find_q(s_pref, a.nq, g);
+        const DevQuery* __restrict__ q = a.query + qi;
+        DevCounters* cnt = &a.out[qi].counters;
+        memo.bind(a, qi);
+        const QDesc& d = a.desc[qi];
+        const uint32_t s = a.lists[d.list_base + d.list_off[k] + (g - s_pref[qi])];
+        const int top = set_top_of(q, s);
+        const int pv = tree_peel_vertex(s, q->adj);
+        const double pbase = gl == 0u ? peel_base(s, pv, *q, memo, cnt) : 0.0;
+        unsigned long long bx = kNoX;
+        uint32_t bl = kFull;
+        const uint32_t rest = s & ~(1u << top);
+        // this lane's split: the member of rest of rank gl (G >= k - 1)
+        if ((int)gl < k - 1) {
+            const uint32_t sl = __ldg(&q->desc[__fns(rest, 0u, gl + 1)]) & s;
+            fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
+        }
+        group_min_x(bx, bl, G, gmask);
+        if (gl == 0u) {
+            const double card_s = peel_finish(pbase, s, pv, *q);
+            memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
+            atomicAdd(&s_sets[qi], 1u);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -943,38 +1005,26 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
 {
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
+    const uint32_t G = level_pref[k * kPrefStride + kMaxBatch + 1];
+    {
+        // a block with no tile (or no group) of this level leaves at once
+        const uint32_t total = level_pref[k * kPrefStride + a.nq];  // tiles, or sets in group mode
+        if (G ? blockIdx.x * (kEvalThreads / G) >= total : blockIdx.x >= total) return;  // block-uniform
+    }
     memo.setup(s_memo);
     for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) s_pref[i] = level_pref[k * kPrefStride + i];
     __syncthreads();
-    if (level_pref[k * kPrefStride + kMaxBatch + 1]) {  // a warp per set (s_pref: set prefix)
-        const uint32_t nsets = s_pref[a.nq];
-        const int lane = threadIdx.x & 31;
-        const uint32_t stride = gridDim.x * (kEvalThreads / 32);
-        for (uint32_t g = blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5); g < nsets; g += stride) {
-            const int qi = find_q(s_pref, a.nq, g);
-            const DevQuery* __restrict__ q = a.query + qi;
-            DevCounters* cnt = &a.out[qi].counters;
-            memo.bind(a, qi);
-            const QDesc& d = a.desc[qi];
-            const uint32_t s = a.lists[d.list_base + d.list_off[k] + (g - s_pref[qi])];
-            const int top = set_top_of(q, s);
-            const int pv = tree_peel_vertex(s, q->adj);
-            const double pbase = lane == 0 ? peel_base(s, pv, *q, memo, cnt) : 0.0;
-            unsigned long long bx = kNoX;
-            uint32_t bl = kFull;
-            if (lane < k - 1) {
-                const int v = (int)__fns(s & ~(1u << top), 0u, lane + 1);
-                const uint32_t sl = __ldg(&q->desc[v]) & s;
-                fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
+    if (G) {  // groups of G lanes per set (s_pref: set prefix); block-uniform
+        __shared__ uint32_t s_sets[kMaxBatch];  // sets evaluated per query
+        for (int i = threadIdx.x; i < a.nq; i += blockDim.x) s_sets[i] = 0u;
+        __syncthreads();
+        eval_tree_groups(a, k, G, memo, s_pref, s_sets);
+        __syncthreads();
+        for (int i = threadIdx.x; i < a.nq; i += blockDim.x)
+            if (s_sets[i]) {
+                atomicAdd(&a.out[i].counters.evaluated[k], (unsigned long long)s_sets[i] * (unsigned long long)(k - 1));
+                atomicAdd(&a.out[i].counters.ccp[k], (unsigned long long)s_sets[i] * (unsigned long long)(k - 1));
             }
-            warp_min_x(bx, bl);
-            if (lane == 0) {
-                const double card_s = peel_finish(pbase, s, pv, *q);
-                memo.put(s, k, set_cost(bx, card_s), card_s, bl, cnt);
-                atomicAdd(&cnt->evaluated[k], (unsigned long long)(k - 1));
-                atomicAdd(&cnt->ccp[k], (unsigned long long)(k - 1));
-            }
-        }
         return;
     }
     const uint32_t tiles = s_pref[a.nq];
@@ -1684,7 +1734,15 @@ static void launch_levels(const BatchArgs& a, const BatchPlan& bp, Memo memo, cu
     for (int k = 2; k <= a.max_n; k++) {
         const unsigned long long tree_tiles = bp.tree_tiles[k], block_tiles = bp.block_tiles[k];
         if (tree_tiles) {
-            const int grid = (int)(tree_tiles < (unsigned long long)cap_blocks ? tree_tiles : cap_blocks);
+            // enough blocks for a level evaluated by groups of lanes: up to
+            // kGroupThreads threads, at most 32 per set
+            unsigned long long want = tree_tiles;
+            if (!bp.pairs) {
+                const unsigned long long groups = kGroupThreads / kEvalThreads;
+                const unsigned long long most = tree_tiles * 32ull < groups ? tree_tiles * 32ull : groups;
+                if (most > want) want = most;
+            }
+            const int grid = (int)(want < (unsigned long long)cap_blocks ? want : cap_blocks);
             if (bp.pairs) {
                 {
                     HookScope hs(hook, MPDP_KC_EVAL, st);
