@@ -54,13 +54,17 @@ BYTES_PER_SET = 16
 # dominant kernels on this bench's 64-query batch (4 lanes of 16 queries), from
 # one ncu capture of this bench command (--cache-control none; profiles/).
 # Each figure describes the kernel whose source fingerprint is given (the
-# kernel's own text plus the device header it includes) and is reported as
-# null once that source changes.
+# kernel's own text, the device functions it relies on and the device header
+# it includes) and is reported as null once that source changes.
 KERNEL_FILE = "paper_2202_13511_gb300/csrc/mpdp_kernels.cu"
 DEVICE_HEADER = "paper_2202_13511_gb300/csrc/mpdp_device.cuh"
-TRAFFIC = {"eval": {"kernel": "k_eval_tree", "sha1": "2e1dd4e15daf43b93c886e5eed77c9171cf1803a", "bytes": 5339831},
-           "filter": {"kernel": "k_filter_connected", "sha1": "0516ed8ef9a7bba748b4ca0e7cc80a54ad9ccca0",
-                      "bytes": 14382372}}
+TRAFFIC = {"eval": {"kernel": "k_eval_tree",
+                    "helpers": ("find_q", "set_top_of", "group_size", "group_min_x", "eval_tree_groups",
+                                "k_level_prefix", "block_prefix"),
+                    "sha1": "efd04f922da922251021c25b1fef3f2b882e374d", "bytes": 5339176},
+           "filter": {"kernel": "k_filter_connected",
+                      "helpers": ("unrank_connected", "connected_items", "block_prefix", "find_q"),
+                      "sha1": "546d6cdb822a46341ddcfeb005e5289aa437834a", "bytes": 14434539}}
 
 
 def parse_args():
@@ -400,13 +404,11 @@ def kernel_passes(opt, step, flush, prof_steps, mpdp):
     return out[0], out[1]
 
 
-def kernel_fingerprint(name):
-    """SHA-1 of a kernel's definition in the kernel file (from its template
-    line or signature to the closing brace) and of the device header."""
-    import hashlib
+def _definition(src, name):
+    """Text of a kernel's or device function's definition in the kernel file:
+    from its template line or signature to the closing brace."""
     import re
-    src = open(os.path.join(ROOT, KERNEL_FILE)).read()
-    m = re.search(r"(template <class Memo>\n)?__global__ void [^\n]*\b" + name + r"\(", src)
+    m = re.search(r"(template <[^\n]*>\n)?(__global__|__device__)[^\n]*\b" + name + r"\(", src)
     if m is None:
         return None
     depth, i = 0, src.index("{", m.end())
@@ -414,7 +416,20 @@ def kernel_fingerprint(name):
         depth += {"{": 1, "}": -1}.get(src[j], 0)
         if depth == 0:
             break
-    h = hashlib.sha1(src[m.start():j + 1].encode())
+    return src[m.start():j + 1]
+
+
+def kernel_fingerprint(name, helpers=()):
+    """SHA-1 of a kernel's definition, of the device functions it relies on
+    (`helpers`, in the kernel file) and of the device header."""
+    import hashlib
+    src = open(os.path.join(ROOT, KERNEL_FILE)).read()
+    h = hashlib.sha1()
+    for part in (name,) + tuple(helpers):
+        text = _definition(src, part)
+        if text is None:
+            return None
+        h.update(text.encode())
     h.update(open(os.path.join(ROOT, DEVICE_HEADER), "rb").read())
     return h.hexdigest()
 
@@ -425,7 +440,7 @@ def traffic_for(kind, measured):
     t = TRAFFIC.get(kind)
     if not measured or t is None:
         return None
-    return t["bytes"] if kernel_fingerprint(t["kernel"]) == t["sha1"] else None
+    return t["bytes"] if kernel_fingerprint(t["kernel"], t["helpers"]) == t["sha1"] else None
 
 
 def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False, serial=None, filter_mode=2):

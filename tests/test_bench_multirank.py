@@ -62,3 +62,18 @@ def test_reference_arm_runs_on_rank_zero_only():
                        timeout=300)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_traffic_fingerprints_resolve():
+    """Every kernel and device function a traffic figure depends on is found
+    in the kernel file, so the fingerprint is well defined; a change to any
+    of them changes it."""
+    src = open(os.path.join(ROOT, bench.KERNEL_FILE)).read()
+    for t in bench.TRAFFIC.values():
+        for name in (t["kernel"],) + tuple(t["helpers"]):
+            text = bench._definition(src, name)
+            assert text is not None and text.rstrip().endswith("}")
+            assert name + "(" in text.splitlines()[0] or name + "(" in text.splitlines()[1]
+        fp = bench.kernel_fingerprint(t["kernel"], t["helpers"])
+        assert fp is not None and len(fp) == 40
+        assert fp != bench.kernel_fingerprint(t["kernel"], t["helpers"][:-1])
