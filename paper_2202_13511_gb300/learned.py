@@ -43,12 +43,10 @@ def edge_labels(q, nodes: np.ndarray) -> np.ndarray:
     over n (plans of n <= 64 carry relation bitmaps)."""
     sets = nodes["set"].astype(np.uint64)
     leaves = nodes["n_leaves"].astype(np.int64)
-    out = np.empty(len(q.edges), dtype=np.float32)
-    for e, (u, v, _s) in enumerate(q.edges):
-        both = np.uint64((1 << u) | (1 << v))
-        hit = (sets & both) == both
-        out[e] = leaves[hit].min() / q.n
-    return out
+    both = np.array([(1 << u) | (1 << v) for u, v, _s in q.edges], dtype=np.uint64)
+    hit = (sets[None, :] & both[:, None]) == both[:, None]
+    # the root holds every relation, so each edge has a hit
+    return (np.where(hit, leaves[None, :], np.iinfo(np.int64).max).min(axis=1) / q.n).astype(np.float32)
 
 
 def build_dataset(opt: "mpdp.Optimizer", queries: Sequence, batch: int = 256) -> Tuple[np.ndarray, np.ndarray]:
