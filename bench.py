@@ -79,6 +79,8 @@ def parse_args():
                    help="skip the extra shapes (star-25, cyclic-20, clique-14)")
     p.add_argument("--no-verify", action="store_true")
     p.add_argument("--tune", action="store_true", help="autotuned launch configuration instead of the library defaults")
+    p.add_argument("--large-queries", type=int, default=LARGE_QUERIES,
+                   help="queries per size in the large and learned lines (the workload's full form: 100)")
     return p.parse_args()
 
 
@@ -230,6 +232,9 @@ def run_reference(args):
 def run_ours(args):
     import numpy as np
     import torch
+
+    global LARGE_QUERIES
+    LARGE_QUERIES = max(1, args.large_queries)
 
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
