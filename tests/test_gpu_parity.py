@@ -130,6 +130,32 @@ def test_snowflake_full_size(opt, n):
             check(opt, q, ref, memo="sample")
 
 
+def test_bench_batch_full_size(opt):
+    """The benchmark's own step: 64 snowflake-25 queries (seeds 0..63) in one
+    device batch in the library's default launch configuration (4 lanes of
+    16; the middle levels then run a thread per set, the small ones groups of
+    lanes).  Every query's cost and plan equal the oracle's, and so do sampled
+    memo entries of one query per lane."""
+    set_cfg(opt)
+    qs = [W.snowflake(25, seed=i) for i in range(64)]
+    refs = [oracle.dpccp(q) for q in qs]
+    hs = opt.submit_batch(qs)
+    try:
+        for i in (0, 21, 42, 63):
+            sets = refs[i].connected_sets()
+            rng = np.random.default_rng(1000 + i)
+            sets = np.sort(rng.choice(sets, size=min(len(sets), 20000), replace=False))
+            costs, lefts = opt.memo_lookup(hs[i], sets)
+            assert np.array_equal(costs.view(np.uint64), refs[i].cost[sets].view(np.uint64))
+            assert np.array_equal(lefts, refs[i].left[sets].astype(np.uint64))
+    finally:
+        plans = opt.collect(hs)
+    for q, p, ref in zip(qs, plans, refs):
+        assert np.float64(p.cost).tobytes() == np.float64(ref.opt_cost).tobytes()
+        assert p.signature() == oracle.plan_signature(oracle.plan_from_memo(q, ref))
+        assert np.array_equal(p.stats["ccp_per_level"][2:], ref.ccp[2:26])
+
+
 def test_snowflake_25_blocks_and_hash(opt):
     """Block-based enumeration and the hash memo agree on trees too."""
     q = W.snowflake(25, seed=5)
