@@ -189,9 +189,23 @@ def cpu_baseline(queries, budget_s: float):
         if time.perf_counter() - t0 >= budget_s:
             break
     el = time.perf_counter() - t0
+    # DPSUB (Algorithm 1, the vertex-based DP the paper's GPU baseline runs)
+    # on one core at 18 relations, where its 3^n pair loop still ends in
+    # seconds, beside DPCCP on the same queries
+    dpsub = {}
+    for kind in ("snowflake", "star"):
+        from paper_2202_13511_gb300 import workloads as W
+        q = W.make(kind, 18, seed=0)
+        t1 = time.perf_counter()
+        oracle.dpsub(q)
+        t2 = time.perf_counter()
+        oracle.dpccp(q)
+        t3 = time.perf_counter()
+        dpsub[f"{kind}18"] = {"dpsub_ms": 1000.0 * (t2 - t1), "dpccp_ms": 1000.0 * (t3 - t2)}
     return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {done} of the step's {len(queries)} queries, DPCCP on 1 host core, "
-                      f"{el:.1f} s"}
+                      f"{el:.1f} s",
+            "dpsub_1core": dpsub}
 
 
 def run_reference(args):
