@@ -158,10 +158,16 @@ typedef struct {
     uint64_t ccp_pairs;
     uint64_t memo_bytes;       /* device bytes of the memo used by this query */
     uint64_t heavy_sets;       /* block mode: sets evaluated by the chunked heavy-set kernel */
-    double device_ms;          /* device time of the DP (CUDA events) */
+    double device_ms;          /* device time of the batch's DP, from after its
+                                  upload and staging to the end of plan fetch (CUDA
+                                  events) */
     int32_t enumeration;       /* MPDP_ENUM_TREE or MPDP_ENUM_BLOCKS as run */
     int32_t memo_kind;         /* MPDP_MEMO_* as run */
-    uint64_t h2d_bytes;        /* host -> device bytes copied for this query */
+    uint64_t h2d_bytes;        /* host -> device bytes copied for this query: its
+                                  descriptor, cards and edges in the batch's one
+                                  upload copy; the batch's first query also carries
+                                  the filter prefixes and alignment padding, so the
+                                  batch's queries sum to the copy's size */
     uint64_t d2h_bytes;        /* device -> host bytes copied for this query */
     uint64_t filter_steps;     /* BFS rounds run by the filter for sets with no isolated vertex */
     uint64_t connected_per_level[MPDP_MAX_LEVELS];
