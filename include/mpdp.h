@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define MPDP_ABI_VERSION 4
+#define MPDP_ABI_VERSION 5
 /* Exact mode uses 32-bit relation bitmaps; memory grows as 2^n (see
  * mpdp_workspace_bytes), so n is further capped by the memo budget. */
 #define MPDP_MAX_EXACT_RELS 30
@@ -203,6 +203,13 @@ typedef struct {
                                  CCP pair's (cost sum, left) to a buffer of
                                  16 B x the largest level's sets x (k - 1),
                                  a second prunes and scatters.  Same results. */
+    int32_t group_threads_log2; /* per-level work split of tree-mode levels: a
+                                 level with k >= 4 whose sets x G stay within
+                                 2^group_threads_log2 threads (G, the power of
+                                 two at or above k - 1) runs G lanes per set,
+                                 one split each; other levels run a thread per
+                                 set.  0 (never groups) or 8..24; default 18.
+                                 Results do not depend on it. */
 } mpdp_config;
 
 /* Create a context on CUDA device `device`.  memo_budget_bytes caps the device

@@ -27,6 +27,9 @@ KERNEL_SPACE: Dict[str, List[int]] = {
     "use_ccc": [0, 1],
     "filter": [2, 0, 1],  # MPDP_FILTER_CONNECTED, _BITMAPS, _UNRANK
     "lanes": [1, 2, 4, 8],
+    # per-level work split of tree levels: groups of lanes per set while a
+    # level's sets x G stay within 2^this threads (0: a thread per set)
+    "group_threads_log2": [18, 16, 17, 19, 20, 0],
 }
 SERVER_SPACE: Dict[str, List[int]] = {
     "slots": [1, 2, 4, 8],
@@ -67,11 +70,15 @@ def coordinate_descent(start: Dict[str, int], space: Dict[str, List[int]],
 
 def relevant_space(queries: Sequence) -> Dict[str, List[int]]:
     """The kernel knobs that can matter for these queries: the block-mode
-    knobs only when some query is not a tree."""
+    knobs only when some query is not a tree, the tree levels' work split
+    only when some query is one."""
     space = dict(KERNEL_SPACE)
-    if all(len(q.edges) == q.n - 1 for q in queries):
+    trees = [len(q.edges) == q.n - 1 for q in queries]
+    if all(trees):
         space.pop("heavy_threshold")
         space.pop("use_ccc")
+    if not any(trees):
+        space.pop("group_threads_log2")
     return space
 
 
@@ -124,7 +131,8 @@ def tune_kernels(queries: Sequence, device: int = 0, reps: int = 3,
     Returns (config dict for Optimizer.set_config / Server kernel config,
     its time in seconds, the measured history)."""
     space = relevant_space(queries)
-    start = {"grid_blocks_per_sm": 8, "heavy_threshold": 64, "use_ccc": 1, "filter": 2, "lanes": 4}
+    start = {"grid_blocks_per_sm": 8, "heavy_threshold": 64, "use_ccc": 1, "filter": 2, "lanes": 4,
+             "group_threads_log2": 18}
     start = {k: v for k, v in start.items() if k in space}
     own = measure is None
     if own:

@@ -27,7 +27,7 @@ using namespace mpdp;
 
 namespace {
 
-const mpdp_config kDefaultConfig = {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 1, 32, MPDP_FILTER_CONNECTED, 8, 4, 1};
+const mpdp_config kDefaultConfig = {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 1, 32, MPDP_FILTER_CONNECTED, 8, 4, 1, 18};
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -680,6 +680,7 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
                             ctx->cfg.grid_blocks_per_sm,
                             ctx->cfg.enumeration,
                             ctx->cfg.fuse_prune,
+                            ctx->cfg.group_threads_log2,
                             n_lanes};
     unsigned long long lbase = 0, mbase = 0, hbase = 0, abase = 0;
     uint32_t fblocks = 0;
@@ -695,6 +696,7 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
             ln.q1 = bounds[lane + 1];
             ln.bp.num_sms = ctx->num_sms;
             ln.bp.blocks_per_sm = ctx->cfg.grid_blocks_per_sm;
+            ln.bp.group_threads = ctx->cfg.group_threads_log2 ? 1u << ctx->cfg.group_threads_log2 : 0u;
             ln.bp.level_pref = ctx->d_level_pref + (size_t)lane * 2 * kLevels * (kMaxBatch + 2);
             ln.a.arena_begin = abase;
             fblocks = 0;
@@ -951,6 +953,8 @@ int mpdp_set_config(mpdp_ctx* ctx, const mpdp_config* cfg)
     if (cfg->grid_blocks_per_sm < 1 || cfg->grid_blocks_per_sm > 32) return MPDP_ERR_INVALID_ARG;
     if (cfg->lanes < 1 || cfg->lanes > MPDP_MAX_LANES) return MPDP_ERR_INVALID_ARG;
     if (cfg->fuse_prune != 0 && cfg->fuse_prune != 1) return MPDP_ERR_INVALID_ARG;
+    if (cfg->group_threads_log2 != 0 && (cfg->group_threads_log2 < 8 || cfg->group_threads_log2 > 24))
+        return MPDP_ERR_INVALID_ARG;
     ctx->cfg = *cfg;
     return MPDP_OK;
 }

@@ -910,18 +910,17 @@ constexpr int kPrefStride = kMaxBatch + 2;  // prefix [0, nq], then the level's 
 // of two at or above the set's k - 1 splits (2..32): each lane takes one
 // split, so a set's cost pairs cost one round of memory latency instead of a
 // thread's ceil((k - 1) / 2).  A level goes to groups when its sets x G stay
-// within kGroupThreads, else it runs a thread per set.
-constexpr uint32_t kGroupThreads = 1u << 18;
-
-__device__ __forceinline__ uint32_t group_size(uint32_t sets, int k)
+// within `limit` threads (the context's per-level split knob; 0: never),
+// else it runs a thread per set.
+__device__ __forceinline__ uint32_t group_size(uint32_t sets, int k, uint32_t limit)
 {
     if (k < 4) return 1u;  // one or two splits: a thread takes them in one round
     uint32_t g = 2u;
     while (g < (uint32_t)(k - 1)) g <<= 1;
-    return (unsigned long long)sets * g <= kGroupThreads ? g : 1u;
+    return (unsigned long long)sets * g <= limit ? g : 1u;
 }
 
-__global__ void __launch_bounds__(256) k_level_prefix(BatchArgs a, uint32_t* __restrict__ pref)
+__global__ void __launch_bounds__(256) k_level_prefix(BatchArgs a, uint32_t* __restrict__ pref, uint32_t group_threads)
 {
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     const int k = blockIdx.x / 2 + 2, mode = (blockIdx.x & 1) ? MPDP_ENUM_BLOCKS : MPDP_ENUM_TREE;
@@ -931,7 +930,7 @@ __global__ void __launch_bounds__(256) k_level_prefix(BatchArgs a, uint32_t* __r
         const uint32_t sets = block_prefix(a.nq, s_pref, [&](int q) {
             return level_tiles(a, q, k, mode) ? a.out[q].counters.list_count[k] : 0u;
         });
-        const uint32_t g = group_size(sets, k);  // block-uniform
+        const uint32_t g = group_size(sets, k, group_threads);  // block-uniform
         group = g > 1u ? g : 0u;
     }
     if (!group) block_prefix(a.nq, s_pref, [&](int q) { return level_tiles(a, q, k, mode); });
@@ -1728,17 +1727,17 @@ static void launch_levels(const BatchArgs& a, const BatchPlan& bp, Memo memo, cu
     for (int k = 2; k <= a.max_n; k++) any = any || bp.tree_tiles[k] != 0 || bp.block_tiles[k] != 0;
     if (any) {
         HookScope hs(hook, MPDP_KC_MEMO_INIT, st);
-        k_level_prefix<<<2 * (a.max_n - 1), 256, 0, st>>>(a, bp.level_pref);
+        k_level_prefix<<<2 * (a.max_n - 1), 256, 0, st>>>(a, bp.level_pref, bp.group_threads);
         launches++;
     }
     for (int k = 2; k <= a.max_n; k++) {
         const unsigned long long tree_tiles = bp.tree_tiles[k], block_tiles = bp.block_tiles[k];
         if (tree_tiles) {
             // enough blocks for a level evaluated by groups of lanes: up to
-            // kGroupThreads threads, at most 32 per set
+            // group_threads threads, at most 32 per set
             unsigned long long want = tree_tiles;
-            if (!bp.pairs) {
-                const unsigned long long groups = kGroupThreads / kEvalThreads;
+            if (!bp.pairs && bp.group_threads) {
+                const unsigned long long groups = bp.group_threads / kEvalThreads;
                 const unsigned long long most = tree_tiles * 32ull < groups ? tree_tiles * 32ull : groups;
                 if (most > want) want = most;
             }

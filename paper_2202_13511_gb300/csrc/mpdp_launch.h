@@ -25,6 +25,7 @@ struct BatchPlan {
     int blocks_per_sm = 8;  // eval grids: 8 x 256 threads = a full SM's worth of warps
     uint32_t filter_blocks = 0;     // bitmap / unrank filter blocks
     uint32_t connected_blocks = 0;  // k_filter_connected grid (tree queries in mode CONNECTED)
+    uint32_t group_threads = 1u << 18;  // tree levels: groups of lanes while sets x G <= this (0: never)
     PairRec* pairs = nullptr;  // non-null: tree levels run unfused (evaluate, then prune + scatter)
     uint32_t* level_pref = nullptr;  // [2][kLevels][kMaxBatch + 1]: per-level tile prefix, tree then block mode
     unsigned long long tree_tiles[kLevels] = {};   // upper bound of level-k tiles, tree queries

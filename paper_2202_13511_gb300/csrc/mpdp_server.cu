@@ -62,7 +62,7 @@ struct mpdp_server {
 namespace {
 
 const mpdp_server_config kDefaultServer = {4, 256, 0, {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 0, 32,
-                                                       MPDP_FILTER_CONNECTED, 8, 4, 1}};
+                                                       MPDP_FILTER_CONNECTED, 8, 4, 1, 18}};
 constexpr size_t kDefaultSlotBudget = (size_t)16 << 30;
 
 size_t slot_budget(const mpdp_server* s)

@@ -82,7 +82,8 @@ class ConfigC(ctypes.Structure):
                 ("heavy_threshold", ctypes.c_int32), ("use_ccc", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("run_length", ctypes.c_int32),
                 ("filter", ctypes.c_int32), ("grid_blocks_per_sm", ctypes.c_int32),
-                ("lanes", ctypes.c_int32), ("fuse_prune", ctypes.c_int32)]
+                ("lanes", ctypes.c_int32), ("fuse_prune", ctypes.c_int32),
+                ("group_threads_log2", ctypes.c_int32)]
 
 
 class ServerConfigC(ctypes.Structure):
@@ -123,6 +124,9 @@ def lib_path() -> str:
     return _build.LIB_PATH
 
 
+ABI_VERSION = 5  # MPDP_ABI_VERSION of include/mpdp.h this binding's structs follow
+
+
 def load(build_if_missing: bool = True):
     """Load libmpdp.so (building it first when it is missing or stale)."""
     global _LIB
@@ -134,6 +138,10 @@ def load(build_if_missing: bool = True):
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
     L = ctypes.CDLL(path)
+    L.mpdp_abi_version.restype = ctypes.c_int32
+    if L.mpdp_abi_version() != ABI_VERSION:
+        raise RuntimeError(f"{path} has ABI {L.mpdp_abi_version()}, this binding needs {ABI_VERSION}; "
+                           "rebuild with __graft_entry__.build()")
     P = ctypes.POINTER
     c_ctx = ctypes.c_void_p
     L.mpdp_create.argtypes = [P(c_ctx), ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]

@@ -34,13 +34,13 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(mpdp.Edge) == 16
     assert ctypes.sizeof(mpdp.PlanNode) == 40
     assert ctypes.sizeof(mpdp.QueryC) == 40
-    assert ctypes.sizeof(mpdp.ConfigC) == 40
+    assert ctypes.sizeof(mpdp.ConfigC) == 44
     assert ctypes.sizeof(mpdp.StatsC) == 6 * 8 + 8 + 8 + 3 * 8 + 3 * 33 * 8
 
 
 def test_abi_version_and_strerror():
     lib = mpdp.load()
-    assert lib.mpdp_abi_version() == 4
+    assert lib.mpdp_abi_version() == 5
     assert mpdp.strerror(0) == "ok"
     for code in mpdp.ERRORS:
         assert mpdp.strerror(code) != "unknown error"

@@ -30,9 +30,12 @@ def test_coordinate_descent_keeps_start_on_ties():
 
 def test_relevant_space_drops_block_knobs_for_trees():
     trees = [W.snowflake(10, seed=s) for s in range(3)]
-    assert set(autotune.relevant_space(trees)) == {"grid_blocks_per_sm", "filter", "lanes"}
+    assert set(autotune.relevant_space(trees)) == {"grid_blocks_per_sm", "filter", "lanes",
+                                                   "group_threads_log2"}
     mixed = trees + [W.cyclic(10, seed=1)]
     assert set(autotune.relevant_space(mixed)) == set(autotune.KERNEL_SPACE)
+    cycles = [W.cyclic(10, seed=s) for s in range(2)]
+    assert set(autotune.relevant_space(cycles)) == set(autotune.KERNEL_SPACE) - {"group_threads_log2"}
 
 
 def test_tune_kernels_with_injected_timer():

@@ -38,7 +38,7 @@ def opt():
 def set_cfg(opt, **kw):
     base = dict(memo_kind=mpdp.MEMO_DENSE, enumeration=mpdp.ENUM_AUTO, heavy_threshold=64,
                 use_ccc=1, use_graphs=1, run_length=32, filter=mpdp.FILTER_CONNECTED,
-                grid_blocks_per_sm=8, lanes=4, fuse_prune=1)
+                grid_blocks_per_sm=8, lanes=4, fuse_prune=1, group_threads_log2=18)
     base.update(kw)
     opt.set_config(**base)
 
@@ -314,8 +314,38 @@ def test_unfused_ablation(opt, lanes):
     set_cfg(opt)
 
 
+@pytest.mark.parametrize("log2", [0, 8, 24])
+def test_group_split_knob(opt, log2):
+    """The tree levels' work split (a thread per set, or groups of lanes
+    while sets x G stay within 2^log2 threads) changes no result: costs,
+    plans, CCP counts and sampled memo entries equal the oracle's at both
+    ends of the knob and with it off."""
+    set_cfg(opt, group_threads_log2=log2)
+    qs = ([W.snowflake(20, seed=s) for s in range(6)] + [W.star(16, seed=1), W.chain(22, seed=2)]
+          + [W.snowflake(25, seed=7)])
+    refs = [oracle.dpccp(q) for q in qs]
+    hs = opt.submit_batch(qs)
+    try:
+        for h, ref in zip(hs, refs):
+            sets = ref.connected_sets()
+            rng = np.random.default_rng(77)
+            sets = np.sort(rng.choice(sets, size=min(len(sets), 5000), replace=False))
+            costs, lefts = opt.memo_lookup(h, sets)
+            assert np.array_equal(costs.view(np.uint64), ref.cost[sets].view(np.uint64))
+            assert np.array_equal(lefts, ref.left[sets].astype(np.uint64))
+    finally:
+        plans = opt.collect(hs)
+    for q, p, ref in zip(qs, plans, refs):
+        assert np.float64(p.cost).tobytes() == np.float64(ref.opt_cost).tobytes()
+        assert p.signature() == oracle.plan_signature(oracle.plan_from_memo(q, ref))
+        assert np.array_equal(p.stats["evaluated_per_level"], p.stats["ccp_per_level"])
+        assert np.array_equal(p.stats["ccp_per_level"][2:], ref.ccp[2:q.n + 1])
+    set_cfg(opt)
+
+
 def test_lanes_bad_config(opt):
-    for kw in (dict(lanes=0), dict(lanes=9), dict(fuse_prune=2)):
+    for kw in (dict(lanes=0), dict(lanes=9), dict(fuse_prune=2), dict(group_threads_log2=7),
+               dict(group_threads_log2=25), dict(group_threads_log2=-1)):
         with pytest.raises(mpdp.MPDPError) as ei:
             opt.set_config(**kw)
         assert ei.value.code == mpdp.ERR["INVALID_ARG"]
