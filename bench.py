@@ -61,10 +61,10 @@ DEVICE_HEADER = "paper_2202_13511_gb300/csrc/mpdp_device.cuh"
 TRAFFIC = {"eval": {"kernel": "k_eval_tree",
                     "helpers": ("find_q", "set_top_of", "group_size", "group_min_x", "eval_tree_groups",
                                 "k_level_prefix", "block_prefix"),
-                    "sha1": "efd04f922da922251021c25b1fef3f2b882e374d", "bytes": 5339176},
+                    "sha1": "14a6e7ac1c41dca0f8fd967cd9a46710f1b08bf6", "bytes": 5319349},
            "filter": {"kernel": "k_filter_connected",
                       "helpers": ("unrank_connected", "connected_items", "block_prefix", "find_q"),
-                      "sha1": "546d6cdb822a46341ddcfeb005e5289aa437834a", "bytes": 14434539}}
+                      "sha1": "546d6cdb822a46341ddcfeb005e5289aa437834a", "bytes": 13892070}}
 
 
 def parse_args():
