@@ -38,6 +38,18 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(mpdp.StatsC) == 6 * 8 + 8 + 8 + 3 * 8 + 3 * 33 * 8
 
 
+def test_binding_follows_the_header_abi():
+    """The binding's struct layouts are written for one ABI version: the
+    header's MPDP_ABI_VERSION, which the library also reports."""
+    m = re.search(r"#define MPDP_ABI_VERSION (\d+)", open(HEADER).read())
+    assert m and int(m.group(1)) == mpdp.ABI_VERSION
+    assert mpdp.load().mpdp_abi_version() == mpdp.ABI_VERSION
+    fields = [f for f, _ in mpdp.ConfigC._fields_]
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\} mpdp_config;", src).group(1)
+    assert re.findall(r"int32_t (\w+);", body) == fields
+
+
 def test_abi_version_and_strerror():
     lib = mpdp.load()
     assert lib.mpdp_abi_version() == 5
