@@ -44,10 +44,19 @@ def test_binding_follows_the_header_abi():
     m = re.search(r"#define MPDP_ABI_VERSION (\d+)", open(HEADER).read())
     assert m and int(m.group(1)) == mpdp.ABI_VERSION
     assert mpdp.load().mpdp_abi_version() == mpdp.ABI_VERSION
-    fields = [f for f, _ in mpdp.ConfigC._fields_]
     src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
-    body = re.search(r"typedef struct \{([^}]*)\} mpdp_config;", src).group(1)
-    assert re.findall(r"int32_t (\w+);", body) == fields
+    for name, cls in (("mpdp_config", mpdp.ConfigC), ("mpdp_query", mpdp.QueryC),
+                      ("mpdp_stats", mpdp.StatsC), ("mpdp_plan_node", mpdp.PlanNode),
+                      ("mpdp_edge", mpdp.Edge)):
+        body = re.search(r"typedef struct \{([^}]*)\} " + name + ";", src).group(1)
+        declared = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if decl:
+                # "type a, b" or "type *p" or "type arr[N]": the field names in order
+                rest = re.sub(r"^(const\s+)?\w+\s*", "", decl)
+                declared += [re.sub(r"[*\s]|\[.*\]", "", v) for v in rest.split(",")]
+        assert declared == [f for f, _ in cls._fields_], name
 
 
 def test_abi_version_and_strerror():
