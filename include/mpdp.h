@@ -76,7 +76,8 @@ enum {
     MPDP_MODE_IDP2 = 1,
     MPDP_MODE_UNIONDP = 2,
     MPDP_MODE_IDP2_LEARNED = 3,
-    MPDP_MODE_UNIONDP_LEARNED = 4
+    MPDP_MODE_UNIONDP_LEARNED = 4,
+    MPDP_MODE_UNIONDP_SIZEFIRST = 5
 };
 
 /* CCP enumeration: AUTO picks TREE when the join graph is a tree
@@ -228,7 +229,14 @@ size_t mpdp_workspace_bytes(int32_t n_rels, const mpdp_config *cfg);
  * stream and return a handle at once (asynchronous).  Exact mode: n <= 30.
  * Heuristic modes (Sec. 4): MPDP_MODE_IDP2 (GOO's plan, then IDP2 with
  * sub-problems of at most k <= 25 relations) and MPDP_MODE_UNIONDP
- * (Algorithm 5 with partitions of at most t and a final DP of at most k),
+ * (Algorithm 5 with partitions of at most t and a final DP of at most k:
+ * each round orders its edges once, before the union loop, by increasing
+ * weight = the card of joining the edge's two nodes, ties by node ids, and
+ * unites the sets across each edge in one pass while their size sum stays
+ * within t), n <= MPDP_MAX_HEURISTIC_RELS.  MPDP_MODE_UNIONDP_SIZEFIRST is
+ * a comparison reading of the same algorithm: after every union the next
+ * edge is the one between different sets with the least (current size
+ * sum, weight, node ids), and an edge whose sum exceeds t is dropped.
  * n <= MPDP_MAX_HEURISTIC_RELS.  Every sub-problem is solved exactly on the
  * device in extended range; these modes run to completion before the call
  * returns.  Plan nodes of n > 64 relations carry set = 0.

@@ -32,17 +32,28 @@ Readings where the paper is silent (the product path follows the same ones):
     cannot change its leaves.  Ties go to the first in pre-order (left
     first).  Re-plan T' with the exact DP over its leaves and replace it by
     the resulting plan, a single leaf.
-  * UnionDP(k, t): if the graph has at most k nodes, the exact DP over all
-    of them.  Otherwise each edge weighs the card of joining its two nodes.
-    Union-find over the nodes (size = number of nodes).  Repeatedly take
-    the edge between different sets with the least (size sum, weight,
-    smaller node, larger node).  Union when the size sum is at most t, else
-    drop the edge: sizes only grow.  Each set of two or more nodes is
-    re-planned with the exact DP.  The sets become the nodes of the next
-    graph (numbered by smallest base relation) and the procedure recurses.
+  * UnionDP(k, t) (Algorithm 5): if the graph has at most k nodes, the
+    exact DP over all of them.  Otherwise each edge weighs the card of
+    joining its two nodes, and union-find runs over the nodes (size =
+    number of nodes).  The edges are ordered once, before the union loop,
+    by (size of the sets across the edge, weight, smaller node, larger
+    node).  Every set is a single node when the order is fixed, so the
+    order is increasing weight (Kruskal's order).  One pass over that
+    order unites the two sets across an edge when they differ and their
+    size sum is at most t.  Each set of two or more nodes is re-planned
+    with the exact DP.  The sets become the nodes of the next graph
+    (numbered by smallest base relation) and the procedure recurses.
     Algorithm 5 has a single bound k.  The paper runs UnionDP with k = 25
     and a partition threshold t = 15 (Sec. 6.3), which is read here as
     partitions <= t and the final DP at <= k nodes.
+  * UnionDP, size-first variant (order="size_first"): the same, except
+    that the next edge is re-picked after every union as the one with the
+    least (current size sum, weight, smaller node, larger node), and an
+    edge whose sum exceeds t is dropped.  This evaluates the ordering key
+    on the current sets instead of fixing it before the loop.  It is kept
+    as a comparison; Table 1's ranking (UnionDP best on snowflakes,
+    because it removes single expensive edges, Sec. 6.3) supports the
+    fixed order.
 """
 from __future__ import annotations
 
@@ -327,27 +338,35 @@ def idp2(g: Graph, k: int, dp=None, start: Optional[Plan] = None) -> Plan:
 # ---------------------------------------------------------------------------
 # UnionDP
 
-def uniondp(g: Graph, k: int, t: Optional[int] = None, dp=None) -> Plan:
-    t = k if t is None else t
-    nodes = [g.leaf(r) for r in range(g.n)]
-    while len(nodes) > k:
-        m = len(nodes)
-        edges = []
-        for i in range(m):
-            for j in range(i + 1, m):
-                s = g.cut_sel(nodes[i].rels, nodes[j].rels, nodes[i].leaves, nodes[j].leaves)
-                if s is not None:
-                    w = xd_mul(xd_mul(nodes[i].card, nodes[j].card), s)
-                    edges.append((i, j, w))
-        parent = list(range(m))
-        size = [1] * m
+def uniondp_partition(g: Graph, nodes: Sequence[Plan], t: int, order: str = "paper") -> List[List[int]]:
+    """The partition phase of Algorithm 5 over the current nodes: groups of
+    node indices (each ascending), ordered by their first index."""
+    m = len(nodes)
+    edges = []
+    for i in range(m):
+        for j in range(i + 1, m):
+            s = g.cut_sel(nodes[i].rels, nodes[j].rels, nodes[i].leaves, nodes[j].leaves)
+            if s is not None:
+                w = xd_mul(xd_mul(nodes[i].card, nodes[j].card), s)
+                edges.append((i, j, w))
+    parent = list(range(m))
+    size = [1] * m
 
-        def find(x):
-            while parent[x] != x:
-                parent[x] = parent[parent[x]]
-                x = parent[x]
-            return x
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
 
+    if order == "paper":
+        # the order is fixed before the loop, when every set is one node
+        ranked = sorted(edges, key=lambda e: (size[e[0]] + size[e[1]], xd_key(e[2]), e[0], e[1]))
+        for i, j, _ in ranked:
+            a, b = find(i), find(j)
+            if a != b and size[a] + size[b] <= t:
+                parent[b] = a
+                size[a] += size[b]
+    elif order == "size_first":
         dropped = set()
         while True:
             best = None
@@ -368,8 +387,18 @@ def uniondp(g: Graph, k: int, t: Optional[int] = None, dp=None) -> Plan:
                 size[a] += size[b]
             else:
                 dropped.add(idx)
-        groups: Dict[int, List[Plan]] = {}
-        for i in range(m):
-            groups.setdefault(find(i), []).append(nodes[i])
-        nodes = sorted((exact_over(g, grp, dp) for grp in groups.values()), key=lambda p: p.minrel)
+    else:
+        raise ValueError(order)
+    groups: Dict[int, List[int]] = {}
+    for i in range(m):
+        groups.setdefault(find(i), []).append(i)
+    return sorted(groups.values(), key=lambda grp: grp[0])
+
+
+def uniondp(g: Graph, k: int, t: Optional[int] = None, dp=None, order: str = "paper") -> Plan:
+    t = k if t is None else t
+    nodes = [g.leaf(r) for r in range(g.n)]
+    while len(nodes) > k:
+        groups = uniondp_partition(g, nodes, t, order)
+        nodes = sorted((exact_over(g, [nodes[i] for i in grp], dp) for grp in groups), key=lambda p: p.minrel)
     return exact_over(g, nodes, dp)

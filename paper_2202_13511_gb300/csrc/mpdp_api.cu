@@ -1004,7 +1004,9 @@ static int validate_heuristic(const mpdp_query* q)
     const int n = q->n_rels, m = q->n_edges;
     if (q->cost_model != MPDP_COST_COUT) return MPDP_ERR_INVALID_ARG;
     const bool idp = q->mode == MPDP_MODE_IDP2 || q->mode == MPDP_MODE_IDP2_LEARNED;
-    if (!idp && q->mode != MPDP_MODE_UNIONDP && q->mode != MPDP_MODE_UNIONDP_LEARNED) return MPDP_ERR_INVALID_ARG;
+    if (!idp && q->mode != MPDP_MODE_UNIONDP && q->mode != MPDP_MODE_UNIONDP_LEARNED &&
+        q->mode != MPDP_MODE_UNIONDP_SIZEFIRST)
+        return MPDP_ERR_INVALID_ARG;
     if (n < 1 || m < 0 || (long long)m > (long long)n * (n - 1) / 2 || !q->card || (m > 0 && !q->edges))
         return MPDP_ERR_INVALID_ARG;
     if (n > MPDP_MAX_HEURISTIC_RELS) return MPDP_ERR_TOO_LARGE;

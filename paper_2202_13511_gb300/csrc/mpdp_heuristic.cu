@@ -19,13 +19,19 @@
 //     subtree with 2..k leaves whose joins cost most (leaves at cost 0: they
 //     cannot change), the first in pre-order on ties, and replaces it by the
 //     exact plan over its leaves.  k <= 1 returns GOO's plan.
-//   * UnionDP(k, t): at most k nodes -> one exact DP.  Otherwise each edge
-//     between nodes weighs the card of joining them; union-find over nodes
-//     (size = nodes), repeatedly the edge between different sets with the
-//     least (size sum, weight, smaller node, larger node), united when the
-//     size sum is at most t, else dropped (sizes only grow); every set is
+//   * UnionDP(k, t) (Algorithm 5): at most k nodes -> one exact DP.
+//     Otherwise each edge between nodes weighs the card of joining them;
+//     union-find over nodes (size = nodes).  The edges are ordered once,
+//     before the union loop, by (size of the sets across the edge, weight,
+//     smaller node, larger node); every set is one node then, so this is
+//     increasing weight.  One pass in that order unites the two sets across
+//     an edge when they differ and their size sum is at most t.  Every set is
 //     re-planned exactly and becomes a node of the next round.  t = k unless
 //     given.
+//   * UnionDP, size-first variant (MPDP_MODE_UNIONDP_SIZEFIRST): the next
+//     edge is re-picked after every union as the one between different sets
+//     with the least (current size sum, weight, smaller node, larger node),
+//     united when the sum is at most t, else dropped (sizes only grow).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -183,7 +189,7 @@ public:
     int goo(int& result);
     int learned_start(int& result);
     int idp2(int k, int& result, bool learned = false);
-    int uniondp(int k, int t, int& result);
+    int uniondp(int k, int t, int& result, bool size_first = false);
     int scores(int m, const std::vector<int>& cur, const std::vector<std::pair<int, int>>& ij,
                const std::vector<XD>& sel, std::vector<float>& out);
 
@@ -434,7 +440,7 @@ int Heuristic::idp2(int k, int& result, bool learned)
 // --------------------------------------------------------------------------
 // UnionDP
 
-int Heuristic::uniondp(int k, int t, int& result)
+int Heuristic::uniondp(int k, int t, int& result, bool size_first)
 {
     std::vector<int> cur(n_);
     for (int r = 0; r < n_; r++) cur[r] = leaf(r);
@@ -468,6 +474,29 @@ int Heuristic::uniondp(int k, int t, int& result)
             return x;
         };
         std::vector<char> dropped(es.size(), 0);
+        if (!model_ && !size_first) {
+            // Algorithm 5's order, fixed before the loop: (size sum of the
+            // sets across the edge, weight, i, j); every set is one node here
+            std::vector<int> order(es.size());
+            for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+            std::sort(order.begin(), order.end(), [&](int x, int y) {
+                const E& a = es[x];
+                const E& b = es[y];
+                const int sa = size[a.i] + size[a.j], sb = size[b.i] + size[b.j];
+                if (sa != sb) return sa < sb;
+                if (!xd_equal(a.w, b.w)) return xd_less(a.w, b.w);
+                if (a.i != b.i) return a.i < b.i;
+                return a.j < b.j;
+            });
+            for (int idx : order) {
+                const int a = find(es[idx].i), b = find(es[idx].j);
+                if (a != b && size[a] + size[b] <= t) {
+                    parent[b] = a;
+                    size[a] += size[b];
+                }
+            }
+            std::fill(dropped.begin(), dropped.end(), 1);
+        }
         if (model_) {
             // learned proposal: edges by predicted score (the share of the
             // query under the edge's join in an optimal plan), lowest first,
@@ -677,6 +706,7 @@ int run_heuristic(const HeuristicQuery& q, XdExecutor& ex, cudaStream_t st, int 
     res.learned_won = false;
     if (q.mode == MPDP_MODE_IDP2) rc = h.idp2(q.k, root);
     else if (q.mode == MPDP_MODE_UNIONDP) rc = h.uniondp(q.k, q.t > 0 ? q.t : q.k, root);
+    else if (q.mode == MPDP_MODE_UNIONDP_SIZEFIRST) rc = h.uniondp(q.k, q.t > 0 ? q.t : q.k, root, true);
     else if (q.mode == MPDP_MODE_UNIONDP_LEARNED) {
         // the learned proposal's plan, with plain UnionDP as the fallback:
         // both are costed exactly and the cheaper one (plain on ties) wins

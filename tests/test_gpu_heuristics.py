@@ -41,6 +41,8 @@ def ref(q, mode, k, t=0):
     g = H.Graph(q)
     if mode == mpdp.MODE_IDP2:
         p = H.goo(g) if k <= 1 else H.idp2(g, k)
+    elif mode == mpdp.MODE_UNIONDP_SIZEFIRST:
+        p = H.uniondp(g, k, t or k, order="size_first")
     else:
         p = H.uniondp(g, k, t or k)
     return H.canonical(p), p.cost
@@ -71,6 +73,11 @@ CASES = [
     ("star", 30, 5, mpdp.MODE_IDP2, 10, 0),
     ("star", 30, 5, mpdp.MODE_UNIONDP, 10, 5),
     ("cyclic", 24, 6, mpdp.MODE_UNIONDP, 8, 4),
+    ("snowflake_plus", 60, 2, mpdp.MODE_UNIONDP_SIZEFIRST, 10, 6),
+    ("snowflake_plus_pkfk", 80, 8, mpdp.MODE_UNIONDP, 12, 6),
+    ("snowflake_plus_pkfk", 80, 8, mpdp.MODE_UNIONDP_SIZEFIRST, 12, 6),
+    ("star", 30, 5, mpdp.MODE_UNIONDP_SIZEFIRST, 10, 5),
+    ("cyclic", 24, 6, mpdp.MODE_UNIONDP_SIZEFIRST, 8, 4),
 ]
 
 
@@ -80,9 +87,20 @@ def test_heuristic_matches_oracle(opt, kind, n, seed, mode, k, t):
     same(run(opt, q, mode, k, t), ref(q, mode, k, t))
 
 
-@pytest.mark.parametrize("mode,k,t", [(mpdp.MODE_IDP2, 25, 0), (mpdp.MODE_UNIONDP, 25, 15)])
+@pytest.mark.parametrize("mode,k,t", [(mpdp.MODE_IDP2, 25, 0), (mpdp.MODE_UNIONDP, 25, 15),
+                                     (mpdp.MODE_UNIONDP_SIZEFIRST, 25, 15)])
 def test_paper_parameters_at_100_relations(opt, mode, k, t):
     q = W.make("snowflake_plus", 100, 11)
+    same(run(opt, q, mode, k, t), ref(q, mode, k, t))
+
+
+@pytest.mark.parametrize("kind,n,seed", [("snowflake_plus", 300, 12), ("snowflake_plus_pkfk", 1000, 13)])
+@pytest.mark.parametrize("mode,k,t", [(mpdp.MODE_IDP2, 25, 0), (mpdp.MODE_UNIONDP, 25, 15)])
+def test_paper_parameters_at_300_and_1000_relations(opt, kind, n, seed, mode, k, t):
+    """The large-query sizes of the heuristic tables (Sec. 6.3): hundreds of
+    IDP2 rounds and several levels of UnionDP recursion, every plan and
+    extended-range cost equal to the oracle's."""
+    q = W.make(kind, n, seed)
     same(run(opt, q, mode, k, t), ref(q, mode, k, t))
 
 

@@ -277,6 +277,50 @@ def test_uniondp_partitions_respect_threshold(monkeypatch):
     assert seen[-1] <= 12 and all(s <= 5 for s in seen[:-1])
 
 
+def test_uniondp_partition_hand_worked():
+    """The partition phase of Algorithm 5 on a 7-relation graph, worked by
+    hand from the algorithm's text.  Every card is 10, so an edge weighs
+    100 * sel: (0,1) 1, (1,2) 2, (2,3) 3, (4,5) 4, (4,6) 5, (3,4) 50,
+    (5,6) 90.  t = 3.
+
+    Edges ordered once, before the loop (all sets single nodes, so by
+    weight): (0,1) unites {0,1}; (1,2) makes {0,1,2}; (2,3) would make 4 > 3;
+    (4,5) unites {4,5}; (4,6) makes {4,5,6}; (3,4) would make 4; (5,6) is
+    inside {4,5,6}.  Partition {0,1,2}, {3}, {4,5,6}.
+
+    Size-first re-picking: (0,1) [sum 2, w 1]; then (2,3) [2, w 3] beats
+    (1,2) [3]; then (4,5) [2, w 4]; then (4,6) [3, w 5] (every pair of
+    singletons is gone: (3,4) is now 2 + 2); then (1,2) [4] and (3,4) [5]
+    are dropped.  Partition {0,1}, {2,3}, {4,5,6}."""
+    q = W.Query(n=7, card=[10.0] * 7,
+                edges=[(0, 1, 0.01), (1, 2, 0.02), (2, 3, 0.03), (3, 4, 0.5), (4, 5, 0.04), (4, 6, 0.05),
+                       (5, 6, 0.9)])
+    g = H.Graph(q)
+    nodes = [g.leaf(r) for r in range(7)]
+    assert H.uniondp_partition(g, nodes, 3) == [[0, 1, 2], [3], [4, 5, 6]]
+    assert H.uniondp_partition(g, nodes, 3, order="size_first") == [[0, 1], [2, 3], [4, 5, 6]]
+    # t = 2: only pairs; the fixed order takes (0,1), (2,3), (4,5) and
+    # leaves 6 alone; size-first does the same here (all sums are 2 first)
+    assert H.uniondp_partition(g, nodes, 2) == [[0, 1], [2, 3], [4, 5], [6]]
+    assert H.uniondp_partition(g, nodes, 2, order="size_first") == [[0, 1], [2, 3], [4, 5], [6]]
+    # the whole UnionDP(k = 4, t = 3): one partition round, then the final
+    # exact DP over the three partition plans, so each partition is a
+    # subtree of the result
+    p = H.uniondp(g, 4, 3)
+    assert p.leaves == 7 and cross_product_free(g, p)
+    subtrees = set()
+
+    def walk(t):
+        subtrees.add(t.rels)
+        if not t.is_leaf:
+            walk(t.left)
+            walk(t.right)
+
+    walk(p)
+    assert {0b0000111, 0b0001000, 0b1110000} <= subtrees
+    assert H.plan_cost(g, p).cost == p.cost
+
+
 def _scores_rebuilding(g, p):
     """Scores for g's edges under which the learned start rebuilds the tree-
     query plan p: each join's one cut edge scores its post-order rank (a join
