@@ -80,3 +80,79 @@ def gradients(p, x, t):
     flat = np.concatenate([grads["W1"].ravel(), grads["b1"], grads["W2"].ravel(), grads["b2"],
                            grads["W3"].ravel(), grads["b3"], dw4, db4])
     return flat, loss
+
+
+# ---------------------------------------------------------------------------
+# Exact regime.  When every operand lies on a dyadic grid and every sum is
+# small enough on that grid, float32 holds every partial sum of every
+# accumulation exactly, in any order and with any alignment of several
+# products, and every single float32 operation (bias add, y - t, division by
+# the row count, products) is exact as well.  The bf16 rounding points then
+# round the same exact values on the device and here.  So a device that
+# follows the rounding points above must reproduce forward() and
+# gradients() bit for bit, whatever its accumulation order.
+
+
+def _grid(a) -> int:
+    """Smallest g >= 0 with a * 2^g integral everywhere (-1: none up to 2^-200)."""
+    a = np.asarray(a, dtype=np.float64)
+    for g in range(0, 200):
+        s = a * (2.0 ** g)
+        if np.all(s == np.floor(s)):
+            return g
+    return -1
+
+
+def _sum_exact(a, b) -> bool:
+    """Every partial sum of every dot product of a @ b is a float32: the
+    products are multiples of 2^-(ga+gb) and their absolute sum stays below
+    2^24 such units."""
+    ga, gb = _grid(a), _grid(b)
+    if ga < 0 or gb < 0:
+        return False
+    return float(np.max(np.abs(a) @ np.abs(b), initial=0.0)) < 2.0 ** (24 - ga - gb)
+
+
+def _fits32(v) -> bool:
+    v = np.asarray(v, dtype=np.float64)
+    return bool(np.all(v.astype(np.float32).astype(np.float64) == v))
+
+
+def exact_regime(p, x, t) -> list:
+    """Steps of forward() and gradients() whose float32 evaluation could
+    round (empty: the whole computation is exact in float32)."""
+    n_in = x.shape[1]
+    W1, b1, W2, b2, W3, b3, w4, b4 = unpack(p, n_in)
+    rows = x.shape[0]
+    bad = []
+    chk = lambda ok, what: None if ok else bad.append(what)
+    chk(_fits32(x) and _fits32(t) and _fits32(p), "inputs are not float32")
+    Ws = [bf16(W1), bf16(W2), bf16(W3)]
+    chk(all(np.array_equal(Wb, W) for Wb, W in zip(Ws, (W1, W2, W3))), "weights are not bf16")
+    bs = [b1, b2, b3]
+    hs = [bf16(x)]
+    for l in range(3):
+        chk(_sum_exact(hs[-1], Ws[l]), f"z{l + 1} accumulation")
+        v = hs[-1] @ Ws[l] + bs[l]
+        chk(_fits32(v), f"z{l + 1} + b{l + 1}")
+        hs.append(bf16(np.maximum(v, 0.0)))
+    h3 = hs[3]
+    chk(_sum_exact(h3, w4[:, None]) and _fits32(h3 * w4[None, :]), "head sum")
+    y = h3 @ w4 + b4[0]
+    chk(_fits32(y), "y + b4")
+    d = y - t
+    chk(_fits32(d) and _fits32(d / rows) and _fits32(d * d), "y - t, (y - t) / rows, (y - t)^2")
+    dy = d / rows
+    chk(_sum_exact(h3.T, dy[:, None]) and _fits32(dy[:, None] * h3), "dw4")
+    chk(_sum_exact(np.ones((1, rows)), dy[:, None]), "db4")
+    dz = np.outer(dy, w4) * (h3 > 0)
+    chk(_fits32(dz), "dz3")
+    for l in (3, 2, 1):
+        dzb = bf16(dz)
+        chk(_sum_exact(np.ones((1, rows)), dz), f"db{l}")
+        chk(_sum_exact(hs[l - 1].T, dzb), f"dW{l}")
+        if l == 1:
+            break
+        chk(_sum_exact(dzb, Ws[l - 1].T), f"dh{l - 1}")
+        dz = (dzb @ Ws[l - 1].T) * (hs[l - 1] > 0)
+    return bad
