@@ -64,7 +64,9 @@ def build_dataset(opt: "mpdp.Optimizer", queries: Sequence, batch: int = 256) ->
 def train(x: np.ndarray, t: np.ndarray, epochs: int = 8, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
           device: int = 0, log: Optional[list] = None) -> "mpdp.Mlp":
     """Train the proposal network on the GPU (minibatch Adam steps in the
-    library's kernels).  log, when given, receives (epoch, loss, seconds)."""
+    library's kernels).  log, when given, receives (epoch, loss, seconds):
+    first (-1, loss of the initial network, 0), then one entry per epoch,
+    each loss over the same first 16,384 rows."""
     import torch
     torch.cuda.set_device(device)
     mlp = mpdp.Mlp(x.shape[1], device, stream=torch.cuda.current_stream())
@@ -74,6 +76,15 @@ def train(x: np.ndarray, t: np.ndarray, epochs: int = 8, batch: int = 4096, lr: 
     rows = dx.shape[0]
     gen = torch.Generator(device="cpu")
     gen.manual_seed(seed)
+    n_eval = min(rows, 16384)
+
+    def eval_loss():
+        _, loss = mlp.gradients(dx[:n_eval].contiguous(), dt[:n_eval].contiguous(), n_eval)
+        torch.cuda.synchronize()
+        return loss
+
+    if log is not None:
+        log.append((-1, eval_loss(), 0.0))
     t0 = time.perf_counter()
     for ep in range(epochs):
         perm = torch.randperm(rows, generator=gen).cuda()
@@ -83,10 +94,7 @@ def train(x: np.ndarray, t: np.ndarray, epochs: int = 8, batch: int = 4096, lr: 
             bt = dt.index_select(0, idx).contiguous()
             mlp.train_step(bx, bt, bx.shape[0], lr)
         if log is not None:
-            n_eval = min(rows, 16384)
-            _, loss = mlp.gradients(dx[:n_eval].contiguous(), dt[:n_eval].contiguous(), n_eval)
-            torch.cuda.synchronize()
-            log.append((ep, loss, time.perf_counter() - t0))
+            log.append((ep, eval_loss(), time.perf_counter() - t0))
     torch.cuda.synchronize()
     return mlp
 

@@ -388,6 +388,24 @@ def test_max_size_30_counts(opt, filt):
     set_cfg(opt)
 
 
+def test_card_peel_order_golden(opt):
+    """The golden card(S) values of the peeling order: the GPU's cost of
+    every 2-relation set is its card (cost = 0 + 0 + card), bit for bit,
+    and every larger set's cost equals the oracle's."""
+    from tests.test_oracle_pins import card_peel_golden
+    q, want = card_peel_golden()
+    plan = opt.optimize(q, keep=True)
+    sets = sorted(want)
+    costs, _ = opt.memo_lookup(plan.handle, sets)
+    ref = oracle.dpccp(q)
+    for s, c in zip(sets, costs):
+        if bin(s).count("1") == 2:
+            assert float(c).hex() == want[s].hex(), bin(s)
+        if bin(s).count("1") >= 2:
+            assert float(c).hex() == float(ref.cost[s]).hex(), bin(s)
+    opt.release(plan.handle)
+
+
 def test_single_relation(opt):
     set_cfg(opt)
     q = W.Query(n=1, card=[123.0], edges=[])

@@ -1,10 +1,12 @@
 """The serving loop (mpdp_server_*) on the GPU: every result of a mixed
-stream is bit-identical to the same query optimized alone, under a burst and
-under Poisson arrivals; admission by memo memory; bad requests are refused
-at submit without touching their neighbours."""
+stream is bit-identical to the same query optimized alone and to the CPU
+oracle's DPCCP (optimal cost and plan), under a burst and under Poisson
+arrivals; admission by memo memory; bad requests are refused at submit
+without touching their neighbours."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2202_13511_gb300 import mpdp
 from paper_2202_13511_gb300 import workloads as W
 
@@ -21,13 +23,18 @@ def mix(count, seed, n_lo=8, n_hi=20):
 @pytest.fixture(scope="module")
 def alone():
     o = mpdp.Optimizer(0)
-    yield lambda q: o.optimize(q)
+    yield lambda q: (q, o.optimize(q))
     o.close()
 
 
-def same(p, ref):
+def same(p, alone_result):
+    """p equals the query optimized alone, and both equal the oracle."""
+    q, ref = alone_result
     assert np.float64(p.cost).tobytes() == np.float64(ref.cost).tobytes()
     assert p.signature() == ref.signature()
+    want = oracle.dpccp(q)
+    assert np.float64(p.cost).tobytes() == np.float64(want.opt_cost).tobytes()
+    assert p.signature() == oracle.plan_signature(oracle.plan_from_memo(q, want))
 
 
 def test_burst_results_equal_alone(alone):
