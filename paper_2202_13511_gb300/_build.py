@@ -18,6 +18,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libmpdp.so")
+# the multi-threaded CPU MPDP (a comparison baseline; plain C, no CUDA)
+CPU_SOURCE = "mpdp_cpu.c"
+CPU_LIB_PATH = os.path.join(OUT_DIR, "libmpdp_cpu.so")
 SOURCES = ["mpdp_kernels.cu", "mpdp_api.cu", "mpdp_noalloc.cu", "mpdp_server.cu", "mpdp_xd.cu",
            "mpdp_heuristic.cu", "mpdp_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,14 +42,30 @@ def _deps():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB_PATH):
+def up_to_date(path: str = LIB_PATH) -> bool:
+    if not os.path.exists(path):
         return False
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(path)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
+def build_cpu(force: bool = False) -> str:
+    """libmpdp_cpu.so: gcc, C11 + pthreads, no FMA contraction."""
+    if not force and up_to_date(CPU_LIB_PATH):
+        return CPU_LIB_PATH
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = CPU_LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O3", "-std=c11", "-pthread", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-I", os.path.join(ROOT, "include"), "-o", tmp, os.path.join(CSRC, CPU_SOURCE), "-lm"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"gcc failed for {CPU_SOURCE}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, CPU_LIB_PATH)
+    return CPU_LIB_PATH
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    build_cpu(force)
     if not force and up_to_date():
         return LIB_PATH
     os.makedirs(OUT_DIR, exist_ok=True)
