@@ -30,6 +30,12 @@ UNIT = "queries/s"
 N_RELS = 25
 QUERIES_PER_STEP = 64
 FLUSH_BYTES = 256 << 20
+# heuristic lines: query sizes where the exact DP still runs, and the
+# large-query sizes of the paper's heuristic tables
+EXACT_SIZES = (26, 28, 30)
+EXACT_QUERIES = 10
+LARGE_SIZES = (100, 300, 1000)
+LARGE_QUERIES = 10
 # Issue-slot peak of the integer filter: 152 SMs x 4 schedulers x 32 lanes x clock.
 SMS, SCHEDULERS, LANES = 152, 4, 32
 # Algorithmic integer operations of the bitmap filter per bitmap examined.
@@ -81,6 +87,14 @@ def parse_args():
     p.add_argument("--tune", action="store_true", help="autotuned launch configuration instead of the library defaults")
     p.add_argument("--large-queries", type=int, default=LARGE_QUERIES,
                    help="queries per size in the large and learned lines (the workload's full form: 100)")
+    p.add_argument("--exact-queries", type=int, default=EXACT_QUERIES,
+                   help="queries per size in the heuristics-against-the-exact-optimum line")
+    p.add_argument("--lines", default="all",
+                   help="comma-separated extra lines to run after the headline: shapes, latency, ablations, "
+                        "large, learned, serving (default: all)")
+    p.add_argument("--case", default=None,
+                   help="kind:n:queries[:lanes[:memo]] -- only run that workload as device batches (warmup + "
+                        "steps of them) and print its status; for profiler captures of one shape")
     return p.parse_args()
 
 
@@ -205,7 +219,37 @@ def cpu_baseline(queries, budget_s: float):
     return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {done} of the step's {len(queries)} queries, DPCCP on 1 host core, "
                       f"{el:.1f} s",
-            "dpsub_1core": dpsub}
+            "dpsub_1core": dpsub,
+            "mpdp_cpu_all_cores": cpu_mpdp_baseline(queries, budget_s)}
+
+
+def cpu_mpdp_baseline(queries, budget_s: float):
+    """The paper's own CPU design of MPDP (Sec. 3.3; "MPDP (24CPU)" in its
+    experiments) on every host core, on a bounded prefix of the workload;
+    its first result is checked against the oracle (cost and plan)."""
+    import oracle
+    from paper_2202_13511_gb300 import cpu_mpdp
+    cores = cpu_mpdp.cores()
+    plan, st = cpu_mpdp.optimize(queries[0], threads=cores)  # warm-up: memo pages, threads
+    ref = oracle.dpccp(queries[0])
+    assert plan.cost == ref.opt_cost
+    assert plan.signature() == oracle.plan_signature(oracle.plan_from_memo(queries[0], ref))
+    one, _ = cpu_mpdp.optimize(queries[0], threads=1)
+    done = 0
+    t0 = time.perf_counter()
+    for q in queries:
+        cpu_mpdp.optimize(q, threads=cores)
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    cpu_mpdp.optimize(queries[0], threads=1)
+    one_s = time.perf_counter() - t1
+    return {"value": done / el, "unit": UNIT, "cores": cores, "kind": "multi-threaded CPU MPDP (Sec. 3.3)",
+            "sample": f"first {done} of the step's {len(queries)} queries on {cores} threads, {el:.1f} s; "
+                      f"query 0 checked against the oracle",
+            "query0_1_thread_ms": 1000.0 * one_s}
 
 
 def run_reference(args):
@@ -247,8 +291,11 @@ def run_ours(args):
     import numpy as np
     import torch
 
-    global LARGE_QUERIES
+    global LARGE_QUERIES, EXACT_QUERIES
     LARGE_QUERIES = max(1, args.large_queries)
+    EXACT_QUERIES = max(1, args.exact_queries)
+    extra = {"shapes", "latency", "ablations", "large", "learned", "serving"} if args.lines == "all" \
+        else set(x.strip() for x in args.lines.split(",") if x.strip())
 
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
@@ -405,15 +452,21 @@ def run_ours(args):
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(queries, args.cpu_sample_s)
     if rank == 0 and not args.no_star:
-        for name in SHAPES:
-            line[name] = shape_line(name, opt, torch, mpdp, W, peaks)
-        line["latency"] = latency_line(opt, torch, W)
+        if "shapes" in extra:
+            for name in SHAPES:
+                line[name] = shape_line(name, opt, torch, mpdp, W, peaks)
+        if "latency" in extra:
+            line["latency"] = latency_line(opt, torch, W)
     if rank == 0 and world == 1 and not args.no_star:
-        line["ablations"] = ablation_line(opt, torch, mpdp, W)
-        line["large"] = heuristic_line(opt, mpdp, W)
-        line["learned"] = learned_line(opt, mpdp, W)
+        if "ablations" in extra:
+            line["ablations"] = ablation_line(opt, torch, mpdp, W)
+        if "large" in extra:
+            line["large"] = heuristic_line(opt, mpdp, W)
+        if "learned" in extra:
+            line["learned"] = learned_line(opt, mpdp, W)
         opt.close()
-        line["serving"] = serving_line(mpdp, W)
+        if "serving" in extra:
+            line["serving"] = serving_line(mpdp, W)
     opt.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -683,11 +736,16 @@ LEARN_EPOCHS = 3
 def learned_line(opt, mpdp, W):
     """Learned proposal: a BF16 MLP trained on the GPU by the library's own
     kernels on the exact plans of LEARN_QUERIES primary-key/foreign-key
-    snowflakes of 10-25 relations, then MODE_IDP2_LEARNED against plain IDP2
-    (k = 25; the learned-IDP plan-cost ratio) and MODE_UNIONDP_LEARNED
-    against plain UnionDP and IDP2 (k = 25, t = 15) on held-out queries of
-    100/300/1000 relations; plan-cost ratios as geometric means and 95th
-    percentiles."""
+    snowflakes of 10-25 relations, then on held-out queries of 100/300/1000
+    relations (k = 25, t = 15): MODE_IDP2_LEARNED against plain IDP2 (the
+    learned-IDP plan-cost ratio) and MODE_UNIONDP_LEARNED against plain
+    UnionDP.  Each learned mode keeps the cheaper of two plans, so two
+    controls under the same rule isolate what training adds: the same modes
+    with an untrained (randomly initialised) network, and a second start
+    that needs no network (IDP2 from the plan joining edges in ascending
+    join card, MODE_IDP2_WEIGHT_START; for UnionDP the cheaper of the
+    fixed-order and size-first readings).  Ratios as geometric means, 95th
+    percentiles and wins over the plain mode."""
     import math
     import numpy as np
     from paper_2202_13511_gb300 import learned as L
@@ -697,58 +755,94 @@ def learned_line(opt, mpdp, W):
     log = []
     mlp = L.train(x, t, epochs=LEARN_EPOCHS, seed=2, log=log)
     t_train = log[-1][2]
+    n_eval = min(len(t), 16384)
     out = {"training": {"queries": LEARN_QUERIES, "edges": int(x.shape[0]), "epochs": LEARN_EPOCHS,
                         "dataset_s": round(t_data, 3), "train_s": round(t_train, 3),
-                        "samples_per_s": LEARN_EPOCHS * x.shape[0] / t_train, "loss_first": log[0][1],
-                        "loss_last": log[-1][1]},
-           "modes": "idp2_learned vs idp2 (k = 25); uniondp_learned vs uniondp and idp2 (k = 25, t = 15)"}
+                        "samples_per_s": LEARN_EPOCHS * x.shape[0] / t_train,
+                        "loss_initial": log[0][1], "loss_per_epoch": [e[1] for e in log[1:]],
+                        "loss_constant_predictor": float(np.var(t[:n_eval].astype(np.float64)) / 2.0),
+                        "loss_rows": n_eval},
+           "queries_per_size": LARGE_QUERIES}
+    untrained = mpdp.Mlp(x.shape[1], 0, stream=None)
+    untrained.init_params(3)
+
+    def cost(q, mode, model=None, k=25, t=0):
+        opt.set_model(model)
+        return opt.optimize(q, mode=mode, k=k, t=t).cost_xd
+
+    def stats(num, den):
+        lr = [math.log2(_xd_ratio(a, b)) for a, b in zip(num, den)]
+        return {"geomean": 2.0 ** float(np.mean(lr)), "p95": 2.0 ** float(np.percentile(lr, 95)),
+                "wins": int(sum(v < 0 for v in lr)), "losses": int(sum(v > 0 for v in lr))}
+
     for n in LARGE_SIZES:
         qs = [W.snowflake_plus_pkfk(n, seed=5000 + i) for i in range(LARGE_QUERIES)]
-        rows = L.evaluate(opt, mlp, qs, 25, 15)
-        lp = [math.log2(L.cost_ratio(l, p)) for p, l, _ in rows]
-        li = [math.log2(L.cost_ratio(l, i)) for p, l, i in rows]
-        t1 = time.perf_counter()
-        irows = L.evaluate_idp2(opt, mlp, qs, 25)
-        t_idp = (time.perf_counter() - t1) / len(qs)
-        ll = [math.log2(L.cost_ratio(l, p)) for p, l in irows]
-        out[f"pkfk_n{n}"] = {"idp2_learned_over_idp2_geomean": 2.0 ** float(np.mean(ll)),
-                             "idp2_learned_over_idp2_p95": 2.0 ** float(np.percentile(ll, 95)),
-                             "idp2_learned_wins": int(sum(v < 0 for v in ll)),
-                             "idp2_pair_s_per_query": round(t_idp, 4),
-                             "learned_over_plain_geomean": 2.0 ** float(np.mean(lp)),
-                             "learned_over_plain_p95": 2.0 ** float(np.percentile(lp, 95)),
-                             "learned_wins": int(sum(v < 0 for v in lp)), "learned_losses": int(sum(v > 0 for v in lp)),
-                             "learned_over_idp2_geomean": 2.0 ** float(np.mean(li))}
+        c = {key: [] for key in ("idp2", "idp2_learned", "idp2_untrained", "idp2_weight_start", "uniondp",
+                                 "uniondp_learned", "uniondp_untrained", "uniondp_sizefirst")}
+        t_learned = 0.0
+        for q in qs:
+            c["idp2"].append(cost(q, mpdp.MODE_IDP2))
+            t1 = time.perf_counter()
+            c["idp2_learned"].append(cost(q, mpdp.MODE_IDP2_LEARNED, mlp))
+            t_learned += time.perf_counter() - t1
+            c["idp2_untrained"].append(cost(q, mpdp.MODE_IDP2_LEARNED, untrained))
+            c["idp2_weight_start"].append(cost(q, mpdp.MODE_IDP2_WEIGHT_START))
+            c["uniondp"].append(cost(q, mpdp.MODE_UNIONDP, t=15))
+            c["uniondp_learned"].append(cost(q, mpdp.MODE_UNIONDP_LEARNED, mlp, t=15))
+            c["uniondp_untrained"].append(cost(q, mpdp.MODE_UNIONDP_LEARNED, untrained, t=15))
+            c["uniondp_sizefirst"].append(cost(q, mpdp.MODE_UNIONDP_SIZEFIRST, t=15))
+        uni_ctrl = [min(a, b, key=lambda v: (v[0] != 0.0, v[1], v[0]))
+                    for a, b in zip(c["uniondp"], c["uniondp_sizefirst"])]
+        out[f"pkfk_n{n}"] = {
+            "idp2_learned_over_idp2": stats(c["idp2_learned"], c["idp2"]),
+            "idp2_untrained_over_idp2": stats(c["idp2_untrained"], c["idp2"]),
+            "idp2_weight_start_over_idp2": stats(c["idp2_weight_start"], c["idp2"]),
+            "idp2_learned_over_weight_start": stats(c["idp2_learned"], c["idp2_weight_start"]),
+            "idp2_learned_s_per_query": round(t_learned / len(qs), 4),
+            "uniondp_learned_over_uniondp": stats(c["uniondp_learned"], c["uniondp"]),
+            "uniondp_untrained_over_uniondp": stats(c["uniondp_untrained"], c["uniondp"]),
+            "uniondp_both_readings_over_uniondp": stats(uni_ctrl, c["uniondp"]),
+            "uniondp_learned_over_idp2": stats(c["uniondp_learned"], c["idp2"]),
+        }
     opt.set_model(None)
+    untrained.close()
     mlp.close()
     return out
 
 
 SERVE_QUERIES = 2000
-LARGE_SIZES = (100, 300, 1000)
-LARGE_QUERIES = 10
+
+
+def heuristic_variants(mpdp):
+    return {"goo": (mpdp.MODE_IDP2, 1, 0), "idp2_15": (mpdp.MODE_IDP2, 15, 0), "idp2_25": (mpdp.MODE_IDP2, 25, 0),
+            "uniondp_25_15": (mpdp.MODE_UNIONDP, 25, 15),
+            "uniondp_sizefirst_25_15": (mpdp.MODE_UNIONDP_SIZEFIRST, 25, 15)}
+
+
+def _xd_ratio(a, b) -> float:
+    import math
+    return a[0] / b[0] * math.pow(2.0, a[1] - b[1])
 
 
 def heuristic_line(opt, mpdp, W):
-    """Large queries (snowflake with fanout 1-5 and no depth cap, plus 5 %
-    extra edges): IDP2 (k = 25, GOO start), UnionDP (k = 25, t = 15) and GOO
-    alone, every sub-problem solved exactly on the GPU in extended range.
-    Wall time per query through mpdp_optimize, and each plan's cost as a
-    ratio to IDP2's (average and 95th percentile, as the paper's tables)."""
-    import math
+    """Heuristic modes (Sec. 4): GOO, IDP2 (k = 15, 25; GOO start), UnionDP
+    (k = 25, t = 15) in Algorithm 5's edge order and in the size-first
+    reading, every sub-problem solved exactly on the GPU in extended range.
+    Plan costs as the paper's Table 1 reports them: per query, the cost over
+    the best cost found, average and 95th percentile.  Where the exact DP
+    still runs (26-30 relations) the reference is the exact optimum itself;
+    at 100 / 300 / 1000 relations it is the best plan any variant found.
+    Wall time per query through mpdp_optimize."""
     import numpy as np
-    variants = {"idp2_25": (mpdp.MODE_IDP2, 25, 0), "uniondp_25_15": (mpdp.MODE_UNIONDP, 25, 15),
-                "goo": (mpdp.MODE_IDP2, 1, 0)}
-    out = {"workload": f"snowflake with fanout 1-5, depth uncapped, +5 % extra edges; {LARGE_QUERIES} queries "
-                       f"per size, seeds 0..{LARGE_QUERIES - 1}.  'independent': cards 10^U(2,8), sels "
-                       "10^U(-6,-1) (card(S) grows ~10^1.5 per relation, so the last joins dominate every "
-                       "plan's cost); 'pkfk': the same graphs with primary-key/foreign-key sels 1/card(key "
-                       "side), the paper's setting for its heuristic tables",
-           "ratio_to": "idp2_25"}
-    for gen, n in [(g, n) for g in ("independent", "pkfk") for n in LARGE_SIZES]:
-        make = W.snowflake_plus if gen == "independent" else W.snowflake_plus_pkfk
-        qs = [make(n, seed=i) for i in range(LARGE_QUERIES)]
-        opt.optimize(qs[0], mode=mpdp.MODE_IDP2, k=25)  # warm-up: device buffers
+    variants = heuristic_variants(mpdp)
+    out = {"variants": {k: {"mode": v[0], "k": v[1], "t": v[2]} for k, v in variants.items()},
+           "workload": "snowflake with fanout 1-5, depth uncapped; 'pkfk_tree': primary-key/foreign-key "
+                       "selectivities 1/card(key side) and no extra edge (Table 1's setting); 'pkfk': the "
+                       "same with +5 % extra edges; 'independent': +5 % extra edges, cards 10^U(2,8) and "
+                       "sels 10^U(-6,-1) drawn independently",
+           "queries_exact_per_size": EXACT_QUERIES, "queries_large_per_size": LARGE_QUERIES}
+
+    def run_variants(qs):
         res = {}
         for name, (mode, k, t) in variants.items():
             times, costs = [], []
@@ -758,16 +852,48 @@ def heuristic_line(opt, mpdp, W):
                 times.append(time.perf_counter() - t0)
                 costs.append(p.cost_xd)
             res[name] = (times, costs)
+        return res
+
+    def summary(res, ref_costs):
         line = {}
-        base = res["idp2_25"][1]
         for name, (times, costs) in res.items():
-            ratios = [m / bm * math.pow(2.0, e - be) for (m, e), (bm, be) in zip(costs, base)]
-            line[name] = {"ms_per_query": 1000.0 * float(np.mean(times)),
-                          "p50_ms": 1000.0 * float(np.median(times)),
-                          "cost_ratio_avg": float(np.mean(ratios)),
+            ratios = [_xd_ratio(c, r) for c, r in zip(costs, ref_costs)]
+            line[name] = {"cost_ratio_avg": float(np.mean(ratios)),
                           "cost_ratio_p95": float(np.percentile(ratios, 95)),
-                          "log2_cost_median": float(np.median([e + math.log2(m) for m, e in costs]))}
-        out[f"{gen}_n{n}"] = line
+                          "cost_ratio_max": float(np.max(ratios)),
+                          "best_of_all": int(sum(r <= 1.0 + 1e-12 for r in ratios)),
+                          "ms_per_query": 1000.0 * float(np.mean(times))}
+        return line
+
+    opt.optimize(W.snowflake_plus_pkfk(100, seed=0), mode=mpdp.MODE_IDP2, k=25)  # warm-up: device buffers
+    exact = {}
+    for shape, frac in (("pkfk_tree", 0.0), ("pkfk", 0.05)):
+        for n in EXACT_SIZES:
+            qs = [W.snowflake_plus_pkfk(n, seed=100 + i, extra_frac=frac) for i in range(EXACT_QUERIES)]
+            opt.optimize(qs[0])  # warm-up at this size
+            t0 = time.perf_counter()
+            opt_costs = [opt.optimize(q).cost for q in qs]
+            t_exact = (time.perf_counter() - t0) / len(qs)
+            res = run_variants(qs)
+            line = summary(res, [(float(np.frexp(c)[0]) * 2.0, int(np.frexp(c)[1]) - 1) for c in opt_costs])
+            line["exact_ms_per_query"] = 1000.0 * t_exact
+            exact[f"{shape}_n{n}"] = line
+    out["vs_exact_optimum"] = exact
+    large = {}
+    for gen, n in [(g, n) for g in ("pkfk_tree", "pkfk", "independent") for n in LARGE_SIZES]:
+        if gen == "independent":
+            qs = [W.snowflake_plus(n, seed=i) for i in range(LARGE_QUERIES)]
+        else:
+            qs = [W.snowflake_plus_pkfk(n, seed=i, extra_frac=0.0 if gen == "pkfk_tree" else 0.05)
+                  for i in range(LARGE_QUERIES)]
+        res = run_variants(qs)
+        best = [min((res[v][1][i] for v in res), key=lambda c: (c[0] != 0.0, c[1], c[0])) for i in range(len(qs))]
+        line = summary(res, best)
+        for name in res:
+            r2 = [_xd_ratio(c, b) for c, b in zip(res[name][1], res["idp2_25"][1])]
+            line[name]["over_idp2_25_avg"] = float(np.mean(r2))
+        large[f"{gen}_n{n}"] = line
+    out["vs_best_found"] = large
     return out
 
 
@@ -822,8 +948,45 @@ def serving_line(mpdp, W):
     return out
 
 
+def run_case(args):
+    """One workload shape as device batches, nothing timed or checked beyond
+    the device status words: the command a profiler wraps to capture the
+    kernels of that shape alone."""
+    import numpy as np
+    import torch
+    parts = args.case.split(":")
+    kind, n, nq = parts[0], int(parts[1]), int(parts[2])
+    lanes = int(parts[3]) if len(parts) > 3 else 0
+    memo = parts[4] if len(parts) > 4 else "dense"
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2202_13511_gb300 import mpdp
+    from paper_2202_13511_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    opt = mpdp.Optimizer(0, stream=torch.cuda.current_stream().cuda_stream,
+                         memo_kind={"dense": mpdp.MEMO_DENSE, "hash": mpdp.MEMO_HASH}[memo])
+    if lanes:
+        opt.set_config(lanes=lanes)
+    qs = [W.make(kind, n, seed=i) for i in range(nq)]
+    d_card = torch.tensor([c for q in qs for c in q.card], dtype=torch.float64, device="cuda")
+    d_edges = torch.from_numpy(mpdp.pack_edges([e for q in qs for e in q.edges]).view(np.uint8).copy()).cuda()
+    d_nodes = torch.zeros((nq, mpdp.PLAN_STRIDE * 40), dtype=torch.uint8, device="cuda")
+    d_cost = torch.zeros(nq, dtype=torch.float64, device="cuda")
+    d_status = torch.full((nq,), -100, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        opt.optimize_batch_device([q.n for q in qs], [len(q.edges) for q in qs], d_card, d_edges, d_nodes, d_cost,
+                                  d_status)
+    torch.cuda.synchronize()
+    bad = [int(x) for x in d_status.cpu().numpy() if x != 0]
+    opt.close()
+    print(json.dumps({"case": args.case, "batches": args.warmup + args.steps, "status": "ok" if not bad else bad}))
+    return 0 if not bad else 1
+
+
 def main():
     args = parse_args()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -77,7 +77,8 @@ enum {
     MPDP_MODE_UNIONDP = 2,
     MPDP_MODE_IDP2_LEARNED = 3,
     MPDP_MODE_UNIONDP_LEARNED = 4,
-    MPDP_MODE_UNIONDP_SIZEFIRST = 5
+    MPDP_MODE_UNIONDP_SIZEFIRST = 5,
+    MPDP_MODE_IDP2_WEIGHT_START = 6
 };
 
 /* CCP enumeration: AUTO picks TREE when the join graph is a tree
@@ -253,6 +254,11 @@ size_t mpdp_workspace_bytes(int32_t n_rels, const mpdp_config *cfg);
  * (min(u, v), max(u, v))), with IDP2 from GOO's plan as the fallback: the
  * cheaper plan is returned (GOO's on ties, and always when no model is
  * set).  t must be 0, as for MPDP_MODE_IDP2.
+ * MPDP_MODE_IDP2_WEIGHT_START: the same rule with a start that needs no
+ * model, a control for what the learned start adds: the query's edges in
+ * ascending join card (card(u) * card(v) * sel(u, v)), each joining the
+ * plans of its two ends while they are apart; IDP2 from GOO's plan is the
+ * fallback, the cheaper plan is returned (GOO's on ties).  t must be 0.
  * mpdp_optimize_batch returns MPDP_ERR_NOT_IMPLEMENTED for any mode but
  * exact. */
 int mpdp_optimize(mpdp_ctx *ctx, const mpdp_query *q, int64_t *handle);

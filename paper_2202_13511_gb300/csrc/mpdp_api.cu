@@ -1003,7 +1003,8 @@ static int validate_heuristic(const mpdp_query* q)
 {
     const int n = q->n_rels, m = q->n_edges;
     if (q->cost_model != MPDP_COST_COUT) return MPDP_ERR_INVALID_ARG;
-    const bool idp = q->mode == MPDP_MODE_IDP2 || q->mode == MPDP_MODE_IDP2_LEARNED;
+    const bool idp = q->mode == MPDP_MODE_IDP2 || q->mode == MPDP_MODE_IDP2_LEARNED ||
+                     q->mode == MPDP_MODE_IDP2_WEIGHT_START;
     if (!idp && q->mode != MPDP_MODE_UNIONDP && q->mode != MPDP_MODE_UNIONDP_LEARNED &&
         q->mode != MPDP_MODE_UNIONDP_SIZEFIRST)
         return MPDP_ERR_INVALID_ARG;

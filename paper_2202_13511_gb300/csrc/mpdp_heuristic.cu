@@ -194,6 +194,7 @@ public:
                const std::vector<XD>& sel, std::vector<float>& out);
 
     mpdp_mlp* model_ = nullptr;
+    bool weight_scores_ = false;  // score edges by log2 of their join card instead of the model
 
     int n_;
     std::vector<PNode> nodes_;
@@ -672,6 +673,12 @@ int Heuristic::scores(int m, const std::vector<int>& cur, const std::vector<std:
         ev[e] = ij[e].second;
         lsel[e] = xd_log2(sel[e]);
     }
+    if (weight_scores_) {
+        // the non-learned control: log2 of each edge's join card
+        out.resize(ij.size());
+        for (size_t e = 0; e < ij.size(); e++) out[e] = (float)(lcard[eu[e]] + lcard[ev[e]] + lsel[e]);
+        return MPDP_OK;
+    }
     std::vector<float> feat;
     edge_features(m, lcard, eu, ev, lsel, feat);
     const int rows = (int)ij.size();
@@ -733,6 +740,21 @@ int run_heuristic(const HeuristicQuery& q, XdExecutor& ex, cudaStream_t st, int 
             h.model_ = nullptr;
             if (rc == MPDP_OK && xd_less(h.nodes_[learned].cost, h.nodes_[root].cost)) {
                 root = learned;
+                res.learned_won = true;
+            }
+        }
+    } else if (q.mode == MPDP_MODE_IDP2_WEIGHT_START) {
+        // the learned mode's rule with a non-learned second start: IDP2 from
+        // the plan that joins the edges in ascending join card, IDP2 from
+        // GOO's plan as the fallback, the cheaper plan wins (GOO's on ties)
+        rc = h.idp2(q.k, root);
+        if (rc == MPDP_OK) {
+            int alt = -1;
+            h.weight_scores_ = true;
+            rc = h.idp2(q.k, alt, true);
+            h.weight_scores_ = false;
+            if (rc == MPDP_OK && xd_less(h.nodes_[alt].cost, h.nodes_[root].cost)) {
+                root = alt;
                 res.learned_won = true;
             }
         }

@@ -29,7 +29,8 @@ ERRORS = {
 }
 ERR = {v: k for k, v in ERRORS.items()}
 
-MODE_EXACT, MODE_IDP2, MODE_UNIONDP, MODE_IDP2_LEARNED, MODE_UNIONDP_LEARNED, MODE_UNIONDP_SIZEFIRST = range(6)
+(MODE_EXACT, MODE_IDP2, MODE_UNIONDP, MODE_IDP2_LEARNED, MODE_UNIONDP_LEARNED, MODE_UNIONDP_SIZEFIRST,
+ MODE_IDP2_WEIGHT_START) = range(7)
 PROFILE_OFF, PROFILE_SERIAL, PROFILE_CONCURRENT = range(3)
 ENUM_AUTO, ENUM_TREE, ENUM_BLOCKS, ENUM_DPSUB = range(4)
 MEMO_DENSE, MEMO_HASH = range(2)
