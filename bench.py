@@ -36,8 +36,9 @@ EXACT_SIZES = (26, 28, 30)
 EXACT_QUERIES = 10
 LARGE_SIZES = (100, 300, 1000)
 LARGE_QUERIES = 10
-# Issue-slot peak of the integer filter: 152 SMs x 4 schedulers x 32 lanes x clock.
-SMS, SCHEDULERS, LANES = 152, 4, 32
+# Issue-slot peak of the integer filter: SMs x 4 schedulers x 32 lanes x clock
+# (the device's SM count and the SM clock sampled during the timed region).
+SCHEDULERS, LANES = 4, 32
 # Algorithmic integer operations of the bitmap filter per bitmap examined.
 # Tree join graphs: a run of 32 bitmaps costs C(base) by byte tables (4 loads,
 # 4 byte extracts, 3 ors), the fixed-part test (3) and, when that passes, the
@@ -424,9 +425,12 @@ def run_ours(args):
     prof_steps = min(args.steps, 5)
     kt, kc = kernel_passes(opt, step, flush, prof_steps, mpdp)
     peaks = read_peaks()
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0
+    l2_gbs = mpdp.probe_read_gbs(32 << 20, 200, local_rank)
     dom = max(kt, key=lambda k: kt[k]["ms"])
     roof = roofline(dom, kc[dom], stats, prof_steps, peaks, bench_batch=(Q == QUERIES_PER_STEP and not tuned),
-                    serial=kt[dom])
+                    serial=kt[dom], sms=sms, mhz=mhz, l2_gbs=l2_gbs)
     kernel_share = {k: round(v["ms"] / max(sum(x["ms"] for x in kt.values()), 1e-12), 4)
                     for k, v in kt.items() if v["launches"]}
 
@@ -454,7 +458,7 @@ def run_ours(args):
     if rank == 0 and not args.no_star:
         if "shapes" in extra:
             for name in SHAPES:
-                line[name] = shape_line(name, opt, torch, mpdp, W, peaks)
+                line[name] = shape_line(name, opt, torch, mpdp, W, peaks, sms=sms, mhz=mhz, l2_gbs=l2_gbs)
         if "latency" in extra:
             line["latency"] = latency_line(opt, torch, W)
     if rank == 0 and world == 1 and not args.no_star:
@@ -532,7 +536,13 @@ def traffic_for(kind, measured):
     return t["bytes"] if kernel_fingerprint(t["kernel"], t["helpers"]) == t["sha1"] else None
 
 
-def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False, serial=None, filter_mode=2):
+def issue_peak(sms: int, mhz: float) -> float:
+    """Integer issue slots in T lane-ops/s: SMs x 4 schedulers x 32 lanes x clock."""
+    return sms * SCHEDULERS * LANES * mhz * 1e6 / 1e12
+
+
+def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False, serial=None, filter_mode=2,
+             sms=152, mhz=2070.0, l2_gbs=None):
     """Roofline of the dominant kernel class.  `stats` are the per-query
     counters of one step's queries, `timing` the class's launches and active
     wall time over `prof_steps` steps with the lanes concurrent (the timed
@@ -554,20 +564,30 @@ def roofline(kind, timing, stats, prof_steps, peaks, bench_batch=False, serial=N
             return OPS_PER_CONNECTED_SET if unranked_connected(s) else OPS_PER_BITMAP_TREE
         ops = sum(per_set(s) * int(s["sets_unranked"]) + OPS_PER_BFS_ROUND * int(s["filter_steps"])
                   for s in stats) * prof_steps / launches
-        mhz = 2070.0
-        peak = SMS * SCHEDULERS * LANES * mhz * 1e6 / 1e12
+        peak = issue_peak(sms, mhz)
         ach = ops / avg_s / 1e12
         kname = "k_filter_connected" if all(unranked_connected(s) for s in stats) else "k_filter_bitmaps"
         return {"kernel": kname, "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "Tops/s", "frac": ach / peak, "traffic": traffic_for("filter", bench_batch),
-                "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz (issue slots)",
+                "peak_source": f"{sms} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz (median SM clock "
+                               f"sampled in the timed region; issue slots)",
                 "ops_per_launch": ops, "avg_launch_ms": avg_s * 1000.0, **extra}
     # memo-traffic kernels: algorithmic bytes per launch
     nbytes = sum(BYTES_PER_CCP * int(s["ccp_pairs"]) + BYTES_PER_SET * int(s["sets_connected"])
                  for s in stats) * prof_steps / launches
     peak = (peaks or {}).get("hbm_gbs", 6800.0)
     ach = nbytes / avg_s / 1e9
-    name = {"eval": "k_eval_tree", "heavy": "k_eval_heavy"}.get(kind, kind)
+    if kind == "eval":  # the tree-mode or the block-mode evaluation, by the queries' enumeration
+        modes = {int(s["enumeration"]) for s in stats}
+        name = "k_eval_tree" if modes == {1} else "k_eval_blocks" if modes == {2} else "k_eval_tree+k_eval_blocks"
+    else:
+        name = {"heavy": "k_eval_heavy"}.get(kind, kind)
+    if l2_gbs:
+        # the same algorithmic bytes against the L2's read bandwidth, measured
+        # on this GPU by one launch re-reading a 32 MiB buffer: most memo
+        # reads of neighbouring sets are L2 hits
+        extra["l2"] = {"peak": l2_gbs, "unit": "GB/s", "frac": ach / l2_gbs,
+                       "peak_source": "mpdp_probe_read_gbs, 32 MiB buffer read 200 times in one launch"}
     return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "traffic": traffic_for(kind, bench_batch and kind == "eval"),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst)" if peaks else "fallback 6800 GB/s",
@@ -613,7 +633,7 @@ SHAPES = {
 }
 
 
-def shape_line(name, opt, torch, mpdp, W, peaks, reps=5):
+def shape_line(name, opt, torch, mpdp, W, peaks, reps=5, sms=152, mhz=2070.0, l2_gbs=None):
     """One extra workload shape: a device batch timed like the main step."""
     import numpy as np
     desc, kind, n, nq, kw = SHAPES[name]
@@ -652,15 +672,15 @@ def shape_line(name, opt, torch, mpdp, W, peaks, reps=5):
             "queries_per_s": nq * 1000.0 / ms_batch, "ccp_pairs_per_s": ccp / (ms_batch / 1000.0),
             "ccp_pairs_per_query": ccp / nq,
             "sets_connected_per_query": sum(int(s["sets_connected"]) for s in stats) / nq,
-            "roofline": roofline(dom, kc[dom], stats, 3, peaks, serial=kt[dom]),
+            "roofline": roofline(dom, kc[dom], stats, 3, peaks, serial=kt[dom], sms=sms, mhz=mhz, l2_gbs=l2_gbs),
             "kernel_share": {k: round(v["ms"] / max(sum(x["ms"] for x in kt.values()), 1e-12), 4)
                              for k, v in kt.items() if v["launches"]}}
 
 
 def ablation_line(opt, torch, mpdp, W):
     """The paper's relative claims on the same kernels: MPDP's block
-    enumeration against DPSUB's vertex-based one (Sec. 6.2: far fewer pairs
-    evaluated), Collaborative Context Collection on / off (Sec. 6.4), the
+    enumeration against DPSUB's vertex-based one (Sec. 7.2: far fewer pairs
+    evaluated), Collaborative Context Collection on / off (Sec. 7.2.5), the
     fusion of evaluate, prune and scatter on / off (Sec. 5), and the batch
     split into 1/2/4/8 concurrent lanes.  Device time of one batch (CUDA
     events, L2 flushed, mean of 3)."""
@@ -836,10 +856,13 @@ def heuristic_line(opt, mpdp, W):
     import numpy as np
     variants = heuristic_variants(mpdp)
     out = {"variants": {k: {"mode": v[0], "k": v[1], "t": v[2]} for k, v in variants.items()},
-           "workload": "snowflake with fanout 1-5, depth uncapped; 'pkfk_tree': primary-key/foreign-key "
-                       "selectivities 1/card(key side) and no extra edge (Table 1's setting); 'pkfk': the "
-                       "same with +5 % extra edges; 'independent': +5 % extra edges, cards 10^U(2,8) and "
-                       "sels 10^U(-6,-1) drawn independently",
+           "workload": "snowflake with fanout 1-5, depth uncapped.  'independent': +5 % extra edges, cards "
+                       "10^U(2,8) and sels 10^U(-6,-1) drawn independently (the configured large-query "
+                       "workload); 'schema_tree': a snowflake schema with primary-key/foreign-key joins "
+                       "(Table 1's setting): fact card 10^U(6,8), each dimension 10^-U(0,2) of the table "
+                       "referencing it, sel 1/card(key side); 'schema': the same +5 % extra PK-FK edges; "
+                       "'pkfk_tree' / 'pkfk': PK-FK selectivities over independent cards, without / with "
+                       "+5 % extra edges",
            "queries_exact_per_size": EXACT_QUERIES, "queries_large_per_size": LARGE_QUERIES}
 
     def run_variants(qs):
@@ -866,10 +889,15 @@ def heuristic_line(opt, mpdp, W):
         return line
 
     opt.optimize(W.snowflake_plus_pkfk(100, seed=0), mode=mpdp.MODE_IDP2, k=25)  # warm-up: device buffers
+    shapes = {"schema_tree": lambda n, s: W.snowflake_schema_pkfk(n, seed=s),
+              "schema": lambda n, s: W.snowflake_schema_pkfk(n, seed=s, extra_frac=0.05),
+              "pkfk_tree": lambda n, s: W.snowflake_plus_pkfk(n, seed=s, extra_frac=0.0),
+              "pkfk": lambda n, s: W.snowflake_plus_pkfk(n, seed=s, extra_frac=0.05),
+              "independent": lambda n, s: W.snowflake_plus(n, seed=s)}
     exact = {}
-    for shape, frac in (("pkfk_tree", 0.0), ("pkfk", 0.05)):
+    for shape in ("schema_tree", "schema", "pkfk_tree", "pkfk"):
         for n in EXACT_SIZES:
-            qs = [W.snowflake_plus_pkfk(n, seed=100 + i, extra_frac=frac) for i in range(EXACT_QUERIES)]
+            qs = [shapes[shape](n, 100 + i) for i in range(EXACT_QUERIES)]
             opt.optimize(qs[0])  # warm-up at this size
             t0 = time.perf_counter()
             opt_costs = [opt.optimize(q).cost for q in qs]
@@ -880,12 +908,8 @@ def heuristic_line(opt, mpdp, W):
             exact[f"{shape}_n{n}"] = line
     out["vs_exact_optimum"] = exact
     large = {}
-    for gen, n in [(g, n) for g in ("pkfk_tree", "pkfk", "independent") for n in LARGE_SIZES]:
-        if gen == "independent":
-            qs = [W.snowflake_plus(n, seed=i) for i in range(LARGE_QUERIES)]
-        else:
-            qs = [W.snowflake_plus_pkfk(n, seed=i, extra_frac=0.0 if gen == "pkfk_tree" else 0.05)
-                  for i in range(LARGE_QUERIES)]
+    for gen, n in [(g, n) for g in ("independent", "schema_tree", "schema", "pkfk") for n in LARGE_SIZES]:
+        qs = [shapes[gen](n, i) for i in range(LARGE_QUERIES)]
         res = run_variants(qs)
         best = [min((res[v][1][i] for v in res), key=lambda c: (c[0] != 0.0, c[1], c[0])) for i in range(len(qs))]
         line = summary(res, best)

@@ -13,7 +13,7 @@
  *     ("Prune", fused) and stores it in the memo ("Scatter");
  *   - the plan is fetched recursively from the memo (Sec. 5, last paragraph).
  *
- * Cost model (the paper's own is unspecified, Sec. 6.1): C_out.
+ * Cost model (the paper's own is unspecified, Sec. 7.1): C_out.
  *   cost({R_i}) = 0;  cost(L join R) = (cost(L) + cost(R)) + card(L u R).
  *   card(S) is a product taken in an order fixed by S alone ("peeling"):
  *   card({r}) = card[r]; otherwise v is the highest-index relation of S
@@ -327,9 +327,9 @@ int mpdp_optimize_device(mpdp_ctx *ctx, int32_t n_rels, int32_t n_edges, const d
  * context is involved and nothing is allocated: the dense memo is a fixed
  * device array inside the library of MPDP_NOALLOC_SCRATCH_BYTES
  * (2^16 sets x 20 bytes), which caps n_rels at MPDP_NOALLOC_MAX_RELS.  One
- * kernel of one block runs the whole DP (levels 2..n, block enumeration of
- * Algorithm 4) and the plan fetch; cost, plan and status are bit-identical
- * to mpdp_optimize_device for the same query.
+ * kernel of one block runs the whole DP (levels 2..n) and the plan fetch;
+ * cost, plan and status are bit-identical to mpdp_optimize_device for the
+ * same query.
  *   n_rels, n_edges: host values; d_card (n_rels doubles), d_edges (n_edges
  *     edges, may be NULL when 0): device, validated on the device as in the
  *     batched path; cost_model: MPDP_COST_COUT;
@@ -342,9 +342,11 @@ int mpdp_optimize_device(mpdp_ctx *ctx, int32_t n_rels, int32_t n_edges, const d
  * MPDP_ERR_TOO_LARGE for n_rels > MPDP_NOALLOC_MAX_RELS, MPDP_ERR_INVALID_ARG
  * for a NULL pointer, n_rels < 1, a bad n_edges or cost model, and
  * MPDP_ERR_CUDA when a runtime call fails.
- * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Nothing in the array has to start at zero (a
+ * Set-up: the first call in each context (in practice, on each device)
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  The
+ * address is kept with the context's unique id, so after a device reset the
+ * next call, in the new context, looks it up again.  Nothing in the array has to start at zero (a
  * call writes every entry before reading it).  Concurrency: every call on a
  * device uses the same array, so calls whose kernels can overlap on the GPU
  * (different streams, unordered host threads) race; order them on one
@@ -402,6 +404,13 @@ int mpdp_profile_read(mpdp_ctx *ctx, double *ms, uint64_t *launches);
 int mpdp_profile_read_active(mpdp_ctx *ctx, double *ms, double *active_ms, uint64_t *launches);
 
 /* Static text for an error code. */
+/* Measurement (not part of the method): read bandwidth of this GPU in GB/s,
+ * the best of five launches that each read a `bytes` buffer `passes` times
+ * (16-byte loads that bypass L1).  A buffer well below the L2 capacity
+ * measures the L2; one far above it, HBM.  The buffer is allocated and freed
+ * by the call; synchronous on the legacy stream. */
+int mpdp_probe_read_gbs(int device, size_t bytes, int passes, double *gbs);
+
 const char *mpdp_strerror(int code);
 /* Text of the last CUDA error seen by this context (or ""). */
 const char *mpdp_last_error(const mpdp_ctx *ctx);

@@ -1,6 +1,6 @@
 /* Multi-threaded CPU MPDP: the paper's own CPU implementation of the method
  * (Sec. 3.3 "MPDP on CPU"), the "MPDP (24CPU)" system its experiments
- * compare the GPU against (Sec. 6.2).  A comparison baseline that runs on
+ * compare the GPU against (Sec. 7.2).  A comparison baseline that runs on
  * the host cores; it shares no code with the GPU library and is not a
  * fallback of it.
  *

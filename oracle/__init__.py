@@ -11,7 +11,7 @@ Contents (each restates a definition of arXiv 2202.13511):
   * ``mpdp_oracle.c`` (plain C, fp64, -ffp-contract=off): card(S), grow and
     connected (Sec. 3.2.1), blocks and cut vertices (Sec. 2.4), generic DPSUB
     (Algorithm 1) and DPCCP (the CCP-only enumeration the paper compares
-    against, Sec. 1 and Sec. 6.2), and the count of block bipartitions that
+    against, Sec. 1 and Sec. 7.2), and the count of block bipartitions that
     Algorithm 4 visits.
   * ``brute_force`` (pure Python, n <= 7): every bushy join tree without cross
     products (Sec. 2.1.1 "Objective"), costed with C_out, minimised under the

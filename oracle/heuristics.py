@@ -3,7 +3,7 @@ the exact DP in extended range (``xd_oracle.c``).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).  Plain Python, slow on
 purpose, written to be read against Sec. 4.1 (IDP2), Algorithm 5 (UnionDP)
-and the GOO description of Sec. 6.3.
+and the GOO description of Sec. 7.3.
 
 Values are extended-range ("XD") pairs (m, e) meaning m * 2^e, with m = 0 or
 1 <= m < 2.  The operations are the ones xd_oracle.c documents, written again
@@ -44,7 +44,7 @@ Readings where the paper is silent (the product path follows the same ones):
     with the exact DP.  The sets become the nodes of the next graph
     (numbered by smallest base relation) and the procedure recurses.
     Algorithm 5 has a single bound k.  The paper runs UnionDP with k = 25
-    and a partition threshold t = 15 (Sec. 6.3), which is read here as
+    and a partition threshold t = 15 (Sec. 7.3), which is read here as
     partitions <= t and the final DP at <= k nodes.
   * UnionDP, size-first variant (order="size_first"): the same, except
     that the next edge is re-picked after every union as the one with the
@@ -52,7 +52,7 @@ Readings where the paper is silent (the product path follows the same ones):
     edge whose sum exceeds t is dropped.  This evaluates the ordering key
     on the current sets instead of fixing it before the loop.  It is kept
     as a comparison; Table 1's ranking (UnionDP best on snowflakes,
-    because it removes single expensive edges, Sec. 6.3) supports the
+    because it removes single expensive edges, Sec. 7.3) supports the
     fixed order.
 """
 from __future__ import annotations

@@ -24,7 +24,7 @@
  *     (Sec. 2.4), by their plain definitions, to count what the block-based
  *     enumeration of Algorithm 4 evaluates.
  *
- * Readings where the paper is silent (the cost model is unspecified, Sec. 6.1):
+ * Readings where the paper is silent (the cost model is unspecified, Sec. 7.1):
  *   - cost model C_out: cost({R_i}) = 0,
  *       cost(L join R) = (cost(L) + cost(R)) + card(L u R);
  *   - card(S) is the product of card[r] over the relations of S and sel over
@@ -42,7 +42,7 @@
  *     the minimum cost; the rule replaces Algorithm 1's "first strict
  *     improvement wins", whose result would depend on enumeration order;
  *   - counters: ccp counts each unordered CCP pair once (this is the reading
- *     under which the 2805x ratio printed in Sec. 2.3 and Sec. 6.2.1 holds).
+ *     under which the 2805x ratio printed in Sec. 2.3 and Sec. 7.2.1 holds).
  */
 #include <math.h>
 #include <stdint.h>

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(OUT_DIR, "libmpdp.so")
 CPU_SOURCE = "mpdp_cpu.c"
 CPU_LIB_PATH = os.path.join(OUT_DIR, "libmpdp_cpu.so")
 SOURCES = ["mpdp_kernels.cu", "mpdp_api.cu", "mpdp_noalloc.cu", "mpdp_server.cu", "mpdp_xd.cu",
-           "mpdp_heuristic.cu", "mpdp_mlp.cu"]
+           "mpdp_heuristic.cu", "mpdp_mlp.cu", "mpdp_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fno-fast-math", "-I", os.path.join(ROOT, "include")]

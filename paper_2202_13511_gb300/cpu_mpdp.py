@@ -1,6 +1,6 @@
 """Binding of the multi-threaded CPU MPDP (include/mpdp_cpu.h): the paper's
 host implementation of the method (Sec. 3.3), kept as the "MPDP (24CPU)"
-comparison of Sec. 6.2.  A baseline that runs on the host cores; the GPU
+comparison of Sec. 7.2.  A baseline that runs on the host cores; the GPU
 library never calls it."""
 from __future__ import annotations
 

@@ -6,7 +6,7 @@
 //   replayed from a CUDA graph captured once per batch shape; a device ->
 //   host copy of every query's plan + counters (host path) or a publish
 //   kernel (device path).  Nothing in between waits for the host: the
-//   paper's per-level host round trip (Sec. 6.2, small queries) is gone, and
+//   paper's per-level host round trip (Sec. 7.2, small queries) is gone, and
 //   all queries of a batch share every launch.
 #include <cuda_runtime.h>
 
@@ -253,6 +253,8 @@ static QuerySize query_size(int n, int enumeration, int memo_kind)
 {
     QuerySize z;
     z.lists = list_entries(n);
+    // block mode: the connectivity bitmap (2^n bits) follows the level lists
+    if (enumeration == MPDP_ENUM_BLOCKS) z.lists += conn_words(n);
     z.heavy = enumeration == MPDP_ENUM_BLOCKS ? binom_host(n, n / 2) : 0;
     if (memo_kind == MPDP_MEMO_DENSE) z.memo = (size_t)1 << n;
     else z.hash = hash_arena_slots(n);
@@ -736,6 +738,10 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
         const QuerySize z = query_size(q.n, q.enumeration, kind);
         d.heavy_base = hbase;
         d.heavy_cap = (uint32_t)z.heavy;
+        // the bitmap sweep writes the connectivity bitmap of the block-mode
+        // queries it serves (the unranking filter forms no bitmap)
+        d.use_conn = (q.enumeration == MPDP_ENUM_BLOCKS && ctx->cfg.filter != MPDP_FILTER_UNRANK) ? 1u : 0u;
+        d.conn_base = lbase + list_entries(q.n);
         lbase += z.lists;
         mbase += z.memo;
         hbase += z.heavy;

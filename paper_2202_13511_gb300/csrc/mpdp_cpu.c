@@ -1,5 +1,5 @@
 /* Multi-threaded CPU MPDP (Sec. 3.3): the paper's host implementation of
- * the method, kept as the "MPDP (24CPU)" comparison of Sec. 6.2.
+ * the method, kept as the "MPDP (24CPU)" comparison of Sec. 7.2.
  *
  * The structure follows the paper's description of its CPU version:
  *   - levels k = 2..n in order, a barrier between them (every set of size

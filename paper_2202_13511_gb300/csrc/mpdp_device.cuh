@@ -143,6 +143,13 @@ struct QDesc {
     uint32_t filter_block_base;        // first filter block of the query
     uint32_t heavy_cap;                // heavy-set entries (and extra chunks) of one level: max_k C(n, k)
     unsigned long long heavy_base;     // first heavy-set entry of the query (block mode only)
+    // Connectivity bitmap (block mode with the bitmap sweep): bit S of word
+    // S / 32 is 1 when G[S] is connected (single relations included, the
+    // empty set not), 2^n bits from list word conn_base on; the sweep writes
+    // every word.  use_conn = 0: no bitmap, the evaluation tests sets itself.
+    unsigned long long conn_base;
+    uint32_t use_conn;
+    uint32_t pad_conn;
 };
 
 // A heavy set (more than heavy_threshold pairs) is cut into nch chunks of
@@ -228,6 +235,18 @@ __device__ __forceinline__ bool connected(uint32_t s, const uint32_t* __restrict
         if (seen == s) return true;
     }
     return seen == s;
+}
+
+// The query's connectivity bitmap, when the bitmap sweep wrote one (block
+// mode; a tree unranked by the connected-set filter has none).
+__device__ __forceinline__ const uint32_t* conn_bitmap(const BatchArgs& a, int q);
+
+// G[X] connected, for a non-empty X: one bit of the connectivity bitmap,
+// a single relation at once, or (no bitmap) the search from min(X).
+__device__ __forceinline__ bool conn_of(uint32_t x, const uint32_t* __restrict__ cw, const uint32_t* __restrict__ adj)
+{
+    if ((x & (x - 1u)) == 0u) return true;
+    return cw ? ((__ldg(&cw[x >> 5]) >> (x & 31u)) & 1u) != 0u : connected(x, adj);
 }
 
 // Neighbourhood N(S) (every relation adjacent to a member of S) by byte tables.
@@ -331,6 +350,12 @@ __device__ __forceinline__ void warp_min_x(unsigned long long& bx, uint32_t& bl)
             bl = ol;
         }
     }
+}
+
+__device__ __forceinline__ const uint32_t* conn_bitmap(const BatchArgs& a, int q)
+{
+    const QDesc& d = a.desc[q];
+    return (d.use_conn && !a.query[q].use_connected) ? a.lists + d.conn_base : nullptr;
 }
 
 // Murmur3's 32-bit finaliser (fmix32), the hash the paper names for the memo.
@@ -571,14 +596,23 @@ constexpr unsigned long long kNoX = 0xffffffffffffffffull;
 // cycle edge-sets gives one class per block with a cycle; its vertices are
 // the class's child vertices plus their parents.  A tree edge on no cycle is
 // a bridge, a block of its own two vertices.  Returns the number of blocks.
+//
+// With `side` given, a bridge block j also gets side[j]: the side of S that
+// holds its lower vertex once the bridge is removed (grow({min}, S \ {max})
+// for that block's only pair).  A bridge is a tree edge (x, par[x]) and its
+// removal cuts off exactly x's subtree, computed for every x bottom-up over
+// the discovery order.  Other blocks get side[j] = 0.
 __device__ __forceinline__ int find_blocks(uint32_t s, const uint32_t* __restrict__ adj,
-                                           uint32_t* __restrict__ blk)
+                                           uint32_t* __restrict__ blk, uint32_t* __restrict__ side = nullptr)
 {
     uint8_t par[kMaxRels];
     uint32_t anc[kMaxRels];
+    uint8_t ord[kMaxRels];
+    int nord = 0;
     const int root = lowest(s);
     par[root] = 0xff;
     anc[root] = 0u;
+    ord[nord++] = (uint8_t)root;
     uint32_t vis = 1u << root, queue = vis;
     while (queue) {
         const int x = lowest(queue);
@@ -591,6 +625,7 @@ __device__ __forceinline__ int find_blocks(uint32_t s, const uint32_t* __restric
             ch &= ch - 1u;
             par[v] = (uint8_t)x;
             anc[v] = anc[x] | (1u << v);
+            ord[nord++] = (uint8_t)v;
         }
     }
     uint32_t cls[kMaxRels];
@@ -630,12 +665,48 @@ __device__ __forceinline__ int find_blocks(uint32_t s, const uint32_t* __restric
         blk[nb++] = b;
     }
     uint32_t br = s & ~in_cycle & ~(1u << root);
+    if (side) {
+        for (int j = 0; j < nb; j++) side[j] = 0u;
+        if (br) {
+            // subtree masks, children before parents (reverse discovery order)
+            uint32_t sub[kMaxRels];
+            for (int i = 0; i < nord; i++) sub[ord[i]] = 1u << ord[i];
+            for (int i = nord - 1; i > 0; i--) sub[par[ord[i]]] |= sub[ord[i]];
+            while (br) {
+                const int v = lowest(br);
+                br &= br - 1u;
+                const int p = par[v];
+                blk[nb] = (1u << v) | (1u << p);
+                side[nb++] = v < p ? sub[v] : s ^ sub[v];
+            }
+        }
+        return nb;
+    }
     while (br) {
         const int v = lowest(br);
         br &= br - 1u;
         blk[nb++] = (1u << v) | (1u << par[v]);
     }
     return nb;
+}
+
+// Every pair of B's vertices adjacent (then every bipartition of B is a CCP).
+__device__ __forceinline__ bool is_clique(uint32_t b, const uint32_t* __restrict__ adj)
+{
+    uint32_t t = b;
+    while (t) {
+        const int v = lowest(t);
+        t &= t - 1u;
+        if ((adj[v] & b) != (b ^ (1u << v))) return false;
+    }
+    return true;
+}
+
+// S_l of a CCP (lb, rb) of a block of S: grow(lb, S \ rb), which is lb
+// itself when the block is all of S.
+__device__ __forceinline__ uint32_t left_side(uint32_t s, uint32_t lb, uint32_t rb, const uint32_t* __restrict__ adj)
+{
+    return (lb | rb) == s ? lb : grow(lb, s & ~rb, adj);
 }
 
 // Unordered bipartitions of a block B visited by the enumeration: every lb

@@ -737,6 +737,14 @@ __global__ void __launch_bounds__(kFilterThreads, 6) k_filter_bitmaps(BatchArgs 
                         if (ok) flags |= 1u << i;
                     }
                 }
+                if (d->use_conn) {
+                    // the query's connectivity bitmap: this run's word, single
+                    // relations included, the empty set excluded
+                    uint32_t w = flags;
+                    if (base == 0u) w &= ~1u;
+                    if (limit - base64 < kBitmapsPerThread) w &= (1u << (uint32_t)(limit - base64)) - 1u;
+                    a.lists[d->conn_base + (base >> 5)] = w;
+                }
                 uint32_t valid = 0xffffffffu;
                 if (limit - base64 < kBitmapsPerThread) valid = (1u << (uint32_t)(limit - base64)) - 1u;
                 if (__popc(base) <= 1)  // the empty set and single relations are not DP sets
@@ -1252,13 +1260,14 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
         }
         DevCounters* cnt = &a.out[qi].counters;
         const QDesc& d = a.desc[qi];
+        const uint32_t* __restrict__ cw = conn_bitmap(a, qi);
         const uint32_t idx = (t - s_pref[qi]) * kEvalThreads + threadIdx.x;
         bool to_heavy = false;
         uint32_t s = 0u, want = 0u;  // want: extra chunks asked for
         if (idx < cnt->list_count[k]) {
             s = a.lists[d.list_base + d.list_off[k] + idx];
-            uint32_t blk[kMaxRels];
-            const int nb = find_blocks(s, sq.adj, blk);
+            uint32_t blk[kMaxRels], side[kMaxRels];
+            const int nb = find_blocks(s, sq.adj, blk, a.dpsub ? nullptr : side);
             uint32_t pairs = 0u;
             for (int j = 0; j < nb; j++) pairs += block_pairs(blk[j]);
             if (a.dpsub) pairs = block_pairs(s);  // the whole set as one block
@@ -1274,12 +1283,19 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
                 const int enb = a.dpsub ? 1 : nb;
                 for (int j = 0; j < enb; j++) {
                     const uint32_t b = a.dpsub ? s : blk[j];
+                    if (!a.dpsub && side[j]) {
+                        // a bridge: its one pair is a CCP, the lower vertex's side known
+                        ccp++;
+                        fold_pair(side[j], s ^ side[j], memo, cnt, bx, bl);
+                        continue;
+                    }
                     const uint32_t mn = b & (0u - b), rest = b ^ mn;
+                    const bool all_ccp = is_clique(b, sq.adj);
                     for (uint32_t sub = 0u; sub != rest; sub = (sub - rest) & rest) {
                         const uint32_t lb = mn | sub, rb = b ^ lb;
-                        if (!connected(lb, sq.adj) || !connected(rb, sq.adj)) continue;
+                        if (!all_ccp && (!conn_of(lb, cw, sq.adj) || !conn_of(rb, cw, sq.adj))) continue;
                         ccp++;
-                        const uint32_t sl = grow(lb, s & ~rb, sq.adj);
+                        const uint32_t sl = left_side(s, lb, rb, sq.adj);
                         fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
                     }
                 }
@@ -1357,6 +1373,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
     __shared__ uint32_t s_bpref[kWarps][kMaxRels + 1];
     __shared__ int s_nb[kWarps];
     __shared__ int s_pv[kWarps];
+    __shared__ uint32_t s_cliq[kWarps];  // bit j: block j is a clique
     __shared__ uint32_t s_stash_l[kWarps][64];
     __shared__ uint32_t s_stash_r[kWarps][64];
     memo.setup(s_memo);
@@ -1403,11 +1420,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
                 s_blk[warp][0] = s;
                 nb = 1;
             }
-            uint32_t acc = 0u;
+            uint32_t acc = 0u, cliq = 0u;
             for (int j = 0; j < nb; j++) {
                 s_bpref[warp][j] = acc;
                 acc += block_pairs(s_blk[warp][j]);
+                if (is_clique(s_blk[warp][j], sq.adj)) cliq |= 1u << j;
             }
+            s_cliq[warp] = cliq;
             s_bpref[warp][nb] = acc;
             s_nb[warp] = nb;
             if (chunk == 0u) {
@@ -1422,27 +1441,43 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
         const uint32_t total = bpref[nb];
         const uint32_t lo = (uint32_t)((unsigned long long)total * chunk / nch);
         const uint32_t hi = (uint32_t)((unsigned long long)total * (chunk + 1u) / nch);
+        const uint32_t* __restrict__ cw = conn_bitmap(a, qi);
+        const uint32_t cliq = s_cliq[warp];
         unsigned long long bx = kNoX;
         uint32_t bl = kFull;
         uint32_t stash = 0u;  // warp-uniform stash fill
-        for (uint32_t p0 = lo; p0 < hi; p0 += 32u) {
-            const uint32_t p = p0 + (uint32_t)lane;
+        // Each lane takes a contiguous run of the chunk's pair indices: the
+        // first one's lb by deposit, the next ones by stepping to the next
+        // submask of the block, (sub - rest) & rest, in index order.
+        const uint32_t per = (hi - lo + 31u) >> 5;
+        uint32_t p = lo + (uint32_t)lane * per;
+        const uint32_t pend = p + per < hi ? p + per : hi;
+        int j = 0;
+        while (j + 1 < nb && bpref[j + 1] <= p) j++;
+        uint32_t b = blk[j], mn = b & (0u - b), rest = b ^ mn;
+        uint32_t sub = p < pend ? deposit(p - bpref[j], rest) : 0u;
+        for (uint32_t round = 0; round < per; round++) {  // warp-uniform trip count
             bool valid = false;
             uint32_t lb = 0u, rb = 0u;
-            if (p < hi) {
-                int j = 0;
-                while (j + 1 < nb && bpref[j + 1] <= p) j++;
-                const uint32_t b = blk[j];
-                const uint32_t mn = b & (0u - b);
-                lb = mn | deposit(p - bpref[j], b ^ mn);
+            if (p < pend) {
+                lb = mn | sub;
                 rb = b ^ lb;
-                valid = connected(lb, sq.adj) && connected(rb, sq.adj);
+                valid = ((cliq >> j) & 1u) || (conn_of(lb, cw, sq.adj) && conn_of(rb, cw, sq.adj));
+                p++;
+                sub = (sub - rest) & rest;
+                if (p < pend && p == bpref[j + 1]) {  // the next block's pairs
+                    j++;
+                    b = blk[j];
+                    mn = b & (0u - b);
+                    rest = b ^ mn;
+                    sub = 0u;
+                }
             }
             const unsigned bal = __ballot_sync(kFull, valid);
             ccp += (lane == 0) ? (unsigned long long)__popc(bal) : 0ull;
             if (!a.use_ccc) {
                 if (valid) {
-                    const uint32_t sl = grow(lb, s & ~rb, sq.adj);
+                    const uint32_t sl = left_side(s, lb, rb, sq.adj);
                     fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
                 }
                 continue;
@@ -1457,7 +1492,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
             if (stash >= 32u) {
                 const uint32_t i = stash - 32u + lane;
                 const uint32_t l2 = s_stash_l[warp][i], r2 = s_stash_r[warp][i];
-                const uint32_t sl = grow(l2, s & ~r2, sq.adj);
+                const uint32_t sl = left_side(s, l2, r2, sq.adj);
                 fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
                 stash -= 32u;
             }
@@ -1465,7 +1500,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
         }
         if (a.use_ccc && lane < (int)stash) {
             const uint32_t l2 = s_stash_l[warp][lane], r2 = s_stash_r[warp][lane];
-            const uint32_t sl = grow(l2, s & ~r2, sq.adj);
+            const uint32_t sl = left_side(s, l2, r2, sq.adj);
             fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
         }
         warp_min_x(bx, bl);
@@ -1647,6 +1682,8 @@ size_t list_entries(int n)
     for (int k = 2; k <= n; k++) off += binom_host(n, k);
     return (size_t)off;
 }
+
+size_t conn_words(int n) { return n >= 5 ? (size_t)1 << (n - 5) : 1; }
 
 size_t hash_arena_slots(int n)
 {

@@ -46,6 +46,8 @@ unsigned long long binom_host(int n, int k);
 // tiles x 256 sets x (k - 1) pairs.
 unsigned long long unfused_pair_records(const BatchPlan& bp);
 size_t list_entries(int n);
+// words of a block-mode query's connectivity bitmap (2^n bits, at least one word)
+size_t conn_words(int n);
 size_t hash_arena_slots(int n);
 // Per-level list offsets and filter warp ranges of one query; returns the
 // query's filter block count in filter_blocks.

@@ -10,6 +10,7 @@
 // this file; the library allocates nothing for it.  Calls whose kernels can
 // overlap on the GPU (other streams, unordered host threads) share that
 // array and race: order them on one stream.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -231,10 +232,52 @@ k_optimize_noalloc(int n, int m, const double* __restrict__ card, const mpdp_edg
     }
 }
 
-// Per-device address of the scratch, looked up once with that device current.
+// Address of the scratch array in the current context.  The runtime maps
+// the array into each context that loads this library's device code, so the
+// address is looked up (cudaGetSymbolAddress) once per context, with that
+// context's device current, and kept per device with the context's unique
+// id (cuCtxGetId, found through the runtime's driver entry points, so the
+// library does not link the driver library).  A call in a different or
+// re-created context of that device (after cudaDeviceReset, say) looks the
+// address up again, so a stale address is never used.
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
 std::mutex g_setup_mu;
 constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_ptr[kMaxDevices] = {};
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;  // 0: not looked up yet (context ids start at 1)
+    unsigned char* ptr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+
+bool resolve_driver_calls()
+{
+    if (g_ctx_get_current && g_ctx_get_id) return true;
+    void *a = nullptr, *b = nullptr;
+    cudaDriverEntryPointQueryResult qa = cudaDriverEntryPointSymbolNotFound, qb = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+        qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b) {
+        cudaGetLastError();
+        return false;
+    }
+    g_ctx_get_current = reinterpret_cast<PfnCtxGetCurrent>(a);
+    g_ctx_get_id = reinterpret_cast<PfnCtxGetId>(b);
+    return true;
+}
+
+// Unique id of the calling thread's current context (0: none current).
+unsigned long long current_ctx_id()
+{
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    if (g_ctx_get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 int scratch_for_device(unsigned char** out)
 {
@@ -244,15 +287,22 @@ int scratch_for_device(unsigned char** out)
         return MPDP_ERR_CUDA;
     }
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (!resolve_driver_calls()) return MPDP_ERR_CUDA;
+    ScratchAddr& e = g_scratch[dev];
+    const unsigned long long id = current_ctx_id();
+    if (id == 0 || e.ctx_id != id || !e.ptr) {
+        // first call in this context (it becomes current here if none was)
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return MPDP_ERR_CUDA;
         }
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+        const unsigned long long now = current_ctx_id();
+        if (now == 0) return MPDP_ERR_CUDA;
+        e.ctx_id = now;
+        e.ptr = static_cast<unsigned char*>(p);
     }
-    *out = g_scratch_ptr[dev];
+    *out = e.ptr;
     return MPDP_OK;
 }
 

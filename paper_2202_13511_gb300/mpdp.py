@@ -111,6 +111,7 @@ EXPORTS = [
     "mpdp_set_model", "mpdp_edge_features",
     "mpdp_server_default_config", "mpdp_server_create", "mpdp_server_destroy", "mpdp_server_submit",
     "mpdp_server_poll", "mpdp_server_drain", "mpdp_server_pending", "mpdp_server_result",
+    "mpdp_probe_read_gbs",
 ]
 PLAN_STRIDE = 63
 NOALLOC_MAX_RELS = 16
@@ -208,6 +209,8 @@ def load(build_if_missing: bool = True):
     for f in ("mpdp_server_default_config", "mpdp_server_create", "mpdp_server_submit",
               "mpdp_server_poll", "mpdp_server_drain", "mpdp_server_pending", "mpdp_server_result"):
         getattr(L, f).restype = ctypes.c_int
+    L.mpdp_probe_read_gbs.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, P(ctypes.c_double)]
+    L.mpdp_probe_read_gbs.restype = ctypes.c_int
     L.mpdp_memo_lookup.argtypes = [c_ctx, ctypes.c_int64, P(ctypes.c_uint64), ctypes.c_int32,
                                    P(ctypes.c_double), P(ctypes.c_uint64)]
     L.mpdp_last_launch_count.argtypes = [c_ctx]
@@ -800,6 +803,16 @@ def workspace_bytes(n: int, memo_kind: int = MEMO_DENSE) -> int:
     L = load()
     c = ConfigC(memo_kind, 0, 64, 1, 1, 32, FILTER_CONNECTED, 8, 4, 1)
     return int(L.mpdp_workspace_bytes(n, ctypes.byref(c)))
+
+
+def probe_read_gbs(nbytes: int, passes: int, device: int = 0) -> float:
+    """Read bandwidth (GB/s) of one launch reading an nbytes buffer `passes`
+    times: below the L2 size it measures the L2, far above it HBM."""
+    out = ctypes.c_double()
+    rc = load().mpdp_probe_read_gbs(int(device), int(nbytes), int(passes), ctypes.byref(out))
+    if rc != MPDP_OK:
+        raise MPDPError(rc, "mpdp_probe_read_gbs", strerror(rc))
+    return out.value
 
 
 def strerror(code: int) -> str:

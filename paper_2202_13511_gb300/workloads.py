@@ -4,11 +4,11 @@ This module is shared by the CUDA path, the CPU oracle tests and the benchmark.
 It only draws random numbers and lays out graphs; it holds none of the join
 ordering arithmetic (no cardinality products, no costs, no connectivity).
 
-Workload shapes follow the paper's synthetic experiments (Sec. 6.2.1, "Synthetic
+Workload shapes follow the paper's synthetic experiments (Sec. 7.2.1, "Synthetic
 Workload"): star graphs (one fact relation joined by every dimension), snowflake
 graphs (trees of maximum depth 4), cliques, plus chains and cyclic graphs built
 from a random spanning tree with extra edges as stand-ins for the real
-MusicBrainz random-walk queries (Sec. 6.2.2), whose data is not available.
+MusicBrainz random-walk queries (Sec. 7.2.2), whose data is not available.
 
 Values:
   * base cardinality  card[i] = 10 ** U(2, 8)   (log-uniform in [1e2, 1e8])
@@ -218,13 +218,44 @@ def snowflake_plus(n: int, seed: int = 0, extra_frac: float = 0.05) -> Query:
 
 def snowflake_plus_pkfk(n: int, seed: int = 0, extra_frac: float = 0.05) -> Query:
     """The snowflake_plus graph with primary-key / foreign-key joins, the
-    setting of the paper's heuristic experiments (Sec. 6.3): every edge
+    setting of the paper's heuristic experiments (Sec. 7.3): every edge
     joins a foreign key to the other relation's primary key, so its
     selectivity is 1 / card(key side).  A tree edge's key side is the child;
     an extra edge's is the relation with the larger index."""
     q = snowflake_plus(n, seed, extra_frac)
     edges = [(u, v, 1.0 / q.card[v]) for (u, v, _s) in q.edges]
     return Query(n=n, card=q.card, edges=edges, kind="snowflake_plus_pkfk", seed=seed, meta=q.meta)
+
+
+def snowflake_schema_pkfk(n: int, seed: int = 0, extra_frac: float = 0.0) -> Query:
+    """A snowflake schema with primary-key / foreign-key joins: the same tree
+    shapes as snowflake_plus (fanout 1-5, depth uncapped), the fact table
+    (relation 0) the largest, card 10^U(6,8), and every dimension smaller
+    than the table that references it, card(child) = card(parent) *
+    10^-U(0,2) (at least 10).  An edge's selectivity is 1 / card(key side),
+    the child for a tree edge, the larger index for an extra edge."""
+    rng = SplitMix64(seed)
+    pairs, _depth = _random_tree_pairs(rng, n, None, 5)
+    parent = {c: p for p, c in pairs}
+    card = [0.0] * n
+    card[0] = 10.0 ** (6.0 + 2.0 * rng.uniform())
+    for i in range(1, n):
+        card[i] = max(10.0, card[parent[i]] * 10.0 ** -(2.0 * rng.uniform()))
+    have = set((min(a, b), max(a, b)) for a, b in pairs)
+    extra = int(round(extra_frac * n))
+    while extra > 0:
+        a = rng.randint(0, n - 1)
+        b = rng.randint(0, n - 1)
+        if a == b:
+            continue
+        e = (min(a, b), max(a, b))
+        if e in have:
+            continue
+        have.add(e)
+        pairs.append(e)
+        extra -= 1
+    edges = [(u, v, 1.0 / card[v]) for (u, v) in pairs]
+    return Query(n=n, card=card, edges=edges, kind="snowflake_schema_pkfk", seed=seed)
 
 
 def uniform_values(n: int, edges_uv, card: float = 1000.0, sel: float = 0.01,
@@ -243,6 +274,7 @@ GENERATORS = {
     "cyclic": cyclic,
     "snowflake_plus": snowflake_plus,
     "snowflake_plus_pkfk": snowflake_plus_pkfk,
+    "snowflake_schema_pkfk": snowflake_schema_pkfk,
 }
 
 

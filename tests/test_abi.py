@@ -104,3 +104,21 @@ def test_packed_batch_layout():
     assert pb.recs["n_edges"].tolist() == [2, 0, 3]
     assert pb.recs["card"].tolist() == [pb.card.ctypes.data + 8 * o for o in (0, 3, 4)]
     assert pb.recs["edges"].tolist() == [pb.edges.ctypes.data, 0, pb.edges.ctypes.data + 16 * 2]
+
+
+CPU_HEADER = os.path.join(os.path.dirname(HEADER), "mpdp_cpu.h")
+
+
+def test_cpu_baseline_library_exports_its_header():
+    """libmpdp_cpu.so (the multi-threaded CPU MPDP) exports exactly what
+    include/mpdp_cpu.h declares, and its stats struct has the header's size."""
+    from paper_2202_13511_gb300 import cpu_mpdp
+    src = re.sub(r"/\*.*?\*/", "", open(CPU_HEADER).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(mpdp_cpu_[a-z_]+)\s*\(", src)))
+    assert names == ["mpdp_cpu_optimize"]
+    lib = cpu_mpdp.load()
+    for name in names:
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+    assert ctypes.sizeof(cpu_mpdp.CpuStats) == 4 * 8 + 2 * 4 + 8
+    m = re.search(r"#define MPDP_CPU_MAX_RELS (\d+)", open(CPU_HEADER).read())
+    assert m and int(m.group(1)) == cpu_mpdp.MAX_RELS

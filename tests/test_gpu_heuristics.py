@@ -116,7 +116,7 @@ def test_paper_parameters_at_100_relations(opt, mode, k, t):
     ("snowflake_plus_pkfk", 1000, 13, mpdp.MODE_UNIONDP_SIZEFIRST, 25, 15),
 ])
 def test_paper_parameters_at_300_and_1000_relations(opt, kind, n, seed, mode, k, t):
-    """The large-query sizes of the heuristic tables (Sec. 6.3): hundreds of
+    """The large-query sizes of the heuristic tables (Sec. 7.3): hundreds of
     IDP2 rounds and several levels of UnionDP recursion, every plan and
     extended-range cost equal to the oracle's."""
     q = W.make(kind, n, seed)

@@ -115,7 +115,7 @@ def test_dpsub_evaluated_on_stars(n):
 
 
 def test_printed_2805_ratio():
-    """Sec. 2.3 / Sec. 6.2.1 print ~2805x more join pairs evaluated by DPSUB
+    """Sec. 2.3 / Sec. 7.2.1 print ~2805x more join pairs evaluated by DPSUB
     than CCP pairs at 25 relations (star).  With the two closed forms pinned
     above, the ratio is 2(3^24-1) / (24 * 2^23)."""
     g = json.load(open(os.path.join(GOLDEN, "printed_ratios.json")))

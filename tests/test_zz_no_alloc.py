@@ -96,6 +96,31 @@ def test_noalloc_back_to_back_mixed_sizes(opt):
         assert np.array_equal(d_nodes.cpu().numpy(), rn)
 
 
+def test_noalloc_on_a_non_default_stream(opt):
+    """Two calls back to back on one torch.cuda.Stream, given once as the
+    torch object and once as its raw cudaStream_t: ordered on that stream,
+    neither sees the other's entries, and both equal the context path."""
+    qs = [W.cyclic(16, seed=21), W.clique(13, seed=22)]
+    refs, outs = [], []
+    for q in qs:
+        d_card, d_edges = device_query(q)
+        refs.append(run_context(opt, q, d_card, d_edges))
+        outs.append((d_card, d_edges, torch.zeros((2 * q.n - 1) * 40, dtype=torch.uint8, device="cuda"),
+                     torch.zeros(1, dtype=torch.float64, device="cuda"),
+                     torch.full((1,), 99, dtype=torch.int32, device="cuda")))
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())  # inputs written on the current stream
+    for (q, o), stream in zip(zip(qs, outs), (side, side.cuda_stream)):
+        d_card, d_edges, d_nodes, d_cost, d_status = o
+        mpdp.optimize_device_noalloc(q.n, len(q.edges), d_card, d_edges, d_nodes, d_cost, d_status,
+                                     stream=stream)
+    side.synchronize()
+    for (rs, rc, rn), (_, _, d_nodes, d_cost, d_status) in zip(refs, outs):
+        assert int(d_status.item()) == rs == 0
+        assert d_cost.cpu().numpy().tobytes() == rc
+        assert np.array_equal(d_nodes.cpu().numpy(), rn)
+
+
 def test_noalloc_rejects_sizes_beyond_the_maximum():
     q = W.chain(mpdp.NOALLOC_MAX_RELS + 1, seed=0)
     d_card, d_edges = device_query(q)
