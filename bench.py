@@ -921,12 +921,45 @@ def heuristic_line(opt, mpdp, W):
     return out
 
 
+PERSIST_SLOTS = 32
+OFFLINE_BATCH = 64
+
+
+def _poisson(srv, queries, sat, fracs, seed):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = {}
+    for frac in fracs:
+        arrivals = np.cumsum(rng.exponential(1.0 / (frac * sat), size=len(queries)))
+        _, lat, makespan = srv.replay(queries, arrivals)
+        out[f"poisson_{int(round(frac * 100))}"] = {
+            "offered_queries_per_s": frac * sat, "queries_per_s": len(queries) / makespan,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3)}
+    return out
+
+
+def _saturated(srv, queries):
+    import numpy as np
+    srv.replay(queries, [0.0] * len(queries))  # warm-up
+    _, lat, makespan = srv.replay(queries, [0.0] * len(queries))
+    return {"queries_per_s": len(queries) / makespan, "makespan_s": makespan,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+
+
 def serving_line(mpdp, W):
     """Batched/served form: 2,000 mixed queries (star / snowflake / cyclic,
-    8-25 relations, weight 3 on 12-18) through the native serving loop,
-    first all at once (saturated throughput), then as Poisson arrivals at
-    50 / 80 / 95 % of it.  Kernel knobs and the server's slots / batch cap
-    come from the autotuner, run on samples of the same mix."""
+    8-25 relations, weight 3 on 12-18) through the native serving loop in
+    its two forms: device batches per slot (kernel knobs and the server's
+    slots / batch cap from the autotuner, run on samples of the same mix),
+    and one persistent kernel over PERSIST_SLOTS query slots that takes
+    requests while it runs.  Each is timed all at once (saturated
+    throughput), then as Poisson arrivals at 50 / 80 / 95 % of its own
+    saturated rate; the persistent form also at the batch form's offered
+    rates.  Beside them: the same stream as plain device batches of
+    OFFLINE_BATCH queries through one context (a fixed offline comparator),
+    and single-query latency through the persistent server."""
+    import time
     import numpy as np
     from paper_2202_13511_gb300 import autotune
     queries = W.mixed_stream(SERVE_QUERIES, seed=0)
@@ -939,27 +972,44 @@ def serving_line(mpdp, W):
            "autotuned": {"kernel": kernel, "server": server_cfg,
                          "configs_timed": len(khist) + len(shist), "tuning_s": round(tune_s, 2)}}
     with mpdp.Server(0, slots=server_cfg["slots"], max_batch=server_cfg["max_batch"], **kernel) as srv:
-        srv.replay(queries, [0.0] * len(queries))  # warm-up
-        _, lat, makespan = srv.replay(queries, [0.0] * len(queries))
-        sat = len(queries) / makespan
-        out["saturated"] = {"queries_per_s": sat, "makespan_s": makespan,
-                            "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                            "p99_ms": float(np.percentile(lat, 99) * 1e3)}
-        rng = np.random.default_rng(1)
-        for frac in (0.5, 0.8, 0.95):
-            arrivals = np.cumsum(rng.exponential(1.0 / (frac * sat), size=len(queries)))
-            _, lat, makespan = srv.replay(queries, arrivals)
-            out[f"poisson_{int(frac * 100)}"] = {
-                "offered_queries_per_s": frac * sat, "queries_per_s": len(queries) / makespan,
-                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "mean_ms": float(lat.mean() * 1e3)}
-    # The same stream as plain device batches of max_batch queries through one
-    # context (tuned kernel knobs, no CUDA graphs since shapes vary): what the
-    # GPU sustains on this mix without the serving loop's scheduling.
+        sat = _saturated(srv, queries)
+        out["saturated"] = sat
+        out.update(_poisson(srv, queries, sat["queries_per_s"], (0.5, 0.8, 0.95), seed=1))
+    batch_sat = sat["queries_per_s"]
+    # persistent kernel over query slots (dense memo, tree levels' work split
+    # from the tuned kernel knobs)
+    pk = {k: v for k, v in kernel.items() if k in ("heavy_threshold", "use_ccc", "group_threads_log2")}
+    with mpdp.Server(0, slots=PERSIST_SLOTS, persistent=True, **pk) as srv:
+        psat = _saturated(srv, queries)
+        pers = {"slots": PERSIST_SLOTS, "max_relations": 25, "kernel": pk, "saturated": psat}
+        pers.update(_poisson(srv, queries, psat["queries_per_s"], (0.5, 0.8, 0.95), seed=1))
+        at_batch = _poisson(srv, queries, batch_sat, (0.5, 0.8), seed=1)
+        pers["at_batch_server_rates"] = {k.replace("poisson", "batch_rate"): v for k, v in at_batch.items()}
+        # one query at a time: submit, wait, result (host wall time)
+        lat = {}
+        for name, kind, n in (("star10", "star", 10), ("snowflake25", "snowflake", 25)):
+            q = W.make(kind, n, seed=0)
+            for _ in range(5):
+                t = srv.submit(q)
+                srv.drain()
+                srv.result(t)
+            ts = []
+            for _ in range(50):
+                t1 = time.perf_counter()
+                t = srv.submit(q)
+                while not srv.poll():
+                    pass
+                ts.append(time.perf_counter() - t1)
+                srv.result(t)
+            lat[name] = {"p50_ms": float(np.percentile(ts, 50) * 1e3), "p99_ms": float(np.percentile(ts, 99) * 1e3)}
+        pers["single_query_latency"] = lat
+    out["persistent"] = pers
+    # The same stream as plain device batches of OFFLINE_BATCH queries
+    # through one context (tuned kernel knobs, no CUDA graphs since shapes
+    # vary): what the GPU sustains on this mix without a serving loop.
     with mpdp.Optimizer(0, **kernel) as o:
         o.set_config(use_graphs=0)
-        mb = server_cfg["max_batch"]
-        chunks = [queries[i:i + mb] for i in range(0, len(queries), mb)]
+        chunks = [queries[i:i + OFFLINE_BATCH] for i in range(0, len(queries), OFFLINE_BATCH)]
         for c in chunks:
             o.optimize_batch(c)  # warm-up: workspace, streams
         t0 = time.perf_counter()
@@ -967,8 +1017,10 @@ def serving_line(mpdp, W):
         for h in pending:
             o.collect(h)
         batch_s = time.perf_counter() - t0
-    out["offline_batches"] = {"queries_per_s": len(queries) / batch_s, "batch": mb,
-                              "serving_over_offline": sat / (len(queries) / batch_s)}
+    offline = len(queries) / batch_s
+    out["offline_batches"] = {"queries_per_s": offline, "batch": OFFLINE_BATCH,
+                              "serving_over_offline": batch_sat / offline,
+                              "persistent_over_offline": psat["queries_per_s"] / offline}
     return out
 
 

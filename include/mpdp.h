@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define MPDP_ABI_VERSION 5
+#define MPDP_ABI_VERSION 6
 /* Exact mode uses 32-bit relation bitmaps; memory grows as 2^n (see
  * mpdp_workspace_bytes), so n is further capped by the memo budget. */
 #define MPDP_MAX_EXACT_RELS 30
@@ -426,7 +426,19 @@ int32_t mpdp_abi_version(void);
  * by memo memory).  Batches of different slots run concurrently on the GPU.
  * A request's plan is bit-identical to the same query optimized alone.
  * Progress happens inside submit / poll / drain; the library runs no
- * background thread.  A server is used by one host thread at a time. */
+ * background thread.  A server is used by one host thread at a time.
+ *
+ * Persistent mode (persistent = 1): one resident kernel serves every request.
+ * `slots` is then the number of query slots (1..1024), each holding one
+ * query of up to the relations its slot_budget_bytes of workspace allows
+ * (0: 25 relations; larger requests get MPDP_ERR_ADMISSION); max_batch is
+ * not used.  A request goes to the device as soon as a slot is free, through
+ * a ring in pinned, device-mapped memory that the running kernel polls; the
+ * kernel advances every slot through ingest, filter, each DP level and the
+ * plan fetch on its own, so requests that arrive while others are on the
+ * GPU start at once and their levels overlap.  The kernel ends itself after
+ * about 20 ms without work and is started again by the next submit or poll.
+ * Needs the dense memo and the CONNECTED or BITMAPS filter. */
 typedef struct mpdp_server mpdp_server; /* opaque, owned by the library */
 
 typedef struct {
@@ -436,6 +448,9 @@ typedef struct {
     mpdp_config kernel;           /* kernel configuration of every slot (default:
                                      context defaults with use_graphs = 0, since
                                      mixed batches rarely repeat a shape) */
+    int32_t persistent;           /* 0 (default): device batches per slot; 1: one
+                                     persistent kernel over query slots */
+    int32_t pad;
 } mpdp_server_config;
 
 /* Fill *cfg with the defaults. */

@@ -22,7 +22,10 @@ LIB_PATH = os.path.join(OUT_DIR, "libmpdp.so")
 CPU_SOURCE = "mpdp_cpu.c"
 CPU_LIB_PATH = os.path.join(OUT_DIR, "libmpdp_cpu.so")
 SOURCES = ["mpdp_kernels.cu", "mpdp_api.cu", "mpdp_noalloc.cu", "mpdp_server.cu", "mpdp_xd.cu",
-           "mpdp_heuristic.cu", "mpdp_mlp.cu", "mpdp_probe.cu"]
+           "mpdp_heuristic.cu", "mpdp_mlp.cu", "mpdp_probe.cu", "mpdp_persist.cu"]
+# per-file extra flags: the persistent serving kernel reads memory that other
+# blocks of the same launch wrote, so its plain global loads skip the L1
+EXTRA_FLAGS = {"mpdp_persist.cu": ["-Xptxas", "-dlcm=cg"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fno-fast-math", "-I", os.path.join(ROOT, "include")]
@@ -74,7 +77,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *EXTRA_FLAGS.get(src, []), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -10,6 +10,20 @@
 
 #include "../../include/mpdp.h"
 
+// Loads of data that stays unchanged for a whole launch go through the
+// read-only path (MPDP_LDG) and pointers to it are restrict-qualified.  A
+// kernel that writes and reads the same memory across its own lifetime (the
+// persistent serving kernel) defines MPDP_COHERENT_LOADS before including
+// this header: its read-only loads then go to the L2 (ld.global.cg), which
+// every SM sees coherently, and no pointer is marked restrict.
+#ifdef MPDP_COHERENT_LOADS
+#define MPDP_LDG(p) __ldcg(p)
+#define MPDP_RESTRICT
+#else
+#define MPDP_LDG(p) __ldg(p)
+#define MPDP_RESTRICT __restrict__
+#endif
+
 namespace mpdp {
 
 constexpr int kMaxRels = 32;        // bitmap width
@@ -209,7 +223,7 @@ __device__ __forceinline__ int lowest(uint32_t s) { return __ffs(s) - 1; }
 // grow(source, restriction) of Sec. 3.2.1: every vertex of the restriction
 // reachable from the source.  The loop pops one frontier vertex per step.
 __device__ __forceinline__ uint32_t grow(uint32_t source, uint32_t restriction,
-                                         const uint32_t* __restrict__ adj)
+                                         const uint32_t* MPDP_RESTRICT adj)
 {
     uint32_t seen = source, frontier = source;
     while (frontier) {
@@ -223,7 +237,7 @@ __device__ __forceinline__ uint32_t grow(uint32_t source, uint32_t restriction,
 }
 
 // connected(S): grow from the lowest member of S inside S reaches all of S.
-__device__ __forceinline__ bool connected(uint32_t s, const uint32_t* __restrict__ adj)
+__device__ __forceinline__ bool connected(uint32_t s, const uint32_t* MPDP_RESTRICT adj)
 {
     uint32_t seen = s & (0u - s), frontier = seen;
     while (frontier) {
@@ -243,14 +257,14 @@ __device__ __forceinline__ const uint32_t* conn_bitmap(const BatchArgs& a, int q
 
 // G[X] connected, for a non-empty X: one bit of the connectivity bitmap,
 // a single relation at once, or (no bitmap) the search from min(X).
-__device__ __forceinline__ bool conn_of(uint32_t x, const uint32_t* __restrict__ cw, const uint32_t* __restrict__ adj)
+__device__ __forceinline__ bool conn_of(uint32_t x, const uint32_t* MPDP_RESTRICT cw, const uint32_t* MPDP_RESTRICT adj)
 {
     if ((x & (x - 1u)) == 0u) return true;
-    return cw ? ((__ldg(&cw[x >> 5]) >> (x & 31u)) & 1u) != 0u : connected(x, adj);
+    return cw ? ((MPDP_LDG(&cw[x >> 5]) >> (x & 31u)) & 1u) != 0u : connected(x, adj);
 }
 
 // Neighbourhood N(S) (every relation adjacent to a member of S) by byte tables.
-__device__ __forceinline__ uint32_t nbhd(uint32_t s, const uint32_t (*__restrict__ t)[256])
+__device__ __forceinline__ uint32_t nbhd(uint32_t s, const uint32_t (*MPDP_RESTRICT t)[256])
 {
     return t[0][s & 255u] | t[1][(s >> 8) & 255u] | t[2][(s >> 16) & 255u] | t[3][s >> 24];
 }
@@ -258,7 +272,7 @@ __device__ __forceinline__ uint32_t nbhd(uint32_t s, const uint32_t (*__restrict
 // connected(S) by whole-frontier rounds, for S (|S| >= 2) with no isolated
 // vertex in G[S]: grow from min(S) one BFS layer per round until S is
 // reached or growth stops.
-__device__ __forceinline__ bool connected_rounds_from(uint32_t s, const uint32_t (*__restrict__ t)[256],
+__device__ __forceinline__ bool connected_rounds_from(uint32_t s, const uint32_t (*MPDP_RESTRICT t)[256],
                                                       uint32_t& rounds)
 {
     uint32_t seen = s & (0u - s);
@@ -273,7 +287,7 @@ __device__ __forceinline__ bool connected_rounds_from(uint32_t s, const uint32_t
 
 // connected(S) for |S| >= 2: first reject S when a member has no neighbour
 // inside S (an isolated vertex of G[S]), then BFS rounds.
-__device__ __forceinline__ bool connected_rounds(uint32_t s, const uint32_t (*__restrict__ t)[256],
+__device__ __forceinline__ bool connected_rounds(uint32_t s, const uint32_t (*MPDP_RESTRICT t)[256],
                                                  uint32_t& rounds)
 {
     if (s & ~nbhd(s, t)) return false;
@@ -307,7 +321,7 @@ __device__ __forceinline__ int highest(uint32_t s) { return 31 - __clz(s); }
 
 // Peel vertex of a connected S (|S| >= 2) whose G[S] is a tree: its highest
 // leaf (a vertex of degree 1 in G[S]), i.e. its highest non-cut vertex.
-__device__ __forceinline__ int tree_peel_vertex(uint32_t s, const uint32_t* __restrict__ adj)
+__device__ __forceinline__ int tree_peel_vertex(uint32_t s, const uint32_t* MPDP_RESTRICT adj)
 {
     uint32_t t = s;
     while (t) {
@@ -398,8 +412,8 @@ struct DenseMemo {
         left = left0 + b;
         shift = (a.query[q].use_connected && a.desc[q].enumeration == MPDP_ENUM_TREE) ? 32 - a.desc[q].n : -1;
     }
-    __device__ __forceinline__ double get_cost(uint32_t s, DevCounters*) const { return __ldg(&cc[at(s)].x); }
-    __device__ __forceinline__ double get_card(uint32_t s, DevCounters*) const { return __ldg(&cc[at(s)].y); }
+    __device__ __forceinline__ double get_cost(uint32_t s, DevCounters*) const { return MPDP_LDG(&cc[at(s)].x); }
+    __device__ __forceinline__ double get_card(uint32_t s, DevCounters*) const { return MPDP_LDG(&cc[at(s)].y); }
     __device__ __forceinline__ void get(uint32_t s, double& c, double& cd, uint32_t& l, DevCounters*) const
     {
         const uint32_t i = at(s);
@@ -433,8 +447,8 @@ struct DensePlainMemo {
         cc = cc0 + b;
         left = left0 + b;
     }
-    __device__ __forceinline__ double get_cost(uint32_t s, DevCounters*) const { return __ldg(&cc[s].x); }
-    __device__ __forceinline__ double get_card(uint32_t s, DevCounters*) const { return __ldg(&cc[s].y); }
+    __device__ __forceinline__ double get_cost(uint32_t s, DevCounters*) const { return MPDP_LDG(&cc[s].x); }
+    __device__ __forceinline__ double get_card(uint32_t s, DevCounters*) const { return MPDP_LDG(&cc[s].y); }
     __device__ __forceinline__ void get(uint32_t s, double& c, double& cd, uint32_t& l, DevCounters*) const
     {
         const double2 v = cc[s];
@@ -462,11 +476,11 @@ struct HashMemo {
     __device__ __forceinline__ const HashSlot* find(uint32_t s, DevCounters* cnt) const
     {
         const int lvl = __popc(s);
-        const HashSlot* t = arena + __ldg(&lay->base[lvl]);
-        const uint32_t m = __ldg(&lay->mask[lvl]);
+        const HashSlot* t = arena + MPDP_LDG(&lay->base[lvl]);
+        const uint32_t m = MPDP_LDG(&lay->mask[lvl]);
         uint32_t h = fmix32(s) & m;
         for (uint32_t i = 0; i <= m; i++) {
-            const uint32_t key = __ldg(&t[h].key);
+            const uint32_t key = MPDP_LDG(&t[h].key);
             if (key == s) return t + h;
             if (key == 0u) break;
             h = (h + 1u) & m;
@@ -477,12 +491,12 @@ struct HashMemo {
     __device__ __forceinline__ double get_cost(uint32_t s, DevCounters* cnt) const
     {
         const HashSlot* e = find(s, cnt);
-        return e ? __ldg(&e->cost) : __longlong_as_double(0x7ff8000000000000ll);
+        return e ? MPDP_LDG(&e->cost) : __longlong_as_double(0x7ff8000000000000ll);
     }
     __device__ __forceinline__ double get_card(uint32_t s, DevCounters* cnt) const
     {
         const HashSlot* e = find(s, cnt);
-        return e ? __ldg(&e->card) : __longlong_as_double(0x7ff8000000000000ll);
+        return e ? MPDP_LDG(&e->card) : __longlong_as_double(0x7ff8000000000000ll);
     }
     __device__ __forceinline__ void get(uint32_t s, double& c, double& card, uint32_t& l, DevCounters* cnt) const
     {
@@ -499,8 +513,8 @@ struct HashMemo {
     __device__ __forceinline__ void put(uint32_t s, int lvl, double c, double card, uint32_t l,
                                         DevCounters* cnt)
     {
-        HashSlot* t = arena + __ldg(&lay->base[lvl]);
-        const uint32_t m = __ldg(&lay->mask[lvl]);
+        HashSlot* t = arena + MPDP_LDG(&lay->base[lvl]);
+        const uint32_t m = MPDP_LDG(&lay->mask[lvl]);
         uint32_t h = fmix32(s) & m;
         for (uint32_t i = 0; i <= m; i++) {
             if (atomicCAS(&t[h].key, 0u, s) == 0u) {
@@ -602,8 +616,8 @@ constexpr unsigned long long kNoX = 0xffffffffffffffffull;
 // for that block's only pair).  A bridge is a tree edge (x, par[x]) and its
 // removal cuts off exactly x's subtree, computed for every x bottom-up over
 // the discovery order.  Other blocks get side[j] = 0.
-__device__ __forceinline__ int find_blocks(uint32_t s, const uint32_t* __restrict__ adj,
-                                           uint32_t* __restrict__ blk, uint32_t* __restrict__ side = nullptr)
+__device__ __forceinline__ int find_blocks(uint32_t s, const uint32_t* MPDP_RESTRICT adj,
+                                           uint32_t* MPDP_RESTRICT blk, uint32_t* MPDP_RESTRICT side = nullptr)
 {
     uint8_t par[kMaxRels];
     uint32_t anc[kMaxRels];
@@ -691,7 +705,7 @@ __device__ __forceinline__ int find_blocks(uint32_t s, const uint32_t* __restric
 }
 
 // Every pair of B's vertices adjacent (then every bipartition of B is a CCP).
-__device__ __forceinline__ bool is_clique(uint32_t b, const uint32_t* __restrict__ adj)
+__device__ __forceinline__ bool is_clique(uint32_t b, const uint32_t* MPDP_RESTRICT adj)
 {
     uint32_t t = b;
     while (t) {
@@ -704,7 +718,7 @@ __device__ __forceinline__ bool is_clique(uint32_t b, const uint32_t* __restrict
 
 // S_l of a CCP (lb, rb) of a block of S: grow(lb, S \ rb), which is lb
 // itself when the block is all of S.
-__device__ __forceinline__ uint32_t left_side(uint32_t s, uint32_t lb, uint32_t rb, const uint32_t* __restrict__ adj)
+__device__ __forceinline__ uint32_t left_side(uint32_t s, uint32_t lb, uint32_t rb, const uint32_t* MPDP_RESTRICT adj)
 {
     return (lb | rb) == s ? lb : grow(lb, s & ~rb, adj);
 }

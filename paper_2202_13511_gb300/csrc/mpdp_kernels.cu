@@ -6,6 +6,12 @@
 // block-per-set launch in block mode) -> plan fetch (block per query).
 // Level k's launch only reads memo entries of levels < k, so launches are the
 // level barrier of the DP (Sec. 2.1.1; Sec. 5, Algorithm "MPDP on GPU").
+//
+// Every kernel's work is a device function over an explicit block index and
+// block count (`bid`, `nblk`); the __global__ wrappers pass blockIdx and
+// gridDim.  A file that defines MPDP_PHASES_ONLY before including this one
+// gets those device functions alone (the persistent serving kernel runs them
+// tile by tile).
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -72,7 +78,7 @@ __device__ __forceinline__ int find_q(const uint32_t* s_pref, int nq, uint32_t t
     return lo;
 }
 
-__device__ __forceinline__ void load_query(SharedQuery& sq, const DevQuery* __restrict__ q)
+__device__ __forceinline__ void load_query(SharedQuery& sq, const DevQuery* MPDP_RESTRICT q)
 {
     const int nsel = 2 * q->n_edges;
     for (int i = threadIdx.x; i < nsel; i += blockDim.x) sq.nsel[i] = q->nsel[i];
@@ -86,7 +92,8 @@ __device__ __forceinline__ void load_query(SharedQuery& sq, const DevQuery* __re
 
 // ---------------------------------------------------------------------------
 // Device-path staging: gather each query from the caller's device buffers.
-__global__ void k_stage(BatchArgs a, const double* __restrict__ card, const mpdp_edge* __restrict__ edges)
+#ifndef MPDP_PHASES_ONLY
+__global__ void k_stage(BatchArgs a, const double* MPDP_RESTRICT card, const mpdp_edge* MPDP_RESTRICT edges)
 {
     const int q = blockIdx.x;
     const QDesc& d = a.desc[q];
@@ -100,10 +107,12 @@ __global__ void k_stage(BatchArgs a, const double* __restrict__ card, const mpdp
     for (int i = threadIdx.x; i < n && i < kMaxRels; i += blockDim.x) st->card[i] = card[d.card_off + i];
     for (int e = threadIdx.x; e < m && e < kMaxEdges; e += blockDim.x) st->edges[e] = edges[d.edge_off + e];
 }
+#endif
 
 // Device-path outputs: plan, cost and status of each query to caller buffers.
-__global__ void k_publish(BatchArgs a, mpdp_plan_node* __restrict__ nodes, double* __restrict__ cost,
-                          int32_t* __restrict__ status)
+#ifndef MPDP_PHASES_ONLY
+__global__ void k_publish(BatchArgs a, mpdp_plan_node* MPDP_RESTRICT nodes, double* MPDP_RESTRICT cost,
+                          int32_t* MPDP_RESTRICT status)
 {
     const int q = blockIdx.x;
     const DevResult& r = a.out[q].result;
@@ -114,6 +123,7 @@ __global__ void k_publish(BatchArgs a, mpdp_plan_node* __restrict__ nodes, doubl
         status[q] = a.out[q].counters.status;
     }
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // a0: ingest (block per query).  Validates the staged query, builds the
@@ -121,12 +131,12 @@ __global__ void k_publish(BatchArgs a, mpdp_plan_node* __restrict__ nodes, doubl
 // the byte neighbourhood tables, checks that the join graph is connected and
 // zeroes the counters.  The dense memo's base entries cost({R_i}) = 0 are
 // written here (Algorithm "MPDP on GPU", memo fill).
-__global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
+static __device__ void ingest_body(const BatchArgs& a, int dense, uint32_t bid, uint32_t nblk)
 {
-    const int qi = blockIdx.x, tid = threadIdx.x;
-    const StagedQuery* __restrict__ st = a.staged + qi;
-    DevQuery* __restrict__ q = a.query + qi;
-    DevCounters* __restrict__ cnt = &a.out[qi].counters;
+    const int qi = bid, tid = threadIdx.x;
+    const StagedQuery* MPDP_RESTRICT st = a.staged + qi;
+    DevQuery* MPDP_RESTRICT q = a.query + qi;
+    DevCounters* MPDP_RESTRICT cnt = &a.out[qi].counters;
     int* cw = reinterpret_cast<int*>(cnt);
     for (int i = tid; i < (int)(sizeof(DevCounters) / sizeof(int)); i += blockDim.x) cw[i] = 0;
     __shared__ int s_status;
@@ -320,6 +330,13 @@ __global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
     }
 }
 
+#ifndef MPDP_PHASES_ONLY
+__global__ void __launch_bounds__(256) k_ingest(BatchArgs a, int dense)
+{
+    ingest_body(a, dense, blockIdx.x, gridDim.x);
+}
+#endif
+
 // ---------------------------------------------------------------------------
 // Binomial coefficients C(i, j), i, j <= 32, built at compile time by
 // Pascal's rule (C(32, 16) < 2^32, so every entry fits 32 bits).
@@ -336,13 +353,13 @@ constexpr BinomTable make_binom_table()
     return t;
 }
 
-__device__ const BinomTable kBinom = make_binom_table();
+static __device__ const BinomTable kBinom = make_binom_table();
 
 // Combinatorial number system (colex order): the k-subset of {0..n-1} with
 // rank r is {c_k > ... > c_1} where r = sum_i C(c_i, i); each c_i is the
 // largest value with C(c_i, i) <= what remains of r.
 __device__ __forceinline__ uint32_t unrank_colex(uint32_t r, int k, int n,
-                                                 const uint32_t* __restrict__ binom)
+                                                 const uint32_t* MPDP_RESTRICT binom)
 {
     uint32_t s = 0u;
     int c = n - 1;
@@ -373,6 +390,7 @@ __device__ __forceinline__ uint32_t next_colex(uint32_t s)
 // lane's connected sets, one atomic per warp reserves room in the level's
 // list, and pass 2 replays the run writing the kept sets: each warp's output
 // is a colex-ordered slice.
+#ifndef MPDP_PHASES_ONLY
 __global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
 {
     __shared__ uint32_t s_binom[33 * 33];
@@ -387,8 +405,8 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
     }
     const int qi = lo;
     const QDesc& d = a.desc[qi];
-    const DevQuery* __restrict__ q = a.query + qi;
-    DevCounters* __restrict__ cnt = &a.out[qi].counters;
+    const DevQuery* MPDP_RESTRICT q = a.query + qi;
+    DevCounters* MPDP_RESTRICT cnt = &a.out[qi].counters;
     for (int t = threadIdx.x; t < 33 * 33; t += blockDim.x) s_binom[t] = kBinom.v[t];
     for (int t = threadIdx.x; t < 4 * 256; t += blockDim.x) {
         s_nbt[t >> 8][t & 255] = q->nbt[t >> 8][t & 255];
@@ -475,6 +493,7 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
         atomicAdd(&cnt->filter_steps, (unsigned long long)rounds);
     }
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // a2 + a3 for tree join graphs (filter mode CONNECTED): the connected sets
@@ -485,30 +504,30 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(BatchArgs a)
 // or out, ascending), then every other child c in ascending order with digit
 // d = x mod (1 + nsub[c]), x /= 1 + nsub[c]; d = 0 leaves c's subtree out,
 // d > 0 takes c's connected set of rank d - 1, decoded the same way.
-__device__ __forceinline__ uint32_t unrank_connected(const DevQuery* __restrict__ q, int v, uint32_t x)
+__device__ __forceinline__ uint32_t unrank_connected(const DevQuery* MPDP_RESTRICT q, int v, uint32_t x)
 {
     uint8_t st_v[kMaxRels];
     uint32_t st_x[kMaxRels];
     int sp = 1;
     st_v[0] = (uint8_t)v;
     st_x[0] = x;
-    const uint32_t leaves = __ldg(&q->leaves);
+    const uint32_t leaves = MPDP_LDG(&q->leaves);
     uint32_t s = 0u;
     while (sp > 0) {
         --sp;
         const int u = st_v[sp];
         uint32_t r = st_x[sp];
         s |= 1u << u;
-        const uint32_t ch = __ldg(&q->chmask[u]);
+        const uint32_t ch = MPDP_LDG(&q->chmask[u]);
         for (uint32_t c = ch & leaves; c; c &= c - 1u) {
             if (r & 1u) s |= c & (0u - c);
             r >>= 1;
         }
         for (uint32_t c = ch & ~leaves; c; c &= c - 1u) {
             const int w = lowest(c);
-            const uint32_t radix = __ldg(&q->nsub[w]) + 1u;
-            const uint32_t t = __umulhi(r, __ldg(&q->dmag[w]));
-            const uint32_t sh = __ldg(&q->dsh[w]);
+            const uint32_t radix = MPDP_LDG(&q->nsub[w]) + 1u;
+            const uint32_t t = __umulhi(r, MPDP_LDG(&q->dmag[w]));
+            const uint32_t sh = MPDP_LDG(&q->dsh[w]);
             const uint32_t quo = (t + ((r - t) >> (sh & 1u))) >> (sh >> 1);
             const uint32_t dgt = r - quo * radix;
             r = quo;
@@ -540,7 +559,7 @@ __device__ __forceinline__ uint32_t connected_items(const BatchArgs& a, int q)
 // item * kConnPerItem + j * blockDim + t.  Places within the block come from
 // shared-memory counters per level, and one global atomic per level present
 // reserves the block's room in that level's list.
-__global__ void __launch_bounds__(kFilterThreads) k_filter_connected(BatchArgs a)
+static __device__ void filter_connected_body(const BatchArgs& a, uint32_t bid, uint32_t nblk)
 {
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     __shared__ uint32_t s_cnt[kLevels];
@@ -549,7 +568,7 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter_connected(BatchArgs a
     const int tid = threadIdx.x;
     int cur = -1;
     unsigned long long formed = 0;  // threads tid < kLevels: sets of level tid formed for query cur
-    for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
+    for (uint32_t it = bid; it < items; it += nblk) {
         const int qi = find_q(s_pref, a.nq, it);  // block-uniform
         if (qi != cur) {
             if (cur >= 0 && tid < kLevels && formed) atomicAdd(&a.out[cur].counters.unranked, formed);
@@ -558,9 +577,9 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter_connected(BatchArgs a
         }
         if (tid < kLevels) s_cnt[tid] = 0u;
         __syncthreads();
-        const DevQuery* __restrict__ q = a.query + qi;
+        const DevQuery* MPDP_RESTRICT q = a.query + qi;
         const int n = q->n;
-        const uint32_t total = __ldg(&q->top_pref[n]);
+        const uint32_t total = MPDP_LDG(&q->top_pref[n]);
         const uint32_t r0 = (it - s_pref[qi]) * kConnPerItem + (uint32_t)tid;
         uint32_t sv[kConnPerThread], off[kConnPerThread];
 #pragma unroll 1
@@ -571,10 +590,10 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter_connected(BatchArgs a
                 int lo = 0, hi = n - 1;  // largest v with top_pref[v] <= r
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (__ldg(&q->top_pref[mid]) <= r) lo = mid;
+                    if (MPDP_LDG(&q->top_pref[mid]) <= r) lo = mid;
                     else hi = mid - 1;
                 }
-                s = unrank_connected(q, lo, r - __ldg(&q->top_pref[lo]));
+                s = unrank_connected(q, lo, r - MPDP_LDG(&q->top_pref[lo]));
             }
             sv[j] = s;
             const int lv = __popc(s);
@@ -596,6 +615,13 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter_connected(BatchArgs a
     }
     if (cur >= 0 && tid < kLevels && formed) atomicAdd(&a.out[cur].counters.unranked, formed);
 }
+
+#ifndef MPDP_PHASES_ONLY
+__global__ void __launch_bounds__(kFilterThreads) k_filter_connected(BatchArgs a)
+{
+    filter_connected_body(a, blockIdx.x, gridDim.x);
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // a2 + a3, bitmap form: every bitmap S < 2^n of every query is tested, in
@@ -625,7 +651,7 @@ constexpr PopcMasks make_popc_masks()
     return m;
 }
 
-__device__ const PopcMasks kPopcMask = make_popc_masks();
+static __device__ const PopcMasks kPopcMask = make_popc_masks();
 
 // Items of kBitmapsPerBlock bitmaps of a query the bitmap sweep serves: all
 // queries but the trees whose connected sets are unranked directly.
@@ -651,7 +677,7 @@ __device__ __forceinline__ void flush_filter_counts(DevCounters* cnt, uint32_t& 
     rounds = 0u;
 }
 
-__global__ void __launch_bounds__(kFilterThreads, 6) k_filter_bitmaps(BatchArgs a)
+static __device__ void filter_bitmaps_body(const BatchArgs& a, uint32_t bid, uint32_t nblk)
 {
     __shared__ uint32_t s_nbt[4][256];
     __shared__ uint32_t s_ctt[4][256];
@@ -668,12 +694,12 @@ __global__ void __launch_bounds__(kFilterThreads, 6) k_filter_bitmaps(BatchArgs 
     bool is_tree = false;
     unsigned long long limit = 0;
     uint32_t rounds = 0u, examined = 0u;
-    for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
+    for (uint32_t it = bid; it < items; it += nblk) {
         const int qi = find_q(s_pref, a.nq, it);  // block-uniform
         if (qi != cur) {
             if (cur >= 0) flush_filter_counts(cnt, examined, rounds);
             __syncthreads();  // every warp is done with the previous tables
-            const DevQuery* __restrict__ q = a.query + qi;
+            const DevQuery* MPDP_RESTRICT q = a.query + qi;
             d = a.desc + qi;
             cnt = &a.out[qi].counters;
             is_tree = q->is_tree != 0;
@@ -843,9 +869,17 @@ __global__ void __launch_bounds__(kFilterThreads, 6) k_filter_bitmaps(BatchArgs 
     if (cur >= 0) flush_filter_counts(cnt, examined, rounds);
 }
 
+#ifndef MPDP_PHASES_ONLY
+__global__ void __launch_bounds__(kFilterThreads, 6) k_filter_bitmaps(BatchArgs a)
+{
+    filter_bitmaps_body(a, blockIdx.x, gridDim.x);
+}
+#endif
+
 // ---------------------------------------------------------------------------
 // Hash memo layout: per query and level k, capacity = the power of two >= 2x
 // the level's connected count (at least 16), carved from one arena.
+#ifndef MPDP_PHASES_ONLY
 __global__ void k_hash_layout(BatchArgs a)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -873,7 +907,9 @@ __global__ void k_hash_layout(BatchArgs a)
         if (base > a.arena_slots) raise_status(cnt, MPDP_ERR_OOM);
     }
 }
+#endif
 
+#ifndef MPDP_PHASES_ONLY
 __global__ void __launch_bounds__(256) k_hash_clear(BatchArgs a)
 {
     const unsigned long long total = a.layout[a.nq - 1].total_slots;
@@ -883,6 +919,7 @@ __global__ void __launch_bounds__(256) k_hash_clear(BatchArgs a)
          i += (unsigned long long)gridDim.x * blockDim.x)
         reinterpret_cast<double4_32a*>(a.arena)[i] = z;
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // Tiles of kEvalThreads sets of one query at level k for queries in mode `mode`.
@@ -902,11 +939,11 @@ __device__ __forceinline__ uint32_t level_tiles(const BatchArgs& a, int q, int k
 // recomputing it from the queries' counters.  A tree level evaluated by
 // groups of lanes (see group_size) gets a set prefix instead.
 // Top of a connected set in a tree query: the member whose descendants cover it.
-__device__ __forceinline__ int set_top_of(const DevQuery* __restrict__ q, uint32_t s)
+__device__ __forceinline__ int set_top_of(const DevQuery* MPDP_RESTRICT q, uint32_t s)
 {
     uint32_t t = s;
     int top = lowest(t);
-    while ((__ldg(&q->desc[top]) & s) != s) {
+    while ((MPDP_LDG(&q->desc[top]) & s) != s) {
         t &= t - 1u;
         top = lowest(t);
     }
@@ -928,7 +965,8 @@ __device__ __forceinline__ uint32_t group_size(uint32_t sets, int k, uint32_t li
     return (unsigned long long)sets * g <= limit ? g : 1u;
 }
 
-__global__ void __launch_bounds__(256) k_level_prefix(BatchArgs a, uint32_t* __restrict__ pref, uint32_t group_threads)
+#ifndef MPDP_PHASES_ONLY
+__global__ void __launch_bounds__(256) k_level_prefix(BatchArgs a, uint32_t* MPDP_RESTRICT pref, uint32_t group_threads)
 {
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     const int k = blockIdx.x / 2 + 2, mode = (blockIdx.x & 1) ? MPDP_ENUM_BLOCKS : MPDP_ENUM_TREE;
@@ -945,6 +983,7 @@ __global__ void __launch_bounds__(256) k_level_prefix(BatchArgs a, uint32_t* __r
     for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) row[i] = s_pref[i];
     if (threadIdx.x == 0) row[kMaxBatch + 1] = group;
 }
+#endif
 
 // (x, left) minimum over the g lanes of a group (g a power of two <= 32,
 // groups aligned within the warp; mask: the group's lanes).
@@ -966,14 +1005,15 @@ __device__ __forceinline__ void group_min_x(unsigned long long& bx, uint32_t& bl
 // its first lane, which writes the memo and counts the set in s_sets.
 template <class Memo>
 __device__ __forceinline__ void eval_tree_groups(const BatchArgs& a, int k, uint32_t G, Memo& memo,
-                                                 const uint32_t* s_pref, uint32_t* s_sets)
+                                                 const uint32_t* s_pref, uint32_t* s_sets, uint32_t bid,
+                                                 uint32_t nblk)
 {
     const uint32_t nsets = s_pref[a.nq];
     const uint32_t gl = threadIdx.x & (G - 1u);
     const unsigned gmask = G == 32u ? kFull : ((1u << G) - 1u) << ((threadIdx.x & 31u) & ~(G - 1u));
-    for (uint32_t g = (blockIdx.x * kEvalThreads + threadIdx.x) / G; g < nsets; g += gridDim.x * (kEvalThreads / G)) {
+    for (uint32_t g = (bid * kEvalThreads + threadIdx.x) / G; g < nsets; g += nblk * (kEvalThreads / G)) {
         const int qi = find_q(s_pref, a.nq, g);
-        const DevQuery* __restrict__ q = a.query + qi;
+        const DevQuery* MPDP_RESTRICT q = a.query + qi;
         DevCounters* cnt = &a.out[qi].counters;
         memo.bind(a, qi);
         const QDesc& d = a.desc[qi];
@@ -986,7 +1026,7 @@ __device__ __forceinline__ void eval_tree_groups(const BatchArgs& a, int k, uint
         const uint32_t rest = s & ~(1u << top);
         // this lane's split: the member of rest of rank gl (G >= k - 1)
         if ((int)gl < k - 1) {
-            const uint32_t sl = __ldg(&q->desc[__fns(rest, 0u, gl + 1)]) & s;
+            const uint32_t sl = MPDP_LDG(&q->desc[__fns(rest, 0u, gl + 1)]) & s;
             fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
         }
         group_min_x(bx, bl, G, gmask);
@@ -1008,7 +1048,7 @@ __device__ __forceinline__ void eval_tree_groups(const BatchArgs& a, int k, uint
 // (cost, left) over the k-1 splits is written to the memo: evaluate, prune
 // and scatter fused in one pass, one memo write per set.
 template <class Memo>
-__global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, Memo memo, const uint32_t* __restrict__ level_pref)
+__device__ void eval_tree_body(const BatchArgs& a, int k, Memo memo, const uint32_t* MPDP_RESTRICT level_pref, uint32_t bid, uint32_t nblk)
 {
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
@@ -1016,7 +1056,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
     {
         // a block with no tile (or no group) of this level leaves at once
         const uint32_t total = level_pref[k * kPrefStride + a.nq];  // tiles, or sets in group mode
-        if (G ? blockIdx.x * (kEvalThreads / G) >= total : blockIdx.x >= total) return;  // block-uniform
+        if (G ? bid * (kEvalThreads / G) >= total : bid >= total) return;  // block-uniform
     }
     memo.setup(s_memo);
     for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) s_pref[i] = level_pref[k * kPrefStride + i];
@@ -1025,7 +1065,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
         __shared__ uint32_t s_sets[kMaxBatch];  // sets evaluated per query
         for (int i = threadIdx.x; i < a.nq; i += blockDim.x) s_sets[i] = 0u;
         __syncthreads();
-        eval_tree_groups(a, k, G, memo, s_pref, s_sets);
+        eval_tree_groups(a, k, G, memo, s_pref, s_sets, bid, nblk);
         __syncthreads();
         for (int i = threadIdx.x; i < a.nq; i += blockDim.x)
             if (s_sets[i]) {
@@ -1041,9 +1081,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
     // consecutive tiles of a block belong to different queries and a
     // switch then costs no block barrier.
     int cur = -1;
-    const DevQuery* __restrict__ q = nullptr;
+    const DevQuery* MPDP_RESTRICT q = nullptr;
     unsigned long long sets = 0;
-    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    for (uint32_t t = bid; t < tiles; t += nblk) {
         const int qi = find_q(s_pref, a.nq, t);
         if (qi != cur) {  // block-uniform
             if (cur >= 0) {
@@ -1069,7 +1109,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
             // desc[v] & S, and the rest: the k-1 CCP pairs of S, one AND each.
             uint32_t t2 = s;
             int top = lowest(t2);
-            while ((__ldg(&q->desc[top]) & s) != s) {
+            while ((MPDP_LDG(&q->desc[top]) & s) != s) {
                 t2 &= t2 - 1u;
                 top = lowest(t2);
             }
@@ -1086,12 +1126,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
             for (int i = 1; i < k; i += 2) {
                 const int v0 = lowest(rest);
                 rest &= rest - 1u;
-                const uint32_t sl0 = __ldg(&q->desc[v0]) & s;
+                const uint32_t sl0 = MPDP_LDG(&q->desc[v0]) & s;
                 uint32_t sl1 = 0u;
                 if (i + 1 < k) {
                     const int v1 = lowest(rest);
                     rest &= rest - 1u;
-                    sl1 = __ldg(&q->desc[v1]) & s;
+                    sl1 = MPDP_LDG(&q->desc[v1]) & s;
                 }
                 const uint32_t sr0 = s ^ sl0, sr1 = s ^ sl1;
                 const double cl0 = (sl0 & (sl0 - 1u)) ? memo.get_cost(sl0, cnt) : 0.0;
@@ -1115,15 +1155,24 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, 
     }
 }
 
+#ifndef MPDP_PHASES_ONLY
+template <class Memo>
+__global__ void __launch_bounds__(kEvalThreads) k_eval_tree(BatchArgs a, int k, Memo memo, const uint32_t* MPDP_RESTRICT level_pref)
+{
+    eval_tree_body(a, k, memo, level_pref, blockIdx.x, gridDim.x);
+}
+#endif
+
 // ---------------------------------------------------------------------------
 // Ablation of the fusion (Sec. 5: evaluate and prune in one kernel): the same
 // tree-mode work as k_eval_tree in two kernels.  The first writes every CCP
 // pair's (x, left) to global memory, slot (tile * 256 + thread) * (k - 1) + i;
 // the second reads a set's k - 1 records back, keeps the (x, left) minimum,
 // computes card(S) and writes the memo.  Same tiles, same results.
+#ifndef MPDP_PHASES_ONLY
 template <class Memo>
 __global__ void __launch_bounds__(kEvalThreads) k_eval_tree_pairs(BatchArgs a, int k, Memo memo,
-                                                                  PairRec* __restrict__ pairs)
+                                                                  PairRec* MPDP_RESTRICT pairs)
 {
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
@@ -1145,7 +1194,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree_pairs(BatchArgs a, i
             memo.bind(a, qi);
             cur = qi;
         }
-        const DevQuery* __restrict__ q = a.query + qi;
+        const DevQuery* MPDP_RESTRICT q = a.query + qi;
         DevCounters* cnt = &a.out[qi].counters;
         const uint32_t idx = (t - s_pref[qi]) * kEvalThreads + threadIdx.x;
         if (idx < cnt->list_count[k]) {
@@ -1153,7 +1202,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree_pairs(BatchArgs a, i
             const uint32_t s = a.lists[d.list_base + d.list_off[k] + idx];
             uint32_t t2 = s;
             int top = lowest(t2);
-            while ((__ldg(&q->desc[top]) & s) != s) {
+            while ((MPDP_LDG(&q->desc[top]) & s) != s) {
                 t2 &= t2 - 1u;
                 top = lowest(t2);
             }
@@ -1162,7 +1211,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree_pairs(BatchArgs a, i
             for (int i = 1; i < k; i++) {
                 const int v = lowest(rest);
                 rest &= rest - 1u;
-                const uint32_t sl = __ldg(&q->desc[v]) & s;
+                const uint32_t sl = MPDP_LDG(&q->desc[v]) & s;
                 unsigned long long bx = kNoX;
                 uint32_t bl = kFull;
                 fold_pair(sl, s ^ sl, memo, cnt, bx, bl);  // one pair: its own (x, left)
@@ -1180,10 +1229,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_tree_pairs(BatchArgs a, i
         }
     }
 }
+#endif
 
+#ifndef MPDP_PHASES_ONLY
 template <class Memo>
 __global__ void __launch_bounds__(kEvalThreads) k_prune_tree(BatchArgs a, int k, Memo memo,
-                                                             const PairRec* __restrict__ pairs)
+                                                             const PairRec* MPDP_RESTRICT pairs)
 {
     __shared__ uint32_t s_pref[kMaxBatch + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
@@ -1196,7 +1247,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_prune_tree(BatchArgs a, int k,
             memo.bind(a, qi);
             cur = qi;
         }
-        const DevQuery* __restrict__ q = a.query + qi;
+        const DevQuery* MPDP_RESTRICT q = a.query + qi;
         DevCounters* cnt = &a.out[qi].counters;
         const uint32_t idx = (t - s_pref[qi]) * kEvalThreads + threadIdx.x;
         if (idx < cnt->list_count[k]) {
@@ -1219,6 +1270,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_prune_tree(BatchArgs a, int k,
         }
     }
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // a4-a8, general join graphs (Algorithm 4), thread per set for light sets.
@@ -1228,7 +1280,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_prune_tree(BatchArgs a, int k,
 // S_r = S \ S_l.  Sets whose pair count exceeds the heavy threshold go to the
 // block-per-set kernel instead.
 template <class Memo>
-__global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k, Memo memo, const uint32_t* __restrict__ level_pref)
+__device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uint32_t* MPDP_RESTRICT level_pref, uint32_t bid, uint32_t nblk)
 {
     __shared__ SharedQuery sq;
     __shared__ uint32_t s_pref[kMaxBatch + 1];
@@ -1240,7 +1292,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
     int cur = -1;
     unsigned long long evaluated = 0, ccp = 0;
     const int lane = threadIdx.x & 31;
-    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    for (uint32_t t = bid; t < tiles; t += nblk) {
         const int qi = find_q(s_pref, a.nq, t);
         if (qi != cur) {
             if (cur >= 0) {
@@ -1260,7 +1312,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
         }
         DevCounters* cnt = &a.out[qi].counters;
         const QDesc& d = a.desc[qi];
-        const uint32_t* __restrict__ cw = conn_bitmap(a, qi);
+        const uint32_t* MPDP_RESTRICT cw = conn_bitmap(a, qi);
         const uint32_t idx = (t - s_pref[qi]) * kEvalThreads + threadIdx.x;
         bool to_heavy = false;
         uint32_t s = 0u, want = 0u;  // want: extra chunks asked for
@@ -1350,6 +1402,14 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
     }
 }
 
+#ifndef MPDP_PHASES_ONLY
+template <class Memo>
+__global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k, Memo memo, const uint32_t* MPDP_RESTRICT level_pref)
+{
+    eval_blocks_body(a, k, memo, level_pref, blockIdx.x, gridDim.x);
+}
+#endif
+
 // Heavy-set evaluation (general mode).  The work items of level k are the
 // pair chunks reserved by k_eval_blocks: a block takes a tile of 8 items of
 // one query, one per warp (the paper evaluates a set with one warp, Sec. 5
@@ -1363,7 +1423,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
 // reduction of (x, left); a set cut into several chunks is folded by the
 // warp that finishes it last (fence, then an arrival count), with no waiting.
 template <class Memo>
-__global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k, Memo memo)
+__device__ void eval_heavy_body(const BatchArgs& a, int k, Memo memo, uint32_t bid, uint32_t nblk)
 {
     constexpr int kWarps = kEvalThreads / 32;
     __shared__ SharedQuery sq;
@@ -1387,7 +1447,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int cur = -1;
     unsigned long long ccp = 0, evaluated = 0, heavy = 0;
-    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    for (uint32_t t = bid; t < tiles; t += nblk) {
         const int qi = find_q(s_pref, a.nq, t);
         if (qi != cur) {
             if (cur >= 0 && lane == 0) {
@@ -1441,7 +1501,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
         const uint32_t total = bpref[nb];
         const uint32_t lo = (uint32_t)((unsigned long long)total * chunk / nch);
         const uint32_t hi = (uint32_t)((unsigned long long)total * (chunk + 1u) / nch);
-        const uint32_t* __restrict__ cw = conn_bitmap(a, qi);
+        const uint32_t* MPDP_RESTRICT cw = conn_bitmap(a, qi);
         const uint32_t cliq = s_cliq[warp];
         unsigned long long bx = kNoX;
         uint32_t bl = kFull;
@@ -1553,15 +1613,23 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k,
     }
 }
 
+#ifndef MPDP_PHASES_ONLY
+template <class Memo>
+__global__ void __launch_bounds__(kEvalThreads) k_eval_heavy(BatchArgs a, int k, Memo memo)
+{
+    eval_heavy_body(a, k, memo, blockIdx.x, gridDim.x);
+}
+#endif
+
 // ---------------------------------------------------------------------------
 // a9: plan fetch (one warp per query).  From the full set, read (cost, card,
 // left) from the memo and expand left and S \ left, one tree depth at a time
 // with one lane per node of that depth; nodes end up in breadth-first order.
 template <class Memo>
-__global__ void __launch_bounds__(32) k_extract(BatchArgs a, Memo memo)
+__device__ void extract_body(const BatchArgs& a, Memo memo, uint32_t bid, uint32_t nblk)
 {
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
-    const int qi = blockIdx.x, lane = threadIdx.x;
+    const int qi = bid, lane = threadIdx.x;
     memo.setup(s_memo);
     memo.bind(a, qi);
     __syncwarp();
@@ -1640,10 +1708,19 @@ __global__ void __launch_bounds__(32) k_extract(BatchArgs a, Memo memo)
     }
 }
 
-// Memo read-back of arbitrary connected sets of one query (parity checks).
+#ifndef MPDP_PHASES_ONLY
 template <class Memo>
-__global__ void k_memo_lookup(BatchArgs a, int qi, const uint32_t* __restrict__ sets, int count,
-                              double* __restrict__ costs, uint32_t* __restrict__ lefts, Memo memo)
+__global__ void __launch_bounds__(32) k_extract(BatchArgs a, Memo memo)
+{
+    extract_body(a, memo, blockIdx.x, gridDim.x);
+}
+#endif
+
+// Memo read-back of arbitrary connected sets of one query (parity checks).
+#ifndef MPDP_PHASES_ONLY
+template <class Memo>
+__global__ void k_memo_lookup(BatchArgs a, int qi, const uint32_t* MPDP_RESTRICT sets, int count,
+                              double* MPDP_RESTRICT costs, uint32_t* MPDP_RESTRICT lefts, Memo memo)
 {
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     memo.setup(s_memo);
@@ -1664,10 +1741,12 @@ __global__ void k_memo_lookup(BatchArgs a, int qi, const uint32_t* __restrict__ 
         lefts[i] = l;
     }
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // Host-side launch sequencing.
 
+#ifndef MPDP_PHASES_ONLY
 unsigned long long binom_host(int n, int k)
 {
     if (k < 0 || k > n) return 0;
@@ -1891,5 +1970,7 @@ cudaError_t enqueue_memo_lookup(const BatchArgs& a, int memo_kind, int qi, const
     }
     return cudaGetLastError();
 }
+
+#endif  // MPDP_PHASES_ONLY
 
 }  // namespace mpdp

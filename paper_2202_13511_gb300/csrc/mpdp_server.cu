@@ -15,11 +15,13 @@
 #include <chrono>
 #include <cstring>
 #include <deque>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
 #include "../../include/mpdp.h"
 #include "mpdp_launch.h"
+#include "mpdp_persist.h"
 
 namespace {
 
@@ -57,12 +59,14 @@ struct mpdp_server {
     std::deque<int64_t> unreported;  // finished, not yet returned by a poll
     int64_t next_ticket = 0;
     int running = 0;
+    mpdp::PersistEngine* engine = nullptr;  // persistent mode
+    std::vector<int> free_slots;            // persistent mode: query slots without a request
 };
 
 namespace {
 
 const mpdp_server_config kDefaultServer = {4, 256, 0, {MPDP_MEMO_DENSE, MPDP_ENUM_AUTO, 64, 1, 0, 32,
-                                                       MPDP_FILTER_CONNECTED, 8, 4, 1, 18}};
+                                                       MPDP_FILTER_CONNECTED, 8, 4, 1, 18}, 0, 0};
 constexpr size_t kDefaultSlotBudget = (size_t)16 << 30;
 
 size_t slot_budget(const mpdp_server* s)
@@ -152,8 +156,51 @@ int launch(mpdp_server* s, Slot& sl)
     return MPDP_OK;
 }
 
+// Persistent mode: collect finished requests, hand queued ones to free slots.
+int progress_persistent(mpdp_server* s)
+{
+    std::vector<mpdp::PersistResult> fin;
+    int rc = mpdp::persist_poll(s->engine, fin);
+    if (rc != MPDP_OK) return rc;
+    const Clock::time_point now = Clock::now();
+    for (mpdp::PersistResult& f : fin) {
+        Request& r = s->reqs[f.ticket];
+        r.state = 2;
+        r.t_done = now;
+        r.status = f.status;
+        r.cost = f.cost;
+        r.nodes = std::move(f.nodes);
+        s->unreported.push_back(f.ticket);
+        s->free_slots.push_back(f.slot);
+        s->running--;
+    }
+    while (!s->queue.empty() && !s->free_slots.empty()) {
+        const int64_t t = s->queue.front();
+        Request& r = s->reqs[t];
+        const int slot = s->free_slots.back();
+        rc = mpdp::persist_submit(s->engine, slot, t, r.n, r.m, r.card.data(), r.edges.empty() ? nullptr : r.edges.data());
+        if (rc != MPDP_OK) return rc;
+        s->free_slots.pop_back();
+        s->queue.pop_front();
+        r.state = 1;
+        s->running++;
+    }
+    return MPDP_OK;
+}
+
 int progress(mpdp_server* s, int64_t* done, int32_t cap, int32_t* count)
 {
+    if (s->engine) {
+        const int rc = progress_persistent(s);
+        if (rc != MPDP_OK) return rc;
+        int found = 0;
+        while (done && found < cap && !s->unreported.empty()) {
+            done[found++] = s->unreported.front();
+            s->unreported.pop_front();
+        }
+        if (count) *count = found;
+        return MPDP_OK;
+    }
     const Clock::time_point now = Clock::now();
     for (Slot& sl : s->slots) {
         if (!sl.busy) continue;
@@ -198,7 +245,12 @@ int mpdp_server_create(mpdp_server** out, int device, const mpdp_server_config* 
     if (!out) return MPDP_ERR_INVALID_ARG;
     *out = nullptr;
     const mpdp_server_config c = cfg ? *cfg : kDefaultServer;
-    if (c.slots < 1 || c.slots > 16 || c.max_batch < 1 || c.max_batch > 1024) return MPDP_ERR_INVALID_ARG;
+    if (c.persistent != 0 && c.persistent != 1) return MPDP_ERR_INVALID_ARG;
+    if (c.persistent) {
+        if (c.slots < 1 || c.slots > 1024) return MPDP_ERR_INVALID_ARG;
+    } else if (c.slots < 1 || c.slots > 16 || c.max_batch < 1 || c.max_batch > 1024) {
+        return MPDP_ERR_INVALID_ARG;
+    }
     mpdp_server* s = new mpdp_server();
     s->device = device;
     s->cfg = c;
@@ -206,6 +258,18 @@ int mpdp_server_create(mpdp_server** out, int device, const mpdp_server_config* 
         cudaGetLastError();
         delete s;
         return MPDP_ERR_CUDA;
+    }
+    if (c.persistent) {
+        const int max_rels = mpdp::persist_max_rels(c.slot_budget_bytes);
+        const int rc = max_rels < 2 ? MPDP_ERR_INVALID_ARG
+                                    : mpdp::persist_create(&s->engine, device, c.slots, max_rels, c.kernel);
+        if (rc != MPDP_OK) {
+            delete s;
+            return rc;
+        }
+        for (int i = c.slots - 1; i >= 0; i--) s->free_slots.push_back(i);
+        *out = s;
+        return MPDP_OK;
     }
     s->slots.resize(c.slots);
     int rc = MPDP_OK;
@@ -232,6 +296,7 @@ int mpdp_server_create(mpdp_server** out, int device, const mpdp_server_config* 
 void mpdp_server_destroy(mpdp_server* s)
 {
     if (!s) return;
+    if (s->engine) mpdp::persist_destroy(s->engine);
     for (Slot& sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.ctx) mpdp_destroy(sl.ctx);
@@ -252,7 +317,9 @@ int mpdp_server_submit(mpdp_server* s, const mpdp_query* q, int64_t* ticket)
     // get a whole batch rejected
     const int vrc = mpdp::validate_host_query(q);
     if (vrc != MPDP_OK) return vrc;
-    if (mpdp::batch_workspace_bytes(&n, &m, 1, s->cfg.kernel) > slot_budget(s)) return MPDP_ERR_ADMISSION;
+    if (s->engine ? n > mpdp::persist_max_rels(s->engine)
+                  : mpdp::batch_workspace_bytes(&n, &m, 1, s->cfg.kernel) > slot_budget(s))
+        return MPDP_ERR_ADMISSION;
     if (cudaSetDevice(s->device) != cudaSuccess) {
         cudaGetLastError();
         return MPDP_ERR_CUDA;
@@ -287,6 +354,17 @@ int mpdp_server_drain(mpdp_server* s)
         cudaGetLastError();
         return MPDP_ERR_CUDA;
     }
+    if (s->engine) {
+        // the kernel finishes every request it holds; bounded wait
+        const Clock::time_point limit = Clock::now() + std::chrono::seconds(300);
+        while (!s->queue.empty() || s->running > 0) {
+            const int rc = progress(s, nullptr, 0, nullptr);
+            if (rc != MPDP_OK) return rc;
+            if (Clock::now() > limit) return MPDP_ERR_TIMEOUT;
+            if (s->running > 0) std::this_thread::sleep_for(std::chrono::microseconds(5));
+        }
+        return MPDP_OK;
+    }
     while (!s->queue.empty() || s->running > 0) {
         for (Slot& sl : s->slots)
             if (sl.busy && cudaEventSynchronize(sl.done) != cudaSuccess) {
@@ -303,6 +381,10 @@ int mpdp_server_pending(const mpdp_server* s, int32_t* queued, int32_t* running)
 {
     if (!s) return MPDP_ERR_INVALID_ARG;
     if (queued) *queued = (int32_t)s->queue.size();
+    if (running && s->engine) {
+        *running = mpdp::persist_busy(s->engine);
+        return MPDP_OK;
+    }
     if (running) {
         int r = 0;
         for (const Slot& sl : s->slots) r += sl.busy ? (int)sl.tickets.size() : 0;

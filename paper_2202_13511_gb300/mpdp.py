@@ -89,7 +89,8 @@ class ConfigC(ctypes.Structure):
 
 class ServerConfigC(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("slot_budget_bytes", ctypes.c_uint64), ("kernel", ConfigC)]
+                ("slot_budget_bytes", ctypes.c_uint64), ("kernel", ConfigC),
+                ("persistent", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 EDGE_DTYPE = np.dtype([("u", "<i4"), ("v", "<i4"), ("sel", "<f8")])
@@ -126,7 +127,7 @@ def lib_path() -> str:
     return _build.LIB_PATH
 
 
-ABI_VERSION = 5  # MPDP_ABI_VERSION of include/mpdp.h this binding's structs follow
+ABI_VERSION = 6  # MPDP_ABI_VERSION of include/mpdp.h this binding's structs follow
 
 
 def load(build_if_missing: bool = True):
@@ -658,13 +659,16 @@ class Mlp:
 class Server:
     """Serving loop over the library's native scheduler (mpdp_server_*):
     continuous batching over `slots` concurrent device batches, admission
-    by memo memory.  Results are bit-identical to optimizing alone."""
+    by memo memory, or (persistent=True) one resident kernel over `slots`
+    query slots that takes requests while it runs.  Results are
+    bit-identical to optimizing alone."""
 
     def __init__(self, device: int = 0, slots: Optional[int] = None, max_batch: Optional[int] = None,
-                 slot_budget_bytes: Optional[int] = None, **kernel_config):
+                 slot_budget_bytes: Optional[int] = None, persistent: bool = False, **kernel_config):
         self._lib = load()
         cfg = ServerConfigC()
         self._check(self._lib.mpdp_server_default_config(ctypes.byref(cfg)), "mpdp_server_default_config")
+        cfg.persistent = 1 if persistent else 0
         if slots is not None:
             cfg.slots = int(slots)
         if max_batch is not None:

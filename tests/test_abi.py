@@ -47,7 +47,7 @@ def test_binding_follows_the_header_abi():
     src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
     for name, cls in (("mpdp_config", mpdp.ConfigC), ("mpdp_query", mpdp.QueryC),
                       ("mpdp_stats", mpdp.StatsC), ("mpdp_plan_node", mpdp.PlanNode),
-                      ("mpdp_edge", mpdp.Edge)):
+                      ("mpdp_edge", mpdp.Edge), ("mpdp_server_config", mpdp.ServerConfigC)):
         body = re.search(r"typedef struct \{([^}]*)\} " + name + ";", src).group(1)
         declared = []
         for decl in body.split(";"):
@@ -61,7 +61,7 @@ def test_binding_follows_the_header_abi():
 
 def test_abi_version_and_strerror():
     lib = mpdp.load()
-    assert lib.mpdp_abi_version() == 5
+    assert lib.mpdp_abi_version() == 6
     assert mpdp.strerror(0) == "ok"
     for code in mpdp.ERRORS:
         assert mpdp.strerror(code) != "unknown error"
