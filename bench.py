@@ -993,11 +993,13 @@ def serving_line(mpdp, W):
                 t = srv.submit(q)
                 srv.drain()
                 srv.result(t)
+            while srv.poll():  # report the warm-up tickets
+                pass
             ts = []
             for _ in range(50):
                 t1 = time.perf_counter()
                 t = srv.submit(q)
-                while not srv.poll():
+                while t not in srv.poll():
                     pass
                 ts.append(time.perf_counter() - t1)
                 srv.result(t)
