@@ -976,9 +976,9 @@ def serving_line(mpdp, W):
         out["saturated"] = sat
         out.update(_poisson(srv, queries, sat["queries_per_s"], (0.5, 0.8, 0.95), seed=1))
     batch_sat = sat["queries_per_s"]
-    # persistent kernel over query slots (dense memo, tree levels' work split
-    # from the tuned kernel knobs)
-    pk = {k: v for k, v in kernel.items() if k in ("heavy_threshold", "use_ccc", "group_threads_log2")}
+    # persistent kernel over query slots (dense memo; the block-mode knobs
+    # from the tuned kernel, the library's default work split of tree levels)
+    pk = {k: v for k, v in kernel.items() if k in ("heavy_threshold", "use_ccc")}
     with mpdp.Server(0, slots=PERSIST_SLOTS, persistent=True, **pk) as srv:
         psat = _saturated(srv, queries)
         pers = {"slots": PERSIST_SLOTS, "max_relations": 25, "kernel": pk, "saturated": psat}

@@ -541,8 +541,61 @@ __device__ __forceinline__ uint32_t unrank_connected(const DevQuery* MPDP_RESTRI
     return s;
 }
 
-// Ranks per thread and per block item of the connected-set filter.
-constexpr int kConnPerThread = 4;
+// The connected set that follows s among the sets with top v, in the order
+// unrank_connected decodes them (false when s is the last one).  An
+// odometer over the same digits: v's leaf children (one bit each, lowest
+// first), then its other children, whose digit is their own odometer (0:
+// the child's subtree left out; a child that overflows drops its subtree and
+// carries to the next digit).  Consecutive ranks differ in their low digits,
+// so a step touches a few digits on average.
+__device__ __forceinline__ bool next_connected(const DevQuery* MPDP_RESTRICT q, int v, uint32_t& s)
+{
+    uint8_t st_u[kMaxRels];
+    uint32_t st_l[kMaxRels], st_n[kMaxRels];
+    const uint32_t leaves = MPDP_LDG(&q->leaves);
+    const uint32_t ch = MPDP_LDG(&q->chmask[v]);
+    st_u[0] = (uint8_t)v;
+    st_l[0] = ch & leaves;
+    st_n[0] = ch & ~leaves;
+    int sp = 1;
+    uint32_t x = s;
+    while (sp > 0) {
+        const int f = sp - 1;
+        if (st_l[f]) {  // a leaf child's bit
+            const uint32_t c = st_l[f] & (0u - st_l[f]);
+            st_l[f] ^= c;
+            if (!(x & c)) {
+                s = x | c;
+                return true;
+            }
+            x &= ~c;
+            continue;
+        }
+        if (st_n[f]) {  // another child: in with its first set, or its own odometer
+            const uint32_t c = st_n[f] & (0u - st_n[f]);
+            st_n[f] ^= c;
+            if (!(x & c)) {
+                s = x | c;
+                return true;
+            }
+            const int w = lowest(c);
+            const uint32_t cw = MPDP_LDG(&q->chmask[w]);
+            st_u[sp] = (uint8_t)w;
+            st_l[sp] = cw & leaves;
+            st_n[sp] = cw & ~leaves;
+            sp++;
+            continue;
+        }
+        // every digit of this node wrapped
+        if (--sp == 0) return false;
+        x &= ~MPDP_LDG(&q->desc[st_u[f]]);
+    }
+    return false;
+}
+
+// Ranks per thread and per block item of the connected-set filter: a thread
+// decodes the first rank of its run and steps to the others.
+constexpr int kConnPerThread = 8;
 constexpr uint32_t kConnPerItem = kFilterThreads * kConnPerThread;
 
 // Items of kConnPerItem consecutive ranks of a tree query in mode CONNECTED
@@ -555,8 +608,10 @@ __device__ __forceinline__ uint32_t connected_items(const BatchArgs& a, int q)
 }
 
 // A block takes an item of kConnPerItem consecutive ranks of one query
-// (grid-stride over the batch's items); thread t decodes ranks
-// item * kConnPerItem + j * blockDim + t.  Places within the block come from
+// (grid-stride over the batch's items); thread t takes the run of
+// kConnPerThread ranks from item * kConnPerItem + t * kConnPerThread on:
+// the first decoded, the next ones by next_connected (the top moves to the
+// next relation when its sets run out).  Places within the block come from
 // shared-memory counters per level, and one global atomic per level present
 // reserves the block's room in that level's list.
 static __device__ void filter_connected_body(const BatchArgs& a, uint32_t bid, uint32_t nblk)
@@ -580,20 +635,30 @@ static __device__ void filter_connected_body(const BatchArgs& a, uint32_t bid, u
         const DevQuery* MPDP_RESTRICT q = a.query + qi;
         const int n = q->n;
         const uint32_t total = MPDP_LDG(&q->top_pref[n]);
-        const uint32_t r0 = (it - s_pref[qi]) * kConnPerItem + (uint32_t)tid;
+        const uint32_t r0 = (it - s_pref[qi]) * kConnPerItem + (uint32_t)tid * kConnPerThread;
         uint32_t sv[kConnPerThread], off[kConnPerThread];
+        int top = 0;
+        uint32_t cur_s = 0u;
+        if (r0 < total) {
+            int lo = 0, hi = n - 1;  // largest v with top_pref[v] <= r0
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (MPDP_LDG(&q->top_pref[mid]) <= r0) lo = mid;
+                else hi = mid - 1;
+            }
+            top = lo;
+            cur_s = unrank_connected(q, lo, r0 - MPDP_LDG(&q->top_pref[lo]));
+        }
 #pragma unroll 1
         for (int j = 0; j < kConnPerThread; j++) {
-            const uint32_t r = r0 + (uint32_t)j * kFilterThreads;
+            const uint32_t r = r0 + (uint32_t)j;
             uint32_t s = 0u;
             if (r < total) {
-                int lo = 0, hi = n - 1;  // largest v with top_pref[v] <= r
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (MPDP_LDG(&q->top_pref[mid]) <= r) lo = mid;
-                    else hi = mid - 1;
+                if (j > 0 && !next_connected(q, top, cur_s)) {
+                    top++;  // the next relation's first set: itself
+                    cur_s = 1u << top;
                 }
-                s = unrank_connected(q, lo, r - MPDP_LDG(&q->top_pref[lo]));
+                s = cur_s;
             }
             sv[j] = s;
             const int lv = __popc(s);
@@ -1040,13 +1105,15 @@ __device__ __forceinline__ void eval_tree_groups(const BatchArgs& a, int k, uint
 
 // ---------------------------------------------------------------------------
 // a4-a8, tree join graphs (Algorithm 2, MPDP:Tree).  One thread per connected
-// set S of level k (tiles of 256 sets of one query per block iteration).
-// Every connected S induces a tree; its CCP pairs are the k-1 splits made by
-// removing one edge of G[S].  A search from min(S) finds each tree edge
-// (x, v) once, with v on the far side from the root; the split is
-// S_l = grow({v}, S \ {x}) (the subtree under v), S_r = S \ S_l.  The best
-// (cost, left) over the k-1 splits is written to the memo: evaluate, prune
-// and scatter fused in one pass, one memo write per set.
+// set S of level k (tiles of 256 sets of one query per block iteration), or
+// a group of lanes per set on levels with few sets.  Every connected S
+// induces a subtree of the query tree T (rooted at relation 0), hanging from
+// its top member (the one whose descendants cover S); its CCP pairs are the
+// k-1 splits made by removing one edge of G[S].  Removing the edge above any
+// other member v leaves S_l = desc[v] & S (the part of S under v) and
+// S_r = S \ S_l: one AND per split, no search.  The best (cost, left) over
+// the k-1 splits is written to the memo: evaluate, prune and scatter fused
+// in one pass, one memo write per set.
 template <class Memo>
 __device__ void eval_tree_body(const BatchArgs& a, int k, Memo memo, const uint32_t* MPDP_RESTRICT level_pref, uint32_t bid, uint32_t nblk)
 {
