@@ -129,14 +129,20 @@ __device__ void publish_phase(PSlot* s, unsigned int epoch, PhaseInfo inf)
     atomicExch(&s->word, (unsigned long long)epoch << 32);
 }
 
-// Claim the next tile of slot s (one thread).
-__device__ bool claim_tile(const PArgs& p, int s, unsigned int& epoch, unsigned int& tile, PhaseInfo& inf)
+// Claim the next tiles of slot s (one thread): [tile, tile + count).  A
+// phase with many tiles left hands them out kClaim at a time, so that the
+// blocks do not all queue on the slot's word for every tile.
+constexpr unsigned int kClaim = 4u;
+
+__device__ bool claim_tile(const PArgs& p, int s, unsigned int& epoch, unsigned int& tile, unsigned int& count,
+                           PhaseInfo& inf)
 {
     PSlot* sl = p.slots + s;
     const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(&sl->word);
     const PhaseInfo i0 = read_info(sl, (unsigned int)(w >> 32));
     if (i0.phase == PH_FREE || (unsigned int)w >= i0.total) return false;
-    const unsigned long long old = atomicAdd(&sl->word, 1ull);
+    const unsigned int want = i0.total - (unsigned int)w >= kClaim * 2u * gridDim.x ? kClaim : 1u;
+    const unsigned long long old = atomicAdd(&sl->word, (unsigned long long)want);
     const unsigned int e = (unsigned int)(old >> 32), t = (unsigned int)old;
     __threadfence();
     const PhaseInfo i1 = read_info(sl, e);
@@ -146,6 +152,7 @@ __device__ bool claim_tile(const PArgs& p, int s, unsigned int& epoch, unsigned 
     if ((unsigned int)(w2 >> 32) != e || i1.phase == PH_FREE || t >= i1.total) return false;
     epoch = e;
     tile = t;
+    count = i1.total - t < want ? i1.total - t : want;
     inf = i1;
     return true;
 }
@@ -317,56 +324,88 @@ __device__ void admit(const PArgs& p, unsigned long long req)
     }
 }
 
-__global__ void __launch_bounds__(kPersistThreads) k_persist(PArgs p)
+__global__ void __launch_bounds__(kPersistThreads, 3) k_persist(PArgs p)
 {
     __shared__ int s_cmd, s_slot;
-    __shared__ unsigned int s_epoch, s_tile;
+    __shared__ unsigned int s_epoch, s_tile, s_count;
     __shared__ PhaseInfo s_inf;
     __shared__ unsigned long long s_req;
     enum { kIdle = 0, kTile = 1, kAdmit = 2, kExit = 3 };
     int idle = 0;
     int start = (int)(blockIdx.x % (unsigned int)p.nslots);
     for (;;) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
+            // warp 0 picks the block's next work: the 32 lanes look at 32 slots
+            // at once (from the one this block last worked on), the first
+            // slot with tiles left is claimed; else a new request is taken
+            const int lane = threadIdx.x;
             int cmd = kIdle;
-            if (*reinterpret_cast<const volatile int*>(p.stop)) {
+            int stop = 0;
+            if (lane == 0) stop = *reinterpret_cast<const volatile int*>(p.stop);
+            if (__shfl_sync(kFull, stop, 0)) {
                 cmd = kExit;
             } else {
-                for (int i = 0; i < p.nslots && cmd == kIdle; i++) {
+                for (int base = 0; base < p.nslots && cmd == kIdle; base += 32) {
+                    const int i = base + lane;
                     const int s = (start + i) % p.nslots;
-                    unsigned int e = 0u, t = 0u;
-                    PhaseInfo inf;
-                    if (claim_tile(p, s, e, t, inf)) {
-                        cmd = kTile;
-                        s_slot = s;
-                        s_epoch = e;
-                        s_tile = t;
-                        s_inf = inf;
+                    bool has = false;
+                    if (i < p.nslots) {
+                        const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(&p.slots[s].word);
+                        const PhaseInfo inf = read_info(p.slots + s, (unsigned int)(w >> 32));
+                        has = inf.phase != PH_FREE && (unsigned int)w < inf.total;
+                    }
+                    unsigned int cand = __ballot_sync(kFull, has);
+                    while (cand && cmd == kIdle) {
+                        const int l = __ffs(cand) - 1;
+                        cand &= cand - 1u;
+                        int got = 0;
+                        if (lane == l) {
+                            unsigned int e = 0u, t = 0u, c = 0u;
+                            PhaseInfo inf;
+                            if (claim_tile(p, s, e, t, c, inf)) {
+                                got = 1;
+                                s_slot = s;
+                                s_epoch = e;
+                                s_tile = t;
+                                s_count = c;
+                                s_inf = inf;
+                            }
+                        }
+                        if (__shfl_sync(kFull, got, l)) cmd = kTile;
                     }
                 }
-                unsigned long long req = 0ull;
-                if (cmd == kIdle && take_request(p, req)) {
-                    cmd = kAdmit;
-                    s_req = req;
+                if (cmd == kIdle) {
+                    int adm = 0;
+                    if (lane == 0) {
+                        unsigned long long req = 0ull;
+                        if (take_request(p, req)) {
+                            adm = 1;
+                            s_req = req;
+                        }
+                    }
+                    if (__shfl_sync(kFull, adm, 0)) cmd = kAdmit;
                 }
             }
-            s_cmd = cmd;
+            if (lane == 0) s_cmd = cmd;
         }
         __syncthreads();
         const int cmd = s_cmd;
         if (cmd == kExit) break;
         if (cmd == kTile) {
             const int s = s_slot;
-            const unsigned int epoch = s_epoch, tile = s_tile;
+            const unsigned int epoch = s_epoch, tile = s_tile, ntiles = s_count;
             const PhaseInfo inf = s_inf;
             start = s;  // stay with this slot while it has tiles
             idle = 0;
-            const bool count = run_tile(p, s, epoch, tile, inf);
-            __syncthreads();
+            bool count = true;
+            for (unsigned int j = 0; j < ntiles && count; j++) {
+                count = run_tile(p, s, epoch, tile + j, inf);
+                __syncthreads();
+            }
             if (count && threadIdx.x == 0) {
                 __threadfence();
                 PSlot* sl = p.slots + s;
-                if (atomicAdd(&sl->done[epoch & 1u], 1u) + 1u == inf.total) {
+                if (atomicAdd(&sl->done[epoch & 1u], ntiles) + ntiles == inf.total) {
                     __threadfence();
                     publish_phase(sl, epoch + 1u, next_phase(p, s, inf));
                 }
@@ -376,7 +415,7 @@ __global__ void __launch_bounds__(kPersistThreads) k_persist(PArgs p)
             admit(p, s_req);
         } else {
             if (++idle > p.idle_polls) break;  // block-uniform
-            if (threadIdx.x == 0) __nanosleep(1000);
+            if (threadIdx.x == 0) __nanosleep(200);
         }
         __syncthreads();
     }
@@ -519,7 +558,7 @@ int persist_create(PersistEngine** out, int device, int slots, int max_rels, con
     PArgs& p = e->args;
     p.nslots = slots;
     p.ring_size = slots;
-    p.idle_polls = 20000;
+    p.idle_polls = 60000;
     p.group_threads = kernel.group_threads_log2 ? 1u << kernel.group_threads_log2 : 0u;
     p.slots = e->d_slots;
     p.slot_args = e->d_args;
