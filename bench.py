@@ -58,20 +58,22 @@ OPS_PER_CONNECTED_SET = 40
 BYTES_PER_CCP = 24
 BYTES_PER_SET = 16
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernels on this bench's 64-query batch (4 lanes of 16 queries), from
-# one ncu capture of this bench command (--cache-control none; profiles/).
+# dominant kernels on this bench's 64-query batch (the library's default 4
+# lanes of 16 queries), from one single-pass ncu capture of that batch
+# (`bench.py --case snowflake:25:64`, --cache-control none; profiles/).
 # Each figure describes the kernel whose source fingerprint is given (the
 # kernel's own text, the device functions it relies on and the device header
 # it includes) and is reported as null once that source changes.
 KERNEL_FILE = "paper_2202_13511_gb300/csrc/mpdp_kernels.cu"
 DEVICE_HEADER = "paper_2202_13511_gb300/csrc/mpdp_device.cuh"
 TRAFFIC = {"eval": {"kernel": "k_eval_tree",
-                    "helpers": ("find_q", "set_top_of", "group_size", "group_min_x", "eval_tree_groups",
-                                "k_level_prefix", "block_prefix"),
-                    "sha1": "14a6e7ac1c41dca0f8fd967cd9a46710f1b08bf6", "bytes": 5319349},
+                    "helpers": ("eval_tree_body", "find_q", "set_top_of", "group_size", "group_min_x",
+                                "eval_tree_groups", "k_level_prefix", "block_prefix"),
+                    "sha1": "8515ce68ab617bb3fcb4556d1abc5020d41374d2", "bytes": 5350101},
            "filter": {"kernel": "k_filter_connected",
-                      "helpers": ("unrank_connected", "connected_items", "block_prefix", "find_q"),
-                      "sha1": "546d6cdb822a46341ddcfeb005e5289aa437834a", "bytes": 13892070}}
+                      "helpers": ("filter_connected_body", "unrank_connected", "next_connected", "connected_items",
+                                  "block_prefix", "find_q"),
+                      "sha1": "d95c093afea6b0243dc4e80e7a5e02a7dd4a6fa4", "bytes": 16580032}}
 
 
 def parse_args():

@@ -314,7 +314,7 @@ def test_unfused_ablation(opt, lanes):
     set_cfg(opt)
 
 
-@pytest.mark.parametrize("log2", [0, 8, 24])
+@pytest.mark.parametrize("log2", [0, 8, 16, 20, 24])
 def test_group_split_knob(opt, log2):
     """The tree levels' work split (a thread per set, or groups of lanes
     while sets x G stay within 2^log2 threads) changes no result: costs,
