@@ -1344,8 +1344,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_prune_tree(BatchArgs a, int k,
 // For each block B of G[S] and each lb (min(B) in lb, lb != B): rb = B \ lb;
 // the CCP block keeps the pair when lb and rb both induce connected subgraphs
 // (they are adjacent since B is connected); then S_l = grow(lb, S \ rb),
-// S_r = S \ S_l.  Sets whose pair count exceeds the heavy threshold go to the
-// block-per-set kernel instead.
+// S_r = S \ S_l.  Sets whose work exceeds the heavy threshold go to the warp
+// path instead.  On a level with at least kFullLevelSets sets (enough to
+// fill the GPU a thread per set) a thread's work counts the pairs of a
+// clique block at 1/kCliqueWeight: each is a CCP with no connectivity test,
+// and sets of up to about a thousand of them then run faster here than on
+// the warp path (measured on clique-14; with fewer sets per level, as on
+// clique-12, the warp path's spread wins).
+constexpr uint32_t kCliqueWeight = 16u;
+constexpr uint32_t kFullLevelSets = 16384u;
 template <class Memo>
 __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uint32_t* MPDP_RESTRICT level_pref, uint32_t bid, uint32_t nblk)
 {
@@ -1356,6 +1363,7 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
     for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) s_pref[i] = level_pref[(kLevels + k) * kPrefStride + i];
     __syncthreads();
     const uint32_t tiles = s_pref[a.nq];
+    const bool full = (unsigned long long)tiles * kEvalThreads >= kFullLevelSets;
     int cur = -1;
     unsigned long long evaluated = 0, ccp = 0;
     const int lane = threadIdx.x & 31;
@@ -1387,10 +1395,22 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
             s = a.lists[d.list_base + d.list_off[k] + idx];
             uint32_t blk[kMaxRels], side[kMaxRels];
             const int nb = find_blocks(s, sq.adj, blk, a.dpsub ? nullptr : side);
-            uint32_t pairs = 0u;
-            for (int j = 0; j < nb; j++) pairs += block_pairs(blk[j]);
-            if (a.dpsub) pairs = block_pairs(s);  // the whole set as one block
-            if (pairs > (uint32_t)a.heavy_threshold) {
+            // pairs: the set's bipartitions; work: what a thread pays for
+            // them, a clique block's pairs at 1/kCliqueWeight (no
+            // connectivity test, every pair a CCP)
+            uint32_t pairs = 0u, work = 0u, cliq = 0u;  // cliq: bit j, block j is a clique
+            for (int j = 0; j < nb; j++) {
+                const uint32_t p = block_pairs(blk[j]);
+                pairs += p;
+                if (!a.dpsub && !side[j] && is_clique(blk[j], sq.adj)) {
+                    cliq |= 1u << j;
+                    work += full ? (p + kCliqueWeight - 1u) / kCliqueWeight : p;
+                } else {
+                    work += p;
+                }
+            }
+            if (a.dpsub) pairs = work = block_pairs(s);  // the whole set as one block
+            if (work > (uint32_t)a.heavy_threshold) {
                 to_heavy = true;
                 const uint32_t nch = (pairs - 1u) / kChunkPairs + 1u;
                 want = (nch < kMaxChunks ? nch : kMaxChunks) - 1u;
@@ -1409,7 +1429,7 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
                         continue;
                     }
                     const uint32_t mn = b & (0u - b), rest = b ^ mn;
-                    const bool all_ccp = is_clique(b, sq.adj);
+                    const bool all_ccp = !a.dpsub && (cliq >> j & 1u);
                     for (uint32_t sub = 0u; sub != rest; sub = (sub - rest) & rest) {
                         const uint32_t lb = mn | sub, rb = b ^ lb;
                         if (!all_ccp && (!conn_of(lb, cw, sq.adj) || !conn_of(rb, cw, sq.adj))) continue;
