@@ -684,16 +684,20 @@ def ablation_line(opt, torch, mpdp, W):
     enumeration against DPSUB's vertex-based one (Sec. 7.2: far fewer pairs
     evaluated), Collaborative Context Collection on / off (Sec. 7.2.5), the
     fusion of evaluate, prune and scatter on / off (Sec. 5), and the batch
-    split into 1/2/4/8 concurrent lanes.  Device time of one batch (CUDA
-    events, L2 flushed, mean of 3)."""
+    split into 1/2/4/8 concurrent lanes, and the paper's open-addressing
+    memo against the dense one.  Device time of one batch (CUDA events, L2
+    flushed before each, mean of 5 batches queued back to back so that the
+    host's preparation of a batch overlaps the device's work on the one
+    before, as in the headline line)."""
     import numpy as np
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def timed(qs, **cfg):
-        base = opt.get_config()
-        opt.set_config(**cfg)
-        stats = [p.stats for p in opt.optimize_batch(qs)]
+    def timed(qs, o=None, **cfg):
+        opt_ = o if o is not None else opt
+        base = opt_.get_config()
+        opt_.set_config(**cfg)
+        stats = [p.stats for p in opt_.optimize_batch(qs)]
         d_card = torch.tensor([c for q in qs for c in q.card], dtype=torch.float64, device="cuda")
         d_edges = torch.from_numpy(mpdp.pack_edges([e for q in qs for e in q.edges]).view(np.uint8).copy()).cuda()
         nq = len(qs)
@@ -701,21 +705,20 @@ def ablation_line(opt, torch, mpdp, W):
         d_cost = torch.zeros(nq, dtype=torch.float64, device="cuda")
         d_status = torch.zeros(nq, dtype=torch.int32, device="cuda")
         ns, ms = [q.n for q in qs], [len(q.edges) for q in qs]
-        run = lambda: opt.optimize_batch_device(ns, ms, d_card, d_edges, d_nodes, d_cost, d_status)
+        run = lambda: opt_.optimize_batch_device(ns, ms, d_card, d_edges, d_nodes, d_cost, d_status)
         run()
         torch.cuda.synchronize()
-        total = 0.0
-        for _ in range(3):
+        events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a, b in events:
             flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             run()
             b.record(stream)
-            torch.cuda.synchronize()
-            total += a.elapsed_time(b)
+        torch.cuda.synchronize()
+        total = sum(a.elapsed_time(b) for a, b in events)
         assert int((d_status != 0).sum().item()) == 0
-        opt.set_config(**base)
-        return total / 3, sum(int(st["pairs_evaluated"]) for st in stats), d_cost.cpu().numpy()
+        opt_.set_config(**base)
+        return total / len(events), sum(int(st["pairs_evaluated"]) for st in stats), d_cost.cpu().numpy()
 
     out = {}
     for name, qs in (("star20", [W.star(20, seed=0)]), ("snowflake20_x64", [W.snowflake(20, seed=i) for i in range(64)]),
@@ -738,6 +741,22 @@ def ablation_line(opt, torch, mpdp, W):
         t_off, _, c_off = timed(qs, fuse_prune=0, lanes=1)
         assert np.array_equal(c_on, c_off)
         out[f"fusion_{name}"] = {"fused_ms": t_on, "unfused_ms": t_off, "gain": t_off / t_on}
+    # memo: the paper's per-level open-addressing tables (Sec. 5) against the
+    # dense bitmap-indexed memo (the default), same kernels otherwise
+    hopt = mpdp.Optimizer(torch.cuda.current_device(), stream=stream.cuda_stream, memo_kind=mpdp.MEMO_HASH)
+    try:
+        # (a device batch reserves each query's tables from the level sizes
+        # C(n, k), about 2 GB at 25 relations, so the batches here are of
+        # 20 and 16 relations)
+        for name, qs in (("snowflake20_x64", [W.snowflake(20, seed=i) for i in range(64)]),
+                         ("star20", [W.star(20, seed=0)]),
+                         ("cyclic16_x64", [W.cyclic(16, seed=i) for i in range(64)])):
+            t_d, _, c_d = timed(qs)
+            t_h, _, c_h = timed(qs, o=hopt)
+            assert np.array_equal(c_d, c_h)
+            out[f"memo_{name}"] = {"dense_ms": t_d, "hash_ms": t_h, "hash_over_dense": t_h / t_d}
+    finally:
+        hopt.close()
     # lanes: one device batch as concurrent sub-batches (a project addition)
     for name, qs in (("snowflake25_x64", [W.snowflake(25, seed=i) for i in range(64)]),
                      ("cyclic20_x64", [W.cyclic(20, seed=i) for i in range(64)])):
