@@ -23,9 +23,8 @@ CPU_SOURCE = "mpdp_cpu.c"
 CPU_LIB_PATH = os.path.join(OUT_DIR, "libmpdp_cpu.so")
 SOURCES = ["mpdp_kernels.cu", "mpdp_api.cu", "mpdp_noalloc.cu", "mpdp_server.cu", "mpdp_xd.cu",
            "mpdp_heuristic.cu", "mpdp_mlp.cu", "mpdp_probe.cu", "mpdp_persist.cu"]
-# per-file extra flags: the persistent serving kernel reads memory that other
-# blocks of the same launch wrote, so its plain global loads skip the L1
-EXTRA_FLAGS = {"mpdp_persist.cu": ["-Xptxas", "-dlcm=cg"]}
+# per-file extra nvcc flags (none at present)
+EXTRA_FLAGS = {}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fno-fast-math", "-I", os.path.join(ROOT, "include")]

@@ -14,10 +14,15 @@
 // read-only path (MPDP_LDG) and pointers to it are restrict-qualified.  A
 // kernel that writes and reads the same memory across its own lifetime (the
 // persistent serving kernel) defines MPDP_COHERENT_LOADS before including
-// this header: its read-only loads then go to the L2 (ld.global.cg), which
-// every SM sees coherently, and no pointer is marked restrict.
+// this header: its loads are then plain global loads (never the
+// non-coherent read-only path) and no pointer is marked restrict.  Such a
+// kernel reads memory that another block wrote only after acquiring it: the
+// writer fences before it publishes (a phase word, an arrival count) and
+// the reader fences (__threadfence, a GPU-scope fence) after it observes the
+// publication, so under the PTX memory model its later loads, L1 hits
+// included, see the published writes.
 #ifdef MPDP_COHERENT_LOADS
-#define MPDP_LDG(p) __ldcg(p)
+#define MPDP_LDG(p) (*(p))
 #define MPDP_RESTRICT
 #else
 #define MPDP_LDG(p) __ldg(p)

@@ -41,9 +41,13 @@
 //
 // Memory written and read within this one launch (the memo, lists, counters
 // and records of a slot, reused by later requests) must never be read
-// through a stale L1 line, so this file is compiled with plain global loads
-// cached in the L2 only (-dlcm=cg) and with MPDP_COHERENT_LOADS (read-only
-// loads through the L2, no restrict pointers).
+// through a stale L1 line.  MPDP_COHERENT_LOADS keeps every load a plain
+// global load (no non-coherent read-only path, no restrict pointers), and
+// every read of another block's writes follows an acquire: a block runs a
+// tile only after its claim (an atomic on the slot word that the phase's
+// publisher wrote after a fence) and a GPU-scope fence, so the PTX memory
+// model makes the phase's inputs, and a reused slot's new contents, visible
+// to it, L1 included.
 #define MPDP_COHERENT_LOADS
 #define MPDP_PHASES_ONLY
 #include "mpdp_kernels.cu"
