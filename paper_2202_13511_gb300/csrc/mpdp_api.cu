@@ -253,8 +253,9 @@ static QuerySize query_size(int n, int enumeration, int memo_kind)
 {
     QuerySize z;
     z.lists = list_entries(n);
-    // block mode: the connectivity bitmap (2^n bits) follows the level lists
-    if (enumeration == MPDP_ENUM_BLOCKS) z.lists += conn_words(n);
+    // block mode: the connectivity bitmap (2^n bits) follows the level lists,
+    // then the block CCP lists
+    if (enumeration == MPDP_ENUM_BLOCKS) z.lists += conn_words(n) + block_list_words(n, enumeration);
     z.heavy = enumeration == MPDP_ENUM_BLOCKS ? binom_host(n, n / 2) : 0;
     if (memo_kind == MPDP_MEMO_DENSE) z.memo = (size_t)1 << n;
     else z.hash = hash_arena_slots(n);
@@ -742,6 +743,11 @@ static int submit_batch(mpdp_ctx* ctx, const std::vector<PlanQuery>& qs, bool ho
         // queries it serves (the unranking filter forms no bitmap)
         d.use_conn = (q.enumeration == MPDP_ENUM_BLOCKS && ctx->cfg.filter != MPDP_FILTER_UNRANK) ? 1u : 0u;
         d.conn_base = lbase + list_entries(q.n);
+        // block CCP lists, except in the DPSUB ablation (which enumerates every
+        // bipartition of the whole set)
+        d.use_bl = (block_list_words(q.n, q.enumeration) > 0 && ctx->cfg.enumeration != MPDP_ENUM_DPSUB) ? 1u : 0u;
+        d.bl_base = d.conn_base + conn_words(q.n);
+        if (d.use_bl) bp.block_lists = true;
         lbase += z.lists;
         mbase += z.memo;
         hbase += z.heavy;

@@ -168,8 +168,37 @@ struct QDesc {
     // every word.  use_conn = 0: no bitmap, the evaluation tests sets itself.
     unsigned long long conn_base;
     uint32_t use_conn;
-    uint32_t pad_conn;
+    // Block CCP lists (block mode, batched path; see kBlTab): use_bl = 1 when
+    // the query has the area at list word bl_base, else every lookup misses.
+    uint32_t use_bl;
+    unsigned long long bl_base;
 };
+
+// Block CCP lists.  The CCP bipartitions of a block B of G[S] depend on B
+// alone, and a block of three or more relations is itself a connected,
+// 2-connected set of an earlier level; a cyclic query has few of those
+// (about 15 at 20 relations with 10-30 % extra edges, 85 at 25) against
+// the 10^5-10^6 connected sets that contain them.  Before the levels, the
+// query's 2-connected sets that are not cliques (a clique's bipartitions are
+// all CCPs) are found and each one's CCP left sides listed once; a set's
+// evaluation then folds a listed block's CCPs instead of enumerating its
+// 2^(|B|-1) - 1 bipartitions.  The lists are a cache: a block that is not
+// listed (larger than kBlMaxBlock, or the table or the store full) is
+// enumerated as before, with the same result.
+// Area words: [0] sets found, [1] left sides reserved, [2, 4) unused,
+// [4, kBlHead) slots {key B, first left side, count, 0} (open addressing on
+// fmix32(B), key 0 empty), then kBlTab sets found, then kBlLbs left sides.
+constexpr uint32_t kBlTab = 1024;
+constexpr uint32_t kBlLbs = 65536;
+constexpr uint32_t kBlHead = 4u + 4u * kBlTab;
+constexpr uint32_t kBlWords = kBlHead + kBlTab + kBlLbs;
+// Queries below kBlMinRels have no lists (on cyclic-16 the two extra
+// launches cost more than they save), and blocks above kBlMaxBlock are not
+// listed (one thread block lists a block, and every level waits for the
+// listing: a block of 18 relations would hold them back longer than its
+// enumeration costs the sets that contain it).
+constexpr int kBlMinRels = 18;
+constexpr int kBlMaxBlock = 14;
 
 // A heavy set (more than heavy_threshold pairs) is cut into nch chunks of
 // its pair index space, each taken by one warp.  Chunk 0 is the main entry;

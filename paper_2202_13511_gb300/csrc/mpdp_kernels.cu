@@ -317,6 +317,12 @@ static __device__ void ingest_body(const BatchArgs& a, int dense, uint32_t bid, 
         memo.bind(a, qi);
         if (tid < n) memo.put(1u << tid, 1, 0.0, s_card[tid], 0u, cnt);
     }
+    {
+        // block CCP lists of this batch: counters and table empty
+        const QDesc& d = a.desc[qi];
+        if (d.use_bl)
+            for (uint32_t i = tid; i < kBlHead; i += blockDim.x) a.lists[d.bl_base + i] = 0u;
+    }
     for (int e = tid; e < 4 * 256; e += blockDim.x) {
         const int b = e >> 8, x = e & 255;
         uint32_t u = 0u, c = 0u;
@@ -1340,6 +1346,144 @@ __global__ void __launch_bounds__(kEvalThreads) k_prune_tree(BatchArgs a, int k,
 #endif
 
 // ---------------------------------------------------------------------------
+// Block CCP lists (the cache described at kBlTab).  Lookup of block b in a
+// query's area: the first left side and the count, false when b is not
+// listed.
+__device__ __forceinline__ bool bl_find(const uint32_t* MPDP_RESTRICT area, uint32_t b, uint32_t& off, uint32_t& cnt)
+{
+    uint32_t h = fmix32(b) & (kBlTab - 1u);
+    for (uint32_t i = 0; i < kBlTab; i++) {
+        const uint32_t* e = area + 4u + 4u * h;
+        const uint32_t key = MPDP_LDG(e);
+        if (key == b) {
+            off = MPDP_LDG(e + 1);
+            cnt = MPDP_LDG(e + 2);
+            return true;
+        }
+        if (key == 0u) return false;
+        h = (h + 1u) & (kBlTab - 1u);
+    }
+    return false;
+}
+
+#ifndef MPDP_PHASES_ONLY
+// The query's connected sets of 3 to kBlMaxBlock relations (all levels, a
+// thread per set) that are 2-connected and not cliques, appended to the
+// area's set array: S is 2-connected when S \ {x} stays connected for every
+// member x, one bit of the connectivity bitmap each.
+__global__ void __launch_bounds__(256) k_block_detect(BatchArgs a)
+{
+    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    const uint32_t tiles = block_prefix(a.nq, s_pref, [&](int q) -> uint32_t {
+        const QDesc& d = a.desc[q];
+        const DevCounters& c = a.out[q].counters;
+        if (!d.use_bl || c.status != 0) return 0u;
+        uint32_t t = 0u;
+        for (int k = 3; k <= d.n && k <= kBlMaxBlock; k++) t += (c.list_count[k] + 255u) / 256u;
+        return t;
+    });
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int qi = find_q(s_pref, a.nq, t);  // block-uniform
+        const QDesc& d = a.desc[qi];
+        const DevCounters& c = a.out[qi].counters;
+        uint32_t r = t - s_pref[qi];
+        int k = 3;
+        for (; k <= d.n && k <= kBlMaxBlock; k++) {
+            const uint32_t lt = (c.list_count[k] + 255u) / 256u;
+            if (r < lt) break;
+            r -= lt;
+        }
+        const uint32_t idx = r * 256u + threadIdx.x;
+        if (k > d.n || k > kBlMaxBlock || idx >= c.list_count[k]) continue;
+        const DevQuery* MPDP_RESTRICT q = a.query + qi;
+        const uint32_t s = a.lists[d.list_base + d.list_off[k] + idx];
+        if (is_clique(s, q->adj)) continue;
+        const uint32_t* MPDP_RESTRICT cw = conn_bitmap(a, qi);
+        bool two = true;
+        for (uint32_t x = s; x != 0u && two; x &= x - 1u) two = conn_of(s & ~(x & (0u - x)), cw, q->adj);
+        if (!two) continue;
+        uint32_t* area = a.lists + d.bl_base;
+        const uint32_t i = atomicAdd(&area[0], 1u);
+        if (i < kBlTab) area[kBlHead + i] = s;
+    }
+}
+
+// One block per set B found by k_block_detect: its bipartitions (lb holding
+// min(B), lb != B) are split over the threads in contiguous runs (the first
+// lb of a run by deposit, the next by stepping to the next submask); a
+// first pass counts the CCPs (lb and rb both connected), the block reserves
+// room in the store, a second pass writes the left sides, and B goes into
+// the table.  No room left: B stays unlisted.
+__global__ void __launch_bounds__(256) k_block_list(BatchArgs a)
+{
+    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    __shared__ uint32_t s_found[256], s_off[257];
+    __shared__ uint32_t s_base, s_total;
+    const uint32_t items = block_prefix(a.nq, s_pref, [&](int q) -> uint32_t {
+        const QDesc& d = a.desc[q];
+        if (!d.use_bl || a.out[q].counters.status != 0) return 0u;
+        const uint32_t f = a.lists[d.bl_base];
+        return f < kBlTab ? f : kBlTab;
+    });
+    for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int qi = find_q(s_pref, a.nq, it);  // block-uniform
+        const QDesc& d = a.desc[qi];
+        const DevQuery* MPDP_RESTRICT q = a.query + qi;
+        const uint32_t* MPDP_RESTRICT cw = conn_bitmap(a, qi);
+        uint32_t* area = a.lists + d.bl_base;
+        const uint32_t b = area[kBlHead + (it - s_pref[qi])];
+        const uint32_t mn = b & (0u - b), rest = b ^ mn;
+        const uint32_t total = block_pairs(b);
+        const uint32_t per = (total + blockDim.x - 1u) / blockDim.x;
+        const uint32_t i0 = threadIdx.x * per < total ? threadIdx.x * per : total;
+        const uint32_t i1 = i0 + per < total ? i0 + per : total;
+        uint32_t found = 0u;
+        {
+            uint32_t sub = i0 < i1 ? deposit(i0, rest) : 0u;
+            for (uint32_t i = i0; i < i1; i++, sub = (sub - rest) & rest) {
+                const uint32_t lb = mn | sub, rb = b ^ lb;
+                if (conn_of(lb, cw, q->adj) && conn_of(rb, cw, q->adj)) found++;
+            }
+        }
+        s_found[threadIdx.x] = found;
+        __syncthreads();
+        const uint32_t all = block_prefix((int)blockDim.x, s_off, [&](int i) { return s_found[i]; });
+        if (threadIdx.x == 0) {
+            // once the store is full no block adds to its count (no wrap)
+            const uint32_t used = *reinterpret_cast<volatile uint32_t*>(&area[1]);
+            s_base = (all <= kBlLbs && used < kBlLbs) ? atomicAdd(&area[1], all) : kBlLbs + 1u;
+            s_total = all;
+        }
+        __syncthreads();
+        const uint32_t base = s_base;
+        if (base <= kBlLbs && s_total <= kBlLbs - base) {  // block-uniform
+            uint32_t* lbs = area + kBlHead + kBlTab + base + s_off[threadIdx.x];
+            uint32_t w = 0u;
+            uint32_t sub = i0 < i1 ? deposit(i0, rest) : 0u;
+            for (uint32_t i = i0; i < i1 && w < found; i++, sub = (sub - rest) & rest) {
+                const uint32_t lb = mn | sub, rb = b ^ lb;
+                if (conn_of(lb, cw, q->adj) && conn_of(rb, cw, q->adj)) lbs[w++] = lb;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t h = fmix32(b) & (kBlTab - 1u);
+                for (uint32_t i = 0; i < kBlTab; i++) {
+                    uint32_t* e = area + 4u + 4u * h;
+                    if (atomicCAS(e, 0u, b) == 0u) {
+                        e[1] = base;
+                        e[2] = s_total;
+                        break;
+                    }
+                    h = (h + 1u) & (kBlTab - 1u);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+#endif
+
+// ---------------------------------------------------------------------------
 // a4-a8, general join graphs (Algorithm 4), thread per set for light sets.
 // For each block B of G[S] and each lb (min(B) in lb, lb != B): rb = B \ lb;
 // the CCP block keeps the pair when lb and rb both induce connected subgraphs
@@ -1388,6 +1532,7 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
         DevCounters* cnt = &a.out[qi].counters;
         const QDesc& d = a.desc[qi];
         const uint32_t* MPDP_RESTRICT cw = conn_bitmap(a, qi);
+        const uint32_t* MPDP_RESTRICT blist = d.use_bl ? a.lists + d.bl_base : nullptr;
         const uint32_t idx = (t - s_pref[qi]) * kEvalThreads + threadIdx.x;
         bool to_heavy = false;
         uint32_t s = 0u, want = 0u;  // want: extra chunks asked for
@@ -1398,13 +1543,19 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
             // pairs: the set's bipartitions; work: what a thread pays for
             // them, a clique block's pairs at 1/kCliqueWeight (no
             // connectivity test, every pair a CCP)
-            uint32_t pairs = 0u, work = 0u, cliq = 0u;  // cliq: bit j, block j is a clique
+            // listed: bit j, block j's CCPs come from the block CCP lists
+            // (its work then their count)
+            uint32_t pairs = 0u, work = 0u, cliq = 0u, listed = 0u;  // cliq: bit j, block j is a clique
             for (int j = 0; j < nb; j++) {
                 const uint32_t p = block_pairs(blk[j]);
                 pairs += p;
+                uint32_t off = 0u, nl = 0u;
                 if (!a.dpsub && !side[j] && is_clique(blk[j], sq.adj)) {
                     cliq |= 1u << j;
                     work += full ? (p + kCliqueWeight - 1u) / kCliqueWeight : p;
+                } else if (blist && !side[j] && bl_find(blist, blk[j], off, nl)) {
+                    listed |= 1u << j;
+                    work += nl;
                 } else {
                     work += p;
                 }
@@ -1426,6 +1577,18 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
                         // a bridge: its one pair is a CCP, the lower vertex's side known
                         ccp++;
                         fold_pair(side[j], s ^ side[j], memo, cnt, bx, bl);
+                        continue;
+                    }
+                    if (listed >> j & 1u) {  // its CCPs, listed once for the query
+                        uint32_t off = 0u, nl = 0u;
+                        bl_find(blist, b, off, nl);
+                        const uint32_t* MPDP_RESTRICT lbs = blist + kBlHead + kBlTab + off;
+                        for (uint32_t i = 0; i < nl; i++) {
+                            const uint32_t lb = MPDP_LDG(&lbs[i]);
+                            ccp++;
+                            const uint32_t sl = left_side(s, lb, b ^ lb, sq.adj);
+                            fold_pair(sl, s ^ sl, memo, cnt, bx, bl);
+                        }
                         continue;
                     }
                     const uint32_t mn = b & (0u - b), rest = b ^ mn;
@@ -1850,6 +2013,10 @@ size_t list_entries(int n)
 }
 
 size_t conn_words(int n) { return n >= 5 ? (size_t)1 << (n - 5) : 1; }
+size_t block_list_words(int n, int enumeration)
+{
+    return (enumeration == MPDP_ENUM_BLOCKS && n >= kBlMinRels) ? kBlWords : 0;
+}
 
 size_t hash_arena_slots(int n)
 {
@@ -1932,6 +2099,12 @@ static void launch_levels(const BatchArgs& a, const BatchPlan& bp, Memo memo, cu
         HookScope hs(hook, MPDP_KC_MEMO_INIT, st);
         k_level_prefix<<<2 * (a.max_n - 1), 256, 0, st>>>(a, bp.level_pref, bp.group_threads);
         launches++;
+    }
+    if (bp.block_lists) {  // block CCP lists, before the levels that read them
+        HookScope hs(hook, MPDP_KC_EVAL, st);
+        k_block_detect<<<cap_blocks, 256, 0, st>>>(a);
+        k_block_list<<<cap_blocks, 256, 0, st>>>(a);
+        launches += 2;
     }
     for (int k = 2; k <= a.max_n; k++) {
         const unsigned long long tree_tiles = bp.tree_tiles[k], block_tiles = bp.block_tiles[k];

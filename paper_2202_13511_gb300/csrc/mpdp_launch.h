@@ -28,6 +28,7 @@ struct BatchPlan {
     uint32_t group_threads = 1u << 18;  // tree levels: groups of lanes while sets x G <= this (0: never)
     PairRec* pairs = nullptr;  // non-null: tree levels run unfused (evaluate, then prune + scatter)
     uint32_t* level_pref = nullptr;  // [2][kLevels][kMaxBatch + 1]: per-level tile prefix, tree then block mode
+    bool block_lists = false;  // some block-mode query of the lane has block CCP lists
     unsigned long long tree_tiles[kLevels] = {};   // upper bound of level-k tiles, tree queries
     unsigned long long block_tiles[kLevels] = {};  // same, block-mode queries
     unsigned long long block_sets[kLevels] = {};   // upper bound of level-k heavy tiles (8 chunks), block-mode queries
@@ -48,6 +49,8 @@ unsigned long long unfused_pair_records(const BatchPlan& bp);
 size_t list_entries(int n);
 // words of a block-mode query's connectivity bitmap (2^n bits, at least one word)
 size_t conn_words(int n);
+// List words of a query's block CCP lists (0 when it has none).
+size_t block_list_words(int n, int enumeration);
 size_t hash_arena_slots(int n);
 // Per-level list offsets and filter warp ranges of one query; returns the
 // query's filter block count in filter_blocks.

@@ -4,6 +4,8 @@ The bar is bit-exact: optimal cost bits, chosen plan, every compared memo
 entry (cost and left mask) and the integer counters (connected sets, CCP
 pairs and evaluated pairs per level).
 """
+import itertools
+
 import numpy as np
 import pytest
 
@@ -194,6 +196,64 @@ def test_heavy_path_and_ccc(opt, threshold, ccc):
     for q in (W.cyclic(12, seed=3), W.clique(9, seed=1), W.cycle(11, seed=2)):
         bc, _ = oracle.block_enum_counts(q)
         check(opt, q, block_counts=bc)
+
+
+def _dense_graph(n, p, seed):
+    """Random graph: a path through all relations plus every other pair with
+    probability p (seeded SplitMix64), cards and sels as the generators draw
+    them."""
+    rng = W.SplitMix64(seed)
+    card = [10.0 ** (2.0 + 6.0 * rng.uniform()) for _ in range(n)]
+    pairs = [(i, i + 1) for i in range(n - 1)]
+    pairs += [(i, j) for i in range(n) for j in range(i + 2, n) if rng.uniform() < p]
+    edges = [(u, v, 10.0 ** (-6.0 + 5.0 * rng.uniform())) for (u, v) in pairs]
+    return W.Query(n=n, card=card, edges=edges, kind="dense", seed=seed)
+
+
+def _two_connected_non_cliques(q, sizes):
+    """Vertex sets of the given sizes whose induced subgraph is 2-connected
+    and not complete (brute force over the subsets)."""
+    adj = [0] * q.n
+    for u, v, _ in q.edges:
+        adj[u] |= 1 << v
+        adj[v] |= 1 << u
+
+    def connected(s):
+        seen = s & -s
+        frontier = seen
+        while frontier:
+            nb = 0
+            x = frontier
+            while x:
+                low = x & -x
+                nb |= adj[low.bit_length() - 1]
+                x ^= low
+            frontier = nb & s & ~seen
+            seen |= frontier
+        return seen == s
+
+    count = 0
+    for k in sizes:
+        for members in itertools.combinations(range(q.n), k):
+            s = sum(1 << v for v in members)
+            if all((adj[v] & s) == s & ~(1 << v) for v in members):
+                continue  # a clique
+            if connected(s) and all(connected(s & ~(1 << v)) for v in members):
+                count += 1
+    return count
+
+
+def test_block_lists_overflow_falls_back(opt):
+    """A dense 18-relation graph has more 2-connected non-clique sets of at
+    most 14 relations than the block CCP lists' table holds (1,024 slots;
+    1,163 of 4-6 relations alone), so some blocks stay unlisted and are
+    enumerated: the oracle's costs, plans, CCP counts and memo entries all
+    the same.  A 19-relation graph of lower density lists its blocks."""
+    q = _dense_graph(18, 0.35, seed=11)
+    assert _two_connected_non_cliques(q, (4, 5, 6)) > 1024
+    check(opt, q, memo="sample")
+    q = _dense_graph(19, 0.25, seed=12)
+    check(opt, q, memo="sample")
 
 
 @pytest.mark.parametrize("run", [1, 5, 32])
