@@ -1494,7 +1494,9 @@ __global__ void __launch_bounds__(256) k_block_list(BatchArgs a)
 // clique block at 1/kCliqueWeight: each is a CCP with no connectivity test,
 // and sets of up to about a thousand of them then run faster here than on
 // the warp path (measured on clique-14; with fewer sets per level, as on
-// clique-12, the warp path's spread wins).
+// clique-12, the warp path's spread wins).  On a level with fewer sets the
+// threshold is halved: a set's thread then works alone at the end of the
+// level, and the warp path's split of its CCPs over 32 lanes is shorter.
 constexpr uint32_t kCliqueWeight = 16u;
 constexpr uint32_t kFullLevelSets = 16384u;
 template <class Memo>
@@ -1545,7 +1547,9 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
             // connectivity test, every pair a CCP)
             // listed: bit j, block j's CCPs come from the block CCP lists
             // (its work then their count)
-            uint32_t pairs = 0u, work = 0u, cliq = 0u, listed = 0u;  // cliq: bit j, block j is a clique
+            // index: the warp path's pair index space (a listed block's CCPs,
+            // any other block's bipartitions)
+            uint32_t pairs = 0u, work = 0u, index = 0u, cliq = 0u, listed = 0u;  // cliq: bit j, block j is a clique
             for (int j = 0; j < nb; j++) {
                 const uint32_t p = block_pairs(blk[j]);
                 pairs += p;
@@ -1553,17 +1557,20 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
                 if (!a.dpsub && !side[j] && is_clique(blk[j], sq.adj)) {
                     cliq |= 1u << j;
                     work += full ? (p + kCliqueWeight - 1u) / kCliqueWeight : p;
+                    index += p;
                 } else if (blist && !side[j] && bl_find(blist, blk[j], off, nl)) {
                     listed |= 1u << j;
                     work += nl;
+                    index += nl;
                 } else {
                     work += p;
+                    index += p;
                 }
             }
-            if (a.dpsub) pairs = work = block_pairs(s);  // the whole set as one block
-            if (work > (uint32_t)a.heavy_threshold) {
+            if (a.dpsub) pairs = work = index = block_pairs(s);  // the whole set as one block
+            if (work > (full ? (uint32_t)a.heavy_threshold : (uint32_t)a.heavy_threshold / 2u)) {
                 to_heavy = true;
-                const uint32_t nch = (pairs - 1u) / kChunkPairs + 1u;
+                const uint32_t nch = (index - 1u) / kChunkPairs + 1u;
                 want = (nch < kMaxChunks ? nch : kMaxChunks) - 1u;
             } else {
                 const double card_s = peel_card(s, block_peel_vertex(s, blk, nb), sq, memo, cnt);
@@ -1684,6 +1691,8 @@ __device__ void eval_heavy_body(const BatchArgs& a, int k, Memo memo, uint32_t b
     __shared__ int s_nb[kWarps];
     __shared__ int s_pv[kWarps];
     __shared__ uint32_t s_cliq[kWarps];  // bit j: block j is a clique
+    __shared__ uint32_t s_list[kWarps];  // bit j: block j's CCPs are listed (block CCP lists)
+    __shared__ uint32_t s_loff[kWarps][kMaxRels];  // first listed left side of block j
     __shared__ uint32_t s_stash_l[kWarps][64];
     __shared__ uint32_t s_stash_r[kWarps][64];
     memo.setup(s_memo);
@@ -1730,17 +1739,33 @@ __device__ void eval_heavy_body(const BatchArgs& a, int k, Memo memo, uint32_t b
                 s_blk[warp][0] = s;
                 nb = 1;
             }
-            uint32_t acc = 0u, cliq = 0u;
+            // pair index space: a listed block contributes its CCPs, any
+            // other block all its bipartitions (the evaluated counter counts
+            // the bipartitions either way)
+            const uint32_t* MPDP_RESTRICT blist = d.use_bl ? a.lists + d.bl_base : nullptr;
+            uint32_t acc = 0u, cliq = 0u, listed = 0u, paper = 0u;
             for (int j = 0; j < nb; j++) {
+                const uint32_t b = s_blk[warp][j], p = block_pairs(b);
+                uint32_t off = 0u, nl = 0u;
                 s_bpref[warp][j] = acc;
-                acc += block_pairs(s_blk[warp][j]);
-                if (is_clique(s_blk[warp][j], sq.adj)) cliq |= 1u << j;
+                paper += p;
+                if (is_clique(b, sq.adj)) {
+                    cliq |= 1u << j;
+                    acc += p;
+                } else if (blist && __popc(b) > 2 && bl_find(blist, b, off, nl)) {
+                    listed |= 1u << j;
+                    s_loff[warp][j] = off;
+                    acc += nl;
+                } else {
+                    acc += p;
+                }
             }
             s_cliq[warp] = cliq;
+            s_list[warp] = listed;
             s_bpref[warp][nb] = acc;
             s_nb[warp] = nb;
             if (chunk == 0u) {
-                evaluated += acc;
+                evaluated += paper;
                 heavy++;
             }
         }
@@ -1752,7 +1777,8 @@ __device__ void eval_heavy_body(const BatchArgs& a, int k, Memo memo, uint32_t b
         const uint32_t lo = (uint32_t)((unsigned long long)total * chunk / nch);
         const uint32_t hi = (uint32_t)((unsigned long long)total * (chunk + 1u) / nch);
         const uint32_t* MPDP_RESTRICT cw = conn_bitmap(a, qi);
-        const uint32_t cliq = s_cliq[warp];
+        const uint32_t cliq = s_cliq[warp], listed = s_list[warp];
+        const uint32_t* MPDP_RESTRICT lbs = d.use_bl ? a.lists + d.bl_base + kBlHead + kBlTab : nullptr;
         unsigned long long bx = kNoX;
         uint32_t bl = kFull;
         uint32_t stash = 0u;  // warp-uniform stash fill
@@ -1765,22 +1791,29 @@ __device__ void eval_heavy_body(const BatchArgs& a, int k, Memo memo, uint32_t b
         int j = 0;
         while (j + 1 < nb && bpref[j + 1] <= p) j++;
         uint32_t b = blk[j], mn = b & (0u - b), rest = b ^ mn;
-        uint32_t sub = p < pend ? deposit(p - bpref[j], rest) : 0u;
+        bool lst = (listed >> j) & 1u;
+        uint32_t sub = (p < pend && !lst) ? deposit(p - bpref[j], rest) : 0u;
         for (uint32_t round = 0; round < per; round++) {  // warp-uniform trip count
             bool valid = false;
             uint32_t lb = 0u, rb = 0u;
             if (p < pend) {
-                lb = mn | sub;
+                if (lst) {  // a listed CCP
+                    lb = MPDP_LDG(&lbs[s_loff[warp][j] + (p - bpref[j])]);
+                    valid = true;
+                } else {
+                    lb = mn | sub;
+                    valid = ((cliq >> j) & 1u) || (conn_of(lb, cw, sq.adj) && conn_of(b ^ lb, cw, sq.adj));
+                    sub = (sub - rest) & rest;
+                }
                 rb = b ^ lb;
-                valid = ((cliq >> j) & 1u) || (conn_of(lb, cw, sq.adj) && conn_of(rb, cw, sq.adj));
                 p++;
-                sub = (sub - rest) & rest;
                 if (p < pend && p == bpref[j + 1]) {  // the next block's pairs
                     j++;
                     b = blk[j];
                     mn = b & (0u - b);
                     rest = b ^ mn;
                     sub = 0u;
+                    lst = (listed >> j) & 1u;
                 }
             }
             const unsigned bal = __ballot_sync(kFull, valid);
