@@ -69,11 +69,11 @@ DEVICE_HEADER = "paper_2202_13511_gb300/csrc/mpdp_device.cuh"
 TRAFFIC = {"eval": {"kernel": "k_eval_tree",
                     "helpers": ("eval_tree_body", "find_q", "set_top_of", "group_size", "group_min_x",
                                 "eval_tree_groups", "k_level_prefix", "block_prefix"),
-                    "sha1": "8515ce68ab617bb3fcb4556d1abc5020d41374d2", "bytes": 5350101},
+                    "sha1": "7cc5a26212c0abe6942d1c0daacfd43eb4b39d50", "bytes": 5356371},
            "filter": {"kernel": "k_filter_connected",
                       "helpers": ("filter_connected_body", "unrank_connected", "next_connected", "connected_items",
                                   "block_prefix", "find_q"),
-                      "sha1": "d95c093afea6b0243dc4e80e7a5e02a7dd4a6fa4", "bytes": 16580032}}
+                      "sha1": "0c19976a3275dc4ea796e0c088db6cbbc9a706a5", "bytes": 16601152}}
 
 
 def parse_args():
