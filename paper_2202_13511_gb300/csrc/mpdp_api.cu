@@ -910,7 +910,8 @@ int mpdp_create(mpdp_ctx** out, int device, size_t memo_budget_bytes, void* cuda
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     bool ok = cudaSetDevice(device) == cudaSuccess &&
               cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) == cudaSuccess;
+              cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              configure_kernels() == cudaSuccess;
     for (int i = 0; ok && i < mpdp_ctx::kRing; i++)
         ok = cudaEventCreateWithFlags(&ctx->ring[i].free_ev, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {

@@ -49,6 +49,9 @@ unsigned long long unfused_pair_records(const BatchPlan& bp);
 size_t list_entries(int n);
 // words of a block-mode query's connectivity bitmap (2^n bits, at least one word)
 size_t conn_words(int n);
+// Per-kernel attributes set once per context (the shared-memory carveout of
+// the tree evaluate); no device-wide setting is touched.
+cudaError_t configure_kernels();
 // List words of a query's block CCP lists (0 when it has none).
 size_t block_list_words(int n, int enumeration);
 size_t hash_arena_slots(int n);
