@@ -620,9 +620,10 @@ __device__ __forceinline__ uint32_t connected_items(const BatchArgs& a, int q)
 // next relation when its sets run out).  Places within the block come from
 // shared-memory counters per level, and one global atomic per level present
 // reserves the block's room in that level's list.
+template <int kQ = kMaxBatch>  // kQ: the most queries of a batch it serves
 static __device__ void filter_connected_body(const BatchArgs& a, uint32_t bid, uint32_t nblk)
 {
-    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    __shared__ uint32_t s_pref[kQ + 1];
     __shared__ uint32_t s_cnt[kLevels];
     __shared__ uint32_t s_base[kLevels];
     const uint32_t items = block_prefix(a.nq, s_pref, [&](int q) { return connected_items(a, q); });
@@ -748,13 +749,14 @@ __device__ __forceinline__ void flush_filter_counts(DevCounters* cnt, uint32_t& 
     rounds = 0u;
 }
 
+template <int kQ = kMaxBatch>  // kQ: the most queries of a batch it serves
 static __device__ void filter_bitmaps_body(const BatchArgs& a, uint32_t bid, uint32_t nblk)
 {
     __shared__ uint32_t s_nbt[4][256];
     __shared__ uint32_t s_ctt[4][256];
     __shared__ uint32_t s_stage[kFilterThreads / 32][32];
     __shared__ uint32_t s_run[16];     // DevQuery::lowrun
-    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    __shared__ uint32_t s_pref[kQ + 1];
     // items of kBitmapsPerBlock bitmaps of every query this filter serves,
     // grid-stride; a block reloads the tables when its query changes
     const uint32_t items = block_prefix(a.nq, s_pref, [&](int q) { return bitmap_items(a, q); });
@@ -1120,10 +1122,10 @@ __device__ __forceinline__ void eval_tree_groups(const BatchArgs& a, int k, uint
 // S_r = S \ S_l: one AND per split, no search.  The best (cost, left) over
 // the k-1 splits is written to the memo: evaluate, prune and scatter fused
 // in one pass, one memo write per set.
-template <class Memo>
+template <class Memo, int kQ = kMaxBatch>  // kQ: the most queries of a batch it serves
 __device__ void eval_tree_body(const BatchArgs& a, int k, Memo memo, const uint32_t* MPDP_RESTRICT level_pref, uint32_t bid, uint32_t nblk)
 {
-    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    __shared__ uint32_t s_pref[kQ + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     const uint32_t G = level_pref[k * kPrefStride + kMaxBatch + 1];
     {
@@ -1135,7 +1137,7 @@ __device__ void eval_tree_body(const BatchArgs& a, int k, Memo memo, const uint3
     for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) s_pref[i] = level_pref[k * kPrefStride + i];
     __syncthreads();
     if (G) {  // groups of G lanes per set (s_pref: set prefix); block-uniform
-        __shared__ uint32_t s_sets[kMaxBatch];  // sets evaluated per query
+        __shared__ uint32_t s_sets[kQ];  // sets evaluated per query
         for (int i = threadIdx.x; i < a.nq; i += blockDim.x) s_sets[i] = 0u;
         __syncthreads();
         eval_tree_groups(a, k, G, memo, s_pref, s_sets, bid, nblk);
@@ -1499,11 +1501,11 @@ __global__ void __launch_bounds__(256) k_block_list(BatchArgs a)
 // level, and the warp path's split of its CCPs over 32 lanes is shorter.
 constexpr uint32_t kCliqueWeight = 16u;
 constexpr uint32_t kFullLevelSets = 16384u;
-template <class Memo>
+template <class Memo, int kQ = kMaxBatch>  // kQ: the most queries of a batch it serves
 __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uint32_t* MPDP_RESTRICT level_pref, uint32_t bid, uint32_t nblk)
 {
     __shared__ SharedQuery sq;
-    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    __shared__ uint32_t s_pref[kQ + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     memo.setup(s_memo);
     for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) s_pref[i] = level_pref[(kLevels + k) * kPrefStride + i];
@@ -1679,12 +1681,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
 // invalid pair during the expensive part.  The prune is a warp shuffle
 // reduction of (x, left); a set cut into several chunks is folded by the
 // warp that finishes it last (fence, then an arrival count), with no waiting.
-template <class Memo>
+template <class Memo, int kQ = kMaxBatch>  // kQ: the most queries of a batch it serves
 __device__ void eval_heavy_body(const BatchArgs& a, int k, Memo memo, uint32_t bid, uint32_t nblk)
 {
     constexpr int kWarps = kEvalThreads / 32;
     __shared__ SharedQuery sq;
-    __shared__ uint32_t s_pref[kMaxBatch + 1];
+    __shared__ uint32_t s_pref[kQ + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     __shared__ uint32_t s_blk[kWarps][kMaxRels];
     __shared__ uint32_t s_bpref[kWarps][kMaxRels + 1];

@@ -260,17 +260,18 @@ __device__ bool run_tile(const PArgs& p, int s, unsigned int epoch, unsigned int
         ingest_body(a, 1, 0u, 1u);
         break;
     case PH_FILTER:
-        if (a.query[0].use_connected) filter_connected_body(a, tile, inf.total);
-        else filter_bitmaps_body(a, tile, inf.total);
+        if (a.query[0].use_connected) filter_connected_body<1>(a, tile, inf.total);
+        else filter_bitmaps_body<1>(a, tile, inf.total);
         break;
     case PH_LEVEL:
         if (a.desc[0].enumeration == MPDP_ENUM_TREE)
-            eval_tree_body(a, inf.level, DenseMemo{a.memo, a.left, nullptr, nullptr}, pref, tile, inf.total);
+            eval_tree_body<DenseMemo, 1>(a, inf.level, DenseMemo{a.memo, a.left, nullptr, nullptr}, pref, tile, inf.total);
         else
-            eval_blocks_body(a, inf.level, DensePlainMemo{a.memo, a.left, nullptr, nullptr}, pref, tile, inf.total);
+            eval_blocks_body<DensePlainMemo, 1>(a, inf.level, DensePlainMemo{a.memo, a.left, nullptr, nullptr}, pref, tile,
+                                                inf.total);
         break;
     case PH_HEAVY:
-        eval_heavy_body(a, inf.level, DensePlainMemo{a.memo, a.left, nullptr, nullptr}, tile, inf.total);
+        eval_heavy_body<DensePlainMemo, 1>(a, inf.level, DensePlainMemo{a.memo, a.left, nullptr, nullptr}, tile, inf.total);
         break;
     case PH_EXTRACT:
         fetch_and_publish(p, s, epoch);
