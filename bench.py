@@ -69,11 +69,11 @@ DEVICE_HEADER = "paper_2202_13511_gb300/csrc/mpdp_device.cuh"
 TRAFFIC = {"eval": {"kernel": "k_eval_tree",
                     "helpers": ("eval_tree_body", "find_q", "set_top_of", "group_size", "group_min_x",
                                 "eval_tree_groups", "k_level_prefix", "block_prefix"),
-                    "sha1": "7cc5a26212c0abe6942d1c0daacfd43eb4b39d50", "bytes": 5361275},
+                    "sha1": "d198f892dcab219f3c5deadf5f13672ee2a80437", "bytes": 5364331},
            "filter": {"kernel": "k_filter_connected",
                       "helpers": ("filter_connected_body", "unrank_connected", "next_connected", "connected_items",
                                   "block_prefix", "find_q"),
-                      "sha1": "0c19976a3275dc4ea796e0c088db6cbbc9a706a5", "bytes": 16512704}}
+                      "sha1": "ff2b308fdc930d3c34ae44e794280753c16db872", "bytes": 16632064}}
 
 
 def parse_args():

@@ -1501,10 +1501,15 @@ __global__ void __launch_bounds__(256) k_block_list(BatchArgs a)
 // level, and the warp path's split of its CCPs over 32 lanes is shorter.
 constexpr uint32_t kCliqueWeight = 16u;
 constexpr uint32_t kFullLevelSets = 16384u;
+// The block-mode bodies' staged query.  At file scope, a kernel that runs
+// both bodies (the persistent kernel) holds one copy rather than two; each
+// batched kernel holds its own as before.
+__shared__ SharedQuery g_block_sq;
+
 template <class Memo, int kQ = kMaxBatch>  // kQ: the most queries of a batch it serves
 __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uint32_t* MPDP_RESTRICT level_pref, uint32_t bid, uint32_t nblk)
 {
-    __shared__ SharedQuery sq;
+    SharedQuery& sq = g_block_sq;
     __shared__ uint32_t s_pref[kQ + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     memo.setup(s_memo);
@@ -1685,7 +1690,7 @@ template <class Memo, int kQ = kMaxBatch>  // kQ: the most queries of a batch it
 __device__ void eval_heavy_body(const BatchArgs& a, int k, Memo memo, uint32_t bid, uint32_t nblk)
 {
     constexpr int kWarps = kEvalThreads / 32;
-    __shared__ SharedQuery sq;
+    SharedQuery& sq = g_block_sq;
     __shared__ uint32_t s_pref[kQ + 1];
     __shared__ __align__(16) char s_memo[Memo::kSharedBytes];
     __shared__ uint32_t s_blk[kWarps][kMaxRels];
