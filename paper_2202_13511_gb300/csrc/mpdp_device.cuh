@@ -143,6 +143,9 @@ struct alignas(32) HashSlot {
     double card;     // card(S)
     double pad;
 };
+// The probes read {key, left, cost} and {card, pad} as two 16-byte words.
+static_assert(sizeof(HashSlot) == 32 && offsetof(HashSlot, cost) == 8 && offsetof(HashSlot, card) == 16,
+              "HashSlot layout");
 
 struct HashLayout {
     unsigned long long base[kLevels];  // first slot of level k's table
@@ -507,38 +510,47 @@ struct HashMemo {
     __device__ __forceinline__ void setup(char*) {}
     // per thread; no shared memory involved
     __device__ __forceinline__ void bind(const BatchArgs& a, int q) { lay = a.layout + q; }
-    __device__ __forceinline__ const HashSlot* find(uint32_t s, DevCounters* cnt) const
+    // Probe for S: each step is one 16-byte load of the slot's {key, left,
+    // cost} (and, with `whole`, a second one of its card, issued together:
+    // the same sector), so a hit costs one round of memory latency per probe
+    // step rather than a key load and then a value load.  False (and the
+    // status PROBE_LIMIT) when S is missing.
+    __device__ __forceinline__ bool probe(uint32_t s, bool whole, uint4& head, uint4& tail, DevCounters* cnt) const
     {
         const int lvl = __popc(s);
         const HashSlot* t = arena + MPDP_LDG(&lay->base[lvl]);
         const uint32_t m = MPDP_LDG(&lay->mask[lvl]);
         uint32_t h = fmix32(s) & m;
         for (uint32_t i = 0; i <= m; i++) {
-            const uint32_t key = MPDP_LDG(&t[h].key);
-            if (key == s) return t + h;
-            if (key == 0u) break;
+            const uint4* e = reinterpret_cast<const uint4*>(t + h);
+            head = MPDP_LDG(e);
+            if (whole) tail = MPDP_LDG(e + 1);
+            if (head.x == s) return true;
+            if (head.x == 0u) break;
             h = (h + 1u) & m;
         }
         raise_status(cnt, MPDP_ERR_PROBE_LIMIT);
-        return nullptr;
+        return false;
     }
     __device__ __forceinline__ double get_cost(uint32_t s, DevCounters* cnt) const
     {
-        const HashSlot* e = find(s, cnt);
-        return e ? MPDP_LDG(&e->cost) : __longlong_as_double(0x7ff8000000000000ll);
+        uint4 head, tail;
+        return probe(s, false, head, tail, cnt) ? __hiloint2double((int)head.w, (int)head.z)
+                                                : __longlong_as_double(0x7ff8000000000000ll);
     }
     __device__ __forceinline__ double get_card(uint32_t s, DevCounters* cnt) const
     {
-        const HashSlot* e = find(s, cnt);
-        return e ? MPDP_LDG(&e->card) : __longlong_as_double(0x7ff8000000000000ll);
+        uint4 head, tail;
+        return probe(s, true, head, tail, cnt) ? __hiloint2double((int)tail.y, (int)tail.x)
+                                               : __longlong_as_double(0x7ff8000000000000ll);
     }
     __device__ __forceinline__ void get(uint32_t s, double& c, double& card, uint32_t& l, DevCounters* cnt) const
     {
-        const HashSlot* e = find(s, cnt);
-        if (e) {
-            c = e->cost;
-            card = e->card;
-            l = e->left;
+        uint4 head, tail;
+        if (probe(s, true, head, tail, cnt)) {
+            c = __hiloint2double((int)head.w, (int)head.z);
+            card = __hiloint2double((int)tail.y, (int)tail.x);
+            l = head.y;
         } else {
             c = card = __longlong_as_double(0x7ff8000000000000ll);
             l = 0xffffffffu;
