@@ -960,11 +960,20 @@ def _poisson(srv, queries, sat, fracs, seed):
     return out
 
 
-def _saturated(srv, queries):
+def _saturated(srv, queries, replays=3):
+    """Every query submitted at once: the replay with the median makespan
+    of `replays` (after a warm-up one; a single replay has been seen to fall
+    far below the others)."""
     import numpy as np
     srv.replay(queries, [0.0] * len(queries))  # warm-up
-    _, lat, makespan = srv.replay(queries, [0.0] * len(queries))
+    runs = []
+    for _ in range(replays):
+        _, lat, makespan = srv.replay(queries, [0.0] * len(queries))
+        runs.append((makespan, lat))
+    runs.sort(key=lambda r: r[0])
+    makespan, lat = runs[len(runs) // 2]
     return {"queries_per_s": len(queries) / makespan, "makespan_s": makespan,
+            "replays_queries_per_s": [round(len(queries) / m, 1) for m, _ in runs],
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)}
 
 

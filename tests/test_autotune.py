@@ -28,6 +28,34 @@ def test_coordinate_descent_keeps_start_on_ties():
     assert best == {"a": 2} and t == 5.0
 
 
+def test_confirm_best_times_the_leaders_again():
+    """A configuration that was only lucky in the search loses the second
+    timing of the leaders; the search history is what gets re-timed."""
+    history = [({"a": 1}, 1.0), ({"a": 2}, 0.5), ({"a": 3}, 0.9), ({"a": 4}, 3.0)]
+    again = {1: 0.95, 2: 1.2, 3: 0.85, 4: 0.1}  # a = 4 was not among the three leaders
+    seen = []
+
+    def measure(cfg):
+        seen.append(cfg["a"])
+        return again[cfg["a"]]
+
+    best, t = autotune.confirm_best(history, measure)
+    assert best == {"a": 3} and t == 0.85
+    assert sorted(seen) == [1, 2, 3]
+
+
+def test_tune_server_confirms_with_its_timer():
+    calls = []
+
+    def measure(cfg):
+        calls.append(dict(cfg))
+        return 1.0 + abs(cfg["slots"] - 2) + (0 if cfg["max_batch"] == 64 else 0.5)
+
+    best, t, hist = autotune.tune_server([], measure=measure)
+    assert best == {"slots": 2, "max_batch": 64} and t == 1.0
+    assert len(calls) == len(hist) + 3  # the search, then the three leaders again
+
+
 def test_relevant_space_drops_block_knobs_for_trees():
     trees = [W.snowflake(10, seed=s) for s in range(3)]
     assert set(autotune.relevant_space(trees)) == {"grid_blocks_per_sm", "filter", "lanes",
