@@ -97,7 +97,8 @@ def parse_args():
                         "large, learned, serving (default: all)")
     p.add_argument("--case", default=None,
                    help="kind:n:queries[:lanes[:memo]] -- only run that workload as device batches (warmup + "
-                        "steps of them) and print its status; for profiler captures of one shape")
+                        "steps of them) and print its status; kind:n:queries:persistent -- serve the queries "
+                        "through a persistent server; for profiler captures of one shape")
     return p.parse_args()
 
 
@@ -1064,13 +1065,26 @@ def run_case(args):
     import torch
     parts = args.case.split(":")
     kind, n, nq = parts[0], int(parts[1]), int(parts[2])
-    lanes = int(parts[3]) if len(parts) > 3 else 0
+    persistent = len(parts) > 3 and parts[3] == "persistent"
+    lanes = int(parts[3]) if len(parts) > 3 and not persistent else 0
     memo = parts[4] if len(parts) > 4 else "dense"
     import __graft_entry__
     __graft_entry__.build()
     from paper_2202_13511_gb300 import mpdp
     from paper_2202_13511_gb300 import workloads as W
     torch.cuda.set_device(0)
+    if persistent:
+        # the queries through a persistent server (one slot each), all at once
+        qs = [W.make(kind, n, seed=i) for i in range(nq)]
+        with mpdp.Server(0, persistent=True, slots=nq) as srv:
+            tickets = [srv.submit(q) for q in qs]
+            done = set()
+            while len(done) < len(tickets):
+                done.update(srv.poll())
+            for t in tickets:
+                srv.result(t)  # raises if the device reported an error for it
+        print(json.dumps({"case": args.case, "served": len(tickets), "status": "ok"}))
+        return 0
     opt = mpdp.Optimizer(0, stream=torch.cuda.current_stream().cuda_stream,
                          memo_kind={"dense": mpdp.MEMO_DENSE, "hash": mpdp.MEMO_HASH}[memo])
     if lanes:
