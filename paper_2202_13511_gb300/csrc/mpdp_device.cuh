@@ -190,8 +190,12 @@ struct QDesc {
 // enumerated as before, with the same result.
 // Area words: [0] sets found, [1] left sides reserved, [2, 4) unused,
 // [4, kBlHead) slots {key B, first left side, count, 0} (open addressing on
-// fmix32(B), key 0 empty), then kBlTab sets found, then kBlLbs left sides.
+// fmix32(B), key 0 empty), then room for kBlTab sets found (kBlSets used),
+// then kBlLbs left sides.
 constexpr uint32_t kBlTab = 1024;
+// Sets listed at most: the table stays at most half full, so that a lookup
+// of an unlisted block ends at an empty slot within a few probes.
+constexpr uint32_t kBlSets = kBlTab / 2;
 constexpr uint32_t kBlLbs = 65536;
 constexpr uint32_t kBlHead = 4u + 4u * kBlTab;
 constexpr uint32_t kBlWords = kBlHead + kBlTab + kBlLbs;

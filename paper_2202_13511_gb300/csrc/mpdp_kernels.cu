@@ -1406,7 +1406,7 @@ __global__ void __launch_bounds__(256) k_block_detect(BatchArgs a)
         if (!two) continue;
         uint32_t* area = a.lists + d.bl_base;
         const uint32_t i = atomicAdd(&area[0], 1u);
-        if (i < kBlTab) area[kBlHead + i] = s;
+        if (i < kBlSets) area[kBlHead + i] = s;
     }
 }
 
@@ -1425,7 +1425,7 @@ __global__ void __launch_bounds__(256) k_block_list(BatchArgs a)
         const QDesc& d = a.desc[q];
         if (!d.use_bl || a.out[q].counters.status != 0) return 0u;
         const uint32_t f = a.lists[d.bl_base];
-        return f < kBlTab ? f : kBlTab;
+        return f < kBlSets ? f : kBlSets;
     });
     for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int qi = find_q(s_pref, a.nq, it);  // block-uniform

@@ -245,10 +245,11 @@ def _two_connected_non_cliques(q, sizes):
 
 def test_block_lists_overflow_falls_back(opt):
     """A dense 18-relation graph has more 2-connected non-clique sets of at
-    most 14 relations than the block CCP lists' table holds (1,024 slots;
-    1,163 of 4-6 relations alone), so some blocks stay unlisted and are
-    enumerated: the oracle's costs, plans, CCP counts and memo entries all
-    the same.  A 19-relation graph of lower density lists its blocks."""
+    most 14 relations than the block CCP lists take (512 of them, half the
+    table's 1,024 slots; 1,163 of 4-6 relations alone), so some blocks stay
+    unlisted and are enumerated: the oracle's costs, plans, CCP counts and
+    memo entries all the same.  A 19-relation graph of lower density lists
+    its blocks."""
     q = _dense_graph(18, 0.35, seed=11)
     assert _two_connected_non_cliques(q, (4, 5, 6)) > 1024
     check(opt, q, memo="sample")
