@@ -69,11 +69,11 @@ DEVICE_HEADER = "paper_2202_13511_gb300/csrc/mpdp_device.cuh"
 TRAFFIC = {"eval": {"kernel": "k_eval_tree",
                     "helpers": ("eval_tree_body", "find_q", "set_top_of", "group_size", "group_min_x",
                                 "eval_tree_groups", "k_level_prefix", "block_prefix"),
-                    "sha1": "d198f892dcab219f3c5deadf5f13672ee2a80437", "bytes": 5364331},
+                    "sha1": "e756240fb8f389aa555909921857a9a6fd246d27", "bytes": 5364029},
            "filter": {"kernel": "k_filter_connected",
                       "helpers": ("filter_connected_body", "unrank_connected", "next_connected", "connected_items",
                                   "block_prefix", "find_q"),
-                      "sha1": "ff2b308fdc930d3c34ae44e794280753c16db872", "bytes": 16632064}}
+                      "sha1": "c32640b43cecddede27f22afeafe8acce45574b1", "bytes": 16641920}}
 
 
 def parse_args():
