@@ -23,7 +23,7 @@ from typing import Callable, Dict, List, Optional, Sequence
 
 KERNEL_SPACE: Dict[str, List[int]] = {
     "grid_blocks_per_sm": [2, 4, 8, 16],
-    "heavy_threshold": [16, 64, 256],
+    "heavy_threshold": [16, 32, 64, 256],
     "use_ccc": [0, 1],
     "filter": [2, 0, 1],  # MPDP_FILTER_CONNECTED, _BITMAPS, _UNRANK
     "lanes": [1, 2, 4, 8],
