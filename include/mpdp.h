@@ -183,12 +183,15 @@ typedef struct {
     int32_t enumeration;      /* MPDP_ENUM_AUTO (default), _TREE, _BLOCKS */
     int32_t heavy_threshold;  /* block mode: a set whose work exceeds this goes
                                  to the heavy-set kernel, one warp per chunk of
-                                 at most 2048 pairs (default 64).  Work: each
-                                 block's bipartitions, except that a block whose
-                                 CCPs are listed counts its CCPs and, on a level
-                                 of at least 16384 sets, a clique block counts
-                                 its pairs / 16; on a level with fewer sets the
-                                 limit is half this.  Results do not depend on it. */
+                                 at most 2048 pairs (default 64).  Clique
+                                 blocks: their pairs, / 16 on a level of at
+                                 least 16384 sets, against this limit (half of
+                                 it on a smaller level).  Other blocks: their
+                                 bipartitions, or their CCPs where listed,
+                                 against this limit x the level's sets / 65536,
+                                 kept within a quarter and twice this limit.
+                                 A set with both weighs each part against its
+                                 own limit.  Results do not depend on it. */
     int32_t use_ccc;          /* 1 (default): collaborative context collection
                                  in the heavy-set kernel (Sec. 5) */
     int32_t use_graphs;       /* 1 (default): replay a captured CUDA graph per shape */

@@ -1499,8 +1499,21 @@ __global__ void __launch_bounds__(256) k_block_list(BatchArgs a)
 // clique-12, the warp path's spread wins).  On a level with fewer sets the
 // threshold is halved: a set's thread then works alone at the end of the
 // level, and the warp path's split of its CCPs over 32 lanes is shorter.
+// The work of the other blocks (candidate bipartitions, listed CCPs) meets a
+// limit that follows the level's size: heavy_threshold * slots / kNcRefSlots
+// for a level of `slots` thread slots, clamped to [kFullLevelSets,
+// kNcMaxSlots] (a quarter to twice heavy_threshold).  On a level that leaves
+// most of the GPU's threads idle the warp path's spread shortens the level's
+// longest chains, and a set whose candidates each cost two dependent bitmap
+// reads is worth spreading at a smaller size than a clique block, whose pairs
+// are all CCPs (measured against one limit for both kinds, 64-query batches:
+// cyclic-16 and cyclic-18 13-14 % faster, cyclic-20 and cyclic-22 6 %,
+// cyclic-25 and the cliques unchanged).  A set mixing both kinds weighs each
+// against its own limit.
 constexpr uint32_t kCliqueWeight = 16u;
 constexpr uint32_t kFullLevelSets = 16384u;
+constexpr uint32_t kNcRefSlots = 65536u;
+constexpr uint32_t kNcMaxSlots = 131072u;
 // The block-mode bodies' staged query.  At file scope, a kernel that runs
 // both bodies (the persistent kernel) holds one copy rather than two; each
 // batched kernel holds its own as before.
@@ -1516,7 +1529,12 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
     for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) s_pref[i] = level_pref[(kLevels + k) * kPrefStride + i];
     __syncthreads();
     const uint32_t tiles = s_pref[a.nq];
-    const bool full = (unsigned long long)tiles * kEvalThreads >= kFullLevelSets;
+    const unsigned long long slots = (unsigned long long)tiles * kEvalThreads;
+    const bool full = slots >= kFullLevelSets;
+    // The heavy test in 1/16 units: 16 * work_cl + nc_w16 * work_nc > lim16.
+    const uint32_t nc_slots = !full ? kFullLevelSets : (slots > kNcMaxSlots ? kNcMaxSlots : (uint32_t)slots);
+    const uint32_t nc_w16 = (full ? 16u : 8u) * kNcRefSlots / nc_slots;
+    const unsigned long long lim16 = 16ull * (full ? (uint32_t)a.heavy_threshold : (uint32_t)a.heavy_threshold / 2u);
     int cur = -1;
     unsigned long long evaluated = 0, ccp = 0;
     const int lane = threadIdx.x & 31;
@@ -1556,26 +1574,30 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
             // (its work then their count)
             // index: the warp path's pair index space (a listed block's CCPs,
             // any other block's bipartitions)
-            uint32_t pairs = 0u, work = 0u, index = 0u, cliq = 0u, listed = 0u;  // cliq: bit j, block j is a clique
+            // work_cl, work_nc: the work of the clique blocks and of the others
+            uint32_t pairs = 0u, work_cl = 0u, work_nc = 0u, index = 0u, cliq = 0u, listed = 0u;  // cliq: bit j, block j is a clique
             for (int j = 0; j < nb; j++) {
                 const uint32_t p = block_pairs(blk[j]);
                 pairs += p;
                 uint32_t off = 0u, nl = 0u;
                 if (!a.dpsub && !side[j] && is_clique(blk[j], sq.adj)) {
                     cliq |= 1u << j;
-                    work += full ? (p + kCliqueWeight - 1u) / kCliqueWeight : p;
+                    work_cl += full ? (p + kCliqueWeight - 1u) / kCliqueWeight : p;
                     index += p;
                 } else if (blist && !side[j] && bl_find(blist, blk[j], off, nl)) {
                     listed |= 1u << j;
-                    work += nl;
+                    work_nc += nl;
                     index += nl;
                 } else {
-                    work += p;
+                    work_nc += p;
                     index += p;
                 }
             }
-            if (a.dpsub) pairs = work = index = block_pairs(s);  // the whole set as one block
-            if (work > (full ? (uint32_t)a.heavy_threshold : (uint32_t)a.heavy_threshold / 2u)) {
+            if (a.dpsub) {  // the whole set as one block
+                pairs = work_nc = index = block_pairs(s);
+                work_cl = 0u;
+            }
+            if (16ull * work_cl + (unsigned long long)nc_w16 * work_nc > lim16) {
                 to_heavy = true;
                 const uint32_t nch = (index - 1u) / kChunkPairs + 1u;
                 want = (nch < kMaxChunks ? nch : kMaxChunks) - 1u;
