@@ -1519,7 +1519,11 @@ constexpr uint32_t kNcMaxSlots = 131072u;
 // batched kernel holds its own as before.
 __shared__ SharedQuery g_block_sq;
 
-template <class Memo, int kQ = kMaxBatch>  // kQ: the most queries of a batch it serves
+// kQ: the most queries of a batch it serves; kLevelLimit: the non-clique
+// limit follows the level's size (else it is the clique blocks' limit: a
+// one-query phase of the persistent kernel shares the GPU with the other
+// slots' phases, so its own level size says little about idle threads)
+template <class Memo, int kQ = kMaxBatch, bool kLevelLimit = true>
 __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uint32_t* MPDP_RESTRICT level_pref, uint32_t bid, uint32_t nblk)
 {
     SharedQuery& sq = g_block_sq;
@@ -1533,7 +1537,7 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
     const bool full = slots >= kFullLevelSets;
     // The heavy test in 1/16 units: 16 * work_cl + nc_w16 * work_nc > lim16.
     const uint32_t nc_slots = !full ? kFullLevelSets : (slots > kNcMaxSlots ? kNcMaxSlots : (uint32_t)slots);
-    const uint32_t nc_w16 = (full ? 16u : 8u) * kNcRefSlots / nc_slots;
+    const uint32_t nc_w16 = kLevelLimit ? (full ? 16u : 8u) * kNcRefSlots / nc_slots : 16u;
     const unsigned long long lim16 = 16ull * (full ? (uint32_t)a.heavy_threshold : (uint32_t)a.heavy_threshold / 2u);
     int cur = -1;
     unsigned long long evaluated = 0, ccp = 0;

@@ -267,7 +267,7 @@ __device__ bool run_tile(const PArgs& p, int s, unsigned int epoch, unsigned int
         if (a.desc[0].enumeration == MPDP_ENUM_TREE)
             eval_tree_body<DenseMemo, 1>(a, inf.level, DenseMemo{a.memo, a.left, nullptr, nullptr}, pref, tile, inf.total);
         else
-            eval_blocks_body<DensePlainMemo, 1>(a, inf.level, DensePlainMemo{a.memo, a.left, nullptr, nullptr}, pref, tile,
+            eval_blocks_body<DensePlainMemo, 1, false>(a, inf.level, DensePlainMemo{a.memo, a.left, nullptr, nullptr}, pref, tile,
                                                 inf.total);
         break;
     case PH_HEAVY:
