@@ -24,7 +24,12 @@
 // kept in one of two records chosen by the epoch's parity, written before
 // the epoch is published, so a block reads the record of the epoch it
 // claimed from; it re-reads the word afterwards and keeps the tile only if
-// the epoch is unchanged and the tile is below the phase's tile count.
+// the epoch is unchanged and the tile is below the phase's tile count.  The
+// block that publishes a phase (the one that ended the previous phase, or
+// admitted the query) publishes it with its first tile already claimed and
+// runs that tile next, so a run of one-tile phases (small levels, heavy-set
+// phases of one chunk group, the plan fetch) costs no other block's poll,
+// scan and claim between phases.
 //
 // Requests: the host writes each request (its slot, ticket, query and the
 // query's layout) into a ring of pinned, device-mapped memory and publishes
@@ -121,8 +126,9 @@ __device__ __forceinline__ PhaseInfo read_info(const PSlot* s, unsigned int pari
     return r;
 }
 
-// Publish epoch `epoch` of slot s with phase `inf` (one thread).
-__device__ void publish_phase(PSlot* s, unsigned int epoch, PhaseInfo inf)
+// Publish epoch `epoch` of slot s with phase `inf` (one thread), its tiles
+// below `taken` already claimed by the publishing block.
+__device__ void publish_phase(PSlot* s, unsigned int epoch, PhaseInfo inf, unsigned int taken = 0u)
 {
     volatile PhaseInfo* v = &s->info[epoch & 1u];
     v->phase = inf.phase;
@@ -130,7 +136,7 @@ __device__ void publish_phase(PSlot* s, unsigned int epoch, PhaseInfo inf)
     v->total = inf.total;
     reinterpret_cast<volatile unsigned int*>(s->done)[epoch & 1u] = 0u;
     __threadfence();
-    atomicExch(&s->word, (unsigned long long)epoch << 32);
+    atomicExch(&s->word, ((unsigned long long)epoch << 32) | taken);
 }
 
 // Claim the next tiles of slot s (one thread): [tile, tile + count).  A
@@ -138,13 +144,12 @@ __device__ void publish_phase(PSlot* s, unsigned int epoch, PhaseInfo inf)
 // blocks do not all queue on the slot's word for every tile.
 constexpr unsigned int kClaim = 4u;
 
-__device__ bool claim_tile(const PArgs& p, int s, unsigned int& epoch, unsigned int& tile, unsigned int& count,
-                           PhaseInfo& inf)
+// w, i0: the slot's word and the record of its epoch as the caller's scan
+// read them (a hint that sizes the claim; the claim itself is validated).
+__device__ bool claim_tile(const PArgs& p, int s, unsigned long long w, PhaseInfo i0, unsigned int& epoch,
+                           unsigned int& tile, unsigned int& count, PhaseInfo& inf)
 {
     PSlot* sl = p.slots + s;
-    const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(&sl->word);
-    const PhaseInfo i0 = read_info(sl, (unsigned int)(w >> 32));
-    if (i0.phase == PH_FREE || (unsigned int)w >= i0.total) return false;
     const unsigned int want = i0.total - (unsigned int)w >= kClaim * 2u * gridDim.x ? kClaim : 1u;
     const unsigned long long old = atomicAdd(&sl->word, (unsigned long long)want);
     const unsigned int e = (unsigned int)(old >> 32), t = (unsigned int)old;
@@ -295,8 +300,10 @@ __device__ bool take_request(const PArgs& p, unsigned long long& req)
     return true;
 }
 
-// Copy request `req` into its slot and start the slot's ingest (whole block).
-__device__ void admit(const PArgs& p, unsigned long long req)
+// Copy request `req` into its slot and start the slot's ingest (whole block),
+// whose one tile the block claims for itself: thread 0 gets the slot and the
+// ingest's epoch.
+__device__ void admit(const PArgs& p, unsigned long long req, int& slot, unsigned int& epoch)
 {
     const PRequest* e = p.ring + (req % (unsigned long long)p.ring_size);
     const int s = *reinterpret_cast<const volatile int32_t*>(&e->slot);
@@ -325,7 +332,9 @@ __device__ void admit(const PArgs& p, unsigned long long req)
         *reinterpret_cast<volatile long long*>(&sl->ticket) = *reinterpret_cast<const volatile long long*>(&e->ticket);
         const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(&sl->word);
         __threadfence();
-        publish_phase(sl, (unsigned int)(w >> 32) + 1u, PhaseInfo{PH_INGEST, 0, 1u, 0u});
+        slot = s;
+        epoch = (unsigned int)(w >> 32) + 1u;
+        publish_phase(sl, epoch, PhaseInfo{PH_INGEST, 0, 1u, 0u}, 1u);
     }
 }
 
@@ -340,29 +349,43 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_persist(PArgs p)
     __shared__ unsigned int s_epoch, s_tile, s_count;
     __shared__ PhaseInfo s_inf;
     __shared__ unsigned long long s_req;
+    // s_chain: the block published a phase (or admitted a query) and holds
+    // its first tile in s_slot / s_epoch / s_tile / s_count / s_inf
+    __shared__ int s_chain;
     enum { kIdle = 0, kTile = 1, kAdmit = 2, kExit = 3 };
     int idle = 0;
     int start = (int)(blockIdx.x % (unsigned int)p.nslots);
+    if (threadIdx.x == 0) s_chain = 0;
+    __syncthreads();
     for (;;) {
         if (threadIdx.x < 32) {
-            // warp 0 picks the block's next work: the 32 lanes look at 32 slots
+            // warp 0 picks the block's next work: the tile the block claimed
+            // when it published a phase, else the 32 lanes look at 32 slots
             // at once (from the one this block last worked on), the first
             // slot with tiles left is claimed; else a new request is taken
             const int lane = threadIdx.x;
             int cmd = kIdle;
-            int stop = 0;
-            if (lane == 0) stop = *reinterpret_cast<const volatile int*>(p.stop);
-            if (__shfl_sync(kFull, stop, 0)) {
+            int stop = 0, chain = 0;
+            if (lane == 0) {
+                chain = s_chain;
+                s_chain = 0;
+                if (!chain) stop = *reinterpret_cast<const volatile int*>(p.stop);
+            }
+            if (__shfl_sync(kFull, chain, 0)) {
+                cmd = kTile;
+            } else if (__shfl_sync(kFull, stop, 0)) {
                 cmd = kExit;
             } else {
                 for (int base = 0; base < p.nslots && cmd == kIdle; base += 32) {
                     const int i = base + lane;
                     const int s = (start + i) % p.nslots;
                     bool has = false;
+                    unsigned long long w = 0ull;
+                    PhaseInfo seen{PH_FREE, 0, 0u, 0u};
                     if (i < p.nslots) {
-                        const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(&p.slots[s].word);
-                        const PhaseInfo inf = read_info(p.slots + s, (unsigned int)(w >> 32));
-                        has = inf.phase != PH_FREE && (unsigned int)w < inf.total;
+                        w = *reinterpret_cast<volatile unsigned long long*>(&p.slots[s].word);
+                        seen = read_info(p.slots + s, (unsigned int)(w >> 32));
+                        has = seen.phase != PH_FREE && (unsigned int)w < seen.total;
                     }
                     unsigned int cand = __ballot_sync(kFull, has);
                     while (cand && cmd == kIdle) {
@@ -372,7 +395,7 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_persist(PArgs p)
                         if (lane == l) {
                             unsigned int e = 0u, t = 0u, c = 0u;
                             PhaseInfo inf;
-                            if (claim_tile(p, s, e, t, c, inf)) {
+                            if (claim_tile(p, s, w, seen, e, t, c, inf)) {
                                 got = 1;
                                 s_slot = s;
                                 s_epoch = e;
@@ -417,12 +440,37 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_persist(PArgs p)
                 PSlot* sl = p.slots + s;
                 if (atomicAdd(&sl->done[epoch & 1u], ntiles) + ntiles == inf.total) {
                     __threadfence();
-                    publish_phase(sl, epoch + 1u, next_phase(p, s, inf));
+                    // the block that ends a phase claims the next phase's
+                    // first tile as it publishes it: a chain of one-tile
+                    // phases (small levels, the plan fetch) then runs
+                    // back to back in this block, with no other block's
+                    // poll, scan and claim between two phases
+                    const PhaseInfo nx = next_phase(p, s, inf);
+                    const bool own = nx.phase != PH_FREE && nx.total > 0u;
+                    publish_phase(sl, epoch + 1u, nx, own ? 1u : 0u);
+                    if (own) {
+                        s_slot = s;
+                        s_epoch = epoch + 1u;
+                        s_tile = 0u;
+                        s_count = 1u;
+                        s_inf = nx;
+                        s_chain = 1;
+                    }
                 }
             }
         } else if (cmd == kAdmit) {
             idle = 0;
-            admit(p, s_req);
+            int slot = 0;
+            unsigned int ep = 0u;
+            admit(p, s_req, slot, ep);
+            if (threadIdx.x == 0) {
+                s_slot = slot;
+                s_epoch = ep;
+                s_tile = 0u;
+                s_count = 1u;
+                s_inf = PhaseInfo{PH_INGEST, 0, 1u, 0u};
+                s_chain = 1;
+            }
         } else {
             if (++idle > p.idle_polls) break;  // block-uniform
             // an idle block polls less often the longer it stays idle (200 ns
