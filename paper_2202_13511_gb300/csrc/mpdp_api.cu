@@ -254,8 +254,9 @@ static QuerySize query_size(int n, int enumeration, int memo_kind)
     QuerySize z;
     z.lists = list_entries(n);
     // block mode: the connectivity bitmap (2^n bits) follows the level lists,
-    // then the block CCP lists
-    if (enumeration == MPDP_ENUM_BLOCKS) z.lists += conn_words(n) + block_list_words(n, enumeration);
+    // then the block CCP lists, then the Find-Blocks cache
+    if (enumeration == MPDP_ENUM_BLOCKS)
+        z.lists += conn_words(n) + block_list_words(n, enumeration) + fb_cache_words(n, enumeration);
     z.heavy = enumeration == MPDP_ENUM_BLOCKS ? binom_host(n, n / 2) : 0;
     if (memo_kind == MPDP_MEMO_DENSE) z.memo = (size_t)1 << n;
     else z.hash = hash_arena_slots(n);

@@ -1514,16 +1514,31 @@ constexpr uint32_t kCliqueWeight = 16u;
 constexpr uint32_t kFullLevelSets = 16384u;
 constexpr uint32_t kNcRefSlots = 65536u;
 constexpr uint32_t kNcMaxSlots = 131072u;
+// Find-Blocks cache (batched kernels): the thread-per-set kernel, which
+// finds a set's blocks to weigh its work, leaves them for the warp path when
+// it appends the set as heavy (main entry i < kFbCap of the level): one
+// 128-B line per set, word 0 the block count, words 1.. the blocks.  Every
+// chunk of the set then reads the line (a word per lane) instead of running
+// Find-Blocks again on one lane while the others wait.  The cache sits after
+// the block CCP lists in the query's list words.
+constexpr uint32_t kFbCap = 4096u;
+constexpr uint32_t kFbStride = 32u;
+__device__ __forceinline__ uint32_t* fb_cache(const BatchArgs& a, const QDesc& d)
+{
+    return a.lists + d.bl_base + (d.n >= kBlMinRels ? kBlWords : 0u);
+}
 // The block-mode bodies' staged query.  At file scope, a kernel that runs
 // both bodies (the persistent kernel) holds one copy rather than two; each
 // batched kernel holds its own as before.
 __shared__ SharedQuery g_block_sq;
 
-// kQ: the most queries of a batch it serves; kLevelLimit: the non-clique
-// limit follows the level's size (else it is the clique blocks' limit: a
-// one-query phase of the persistent kernel shares the GPU with the other
-// slots' phases, so its own level size says little about idle threads)
-template <class Memo, int kQ = kMaxBatch, bool kLevelLimit = true>
+// kQ: the most queries of a batch it serves.  kBatched: the batched
+// kernels' form, where the non-clique limit follows the level's size and
+// heavy sets leave their blocks in the Find-Blocks cache.  The persistent
+// kernel's one-query phases take neither: such a phase shares the GPU with
+// the other slots' phases, so its own level size says little about idle
+// threads, and its slots have no cache.
+template <class Memo, int kQ = kMaxBatch, bool kBatched = true>
 __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uint32_t* MPDP_RESTRICT level_pref, uint32_t bid, uint32_t nblk)
 {
     SharedQuery& sq = g_block_sq;
@@ -1537,7 +1552,7 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
     const bool full = slots >= kFullLevelSets;
     // The heavy test in 1/16 units: 16 * work_cl + nc_w16 * work_nc > lim16.
     const uint32_t nc_slots = !full ? kFullLevelSets : (slots > kNcMaxSlots ? kNcMaxSlots : (uint32_t)slots);
-    const uint32_t nc_w16 = kLevelLimit ? (full ? 16u : 8u) * kNcRefSlots / nc_slots : 16u;
+    const uint32_t nc_w16 = kBatched ? (full ? 16u : 8u) * kNcRefSlots / nc_slots : 16u;
     const unsigned long long lim16 = 16ull * (full ? (uint32_t)a.heavy_threshold : (uint32_t)a.heavy_threshold / 2u);
     int cur = -1;
     unsigned long long evaluated = 0, ccp = 0;
@@ -1567,10 +1582,12 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
         const uint32_t idx = (t - s_pref[qi]) * kEvalThreads + threadIdx.x;
         bool to_heavy = false;
         uint32_t s = 0u, want = 0u;  // want: extra chunks asked for
+        uint32_t blk[kMaxRels];
+        int nb = 0;
         if (idx < cnt->list_count[k]) {
             s = a.lists[d.list_base + d.list_off[k] + idx];
-            uint32_t blk[kMaxRels], side[kMaxRels];
-            const int nb = find_blocks(s, sq.adj, blk, a.dpsub ? nullptr : side);
+            uint32_t side[kMaxRels];
+            nb = find_blocks(s, sq.adj, blk, a.dpsub ? nullptr : side);
             // pairs: the set's bipartitions; work: what a thread pays for
             // them, a clique block's pairs at 1/kCliqueWeight (no
             // connectivity test, every pair a CCP)
@@ -1679,6 +1696,11 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
                 hm[i] = HeavyMain{s, 1u + got, ebase + pre, 0u, kNoX, kFull, 0u};
                 HeavyExtra* he = a.hextra + d.heavy_base + ebase + pre;
                 for (uint32_t c = 0; c < got; c++) he[c] = HeavyExtra{i, kFull, kNoX};
+                if (kBatched && i < min(d.heavy_cap, kFbCap)) {
+                    uint32_t* e = fb_cache(a, d) + (size_t)i * kFbStride;
+                    e[0] = (uint32_t)nb;
+                    for (int j = 0; j < nb; j++) e[1 + j] = blk[j];
+                }
             }
         }
     }
@@ -1712,7 +1734,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_blocks(BatchArgs a, int k
 // invalid pair during the expensive part.  The prune is a warp shuffle
 // reduction of (x, left); a set cut into several chunks is folded by the
 // warp that finishes it last (fence, then an arrival count), with no waiting.
-template <class Memo, int kQ = kMaxBatch>  // kQ: the most queries of a batch it serves
+template <class Memo, int kQ = kMaxBatch, bool kBatched = true>  // as eval_blocks_body
 __device__ void eval_heavy_body(const BatchArgs& a, int k, Memo memo, uint32_t bid, uint32_t nblk)
 {
     constexpr int kWarps = kEvalThreads / 32;
@@ -1765,8 +1787,18 @@ __device__ void eval_heavy_body(const BatchArgs& a, int k, Memo memo, uint32_t b
         const uint32_t mi = item < nmain ? item : he[item - nmain].main;
         const uint32_t s = hm[mi].set, nch = hm[mi].nch, ebase = hm[mi].ebase;
         const uint32_t chunk = item < nmain ? 0u : item - nmain - ebase + 1u;
+        // the set's blocks: from the Find-Blocks cache when the thread-per-set
+        // kernel left them there (one line, a word per lane), else found here
+        const bool cached = kBatched && mi < min(d.heavy_cap, kFbCap);  // warp-uniform
+        int nb_cached = 0;
+        if (cached) {
+            const uint32_t v = MPDP_LDG(fb_cache(a, d) + (size_t)mi * kFbStride + lane);
+            nb_cached = (int)__shfl_sync(kFull, v, 0);
+            if (lane >= 1 && lane <= nb_cached) s_blk[warp][lane - 1] = v;
+            __syncwarp();
+        }
         if (lane == 0) {
-            int nb = find_blocks(s, sq.adj, s_blk[warp]);
+            int nb = cached ? nb_cached : find_blocks(s, sq.adj, s_blk[warp]);
             s_pv[warp] = block_peel_vertex(s, s_blk[warp], nb);
             if (a.dpsub) {  // the whole set as one block
                 s_blk[warp][0] = s;
@@ -2082,6 +2114,12 @@ size_t conn_words(int n) { return n >= 5 ? (size_t)1 << (n - 5) : 1; }
 size_t block_list_words(int n, int enumeration)
 {
     return (enumeration == MPDP_ENUM_BLOCKS && n >= kBlMinRels) ? kBlWords : 0;
+}
+size_t fb_cache_words(int n, int enumeration)
+{
+    if (enumeration != MPDP_ENUM_BLOCKS) return 0;
+    const unsigned long long c = binom_host(n, n / 2);
+    return (size_t)(c < kFbCap ? c : kFbCap) * kFbStride;
 }
 
 size_t hash_arena_slots(int n)

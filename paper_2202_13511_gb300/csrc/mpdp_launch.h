@@ -54,6 +54,8 @@ size_t conn_words(int n);
 cudaError_t configure_kernels();
 // List words of a query's block CCP lists (0 when it has none).
 size_t block_list_words(int n, int enumeration);
+// Find-Blocks cache words of a query (block mode; after the block CCP lists).
+size_t fb_cache_words(int n, int enumeration);
 size_t hash_arena_slots(int n);
 // Per-level list offsets and filter warp ranges of one query; returns the
 // query's filter block count in filter_blocks.

@@ -276,7 +276,7 @@ __device__ bool run_tile(const PArgs& p, int s, unsigned int epoch, unsigned int
                                                 inf.total);
         break;
     case PH_HEAVY:
-        eval_heavy_body<DensePlainMemo, 1>(a, inf.level, DensePlainMemo{a.memo, a.left, nullptr, nullptr}, tile, inf.total);
+        eval_heavy_body<DensePlainMemo, 1, false>(a, inf.level, DensePlainMemo{a.memo, a.left, nullptr, nullptr}, tile, inf.total);
         break;
     case PH_EXTRACT:
         fetch_and_publish(p, s, epoch);

@@ -257,6 +257,18 @@ def test_block_lists_overflow_falls_back(opt):
     check(opt, q, memo="sample")
 
 
+@pytest.mark.parametrize("threshold", [0, 64])
+def test_heavy_find_blocks_cache_overflow(opt, threshold):
+    """With every set heavy (threshold 0), the middle levels of a 15-clique
+    (C(15, 7) = 6,435 sets) and of a dense 16-relation graph append more
+    heavy sets than the Find-Blocks cache keeps (4,096 per level): the sets
+    past it find their blocks again in the warp path, the ones below read
+    them.  Every result is the oracle's."""
+    set_cfg(opt, heavy_threshold=threshold)
+    for q in (W.clique(15, seed=2), _dense_graph(16, 0.5, seed=5)):
+        check(opt, q, memo="sample")
+
+
 @pytest.mark.parametrize("run", [1, 5, 32])
 def test_run_lengths(opt, run):
     """Ragged unrank runs (run lengths that do not divide C(n,k))."""
