@@ -1516,13 +1516,14 @@ constexpr uint32_t kNcRefSlots = 65536u;
 constexpr uint32_t kNcMaxSlots = 131072u;
 // Find-Blocks cache (batched kernels): the thread-per-set kernel, which
 // finds a set's blocks to weigh its work, leaves them for the warp path when
-// it appends the set as heavy (main entry i < kFbCap of the level): one
-// 128-B line per set, word 0 the block count, words 1.. the blocks.  Every
+// it appends the set as heavy (main entry i < kFbCap of the level): one line
+// per set, word 0 the block count, words 1.. the blocks (64 B for queries of
+// up to 16 relations, whose sets have at most 15 blocks; else 128 B).  Every
 // chunk of the set then reads the line (a word per lane) instead of running
 // Find-Blocks again on one lane while the others wait.  The cache sits after
 // the block CCP lists in the query's list words.
 constexpr uint32_t kFbCap = 4096u;
-constexpr uint32_t kFbStride = 32u;
+__host__ __device__ __forceinline__ uint32_t fb_stride(int n) { return n <= 16 ? 16u : 32u; }
 __device__ __forceinline__ uint32_t* fb_cache(const BatchArgs& a, const QDesc& d)
 {
     return a.lists + d.bl_base + (d.n >= kBlMinRels ? kBlWords : 0u);
@@ -1697,7 +1698,7 @@ __device__ void eval_blocks_body(const BatchArgs& a, int k, Memo memo, const uin
                 HeavyExtra* he = a.hextra + d.heavy_base + ebase + pre;
                 for (uint32_t c = 0; c < got; c++) he[c] = HeavyExtra{i, kFull, kNoX};
                 if (kBatched && i < min(d.heavy_cap, kFbCap)) {
-                    uint32_t* e = fb_cache(a, d) + (size_t)i * kFbStride;
+                    uint32_t* e = fb_cache(a, d) + (size_t)i * fb_stride(d.n);
                     e[0] = (uint32_t)nb;
                     for (int j = 0; j < nb; j++) e[1 + j] = blk[j];
                 }
@@ -1792,7 +1793,8 @@ __device__ void eval_heavy_body(const BatchArgs& a, int k, Memo memo, uint32_t b
         const bool cached = kBatched && mi < min(d.heavy_cap, kFbCap);  // warp-uniform
         int nb_cached = 0;
         if (cached) {
-            const uint32_t v = MPDP_LDG(fb_cache(a, d) + (size_t)mi * kFbStride + lane);
+            const uint32_t st = fb_stride(d.n);
+            const uint32_t v = (uint32_t)lane < st ? MPDP_LDG(fb_cache(a, d) + (size_t)mi * st + lane) : 0u;
             nb_cached = (int)__shfl_sync(kFull, v, 0);
             if (lane >= 1 && lane <= nb_cached) s_blk[warp][lane - 1] = v;
             __syncwarp();
@@ -2119,7 +2121,7 @@ size_t fb_cache_words(int n, int enumeration)
 {
     if (enumeration != MPDP_ENUM_BLOCKS) return 0;
     const unsigned long long c = binom_host(n, n / 2);
-    return (size_t)(c < kFbCap ? c : kFbCap) * kFbStride;
+    return (size_t)(c < kFbCap ? c : kFbCap) * fb_stride(n);
 }
 
 size_t hash_arena_slots(int n)
