@@ -803,9 +803,11 @@ def optimize_device_noalloc(n: int, n_edges: int, d_card, d_edges, d_nodes, d_co
         raise MPDPError(rc, "mpdp_optimize_device_noalloc", strerror(rc))
 
 
-def workspace_bytes(n: int, memo_kind: int = MEMO_DENSE) -> int:
+def workspace_bytes(n: int, memo_kind: int = MEMO_DENSE, enumeration: int = ENUM_AUTO) -> int:
+    """Device workspace of one exact query of n relations (ENUM_AUTO: a tree
+    query; ENUM_BLOCKS: a general join graph)."""
     L = load()
-    c = ConfigC(memo_kind, 0, 64, 1, 1, 32, FILTER_CONNECTED, 8, 4, 1)
+    c = ConfigC(memo_kind, enumeration, 64, 1, 1, 32, FILTER_CONNECTED, 8, 4, 1)
     return int(L.mpdp_workspace_bytes(n, ctypes.byref(c)))
 
 

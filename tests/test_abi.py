@@ -79,6 +79,22 @@ def test_workspace_bytes_host_only():
     assert h > 0
 
 
+def test_block_workspace_holds_the_find_blocks_cache():
+    """A general join graph's workspace adds to a tree query's the
+    connectivity bitmap, the block CCP lists (18 relations up), the heavy
+    entries (48 B each, C(n, n/2) of them) and the Find-Blocks cache
+    (min(C(n, n/2), 4096) lines of 64 B up to 16 relations, 128 B above).
+    A 15-relation one still fits the budget of a 16-relation tree query,
+    which the GPU budget tests rely on."""
+    from math import comb
+    for n in range(4, 26):
+        tree, blocks = mpdp.workspace_bytes(n), mpdp.workspace_bytes(n, enumeration=mpdp.ENUM_BLOCKS)
+        c = comb(n, n // 2)
+        cache = min(c, 4096) * (64 if n <= 16 else 128)
+        assert blocks - tree >= 48 * c + cache + 2 ** n // 8, n
+    assert mpdp.workspace_bytes(15, enumeration=mpdp.ENUM_BLOCKS) < mpdp.workspace_bytes(16)
+
+
 def test_create_without_gpu_fails_cleanly():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
